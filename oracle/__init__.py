@@ -1,0 +1,222 @@
+"""Python access to the FP64 CPU oracle (oracle/sph_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` use it; the product package never
+imports it. It is built with plain gcc (``build()``), independent of the CUDA
+library, and takes problem descriptions from the ``workloads`` input module.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libsph_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, OpenMP). Returns the .so path."""
+    src = os.path.join(_HERE, "sph_oracle.c")
+    hdr = os.path.join(_HERE, "sph_oracle.h")
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= max(os.path.getmtime(src), os.path.getmtime(hdr))):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c99", "-fopenmp", "-fPIC", "-shared", "-Wall", "-Wno-unused-function",
+           "-o", tmp, src, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class Shape(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("keep_inside", C.c_int32),
+                ("center", C.c_double * 3), ("size", C.c_double * 3)]
+
+
+class Problem(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("n_shapes", C.c_int32),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("shapes", Shape * 4),
+                ("field_kind", C.c_int32), ("dist_shape", C.c_int32),
+                ("s0", C.c_double), ("a", C.c_double), ("b", C.c_double),
+                ("n_poly", C.c_int32), ("eos_general", C.c_int32), ("poly", C.c_double * 8),
+                ("rho_scale", C.c_double),
+                ("P0", C.c_double), ("gamma", C.c_double), ("sigma0", C.c_double),
+                ("tau", C.c_double), ("kappa", C.c_double),
+                ("t0", C.c_double), ("t1", C.c_double)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("sigma", C.c_double), ("dt1", C.c_double), ("dt2", C.c_double),
+                ("min_rc_over_a", C.c_double), ("max_a", C.c_double),
+                ("sum_rho", C.c_double), ("err_l2", C.c_double), ("err_max", C.c_double),
+                ("interface_pairs", C.c_int64), ("force_pairs", C.c_int64),
+                ("wall_moved", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_dp = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+_u8p = np.ctypeslib.ndpointer(dtype=np.uint8, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = C.CDLL(build())
+            L.orc_W.restype = C.c_double
+            L.orc_W.argtypes = [C.c_double, C.c_double, C.c_int]
+            L.orc_dW.restype = C.c_double
+            L.orc_dW.argtypes = [C.c_double, C.c_double, C.c_int]
+            L.orc_phi.restype = C.c_double
+            L.orc_phi.argtypes = [C.POINTER(Problem), _dp]
+            L.orc_project.restype = C.c_int
+            L.orc_project.argtypes = [C.POINTER(Problem), _dp]
+            L.orc_rho_t.restype = C.c_double
+            L.orc_rho_t.argtypes = [C.POINTER(Problem), _dp]
+            L.orc_h.restype = C.c_double
+            L.orc_h.argtypes = [C.POINTER(Problem), _dp]
+            L.orc_sigma.restype = C.c_double
+            L.orc_sigma.argtypes = [C.POINTER(Problem), C.c_double]
+            L.orc_total_mass.restype = C.c_double
+            L.orc_total_mass.argtypes = [C.POINTER(Problem), C.c_int]
+            L.orc_neighbor_sets.restype = C.c_int
+            L.orc_neighbor_sets.argtypes = [C.POINTER(Problem), C.c_int64, _dp, C.c_int,
+                                            _i32p, _i32p, _i64p, _i64p, _i64p, _i64p]
+            L.orc_step.restype = C.c_int
+            L.orc_step.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int,
+                                   C.POINTER(StepInfo), C.c_void_p, C.c_void_p, C.c_void_p,
+                                   C.c_void_p, C.c_void_p]
+            L.orc_num_threads.restype = C.c_int
+            L.orc_num_threads.argtypes = []
+            _lib = L
+    return _lib
+
+
+def to_c(p) -> Problem:
+    """Marshal a workloads.Problem into the oracle's struct."""
+    c = Problem()
+    c.dim = p.dim
+    c.n_shapes = len(p.shapes)
+    for k in range(3):
+        c.lo[k] = float(p.lo[k]) if k < len(p.lo) else 0.0
+        c.hi[k] = float(p.hi[k]) if k < len(p.hi) else 0.0
+    for s_i, s in enumerate(p.shapes):
+        c.shapes[s_i].kind = s.kind
+        c.shapes[s_i].keep_inside = 1 if s.keep_inside else 0
+        for k in range(3):
+            c.shapes[s_i].center[k] = float(s.center[k]) if k < len(s.center) else 0.0
+            c.shapes[s_i].size[k] = float(s.size[k]) if k < len(s.size) else 0.0
+    c.field_kind = p.field_kind
+    c.dist_shape = p.dist_shape
+    c.s0, c.a, c.b = p.s0, p.a, p.b
+    c.n_poly = len(p.poly)
+    c.eos_general = 1 if getattr(p, 'eos_general', False) else 0
+    for k, v in enumerate(p.poly[:8]):
+        c.poly[k] = float(v)
+    c.rho_scale = p.rho_scale
+    c.P0, c.gamma, c.sigma0, c.tau, c.kappa = p.P0, p.gamma, p.sigma0, p.tau, p.kappa
+    c.t0, c.t1 = p.t0, p.t1
+    return c
+
+
+def W(r, H, dim):
+    return lib().orc_W(float(r), float(H), int(dim))
+
+
+def dW(r, H, dim):
+    return lib().orc_dW(float(r), float(H), int(dim))
+
+
+def _pt(p, x):
+    v = np.zeros(3)
+    v[: p.dim] = np.asarray(x, dtype=np.float64)[: p.dim]
+    return v
+
+
+def phi(p, x):
+    return lib().orc_phi(C.byref(to_c(p)), _pt(p, x))
+
+
+def project(p, x):
+    v = _pt(p, x)
+    lib().orc_project(C.byref(to_c(p)), v)
+    return v[: p.dim]
+
+
+def rho_t(p, x):
+    return lib().orc_rho_t(C.byref(to_c(p)), _pt(p, x))
+
+
+def h_of(p, x):
+    return lib().orc_h(C.byref(to_c(p)), _pt(p, x))
+
+
+def sigma(p, t):
+    return lib().orc_sigma(C.byref(to_c(p)), float(t))
+
+
+def total_mass(p, res):
+    return lib().orc_total_mass(C.byref(to_c(p)), int(res))
+
+
+def neighbor_sets(p, pos, mode=1):
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    n = pos.shape[0]
+    dc = np.zeros(n, np.int32); fc = np.zeros(n, np.int32)
+    ds = np.zeros(n, np.int64); fs = np.zeros(n, np.int64)
+    dx = np.zeros(n, np.int64); fx = np.zeros(n, np.int64)
+    rc = lib().orc_neighbor_sets(C.byref(to_c(p)), n, pos, int(mode), dc, fc, ds, fs, dx, fx)
+    if rc != 0:
+        raise RuntimeError("oracle neighbour search failed")
+    return dict(dens_count=dc, force_count=fc, dens_idsum=ds, force_idsum=fs,
+                dens_idxor=dx, force_idxor=fx)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def step(p, pos, col, step_index=0, mode=1, want=True):
+    """One relaxation step on a copy of pos. Returns (new_pos, info dict, fields)
+    where fields holds rho, acc (a_n), visc (a~), pair_abs_a, pair_abs_b."""
+    pos = np.array(pos, dtype=np.float64, order="C", copy=True)
+    col = np.ascontiguousarray(col, dtype=np.uint8)
+    n, d = pos.shape
+    info = StepInfo()
+    f = {}
+    if want:
+        f = dict(rho=np.zeros(n), acc=np.zeros((n, d)), visc=np.zeros((n, d)),
+                 pair_abs_a=np.zeros(n), pair_abs_b=np.zeros(n))
+    rc = lib().orc_step(C.byref(to_c(p)), n, pos, col, int(step_index), int(mode), C.byref(info),
+                        _ptr(f.get("rho")), _ptr(f.get("acc")), _ptr(f.get("visc")),
+                        _ptr(f.get("pair_abs_a")), _ptr(f.get("pair_abs_b")))
+    if rc != 0:
+        raise RuntimeError("oracle step failed")
+    return pos, info.as_dict(), f
+
+
+def run(p, pos, col, n_steps, start_step=0, mode=1):
+    """n_steps steps; returns (pos, list of info dicts)."""
+    infos = []
+    for s in range(n_steps):
+        pos, info, _ = step(p, pos, col, start_step + s, mode, want=False)
+        infos.append(info)
+    return pos, infos
+
+
+def num_threads():
+    return lib().orc_num_threads()

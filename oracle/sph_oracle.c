@@ -1,0 +1,582 @@
+/*
+ * FP64 CPU oracle of the multi-phase SPH relaxation step (arXiv 1906.07925).
+ * TEST INFRASTRUCTURE ONLY: loaded by the tests, the smoke check and the
+ * CPU-baseline leg of the bench, never by the product path.
+ *
+ * Each function cites the passage it follows. Where the paper is silent or
+ * self-contradictory the reading taken is stated at the point of use.
+ */
+#include "sph_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define PI 3.14159265358979323846
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------------ */
+/* Kernel. The paper uses "a smooth isotropic kernel" (Sec. 3.3) without     */
+/* printing it. Reading: Wendland C2, W = alpha_d (1-q)^4 (1+4q), q = r/H,    */
+/* alpha_2 = 7/(pi H^2), alpha_3 = 21/(2 pi H^3); zero for q >= 1.           */
+/* ------------------------------------------------------------------------ */
+static double wendland_alpha(double H, int dim) {
+  return dim == 2 ? 7.0 / (PI * H * H) : 21.0 / (2.0 * PI * H * H * H);
+}
+
+double orc_W(double r, double H, int dim) {
+  double q = r / H;
+  if (q >= 1.0) return 0.0;
+  double u = 1.0 - q;
+  return wendland_alpha(H, dim) * u * u * u * u * (1.0 + 4.0 * q);
+}
+
+/* dW/dr = alpha_d / H * d/dq[(1-q)^4 (1+4q)] = alpha_d / H * (-20 q (1-q)^3). */
+double orc_dW(double r, double H, int dim) {
+  double q = r / H;
+  if (q >= 1.0) return 0.0;
+  double u = 1.0 - q;
+  return wendland_alpha(H, dim) / H * (-20.0 * q * u * u * u);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Geometry: level set phi, positive in the mesh region (Sec. 3.1,           */
+/* Eq. level_set_function). The region is the box [lo,hi] intersected with  */
+/* each shape constraint; phi is the minimum of the constraint distances.    */
+/* ------------------------------------------------------------------------ */
+
+/* signed distance, positive inside the shape */
+static double shape_inside_distance(const orc_shape* s, const double* x, int dim) {
+  if (s->kind == ORC_SPHERE) {
+    double r2 = 0.0;
+    for (int k = 0; k < dim; ++k) r2 += (x[k] - s->center[k]) * (x[k] - s->center[k]);
+    return s->size[0] - sqrt(r2);
+  }
+  double outside2 = 0.0, qmax = -INFINITY;
+  for (int k = 0; k < dim; ++k) {
+    double q = fabs(x[k] - s->center[k]) - s->size[k];
+    if (q > 0) outside2 += q * q;
+    if (q > qmax) qmax = q;
+  }
+  double inside = qmax < 0 ? qmax : 0.0;
+  return -(sqrt(outside2) + inside);
+}
+
+static double constraint_phi(const orc_shape* s, const double* x, int dim) {
+  double v = shape_inside_distance(s, x, dim);
+  return s->keep_inside ? v : -v;
+}
+
+static orc_shape box_shape(const orc_problem* p) {
+  orc_shape b;
+  b.kind = ORC_BOX;
+  b.keep_inside = 1;
+  for (int k = 0; k < 3; ++k) {
+    b.center[k] = 0.5 * (p->lo[k] + p->hi[k]);
+    b.size[k] = 0.5 * (p->hi[k] - p->lo[k]);
+  }
+  return b;
+}
+
+double orc_phi(const orc_problem* p, const double* x) {
+  orc_shape b = box_shape(p);
+  double phi = constraint_phi(&b, x, p->dim);
+  for (int s = 0; s < p->n_shapes; ++s) {
+    double v = constraint_phi(&p->shapes[s], x, p->dim);
+    if (v < phi) phi = v;
+  }
+  return phi;
+}
+
+/* Eq. displacement_surface, r <- r - phi N with N = grad(phi), for a particle
+ * that left the region (phi < 0). For an exact distance function this moves the
+ * point to the closest point of the violated constraint's surface:
+ *  - box kept inside: clamp to the box;
+ *  - box kept outside: push out through the nearest face;
+ *  - sphere (either side): c + R (x - c)/|x - c|.
+ * Reading: constraints are applied in order, the bounding box first. */
+static int project_one(const orc_shape* s, double* x, int dim) {
+  double phi = constraint_phi(s, x, dim);
+  if (!(phi < 0.0)) return 0;
+  if (s->kind == ORC_SPHERE) {
+    double d[3] = {0, 0, 0}, r2 = 0.0;
+    for (int k = 0; k < dim; ++k) { d[k] = x[k] - s->center[k]; r2 += d[k] * d[k]; }
+    double r = sqrt(r2);
+    if (r == 0.0) { d[0] = 1.0; r = 1.0; }
+    for (int k = 0; k < dim; ++k) x[k] = s->center[k] + s->size[0] * d[k] / r;
+    return 1;
+  }
+  if (s->keep_inside) {
+    for (int k = 0; k < dim; ++k) {
+      double lo = s->center[k] - s->size[k], hi = s->center[k] + s->size[k];
+      if (x[k] < lo) x[k] = lo;
+      if (x[k] > hi) x[k] = hi;
+    }
+    return 1;
+  }
+  /* inside a box that must be kept outside: leave through the nearest face */
+  int best = 0; double bestd = INFINITY, sign = 1.0;
+  for (int k = 0; k < dim; ++k) {
+    double dlo = x[k] - (s->center[k] - s->size[k]);
+    double dhi = (s->center[k] + s->size[k]) - x[k];
+    if (dlo < bestd) { bestd = dlo; best = k; sign = -1.0; }
+    if (dhi < bestd) { bestd = dhi; best = k; sign = 1.0; }
+  }
+  x[best] = s->center[best] + sign * s->size[best];
+  return 1;
+}
+
+int orc_project(const orc_problem* p, double* x) {
+  orc_shape b = box_shape(p);
+  int moved = project_one(&b, x, p->dim);
+  for (int s = 0; s < p->n_shapes; ++s) moved |= project_one(&p->shapes[s], x, p->dim);
+  return moved;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Target information (Sec. 2.3, Eq. rho_target_function; Sec. 3.2).         */
+/* rho_t = rho_scale * s(x)^-d * (1 + sum_k poly_k b_k(x~)), where s is the   */
+/* user spacing shape (uniform s0, or a + b * distance to a shape surface).   */
+/* ------------------------------------------------------------------------ */
+static double poly_factor(const orc_problem* p, const double* x) {
+  if (p->n_poly <= 0) return 1.0;
+  double t[3];
+  for (int k = 0; k < p->dim; ++k) t[k] = 2.0 * (x[k] - p->lo[k]) / (p->hi[k] - p->lo[k]) - 1.0;
+  double b[8];
+  if (p->dim == 2) {
+    double X = t[0], Y = t[1];
+    b[0] = X; b[1] = Y; b[2] = X * X; b[3] = X * Y; b[4] = Y * Y;
+    b[5] = X * X * X; b[6] = X * X * Y; b[7] = X * Y * Y;
+  } else {
+    double X = t[0], Y = t[1], Z = t[2];
+    b[0] = X; b[1] = Y; b[2] = Z; b[3] = X * X; b[4] = Y * Y; b[5] = Z * Z;
+    b[6] = X * Y; b[7] = Y * Z;
+  }
+  double f = 1.0;
+  for (int k = 0; k < p->n_poly && k < 8; ++k) f += p->poly[k] * b[k];
+  return f;
+}
+
+static double spacing(const orc_problem* p, const double* x) {
+  if (p->field_kind == ORC_FIELD_UNIFORM) return p->s0;
+  double dist = fabs(shape_inside_distance(&p->shapes[p->dist_shape], x, p->dim));
+  return p->a + p->b * dist;
+}
+
+double orc_rho_t(const orc_problem* p, const double* x) {
+  double s = spacing(p, x);
+  return p->rho_scale * pow(s, -(double)p->dim) * poly_factor(p, x);
+}
+
+/* Eq. scale_SPH_particle with m_i = 1 (Eq. mass_SPH_particle). */
+double orc_h(const orc_problem* p, const double* x) {
+  return p->tau * pow(1.0 / orc_rho_t(p, x), 1.0 / p->dim);
+}
+
+/* Eq. sph_st_sigma (the printed ramp, read with t in steps): sigma0 up to t0,
+ * sigma0 (1 - (t0 - t)/(t0 - t1)) on (t0, t1], 0 afterwards. */
+double orc_sigma(const orc_problem* p, double t) {
+  if (p->t0 < 0.0 || t <= p->t0) return p->sigma0;
+  if (t <= p->t1) return p->sigma0 * (1.0 - (p->t0 - t) / (p->t0 - p->t1));
+  return 0.0;
+}
+
+/* Eq. total_mass_2: M_v = integral of rho_t over the positive phase. */
+double orc_total_mass(const orc_problem* p, int res) {
+  int d = p->dim;
+  double step[3], cellvol = 1.0;
+  for (int k = 0; k < d; ++k) { step[k] = (p->hi[k] - p->lo[k]) / res; cellvol *= step[k]; }
+  int64_t total = 1;
+  for (int k = 0; k < d; ++k) total *= res;
+  double sum = 0.0;
+#pragma omp parallel for reduction(+ : sum) schedule(static)
+  for (int64_t c = 0; c < total; ++c) {
+    double x[3] = {0, 0, 0};
+    int64_t r = c;
+    for (int k = 0; k < d; ++k) { x[k] = p->lo[k] + ((double)(r % res) + 0.5) * step[k]; r /= res; }
+    if (orc_phi(p, x) > 0.0) sum += orc_rho_t(p, x);
+  }
+  return sum * cellvol;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neighbour search (Algorithm 1, line 8).                                   */
+/* Density set of i: all j (self included) with r_ij < kappa h_i            */
+/*   (Eq. density_sum gathers with h_i).                                     */
+/* Force set of i: all j != i with r_ij < kappa h_ij, h_ij = (h_i + h_j)/2   */
+/*   (Eq. sph_pressure_force_2).                                            */
+/* The union is found by brute force or a uniform grid; lists are ascending. */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int64_t* dstart; int32_t* dlist;  /* CSR density sets */
+  int64_t* fstart; int32_t* flist;  /* CSR force sets */
+} nbr_sets;
+
+static double dist2(const double* a, const double* b, int d) {
+  double s = 0.0;
+  for (int k = 0; k < d; ++k) s += (a[k] - b[k]) * (a[k] - b[k]);
+  return s;
+}
+
+typedef struct {
+  int d; double lo[3]; double c; int64_t nc[3];
+  int64_t* start; int32_t* items;
+} ugrid;
+
+static int64_t cell_coord(double x, double lo, double c, int64_t nc) {
+  int64_t v = (int64_t)floor((x - lo) / c);
+  if (v < 0) v = 0;
+  if (v >= nc) v = nc - 1;
+  return v;
+}
+
+static int ugrid_build(ugrid* g, const orc_problem* p, int64_t n, const double* pos, double c) {
+  int d = p->dim;
+  g->d = d; g->c = c;
+  int64_t total = 1;
+  for (int k = 0; k < 3; ++k) {
+    g->lo[k] = p->lo[k];
+    g->nc[k] = 1;
+    if (k < d) {
+      g->nc[k] = (int64_t)ceil((p->hi[k] - p->lo[k]) / c);
+      if (g->nc[k] < 1) g->nc[k] = 1;
+    }
+    total *= g->nc[k];
+  }
+  g->start = (int64_t*)calloc((size_t)total + 1, sizeof(int64_t));
+  g->items = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+  int64_t* cell = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  if (!g->start || !g->items || !cell) { free(cell); return -1; }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t id = 0, mul = 1;
+    for (int k = 0; k < d; ++k) { id += cell_coord(pos[i * d + k], g->lo[k], c, g->nc[k]) * mul; mul *= g->nc[k]; }
+    cell[i] = id;
+    g->start[id + 1]++;
+  }
+  for (int64_t t = 0; t < total; ++t) g->start[t + 1] += g->start[t];
+  int64_t* fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)total);
+  if (!fill) { free(cell); return -1; }
+  memcpy(fill, g->start, sizeof(int64_t) * (size_t)total);
+  for (int64_t i = 0; i < n; ++i) g->items[fill[cell[i]]++] = (int32_t)i;  /* ascending i per cell */
+  free(fill); free(cell);
+  return 0;
+}
+
+static void ugrid_free(ugrid* g) { free(g->start); free(g->items); }
+
+static int cmp_i32(const void* a, const void* b) {
+  int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  return (x > y) - (x < y);
+}
+
+/* candidates of i: every j whose distance could satisfy either criterion
+ * (r_ij < kappa max(h_i, h_ij) <= kappa (h_i + hmax)/2) */
+static int32_t gather_candidates(const ugrid* g, const double* pos, int64_t i, double R, int32_t* out, int64_t cap) {
+  int d = g->d;
+  int64_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int k = 0; k < d; ++k) {
+    lo[k] = cell_coord(pos[i * d + k] - R, g->lo[k], g->c, g->nc[k]);
+    hi[k] = cell_coord(pos[i * d + k] + R, g->lo[k], g->c, g->nc[k]);
+  }
+  int64_t cnt = 0;
+  for (int64_t cz = lo[2]; cz <= hi[2]; ++cz)
+    for (int64_t cy = lo[1]; cy <= hi[1]; ++cy)
+      for (int64_t cx = lo[0]; cx <= hi[0]; ++cx) {
+        int64_t id = cx + g->nc[0] * (cy + g->nc[1] * cz);
+        for (int64_t t = g->start[id]; t < g->start[id + 1]; ++t) {
+          if (cnt < cap) out[cnt] = g->items[t];
+          cnt++;
+        }
+      }
+  return (int32_t)cnt;
+}
+
+static int build_sets(const orc_problem* p, int64_t n, const double* pos, const double* h,
+                      int mode, nbr_sets* S) {
+  int d = p->dim;
+  double kappa = p->kappa;
+  double hmax = 0.0, hmin = INFINITY;
+  for (int64_t i = 0; i < n; ++i) { if (h[i] > hmax) hmax = h[i]; if (h[i] < hmin) hmin = h[i]; }
+  ugrid g; memset(&g, 0, sizeof g);
+  if (mode == 1 && n > 0) {
+    /* cells of the smallest support; each i scans the cells within its reach */
+    double c = kappa * hmin;
+    double ext = 0.0;
+    for (int k = 0; k < d; ++k) if (p->hi[k] - p->lo[k] > ext) ext = p->hi[k] - p->lo[k];
+    /* keep the grid at most ~16M cells */
+    if (d == 3 && c < ext / 256.0) c = ext / 256.0;
+    if (d == 2 && c < ext / 4096.0) c = ext / 4096.0;
+    if (ugrid_build(&g, p, n, pos, c) != 0) return -1;
+  }
+  S->dstart = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  S->fstart = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+  if (!S->dstart || !S->fstart) return -1;
+  int32_t* dcount = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+  int32_t* fcount = (int32_t*)calloc((size_t)n + 1, sizeof(int32_t));
+  int err = 0;
+  /* pass 1: counts; pass 2: fill */
+  for (int pass = 0; pass < 2 && !err; ++pass) {
+#pragma omp parallel
+    {
+      int64_t cap = 1024;
+      int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * (size_t)cap);
+#pragma omp for schedule(dynamic, 256)
+      for (int64_t i = 0; i < n; ++i) {
+        const double* xi = pos + i * d;
+        double Rd = kappa * h[i];
+        int64_t nd = 0, nf = 0;
+        int32_t m;
+        if (mode == 1) {
+          double R = kappa * 0.5 * (h[i] + hmax);
+          if (R < Rd) R = Rd;
+          m = gather_candidates(&g, pos, i, R, cand, cap);
+          if (m > cap) {
+            cap = 2 * (int64_t)m;
+            cand = (int32_t*)realloc(cand, sizeof(int32_t) * (size_t)cap);
+            m = gather_candidates(&g, pos, i, R, cand, cap);
+          }
+          qsort(cand, (size_t)m, sizeof(int32_t), cmp_i32);
+        } else {
+          m = (int32_t)n;
+        }
+        for (int32_t t = 0; t < m; ++t) {
+          int64_t j = mode == 1 ? cand[t] : t;
+          double r = sqrt(dist2(xi, pos + j * d, d));
+          int in_d = r < Rd;
+          int in_f = (j != i) && r < kappa * 0.5 * (h[i] + h[j]);
+          if (pass == 1) {
+            if (in_d) S->dlist[S->dstart[i] + nd] = (int32_t)j;
+            if (in_f) S->flist[S->fstart[i] + nf] = (int32_t)j;
+          }
+          nd += in_d; nf += in_f;
+        }
+        if (pass == 0) { dcount[i] = (int32_t)nd; fcount[i] = (int32_t)nf; }
+      }
+      free(cand);
+    }
+    if (pass == 0) {
+      for (int64_t i = 0; i < n; ++i) {
+        S->dstart[i + 1] = S->dstart[i] + dcount[i];
+        S->fstart[i + 1] = S->fstart[i] + fcount[i];
+      }
+      S->dlist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(S->dstart[n] + 1));
+      S->flist = (int32_t*)malloc(sizeof(int32_t) * (size_t)(S->fstart[n] + 1));
+      if (!S->dlist || !S->flist) err = 1;
+    }
+  }
+  free(dcount); free(fcount);
+  if (mode == 1 && n > 0) ugrid_free(&g);
+  return err ? -1 : 0;
+}
+
+static void free_sets(nbr_sets* S) { free(S->dstart); free(S->dlist); free(S->fstart); free(S->flist); }
+
+int orc_neighbor_sets(const orc_problem* p, int64_t n, const double* pos, int mode,
+                      int32_t* dens_count, int32_t* force_count,
+                      int64_t* dens_idsum, int64_t* force_idsum,
+                      int64_t* dens_idxor, int64_t* force_idxor) {
+  double* h = (double*)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+  if (!h) return -1;
+  for (int64_t i = 0; i < n; ++i) h[i] = orc_h(p, pos + i * p->dim);
+  nbr_sets S; memset(&S, 0, sizeof S);
+  if (build_sets(p, n, pos, h, mode, &S) != 0) { free(h); return -1; }
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t s = 0, x = 0;
+    for (int64_t t = S.dstart[i]; t < S.dstart[i + 1]; ++t) { s += S.dlist[t]; x ^= S.dlist[t]; }
+    if (dens_count) dens_count[i] = (int32_t)(S.dstart[i + 1] - S.dstart[i]);
+    if (dens_idsum) dens_idsum[i] = s;
+    if (dens_idxor) dens_idxor[i] = x;
+    s = 0; x = 0;
+    for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) { s += S.flist[t]; x ^= S.flist[t]; }
+    if (force_count) force_count[i] = (int32_t)(S.fstart[i + 1] - S.fstart[i]);
+    if (force_idsum) force_idsum[i] = s;
+    if (force_idxor) force_idxor[i] = x;
+  }
+  free_sets(&S); free(h);
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One relaxation step (Algorithm 1, lines 6-16).                            */
+/* ------------------------------------------------------------------------ */
+int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,
+             int mode, orc_step_info* info, double* rho_out, double* acc_out, double* visc_out,
+             double* pair_abs_a, double* pair_abs_b) {
+  const int d = p->dim;
+  const double kappa = p->kappa, P0 = p->P0, gamma = p->gamma;
+  const double sigma = orc_sigma(p, (double)step);
+  orc_step_info I; memset(&I, 0, sizeof I);
+  I.sigma = sigma;
+  if (n <= 0) { if (info) *info = I; return 0; }
+
+  size_t nd = (size_t)n * (size_t)d;
+  double* h = (double*)malloc(sizeof(double) * (size_t)n);
+  double* rt = (double*)malloc(sizeof(double) * (size_t)n);
+  double* rho = (double*)malloc(sizeof(double) * (size_t)n);
+  double* Pc = (double*)malloc(sizeof(double) * (size_t)n);
+  double* a = (double*)malloc(sizeof(double) * nd);
+  double* vt = (double*)malloc(sizeof(double) * nd);
+  double* at = (double*)malloc(sizeof(double) * nd);
+  double* eta = (double*)malloc(sizeof(double) * (size_t)n);
+  if (!h || !rt || !rho || !Pc || !a || !vt || !at || !eta) return -1;
+
+  /* line 6: target density and scale at r_i^n */
+  for (int64_t i = 0; i < n; ++i) {
+    rt[i] = orc_rho_t(p, pos + i * d);
+    h[i] = p->tau * pow(1.0 / rt[i], 1.0 / d);
+  }
+  /* lines 7-8: neighbour sets */
+  nbr_sets S; memset(&S, 0, sizeof S);
+  if (build_sets(p, n, pos, h, mode, &S) != 0) return -1;
+
+  /* Eq. density_sum: rho_i = sum_j m_j W(r_ij, h_i), m_j = 1 */
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t t = S.dstart[i]; t < S.dstart[i + 1]; ++t) {
+      int64_t j = S.dlist[t];
+      s += orc_W(sqrt(dist2(pos + i * d, pos + j * d, d)), kappa * h[i], d);
+    }
+    rho[i] = s;
+  }
+  /* Pressure coefficient p_i / rho_i^2 with the EOS p = P0 (rho/rho_t)^gamma
+   * (Eq. EOS_current). For gamma = 2 it is P0 / rho_t^2 and the density drops out
+   * (Eq. EOS_2 / sph_pressure_force_2); the printed gamma = 2 form is used then. */
+  for (int64_t i = 0; i < n; ++i) {
+    if (gamma == 2.0 && !p->eos_general) Pc[i] = P0 / (rt[i] * rt[i]);
+    else Pc[i] = P0 * pow(rho[i] / rt[i], gamma) / (rho[i] * rho[i]);
+  }
+
+  /* line 9: velocity reset (v_n = 0, infinite friction, Sec. 3.3);
+   * lines 10-11: a_n = -F_p + F_s (Eq. momentum_equation without F_v), with
+   *   F_p,i = sum_j (P_i + P_j) dW(r_ij, h_ij)/dr e_ij          (pressure)
+   *   F_s,i = -sum_j beta_ij (P0/rho_t,i^2 + P0/rho_t,j^2) dW e_ij (surface tension)
+   * beta_ij = sigma(t) for distinct colours, 0 otherwise (Eq. sph_st_beta).
+   * Reading: e_ij = (r_i - r_j)/r_ij (the paper defines r_ij = r_i - r_j but
+   * calls e_ij "from i to j"); with dW/dr < 0 both forces then repel. */
+  int64_t ipairs = 0, fpairs = 0;
+#pragma omp parallel for schedule(static) reduction(+ : ipairs, fpairs)
+  for (int64_t i = 0; i < n; ++i) {
+    double ai[3] = {0, 0, 0}, sabs = 0.0;
+    for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
+      int64_t j = S.flist[t];
+      double r = sqrt(dist2(pos + i * d, pos + j * d, d));
+      double hij = 0.5 * (h[i] + h[j]);
+      double dw = orc_dW(r, kappa * hij, d);
+      double beta = (col[i] != col[j]) ? sigma : 0.0;
+      double coef = (Pc[i] + Pc[j]) + beta * (P0 / (rt[i] * rt[i]) + P0 / (rt[j] * rt[j]));
+      for (int k = 0; k < d; ++k) ai[k] -= coef * dw * (pos[i * d + k] - pos[j * d + k]) / r;
+      sabs += fabs(coef * dw);
+      fpairs += 1;
+      ipairs += (col[i] != col[j]);
+    }
+    for (int k = 0; k < d; ++k) a[i * d + k] = ai[k];
+    if (pair_abs_a) pair_abs_a[i] = sabs;
+  }
+  I.interface_pairs = ipairs / 2;
+  I.force_pairs = fpairs / 2;
+
+  /* line 13: Eq. time_step_size with v_n = 0 leaves only the body-force term:
+   * dt1 = min_i 0.25 sqrt(r_c,i / |a_i|), r_c,i = kappa h_i (global minimum).
+   * Reading: if every a_i = 0 nothing moves (dt = 0). */
+  double dt1 = INFINITY, mra = INFINITY, amax = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double an = 0.0;
+    for (int k = 0; k < d; ++k) an += a[i * d + k] * a[i * d + k];
+    an = sqrt(an);
+    if (an > amax) amax = an;
+    if (an > 0.0) {
+      double rc = kappa * h[i];
+      double t = 0.25 * sqrt(rc / an);
+      if (t < dt1) dt1 = t;
+      if (rc / an < mra) mra = rc / an;
+    }
+  }
+  if (!(dt1 < INFINITY)) dt1 = 0.0;
+  /* Eq. time_int_01: v~ = v_n + a_n dt1 / 2 with v_n = 0 */
+  for (size_t q = 0; q < nd; ++q) vt[q] = 0.5 * a[q] * dt1;
+
+  /* line 15: Eq. time_step_size again with v~: the CFL term r_c/(40|v~|) and the
+   * viscous term 0.125 r_c^2 / nu with nu = 0.1 r_c |v~| (Eq. viscosity_coefficient),
+   * together with the body-force term of line 13 (reading: dt2 <= dt1). */
+  double dt2 = dt1;
+  for (int64_t i = 0; i < n; ++i) {
+    double vn = 0.0;
+    for (int k = 0; k < d; ++k) vn += vt[i * d + k] * vt[i * d + k];
+    vn = sqrt(vn);
+    double rc = kappa * h[i];
+    double nu = 0.1 * rc * vn;
+    eta[i] = rt[i] * nu; /* eta = rho nu with rho := rho_t (Eq. sph_viscous_force_2) */
+    if (vn > 0.0) {
+      double t1 = rc / (40.0 * vn);
+      double t2 = 0.125 * rc * rc / nu;
+      if (t1 < dt2) dt2 = t1;
+      if (t2 < dt2) dt2 = t2;
+    }
+  }
+
+  /* line 14: Eq. sph_viscous_force with rho := rho_t (Eq. sph_viscous_force_2):
+   * a~_i = sum_j 2 eta_i eta_j/(eta_i + eta_j) (1/rho_t,i^2 + 1/rho_t,j^2)
+   *        dW(r_ij, h_ij)/dr (v~_i - v~_j) / r_ij ;
+   * reading: the harmonic mean is 0 when eta_i + eta_j = 0. */
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    double s[3] = {0, 0, 0}, sabs = 0.0;
+    for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
+      int64_t j = S.flist[t];
+      double r = sqrt(dist2(pos + i * d, pos + j * d, d));
+      double hij = 0.5 * (h[i] + h[j]);
+      double dw = orc_dW(r, kappa * hij, d);
+      double es = eta[i] + eta[j];
+      double hm = es > 0.0 ? 2.0 * eta[i] * eta[j] / es : 0.0;
+      double coef = hm * (1.0 / (rt[i] * rt[i]) + 1.0 / (rt[j] * rt[j])) * dw / r;
+      double vn = 0.0;
+      for (int k = 0; k < d; ++k) {
+        double vij = vt[i * d + k] - vt[j * d + k];
+        s[k] += coef * vij;
+        vn += vij * vij;
+      }
+      sabs += fabs(coef) * sqrt(vn);
+    }
+    for (int k = 0; k < d; ++k) at[i * d + k] = s[k];
+    if (pair_abs_b) pair_abs_b[i] = sabs;
+  }
+
+  /* Eq. time_int_02 and time_int_03 with dt2, then line 16 (Eq. displacement_surface). */
+  int64_t moved = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int k = 0; k < d; ++k) {
+      double v = vt[i * d + k] + 0.5 * at[i * d + k] * dt2;
+      pos[i * d + k] += v * dt2;
+    }
+    moved += orc_project(p, pos + i * d);
+  }
+
+  /* diagnostics */
+  double srho = 0.0, el2 = 0.0, emax = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double e = rho[i] / rt[i] - 1.0;
+    srho += rho[i]; el2 += e * e;
+    if (fabs(e) > emax) emax = fabs(e);
+  }
+  I.dt1 = dt1; I.dt2 = dt2; I.min_rc_over_a = mra; I.max_a = amax;
+  I.sum_rho = srho; I.err_l2 = el2; I.err_max = emax; I.wall_moved = moved;
+  if (info) *info = I;
+  if (rho_out) memcpy(rho_out, rho, sizeof(double) * (size_t)n);
+  if (acc_out) memcpy(acc_out, a, sizeof(double) * nd);
+  if (visc_out) memcpy(visc_out, at, sizeof(double) * nd);
+
+  free_sets(&S);
+  free(h); free(rt); free(rho); free(Pc); free(a); free(vt); free(at); free(eta);
+  return 0;
+}

@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: a quadrature
+by scipy, an independent neighbour search (scipy's k-d tree), a symmetry that
+forces an exact zero, a conservation law, a variational identity (the SPH
+pressure force is minus the gradient of an internal energy), an exact scaling
+invariance, or a constant printed in the paper (tests/golden/paper_constants.json).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import integrate
+from scipy.spatial import cKDTree
+
+import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")
+
+
+def _free_cluster(dim, n, seed, graded=True, ncol=3):
+    """Particles in a small cube far from every wall, with a graded field whose
+    target density matches the cluster's number density (so h = 2 x spacing)."""
+    rng = np.random.default_rng(seed)
+    p = W.Problem(dim=dim, lo=[0, 0, 0], hi=[1, 1, 1 if dim == 3 else 0],
+                  shapes=[W.Shape(W.SPHERE, False, [0.1, 0.1, 0.1 if dim == 3 else 0], [0.02, 0, 0])],
+                  field_kind=W.FIELD_LINEAR_DISTANCE if graded else W.FIELD_UNIFORM,
+                  a=0.01, b=0.05, s0=0.01, dist_shape=0, rho_scale=1.0, n_colors=ncol)
+    c = np.full(dim, 0.6)
+    side = 0.04
+    x = c + side * (rng.random((n, dim)) - 0.5)
+    col = rng.integers(0, ncol, size=n).astype(np.uint8)
+    sc = W.spacing_shape(p, c[None, :])[0]  # s^-d at the centre
+    p.rho_scale = (n / side ** dim) / sc
+    return p, x, col
+
+
+# ---------------------------------------------------------------- kernel ----
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kernel_normalised(orc, dim):
+    """int W dV = 1 (scipy adaptive quadrature of the radial integral)."""
+    H = 0.37
+    shell = (lambda r: 2 * math.pi * r) if dim == 2 else (lambda r: 4 * math.pi * r * r)
+    val, err = integrate.quad(lambda r: orc.W(r, H, dim) * shell(r), 0.0, H, epsabs=1e-14, epsrel=1e-14)
+    assert abs(val - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_kernel_derivative_and_support(orc, dim):
+    H = 0.8
+    for q in np.linspace(0.05, 0.95, 19):
+        r = q * H
+        e = 1e-6 * H
+        fd = (orc.W(r + e, H, dim) - orc.W(r - e, H, dim)) / (2 * e)
+        assert abs(orc.dW(r, H, dim) - fd) <= 1e-7 * abs(fd) + 1e-12
+        assert orc.W(r, H, dim) > 0 and orc.dW(r, H, dim) < 0
+    assert orc.W(H, H, dim) == 0.0 and orc.dW(H, H, dim) == 0.0
+    assert orc.W(1.5 * H, H, dim) == 0.0
+    # C2 at the support edge: W and dW/dr vanish, second derivative -> 0
+    e = 1e-4 * H
+    d2 = (orc.dW(H - e, H, dim) - orc.dW(H - 2 * e, H, dim)) / e
+    assert abs(d2) < 1e-5 * abs(orc.dW(0.5 * H, H, dim)) / H * 1e3
+
+
+def test_kernel_lattice_sum_tends_to_number_density(orc):
+    """sum over a fine square lattice of W(|k| s, H) s^2 -> 1 (int W = 1,
+    Poisson summation) as H/s grows."""
+    s = 1.0
+    for ratio, tol in [(4.0, 5e-3), (8.0, 2e-4)]:
+        H = ratio * s
+        m = int(math.ceil(ratio)) + 1
+        tot = 0.0
+        for i in range(-m, m + 1):
+            for j in range(-m, m + 1):
+                tot += orc.W(math.hypot(i, j) * s, H, 2)
+        assert abs(tot * s * s - 1.0) < tol
+
+
+# ---------------------------------------------------------- neighbours ----
+
+@pytest.mark.parametrize("dim,n", [(2, 1500), (3, 1200)])
+def test_neighbor_sets_match_kdtree(orc, dim, n):
+    """Oracle brute force and grid search agree exactly with scipy's k-d tree
+    on a graded field (h varies across the cluster)."""
+    p, x, col = _free_cluster(dim, n, seed=7)
+    h = np.array([orc.h_of(p, xi) for xi in x])
+    tree = cKDTree(x)
+    dens = tree.query_ball_point(x, p.kappa * h * (1 - 1e-12))
+    hmax = h.max()
+    cand = tree.query_ball_point(x, p.kappa * 0.5 * (h + hmax))
+    want_dc = np.array([len(d) for d in dens])
+    want_ds = np.array([sum(d) for d in dens])
+    want_fc = np.zeros(n, int); want_fs = np.zeros(n, int)
+    for i in range(n):
+        js = np.array([j for j in cand[i] if j != i], dtype=int)
+        r = np.linalg.norm(x[js] - x[i], axis=1)
+        ok = r < p.kappa * 0.5 * (h[i] + h[js])
+        want_fc[i] = ok.sum(); want_fs[i] = js[ok].sum()
+    for mode in (0, 1):
+        got = orc.neighbor_sets(p, x, mode)
+        assert np.array_equal(got["dens_count"], want_dc)
+        assert np.array_equal(got["dens_idsum"], want_ds)
+        assert np.array_equal(got["force_count"], want_fc)
+        assert np.array_equal(got["force_idsum"], want_fs)
+    assert want_fc.mean() > 5
+
+
+# -------------------------------------------------------------- forces ----
+
+@pytest.mark.parametrize("dim,nper", [(2, 24), (3, 12)])
+def test_lattice_interior_force_vanishes(orc, dim, nper):
+    """A perfect lattice at uniform target density is an equilibrium: by
+    inversion symmetry every interior particle feels zero net force."""
+    p = W.Problem(dim=dim, lo=[0, 0, 0], hi=[1, 1, 1 if dim == 3 else 0], field_kind=W.FIELD_UNIFORM,
+                  s0=1.0 / nper, rho_scale=1.0, sigma0=3.0)
+    x = W.lattice(p, nper)
+    col = np.zeros(len(x), np.uint8)
+    _, info, f = orc.step(p, x, col, 0)
+    R = p.kappa * p.tau / nper
+    interior = np.all((x > 1.5 * R) & (x < 1 - 1.5 * R), axis=1)
+    assert interior.sum() > 10
+    a = np.linalg.norm(f["acc"][interior], axis=1)
+    assert np.all(a <= 1e-13 * f["pair_abs_a"][interior])
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("gamma", [2.0, 1.4])
+def test_momentum_conserved(orc, dim, gamma):
+    """Pair forces are antisymmetric (symmetric coefficients, symmetric h_ij,
+    antisymmetric e_ij): sum_i a_i = 0 and sum_i a~_i = 0 on a free cluster
+    with mixed colours and graded h."""
+    p, x, col = _free_cluster(dim, 400, seed=3)
+    p.gamma = gamma
+    _, info, f = orc.step(p, x, col, 0)
+    for key in ("acc", "visc"):
+        tot = np.abs(f[key].sum(axis=0)).max()
+        scale = np.abs(f[key]).sum()
+        assert tot <= 1e-12 * scale, key
+    assert info["interface_pairs"] > 0
+
+
+def test_viscous_term_dissipates(orc):
+    """sum_i v~_i . a~_i <= 0: the viscous term only removes relative motion."""
+    p, x, col = _free_cluster(2, 500, seed=11)
+    _, info, f = orc.step(p, x, col, 0)
+    vt = 0.5 * f["acc"] * info["dt1"]
+    assert float(np.sum(vt * f["visc"])) < 0.0
+
+
+@pytest.mark.parametrize("gamma,sigma0", [(2.0, 0.0), (1.4, 0.0), (3.0, 2.5)])
+def test_force_is_minus_energy_gradient(orc, gamma, sigma0):
+    """Variational pin: at uniform h and uniform rho_t, with the summation
+    density and u(rho) = P0 rho_t^-g rho^(g-1)/(g-1) (so du/drho = p/rho^2), the
+    acceleration equals -dE/dr_i for
+        E = sum_i u(rho_i) + sum_{i<j, C_i != C_j} sigma (2 P0 / rho_t^2) W(r_ij).
+    Checked by central differences of E built from the oracle's own densities."""
+    rng = np.random.default_rng(5)
+    n = 120
+    s = 0.01
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0], field_kind=W.FIELD_UNIFORM, s0=s,
+                  rho_scale=1.0, gamma=gamma, sigma0=sigma0, P0=1.3)
+    side = int(math.ceil(math.sqrt(n)))
+    g = np.stack(np.meshgrid(np.arange(side), np.arange(side), indexing="ij"), -1).reshape(-1, 2)[:n]
+    x = 0.5 + s * (g - side / 2) + 0.3 * s * (rng.random((n, 2)) - 0.5)
+    col = (g[:, 0] > side // 2).astype(np.uint8)
+    rt = orc.rho_t(p, x[0])
+    H = p.kappa * orc.h_of(p, x[0])
+
+    def energy(xx):
+        _, _, f = orc.step(p, xx, col, 0)
+        rho = f["rho"]
+        if gamma == 1.0:
+            raise AssertionError
+        e = np.sum(p.P0 * rt ** (-gamma) * rho ** (gamma - 1) / (gamma - 1))
+        if sigma0:
+            for i in range(n):
+                for j in range(i + 1, n):
+                    if col[i] != col[j]:
+                        e += sigma0 * 2 * p.P0 / rt ** 2 * orc.W(np.linalg.norm(xx[i] - xx[j]), H, 2)
+        return e
+
+    _, _, f0 = orc.step(p, x, col, 0)
+    eps = 1e-6 * s
+    for i in [0, 17, 55, 60, 101]:
+        for k in range(2):
+            xp = x.copy(); xp[i, k] += eps
+            xm = x.copy(); xm[i, k] -= eps
+            grad = (energy(xp) - energy(xm)) / (2 * eps)
+            a = f0["acc"][i, k]
+            assert abs(a + grad) <= 2e-6 * f0["pair_abs_a"][i], (i, k, a, -grad)
+
+
+def test_gamma2_general_form_equals_printed_form(orc):
+    """At gamma = 2, p/rho^2 = P0/rho_t^2: the general EOS path reproduces the
+    density-free pressure force of the printed form."""
+    p, x, col = _free_cluster(2, 400, seed=9)
+    _, i1, f1 = orc.step(p, x, col, 0)
+    _, i2, f2 = orc.step(p.copy(eos_general=True), x, col, 0)
+    assert np.all(np.abs(f1["acc"] - f2["acc"]).max(axis=1) <= 1e-13 * f1["pair_abs_a"])
+
+
+def test_colours_irrelevant_without_surface_tension(orc):
+    p, x, col = _free_cluster(2, 300, seed=4)
+    p.sigma0 = 0.0
+    x1, _, f1 = orc.step(p, x, col, 0)
+    x2, _, f2 = orc.step(p, x, np.zeros_like(col), 0)
+    assert np.array_equal(x1, x2) and np.array_equal(f1["acc"], f2["acc"])
+
+
+def test_surface_tension_repels_distinct_colours(orc):
+    """Two particles of distinct colour: the surface-tension part adds to the
+    pressure repulsion by the factor (1 + sigma) (Eqs. sph_pressure_force_2,
+    sph_st_force, sph_st_beta)."""
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0], field_kind=W.FIELD_UNIFORM, s0=0.05,
+                  rho_scale=1.0, sigma0=3.0)
+    x = np.array([[0.5, 0.5], [0.53, 0.5]])
+    _, _, same = orc.step(p, x, np.array([0, 0], np.uint8), 0)
+    _, _, diff = orc.step(p, x, np.array([0, 1], np.uint8), 0)
+    assert same["acc"][0, 0] < 0 < same["acc"][1, 0]  # repulsive
+    assert diff["acc"][0, 0] == pytest.approx(4.0 * same["acc"][0, 0], rel=1e-14)
+
+
+def test_P0_scaling_gives_bit_identical_trajectory(orc):
+    """The adaptive time step makes the trajectory independent of P0; with
+    P0 -> 4 P0 every intermediate scales by an exact power of two."""
+    p, x, col = _free_cluster(2, 300, seed=2)
+    xa, xb = x.copy(), x.copy()
+    q = p.copy(P0=4.0 * p.P0)
+    for s in range(3):
+        xa, ia, _ = orc.step(p, xa, col, s)
+        xb, ib, _ = orc.step(q, xb, col, s)
+    assert np.array_equal(xa, xb)
+    assert ib["dt1"] == 0.5 * ia["dt1"]
+
+
+def test_time_step_rule_constants(orc):
+    """With v_n = 0 every term of Eq. time_step_size is a monotone function of
+    r_c/|a|: dt1 = 0.25 sqrt(m), r_c/(40|v~|) = 0.2 sqrt(m), 0.125 r_c^2/nu =
+    10 sqrt(m) (m = min r_c/|a|), hence dt2 = 0.8 dt1."""
+    gold = json.load(open(GOLD))
+    p, x, col = _free_cluster(2, 300, seed=8)
+    _, info, _ = orc.step(p, x, col, 0)
+    m = info["min_rc_over_a"]
+    assert info["dt1"] == pytest.approx(gold["dt_body_force_factor"] * math.sqrt(m), rel=1e-14)
+    cfl = 1.0 / (gold["cfl_divisor"] * 0.5 * gold["dt_body_force_factor"])
+    assert info["dt2"] == pytest.approx(min(gold["dt_body_force_factor"], cfl) * math.sqrt(m), rel=1e-14)
+    assert info["dt2"] == pytest.approx(0.8 * info["dt1"], rel=1e-14)
+
+
+def test_zero_force_means_no_motion(orc):
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0], field_kind=W.FIELD_UNIFORM, s0=0.01, rho_scale=1.0)
+    x = np.array([[0.2, 0.2], [0.7, 0.7]])
+    x1, info, _ = orc.step(p, x, np.zeros(2, np.uint8), 0)
+    assert info["dt1"] == 0.0 and np.array_equal(x1, x)
+
+
+# ----------------------------------------------------------- density ----
+
+def test_density_positive_and_lattice_value(orc):
+    """rho >= 0; at the interior of a lattice the summation density of a lattice
+    with H = 2 s is the lattice sum, which lies within 1 % of 1/s^2."""
+    nper = 32
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0], field_kind=W.FIELD_UNIFORM, s0=1.0 / nper,
+                  rho_scale=1.0)
+    x = W.lattice(p, nper)
+    _, _, f = orc.step(p, x, np.zeros(len(x), np.uint8), 0)
+    assert np.all(f["rho"] > 0)
+    interior = np.all((x > 0.1) & (x < 0.9), axis=1)
+    r = f["rho"][interior] / nper ** 2
+    assert np.ptp(r) < 1e-12 and abs(r.mean() - 1.0) < 0.05
+
+
+# ---------------------------------------------------------- geometry ----
+
+def test_sigma_ramp_matches_paper(orc):
+    gold = json.load(open(GOLD))
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0], sigma0=gold["sigma_initial"], t0=100, t1=120)
+    assert orc.sigma(p, 0) == 3.0 and orc.sigma(p, 100) == 3.0
+    assert orc.sigma(p, 110) == pytest.approx(1.5, rel=1e-15)
+    assert orc.sigma(p, 120) == 0.0 and orc.sigma(p, 500) == 0.0
+    q = p.copy(t0=-1.0)
+    assert orc.sigma(q, 10 ** 6) == 3.0
+
+
+def test_projection_and_wall(orc):
+    p = W.graded_hole_2d(20000, 8, rho_scale=1.0)
+    # inside the hole -> onto the circle; outside the box -> clamped
+    y = orc.project(p, [0.55, 0.52])
+    assert abs(np.linalg.norm(y - 0.5) - 0.2) < 1e-15
+    assert np.allclose(orc.project(p, [1.2, -0.1]), [1.0, 0.0])
+    assert orc.phi(p, [0.5, 0.9]) == pytest.approx(0.1)
+    assert orc.phi(p, [0.5, 0.75]) == pytest.approx(0.05)
+    pb = W.Problem(dim=3, lo=[0, 0, 0], hi=[1, 1, 1],
+                   shapes=[W.Shape(W.BOX, False, [0.5, 0.5, 0.5], [0.1, 0.2, 0.3])])
+    assert np.allclose(orc.project(pb, [0.55, 0.5, 0.5]), [0.6, 0.5, 0.5])
+
+
+def test_particles_stay_in_region(orc):
+    p = W.graded_hole_2d(3000, 4)
+    x, col, _ = W.sample_density(p, 3000, seed=1)
+    for s in range(4):
+        x, info, _ = orc.step(p, x, col, s)
+    phi = np.array([orc.phi(p, xi) for xi in x])
+    assert phi.min() >= -1e-12
+
+
+def test_total_mass(orc):
+    p = W.uniform_square_2d(64)
+    assert orc.total_mass(p, 256) == pytest.approx(4096.0, rel=1e-12)
+    q = p.copy(shapes=[W.Shape(W.SPHERE, False, [0.5, 0.5, 0], [0.2, 0, 0])])
+    assert orc.total_mass(q, 2048) == pytest.approx(4096.0 * (1 - math.pi * 0.04), rel=2e-5)
+
+
+def _scaled(p, L):
+    """The same problem with every length multiplied by L (rho_scale kept)."""
+    sh = [W.Shape(s.kind, s.keep_inside, [L * c for c in s.center], [L * v for v in s.size])
+          for s in p.shapes]
+    return p.copy(lo=[L * v for v in p.lo], hi=[L * v for v in p.hi], shapes=sh,
+                  s0=L * p.s0, a=L * p.a, b=p.b)
+
+
+@pytest.mark.parametrize("dim,L", [(2, 2.0), (3, 4.0)])
+def test_length_scaling_is_exact(orc, dim, L):
+    """Dimensional consistency: with rho_t ~ L^-d, a ~ L^(d-1) and the adaptive
+    time step (dt^2 ~ r_c/|a| ~ L^(2-d)), stretching every length by L stretches
+    the trajectory by L. For these power-of-two choices of L every intermediate
+    scales by an exact power of two."""
+    if dim == 2:
+        p = W.graded_hole_2d(2000, 4)
+        x, col, _ = W.sample_density(p, 2000, seed=12)
+    else:
+        p = W.graded_inclusion_3d(2500, 4)
+        x, col, _ = W.sample_density(p, 2500, seed=12)
+    q = _scaled(p, L)
+    xa, xb = x.copy(), L * x
+    for s in range(3):
+        xa, ia, fa = orc.step(p, xa, col, s)
+        xb, ib, fb = orc.step(q, xb, col, s)
+    assert np.allclose(xb, L * xa, rtol=0, atol=1e-14 * L)
+    sc = L ** (dim - 1)
+    assert np.all(np.abs(fb["visc"] - sc * fa["visc"]) <= 1e-12 * sc * fa["pair_abs_b"][:, None])
+    assert np.all(np.abs(fb["acc"] - sc * fa["acc"]) <= 1e-12 * sc * fa["pair_abs_a"][:, None])
+
+
+def test_density_gathers_with_own_smoothing_length(orc):
+    """Eq. density_sum uses W(r_ij, h_i): in a graded field a close pair with
+    r < kappa h_i but r > kappa h_j adds W(r, h_i) to rho_i and nothing to rho_j."""
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0],
+                  shapes=[W.Shape(W.SPHERE, False, [0.0, 0.5, 0], [0.05, 0, 0])],
+                  field_kind=W.FIELD_LINEAR_DISTANCE, a=0.002, b=0.2, dist_shape=0, rho_scale=1.0)
+    xi = np.array([0.07, 0.5]); xj = np.array([0.06, 0.5])  # i farther from the hole: larger h
+    hi, hj = orc.h_of(p, xi), orc.h_of(p, xj)
+    r = 0.01
+    assert p.kappa * hj < r < p.kappa * hi
+    _, _, f = orc.step(p, np.stack([xi, xj]), np.zeros(2, np.uint8), 0)
+    assert f["rho"][0] == pytest.approx(orc.W(0, p.kappa * hi, 2) + orc.W(r, p.kappa * hi, 2), rel=1e-14)
+    assert f["rho"][1] == pytest.approx(orc.W(0, p.kappa * hj, 2), rel=1e-14)
+
+
+def test_viscous_kick_slows_separation(orc):
+    """Two repelling particles: the viscous force opposes their relative
+    velocity, so each moves less than the inviscid displacement
+    (1/2) a dt1 dt2 and along the line joining them."""
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0], field_kind=W.FIELD_UNIFORM, s0=0.05, rho_scale=1.0)
+    x = np.array([[0.5, 0.5], [0.53, 0.51]])
+    x1, info, f = orc.step(p, x, np.zeros(2, np.uint8), 0)
+    d = x1 - x
+    inviscid = 0.5 * f["acc"] * info["dt1"] * info["dt2"]
+    e = (x[0] - x[1]) / np.linalg.norm(x[0] - x[1])
+    for i in range(2):
+        assert np.linalg.norm(d[i]) < np.linalg.norm(inviscid[i])
+        assert abs(d[i, 0] * e[1] - d[i, 1] * e[0]) < 1e-15
+    assert np.dot(d[0], e) > 0 > np.dot(d[1], e)
