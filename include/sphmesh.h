@@ -1,0 +1,232 @@
+/*
+ * sphmesh — GB300 (sm_103a) multi-phase SPH particle relaxation.
+ *
+ * C ABI of the relaxation step of "A Consistent Parallel Isotropic Unstructured
+ * Mesh Generation Method based on Multi-phase SPH" (Ji, Fu, Hu, Adams,
+ * arXiv 1906.07925): coloured particles relax toward a target density field;
+ * the pressure force of a tailored EOS regularises the point distribution and an
+ * inter-colour surface-tension force keeps the colours (sub-domains) compact.
+ *
+ * Every call here runs on the GPU through hand-written CUDA kernels; there is
+ * no CPU fallback. Plain pointers and sizes only.
+ *
+ * Ownership. A handle owns its device buffers. They are obtained at creation
+ * through the caller's allocator (sph_alloc; NULL: cudaMallocAsync on the
+ * given stream) and returned through it in sph_destroy. Device work is issued
+ * on the stream given at creation. No global state: handles are independent,
+ * but one handle must not be used from two threads at once.
+ *
+ * Errors. Every call returns sph_status. Device-side problems (non-finite
+ * force, a particle outside the grid, a sampling budget exhausted) are latched
+ * in a device error word; calls that synchronise (sph_get_*, sph_sync) report
+ * them. sph_last_error() gives a message for the last failing call.
+ *
+ * Layouts. Positions cross the boundary as row-major n x dim doubles in
+ * original particle order (particle id = row), colours as n uint8, whatever
+ * order the library keeps internally. A pointer argument named *_dev is device
+ * memory when the accompanying `on_device` flag is 1, host memory otherwise.
+ */
+#ifndef SPHMESH_H
+#define SPHMESH_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SPH_OK = 0,
+  SPH_ERR_INVALID_ARG = 1,   /* bad argument; nothing was changed */
+  SPH_ERR_OOM = 2,           /* the allocator returned NULL */
+  SPH_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  SPH_ERR_NONFINITE = 4,     /* a density, force or position became NaN/Inf */
+  SPH_ERR_OUT_OF_DOMAIN = 5, /* a particle left the grid (after projection) */
+  SPH_ERR_CELL_OVERFLOW = 6, /* the cell grid would exceed its index range */
+  SPH_ERR_TIMEOUT = 7,       /* a bounded device loop gave up */
+  SPH_ERR_STATE = 8          /* call not valid in the handle's current state */
+} sph_status;
+
+/* Level-set constraints (Sec. 3.1, Eq. level_set_function). The mesh region
+ * (phi > 0) is the box [lo, hi] intersected with every shape constraint. */
+enum { SPH_SHAPE_SPHERE = 0, SPH_SHAPE_BOX = 1 };
+
+typedef struct {
+  int32_t kind;        /* SPH_SHAPE_SPHERE or SPH_SHAPE_BOX */
+  int32_t keep_inside; /* 1: region inside the shape; 0: outside (a hole) */
+  double center[3];
+  double size[3];      /* sphere: size[0] = radius; box: half extents */
+} sph_shape;
+
+typedef struct {
+  int32_t dim;         /* 2 or 3 */
+  int32_t n_shapes;    /* 0..4 */
+  double lo[3], hi[3]; /* bounding box (third component ignored in 2D) */
+  sph_shape shapes[4];
+} sph_domain;
+
+/* Target density (Sec. 2.3, Eq. rho_target_function):
+ *   rho_t(x) = rho_scale * s(x)^-d * (1 + sum_k poly[k] b_k(x~)),
+ * s = s0 (SPH_FIELD_UNIFORM) or a + b * |distance to shapes[dist_shape]|
+ * (SPH_FIELD_LINEAR_DISTANCE); x~ = 2 (x - lo)/(hi - lo) - 1 and b_k are
+ *   2D: x, y, x^2, xy, y^2, x^3, x^2 y, x y^2;  3D: x, y, z, x^2, y^2, z^2, xy, yz.
+ * rho_scale = 0 asks sph_create to choose it so that the total mass
+ * M_v = integral of rho_t over the region (Eq. total_mass_2) equals the
+ * particle count (unit mass, Eq. mass_SPH_particle). sum_k |poly[k]| < 1. */
+enum { SPH_FIELD_UNIFORM = 0, SPH_FIELD_LINEAR_DISTANCE = 1 };
+
+typedef struct {
+  int32_t kind;
+  int32_t dist_shape;
+  double s0, a, b;
+  int32_t n_poly;      /* 0..8 */
+  int32_t reserved;
+  double poly[8];
+  double rho_scale;
+} sph_field;
+
+enum { SPH_PREC_FP32_SPLIT = 0, SPH_PREC_FP64 = 1 };
+
+typedef struct {
+  double P0;           /* EOS reference pressure (Eq. EOS_current) */
+  double gamma;        /* EOS exponent; 2 gives the density-free force (Eq. EOS_2) */
+  double sigma0;       /* initial surface-tension coefficient, 3 (Eq. sph_st_sigma) */
+  double tau;          /* h = tau (m/rho_t)^(1/d) (Eq. scale_SPH_particle) */
+  double kappa;        /* kernel support = kappa * h */
+  int32_t precision;   /* SPH_PREC_FP32_SPLIT (FP32 offsets from cell origins) or SPH_PREC_FP64 */
+  int32_t kernel_id;   /* 0: Wendland C2 (the only one) */
+  uint64_t seed;       /* seed of the initial sampling (Philox4x32-10) */
+  double cell_factor;  /* finest cell edge / smallest support; 0 -> 1.0 */
+  int32_t block_size;  /* threads per block of the neighbour kernels; 0 -> auto */
+  int32_t use_graph;   /* 1: sph_step replays a captured CUDA graph of one step */
+  int32_t record_fields; /* 1: keep rho, a_n and a~ of the last step for sph_get_field */
+  int32_t reserved;
+} sph_params;
+
+typedef struct {
+  /* returns device memory of `bytes` bytes (16-byte aligned) or NULL */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, size_t bytes, void* ctx);
+  void* ctx;
+} sph_alloc;
+
+typedef struct {
+  int64_t step;            /* steps taken so far */
+  double sigma;            /* surface-tension coefficient used in the last step */
+  double dt1, dt2;         /* the two time-step sizes of the last step (Eq. time_step_size) */
+  double min_rc_over_a;    /* min_i r_c,i/|a_i| of the last step */
+  double max_a;            /* max_i |a_i| */
+  double sum_rho;          /* sum_i rho_i (FP64 reduction) */
+  double err_l2;           /* sum_i (rho_i/rho_t,i - 1)^2 */
+  double err_max;          /* max_i |rho_i/rho_t,i - 1| */
+  int64_t interface_pairs; /* unordered neighbour pairs with distinct colours */
+  int64_t force_pairs;     /* unordered neighbour pairs (r_ij < kappa h_ij) */
+  int64_t wall_moved;      /* particles moved by the level-set projection */
+  double rho_scale;        /* rho_scale in use */
+  int32_t error_flags;     /* latched device error bits (1 << sph_status) */
+  int32_t n_levels;        /* cell levels of the multi-resolution grid */
+} sph_stats;
+
+typedef struct {
+  int32_t n_levels;
+  int32_t dim;
+  double lo[3];
+  double h0;               /* smoothing length at the bottom of level 0 */
+  double lip_h;            /* Lipschitz bound of h used to pick searched levels */
+  double cell[8];          /* cell edge of each level (level l: cell[0] * 2^l) */
+  int32_t dims[8][3];      /* cells per axis of each level */
+  uint32_t base[9];        /* first cell key of each level; base[n_levels] = total */
+} sph_grid_info;
+
+typedef struct sph_handle sph_handle;
+
+/* Create a relaxation instance: validate, fix rho_scale (Eq. total_mass_2),
+ * draw n_particles positions with density proportional to rho_t in the region
+ * and colour each by the nearest of n_colors generators drawn uniformly in the
+ * region (the Voronoi initialisation of Sec. 4.2), build the multi-resolution
+ * grid. n_colors in 1..256. `stream` is a cudaStream_t (NULL: legacy default).
+ * Errors: INVALID_ARG, OOM, CUDA, CELL_OVERFLOW. */
+sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_particles,
+                      int32_t n_colors, const sph_params* params, const sph_alloc* alloc,
+                      void* stream, sph_handle** out);
+
+/* Replace the particle state (Algorithm 1 state = positions + colours; velocity
+ * is zeroed every step, Sec. 3.3). xyz: n x dim doubles, col: n uint8 (colour <
+ * 256), both in particle-id order, on the device if on_device else on the host.
+ * Resets the step counter. Errors: INVALID_ARG, CUDA. */
+sph_status sph_set_state(sph_handle* h, const double* xyz, const uint8_t* col, int32_t on_device);
+
+/* Advance n_steps relaxation steps (Algorithm 1, lines 6-16): cell list,
+ * density + pressure + surface-tension forces, time step, viscous force,
+ * two-stage integration, level-set projection. Asynchronous on the handle's
+ * stream. Errors: INVALID_ARG, CUDA, STATE. */
+sph_status sph_step(sph_handle* h, int32_t n_steps);
+
+/* Like sph_step, but with direct launches and CUDA events on the handle's
+ * stream around each phase; ms_out[0..2] receive the summed device time (ms)
+ * of the cell-list build, pass A (density, pressure, surface tension,
+ * reductions) and pass B (viscous force, integration, projection, re-keying)
+ * over the n_steps steps. Synchronises. Errors: INVALID_ARG, CUDA. */
+sph_status sph_step_profiled(sph_handle* h, int32_t n_steps, float* ms_out);
+
+/* Surface-tension schedule (Eq. sph_st_sigma): sigma = sigma0 for step <= t0,
+ * linear to 0 on (t0, t1], 0 after; step counted from sph_set_state/create.
+ * t0 < 0 removes the ramp. Errors: INVALID_ARG (t1 <= t0 with t0 >= 0). */
+sph_status sph_ramp_surface_tension(sph_handle* h, int64_t t0_step, int64_t t1_step);
+
+/* Current positions (n x dim doubles, particle-id order). Synchronises. */
+sph_status sph_get_positions(sph_handle* h, double* out, int32_t on_device);
+
+/* Colours (n uint8, particle-id order). Synchronises. */
+sph_status sph_get_colors(sph_handle* h, uint8_t* out, int32_t on_device);
+
+/* Reductions of the last step (FP64 on the device). Synchronises and reports
+ * latched device errors. */
+sph_status sph_get_stats(sph_handle* h, sph_stats* out);
+
+/* Per-particle results of the last step, particle-id order, as doubles:
+ * SPH_OUT_RHO (n): summation density (Eq. density_sum);
+ * SPH_OUT_ACC (n x dim): a_n = -F_p + F_s (Eqs. sph_pressure_force_2, sph_st_force);
+ * SPH_OUT_VISC (n x dim): a~ (Eq. sph_viscous_force with rho := rho_t).
+ * Needs params.record_fields = 1. Errors: STATE if nothing was recorded. */
+enum { SPH_OUT_RHO = 0, SPH_OUT_ACC = 1, SPH_OUT_VISC = 2 };
+sph_status sph_get_field(sph_handle* h, int32_t which, double* out, int32_t on_device);
+
+/* Neighbour sets of the current state (Algorithm 1, line 8), per particle id:
+ * density set (r_ij < kappa h_i, self included) and force set (j != i,
+ * r_ij < kappa (h_i + h_j)/2): sizes and the sum of member ids. Any output may
+ * be NULL. Host arrays. Synchronises. */
+sph_status sph_neighbor_sets(sph_handle* h, int32_t* dens_count, int32_t* force_count,
+                             int64_t* dens_idsum, int64_t* force_idsum);
+
+/* Cell list of the current state: cell key of each particle (particle-id
+ * order) and the particle ids in sorted order (stable: equal keys keep the
+ * order they had before the sort). Host arrays. Synchronises. */
+sph_status sph_get_cell_list(sph_handle* h, uint32_t* key_by_id, uint32_t* sorted_ids);
+
+/* Grid description (levels, cell edges, dims, key bases). */
+sph_status sph_get_grid(sph_handle* h, sph_grid_info* out);
+
+/* Wait for the handle's stream; report latched device errors. */
+sph_status sph_sync(sph_handle* h);
+
+/* Checkpoint: the full state is positions + colours + step counter + the
+ * sigma schedule (velocity is not state). With buf == NULL, *nbytes receives
+ * the size needed. Synchronises. */
+sph_status sph_save(sph_handle* h, void* buf, size_t* nbytes);
+sph_status sph_load(sph_handle* h, const void* buf, size_t nbytes);
+
+/* Message of the last failing call on this handle (never NULL). */
+const char* sph_last_error(const sph_handle* h);
+
+/* Particle count, dimension and the rho_scale in use. */
+sph_status sph_get_info(const sph_handle* h, int64_t* n_particles, int32_t* dim, double* rho_scale);
+
+/* Release every buffer through the allocator that created it. */
+void sph_destroy(sph_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPHMESH_H */

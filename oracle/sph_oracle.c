@@ -540,13 +540,15 @@ int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, i
       double es = eta[i] + eta[j];
       double hm = es > 0.0 ? 2.0 * eta[i] * eta[j] / es : 0.0;
       double coef = hm * (1.0 / (rt[i] * rt[i]) + 1.0 / (rt[j] * rt[j])) * dw / r;
-      double vn = 0.0;
+      double vi2 = 0.0, vj2 = 0.0;
       for (int k = 0; k < d; ++k) {
         double vij = vt[i * d + k] - vt[j * d + k];
         s[k] += coef * vij;
-        vn += vij * vij;
+        vi2 += vt[i * d + k] * vt[i * d + k];
+        vj2 += vt[j * d + k] * vt[j * d + k];
       }
-      sabs += fabs(coef) * sqrt(vn);
+      /* normaliser: magnitudes of the two velocity terms of the pair */
+      sabs += fabs(coef) * (sqrt(vi2) + sqrt(vj2));
     }
     for (int k = 0; k < d; ++k) at[i * d + k] = s[k];
     if (pair_abs_b) pair_abs_b[i] = sabs;

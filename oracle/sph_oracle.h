@@ -95,8 +95,8 @@ int orc_neighbor_sets(const orc_problem* p, int64_t n, const double* pos, int mo
 /* One relaxation step (Algorithm 1, lines 6-16) advancing pos in place.
  * Any of the per-particle outputs may be NULL:
  *   rho (n), acc (n*dim) = a_n, visc (n*dim) = a~, pair_abs_a (n) = sum_j of
- *   |pair term| of a_i, pair_abs_b (n) = same for a~ (normalisers of the parity
- *   tolerance). Returns 0 on success. */
+ *   |pair term| of a_i, pair_abs_b (n) = sum_j |coefficient of a~ pair term| *
+ *   (|v~_i| + |v~_j|) (normalisers of the parity tolerance). Returns 0 on success. */
 int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,
              int mode, orc_step_info* info, double* rho, double* acc, double* visc,
              double* pair_abs_a, double* pair_abs_b);

@@ -1,0 +1,228 @@
+"""GB300-native multi-phase SPH particle relaxation (arXiv 1906.07925).
+
+Python face of libsphmesh (include/sphmesh.h). Every step of the relaxation
+runs in the library's CUDA kernels; this module only marshals arguments and
+lends PyTorch's caching allocator and a CUDA stream to the library.
+
+    from paper_1906_07925_gb300 import Relaxation
+    r = Relaxation(problem, n_particles=1 << 20, precision="fp32")
+    r.step(500); r.ramp_surface_tension(500, 700); r.step(200)
+    x, c = r.positions(), r.colors()
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _binding as B
+
+__all__ = ["Relaxation", "SphError", "build", "load_library", "problem_structs"]
+
+
+class SphError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{B.STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def build(force=False):
+    from .build import build as _b
+    return _b(force=force)
+
+
+def load_library():
+    return B.load()
+
+
+def problem_structs(p, precision="fp32", seed=0, cell_factor=0.0, use_graph=True, record_fields=False):
+    """Marshal a problem description (attributes: dim, lo, hi, shapes, field_kind,
+    s0, a, b, dist_shape, poly, rho_scale, P0, gamma, sigma0, tau, kappa) into
+    the C structs."""
+    d = B.sph_domain()
+    d.dim = p.dim
+    d.n_shapes = len(p.shapes)
+    for k in range(3):
+        d.lo[k] = float(p.lo[k]) if k < len(p.lo) else 0.0
+        d.hi[k] = float(p.hi[k]) if k < len(p.hi) else 0.0
+    for i, s in enumerate(p.shapes):
+        d.shapes[i].kind = int(s.kind)
+        d.shapes[i].keep_inside = 1 if s.keep_inside else 0
+        for k in range(3):
+            d.shapes[i].center[k] = float(s.center[k]) if k < len(s.center) else 0.0
+            d.shapes[i].size[k] = float(s.size[k]) if k < len(s.size) else 0.0
+    f = B.sph_field()
+    f.kind = int(p.field_kind)
+    f.dist_shape = int(p.dist_shape)
+    f.s0, f.a, f.b = float(p.s0), float(p.a), float(p.b)
+    f.n_poly = len(p.poly)
+    for k, v in enumerate(list(p.poly)[:8]):
+        f.poly[k] = float(v)
+    f.rho_scale = float(p.rho_scale or 0.0)
+    q = B.sph_params()
+    q.P0, q.gamma, q.sigma0, q.tau, q.kappa = float(p.P0), float(p.gamma), float(p.sigma0), float(p.tau), float(p.kappa)
+    q.precision = B.SPH_PREC_FP64 if precision in ("fp64", "f64", "double") else B.SPH_PREC_FP32_SPLIT
+    q.kernel_id = 0
+    q.seed = int(seed)
+    q.cell_factor = float(cell_factor)
+    q.use_graph = 1 if use_graph else 0
+    q.record_fields = 1 if record_fields else 0
+    return d, f, q
+
+
+class Relaxation:
+    """One relaxation instance on the current CUDA device.
+
+    problem: geometry/field/parameters (see problem_structs); n_particles and
+    n_colors size the initial state drawn by the library (density-proportional
+    sampling, nearest-generator colours); set_state() replaces it.
+    """
+
+    def __init__(self, problem, n_particles, n_colors=None, precision="fp32", seed=0, cell_factor=0.0,
+                 use_graph=True, record_fields=False, device=None):
+        import torch
+        self._torch = torch
+        self.lib = B.load()
+        if not torch.cuda.is_available():
+            raise SphError(3, "no CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.dim = int(problem.dim)
+        self.n = int(n_particles)
+        ncol = int(n_colors if n_colors is not None else getattr(problem, "n_colors", 1))
+        dom, fld, par = problem_structs(problem, precision, seed, cell_factor, use_graph, record_fields)
+        dev, stream = self.device, self.stream
+
+        def _alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+            except Exception:  # out of memory -> NULL -> SPH_ERR_OOM
+                return None
+
+        def _free(ptr, nbytes, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._cb = (B.ALLOC_FN(_alloc), B.FREE_FN(_free))
+        al = B.sph_alloc(self._cb[0], self._cb[1], None)
+        h = B.H()
+        with torch.cuda.device(self.device):
+            st = self.lib.sph_create(C.byref(dom), C.byref(fld), self.n, ncol, C.byref(par), C.byref(al),
+                                     C.c_void_p(stream.cuda_stream), C.byref(h))
+        if st != B.SPH_OK:
+            raise SphError(st, "sph_create failed (details on stderr)")
+        self.h = h
+        t0 = getattr(problem, "t0", -1.0)
+        if t0 is not None and t0 >= 0:
+            self.ramp_surface_tension(int(t0), int(problem.t1))
+
+    # ------------------------------------------------------------------ util
+    def _check(self, st):
+        if st != B.SPH_OK:
+            raise SphError(st, self.lib.sph_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.sph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ------------------------------------------------------------------- API
+    def set_state(self, pos, col):
+        torch = self._torch
+        if isinstance(pos, torch.Tensor) and pos.is_cuda:
+            pos = pos.to(torch.float64).contiguous()
+            col = col.to(torch.uint8).contiguous()
+            self._check(self.lib.sph_set_state(self.h, pos.data_ptr(), col.data_ptr(), 1))
+            return
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        col = np.ascontiguousarray(col, dtype=np.uint8)
+        assert pos.shape == (self.n, self.dim) and col.shape == (self.n,)
+        self._check(self.lib.sph_set_state(self.h, pos.ctypes.data, col.ctypes.data, 0))
+
+    def step(self, n=1):
+        self._check(self.lib.sph_step(self.h, int(n)))
+
+    def step_profiled(self, n=1):
+        """n steps with per-phase CUDA-event timing: (cells_ms, pass_a_ms, pass_b_ms) summed."""
+        ms = (C.c_float * 3)()
+        self._check(self.lib.sph_step_profiled(self.h, int(n), ms))
+        return tuple(float(v) for v in ms)
+
+    def ramp_surface_tension(self, t0, t1):
+        self._check(self.lib.sph_ramp_surface_tension(self.h, int(t0), int(t1)))
+
+    def positions(self, out=None):
+        """(n, dim) float64 in particle-id order: numpy, or into a CUDA tensor `out`."""
+        if out is not None:
+            self._check(self.lib.sph_get_positions(self.h, out.data_ptr(), 1))
+            return out
+        x = np.empty((self.n, self.dim), np.float64)
+        self._check(self.lib.sph_get_positions(self.h, x.ctypes.data, 0))
+        return x
+
+    def colors(self):
+        c = np.empty(self.n, np.uint8)
+        self._check(self.lib.sph_get_colors(self.h, c.ctypes.data, 0))
+        return c
+
+    def stats(self):
+        s = B.sph_stats()
+        self._check(self.lib.sph_get_stats(self.h, C.byref(s)))
+        return s.as_dict()
+
+    def field(self, which):
+        k = {"rho": B.SPH_OUT_RHO, "acc": B.SPH_OUT_ACC, "visc": B.SPH_OUT_VISC}[which]
+        out = np.empty(self.n if k == B.SPH_OUT_RHO else (self.n, self.dim), np.float64)
+        self._check(self.lib.sph_get_field(self.h, k, out.ctypes.data, 0))
+        return out
+
+    def neighbor_sets(self):
+        n = self.n
+        dc = np.zeros(n, np.int32); fc = np.zeros(n, np.int32)
+        ds = np.zeros(n, np.int64); fs = np.zeros(n, np.int64)
+        self._check(self.lib.sph_neighbor_sets(self.h, dc.ctypes.data, fc.ctypes.data, ds.ctypes.data,
+                                               fs.ctypes.data))
+        return dict(dens_count=dc, force_count=fc, dens_idsum=ds, force_idsum=fs)
+
+    def cell_list(self):
+        k = np.zeros(self.n, np.uint32); s = np.zeros(self.n, np.uint32)
+        self._check(self.lib.sph_get_cell_list(self.h, k.ctypes.data, s.ctypes.data))
+        return k, s
+
+    def grid(self):
+        g = B.sph_grid_info()
+        self._check(self.lib.sph_get_grid(self.h, C.byref(g)))
+        L = g.n_levels
+        return dict(n_levels=L, dim=g.dim, lo=list(g.lo), h0=g.h0, lip_h=g.lip_h,
+                    cell=[g.cell[l] for l in range(L)], dims=[list(g.dims[l]) for l in range(L)],
+                    base=[g.base[l] for l in range(L + 1)])
+
+    def sync(self):
+        self._check(self.lib.sph_sync(self.h))
+
+    def save(self) -> bytes:
+        n = C.c_size_t(0)
+        self._check(self.lib.sph_save(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.sph_save(self.h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def load(self, blob: bytes):
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(self.lib.sph_load(self.h, buf, len(blob)))
+
+    def info(self):
+        n = C.c_int64(); d = C.c_int32(); rs = C.c_double()
+        self._check(self.lib.sph_get_info(self.h, C.byref(n), C.byref(d), C.byref(rs)))
+        return dict(n=n.value, dim=d.value, rho_scale=rs.value)

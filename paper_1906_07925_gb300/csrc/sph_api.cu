@@ -1,0 +1,808 @@
+// Host side of the C ABI (include/sphmesh.h): handle, validation, grid set-up,
+// buffer ownership through the caller's allocator, step orchestration (direct
+// launches or a replayed CUDA graph of one step), accessors, checkpoints.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sphmesh.h"
+#include "sph_internal.h"
+
+using namespace sph;
+
+struct sph_handle {
+  int dim = 2, prec = SPH_PREC_FP32_SPLIT, ncol = 1;
+  int64_t n = 0;
+  sph_domain dom{};
+  sph_field field{};
+  sph_params par{};
+  sph_alloc alloc{};
+  bool default_alloc = false;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  double rho_scale = 1.0, h0 = 0.0, lip_h = 0.0, cell0 = 0.0, hmin = 0.0, hmax = 0.0;
+  int n_levels = 1;
+  Grid<float> Gf{};
+  Grid<double> Gd{};     // canonical grid (cell edges exactly those of the working precision)
+  Grid<double> Gdw{};    // grid in the working precision when it is double
+  Geom<float> geof{};
+  Geom<double> geod{};
+  Phys<float> Pf{};
+  Phys<double> Pd{};
+  DevState S{};
+  std::vector<std::pair<void*, size_t>> blocks;
+  int64_t steps = 0;
+  double t0 = -1.0, t1 = -1.0;
+  bool recorded = false;
+  cudaGraphExec_t gexec = nullptr;
+  int graph_record = -1;
+  std::string err;
+};
+
+namespace {
+
+// ------------------------------------------------------------------ util --
+void* default_alloc_fn(size_t bytes, void* ctx) {
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, (cudaStream_t)ctx) != cudaSuccess) return nullptr;
+  return p;
+}
+void default_free_fn(void* p, size_t, void* ctx) { cudaFreeAsync(p, (cudaStream_t)ctx); }
+
+sph_status fail(sph_handle* h, sph_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+sph_status cuda_fail(sph_handle* h, cudaError_t e, const char* where) {
+  return fail(h, SPH_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define SPH_CUDA(h, expr)                                   \
+  do {                                                      \
+    cudaError_t e_ = (expr);                                \
+    if (e_ != cudaSuccess) return cuda_fail((h), e_, #expr); \
+  } while (0)
+
+template <class P>
+sph_status grab(sph_handle* h, P*& out, size_t count) {
+  size_t bytes = std::max<size_t>(count * sizeof(P), 16);
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = h->alloc.alloc(bytes, h->alloc.ctx);
+  if (!p) return fail(h, SPH_ERR_OOM, "allocation of " + std::to_string(bytes) + " bytes failed");
+  h->blocks.emplace_back(p, bytes);
+  out = (P*)p;
+  return SPH_OK;
+}
+
+#define SPH_TRY(expr)                 \
+  do {                                \
+    sph_status s_ = (expr);           \
+    if (s_ != SPH_OK) return s_;      \
+  } while (0)
+
+sph_status status_from_flags(sph_handle* h, int flags) {
+  if (flags & kErrNonfinite) return fail(h, SPH_ERR_NONFINITE, "non-finite density, force or position");
+  if (flags & kErrOutOfDomain) return fail(h, SPH_ERR_OUT_OF_DOMAIN, "a particle was outside the box");
+  if (flags & kErrTimeout) return fail(h, SPH_ERR_TIMEOUT, "a bounded device loop gave up");
+  return SPH_OK;
+}
+
+template <class T>
+void fill_geom(const sph_domain& d, const sph_field& f, double hfac, double rho_scale, Geom<T>& g) {
+  memset(&g, 0, sizeof g);
+  g.dim = d.dim;
+  g.n_shapes = d.n_shapes;
+  g.field_kind = f.kind;
+  g.dist_shape = f.dist_shape;
+  g.n_poly = f.n_poly;
+  for (int k = 0; k < 3; ++k) {
+    g.lo[k] = (T)d.lo[k];
+    g.hi[k] = (T)d.hi[k];
+    g.ext[k] = (T)(d.hi[k] - d.lo[k]);
+  }
+  for (int s = 0; s < d.n_shapes; ++s) {
+    g.kind[s] = d.shapes[s].kind;
+    g.keep_inside[s] = d.shapes[s].keep_inside;
+    for (int k = 0; k < 3; ++k) {
+      g.center[s][k] = (T)d.shapes[s].center[k];
+      g.size[s][k] = (T)d.shapes[s].size[k];
+    }
+  }
+  g.s0 = (T)f.s0;
+  g.a = (T)f.a;
+  g.b = (T)f.b;
+  for (int k = 0; k < 8; ++k) g.poly[k] = (T)f.poly[k];
+  g.hfac = (T)hfac;
+  g.rho_scale = (T)rho_scale;
+}
+
+template <class T>
+void fill_phys(const sph_handle* h, Phys<T>& P) {
+  P.P0 = (T)h->par.P0;
+  P.gamma = (T)h->par.gamma;
+  P.kappa = (T)h->par.kappa;
+  P.inv_tau = (T)(1.0 / h->par.tau);
+  P.alpha = (T)(h->dim == 2 ? 7.0 / M_PI : 21.0 / (2.0 * M_PI));
+}
+
+// Upper bound of |grad h| over the box for h = hfac s (1+P)^(-1/d):
+// |grad s| <= b (distance functions are 1-Lipschitz); |P| <= sum|c_k| = S on
+// x~ in [-1,1]^d; |dP/dx| <= 3 sqrt(d) S * 2/min(ext) (each monomial has
+// |d/dx~| <= 3 there).
+double lipschitz_h(const sph_handle* h, double hfac, double smax) {
+  const sph_field& f = h->field;
+  const int d = h->dim;
+  double S = 0.0;
+  for (int k = 0; k < f.n_poly; ++k) S += fabs(f.poly[k]);
+  double ext_min = DBL_MAX;
+  for (int k = 0; k < d; ++k) ext_min = std::min(ext_min, h->dom.hi[k] - h->dom.lo[k]);
+  const double gb = f.kind == SPH_FIELD_UNIFORM ? 0.0 : fabs(f.b);
+  const double fmin = 1.0 - S;
+  const double gradP = 3.0 * sqrt((double)d) * S * 2.0 / ext_min;
+  const double L = hfac * (gb * pow(fmin, -1.0 / d) + smax / d * pow(fmin, -1.0 / d - 1.0) * gradP);
+  return L * 1.05;
+}
+
+template <class T>
+void fill_grid(const sph_handle* h, Grid<T>& G) {
+  memset(&G, 0, sizeof G);
+  G.n_levels = h->n_levels;
+  G.dim = h->dim;
+  for (int l = 0; l < h->n_levels; ++l) {
+    G.nx[l] = h->Gd.nx[l];
+    G.ny[l] = h->Gd.ny[l];
+    G.nz[l] = h->Gd.nz[l];
+    G.cell[l] = (T)h->Gd.cell[l];
+    G.inv_cell[l] = (T)h->Gd.inv_cell[l];
+    for (int k = 0; k < 3; ++k) G.wall_hi[l][k] = (T)h->Gd.wall_hi[l][k];
+  }
+  for (int l = 0; l <= h->n_levels; ++l) G.base[l] = h->Gd.base[l];
+  for (int k = 0; k < 3; ++k) G.lo[k] = (T)h->dom.lo[k];
+  G.inv_h0 = (T)(1.0 / h->h0);
+  G.lip_h = (T)h->lip_h;
+  G.rfac = (T)h->Gd.rfac;
+}
+
+sph_status build_grid(sph_handle* h) {
+  const int d = h->dim;
+  const double kappa = h->par.kappa;
+  double cf = h->par.cell_factor > 0 ? h->par.cell_factor : 1.0;
+  h->h0 = h->hmin * 0.98;
+  if (!(h->h0 > 0)) return fail(h, SPH_ERR_INVALID_ARG, "target field gives a non-positive smoothing length");
+  if (kappa * h->lip_h >= 1.5) return fail(h, SPH_ERR_INVALID_ARG, "target field varies too fast (kappa |grad h| >= 1.5)");
+  int L = 1;
+  while (L < kMaxLevels && h->h0 * std::ldexp(1.0, L) <= h->hmax) ++L;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    double c0 = cf * kappa * h->h0;
+    if (h->prec == SPH_PREC_FP32_SPLIT) c0 = (double)(float)c0;
+    uint64_t total = 0;
+    Grid<double>& G = h->Gd;
+    memset(&G, 0, sizeof G);
+    bool ok = true;
+    for (int l = 0; l < L; ++l) {
+      const double c = std::ldexp(c0, l);
+      int dims[3] = {1, 1, 1};
+      for (int k = 0; k < d; ++k) {
+        const double e = h->dom.hi[k] - h->dom.lo[k];
+        const double nd = std::ceil(e / c);
+        if (nd > (1 << 23)) ok = false;
+        dims[k] = std::max(1, (int)nd);
+      }
+      G.nx[l] = dims[0];
+      G.ny[l] = dims[1];
+      G.nz[l] = dims[2];
+      G.cell[l] = c;
+      G.inv_cell[l] = 1.0 / c;
+      for (int k = 0; k < 3; ++k) G.wall_hi[l][k] = k < d ? (h->dom.hi[k] - h->dom.lo[k]) - (dims[k] - 1) * c : 0.0;
+      G.base[l] = (uint32_t)total;
+      total += (uint64_t)dims[0] * dims[1] * dims[2];
+    }
+    if (ok && total < (1ull << 28)) {
+      G.base[L] = (uint32_t)total;
+      G.n_levels = L;
+      G.dim = d;
+      for (int k = 0; k < 3; ++k) G.lo[k] = h->dom.lo[k];
+      G.inv_h0 = 1.0 / h->h0;
+      G.lip_h = h->lip_h;
+      G.rfac = (1.0 + 1e-5) / (1.0 - 0.5 * kappa * h->lip_h);
+      h->n_levels = L;
+      h->cell0 = c0;
+      h->S.total_cells = (uint32_t)total;
+      return SPH_OK;
+    }
+    cf *= 1.25;
+  }
+  return fail(h, SPH_ERR_CELL_OVERFLOW, "cell grid too large");
+}
+
+sph_status validate(const sph_domain* dom, const sph_field* f, int64_t n, int32_t ncol, const sph_params* p,
+                    std::string& why) {
+  if (!dom || !f || !p) { why = "null argument"; return SPH_ERR_INVALID_ARG; }
+  if (dom->dim != 2 && dom->dim != 3) { why = "dim must be 2 or 3"; return SPH_ERR_INVALID_ARG; }
+  if (dom->n_shapes < 0 || dom->n_shapes > kMaxShapes) { why = "n_shapes out of range"; return SPH_ERR_INVALID_ARG; }
+  for (int k = 0; k < dom->dim; ++k)
+    if (!(dom->hi[k] > dom->lo[k])) { why = "empty box"; return SPH_ERR_INVALID_ARG; }
+  for (int s = 0; s < dom->n_shapes; ++s) {
+    const sph_shape& sh = dom->shapes[s];
+    if (sh.kind != SPH_SHAPE_SPHERE && sh.kind != SPH_SHAPE_BOX) { why = "bad shape kind"; return SPH_ERR_INVALID_ARG; }
+    if (!(sh.size[0] > 0)) { why = "bad shape size"; return SPH_ERR_INVALID_ARG; }
+  }
+  if (n < 0 || n > (int64_t)(1u << 30)) { why = "particle count out of range"; return SPH_ERR_INVALID_ARG; }
+  if (ncol < 1 || ncol > 256) { why = "n_colors must be in 1..256"; return SPH_ERR_INVALID_ARG; }
+  if (f->kind == SPH_FIELD_UNIFORM) {
+    if (!(f->s0 > 0)) { why = "s0 must be > 0"; return SPH_ERR_INVALID_ARG; }
+  } else if (f->kind == SPH_FIELD_LINEAR_DISTANCE) {
+    if (!(f->a > 0) || !(f->b >= 0) || f->dist_shape < 0 || f->dist_shape >= dom->n_shapes) {
+      why = "bad linear-distance field";
+      return SPH_ERR_INVALID_ARG;
+    }
+  } else { why = "bad field kind"; return SPH_ERR_INVALID_ARG; }
+  if (f->n_poly < 0 || f->n_poly > 8) { why = "n_poly out of range"; return SPH_ERR_INVALID_ARG; }
+  double S = 0;
+  for (int k = 0; k < f->n_poly; ++k) S += fabs(f->poly[k]);
+  if (!(S < 1.0)) { why = "sum |poly| must be < 1"; return SPH_ERR_INVALID_ARG; }
+  if (!(f->rho_scale >= 0)) { why = "rho_scale must be >= 0"; return SPH_ERR_INVALID_ARG; }
+  if (!(p->P0 > 0) || !(p->gamma > 0) || !(p->sigma0 >= 0) || !(p->tau > 0) || !(p->kappa > 0)) {
+    why = "P0, gamma, tau, kappa must be > 0 and sigma0 >= 0";
+    return SPH_ERR_INVALID_ARG;
+  }
+  if (p->precision != SPH_PREC_FP32_SPLIT && p->precision != SPH_PREC_FP64) { why = "bad precision"; return SPH_ERR_INVALID_ARG; }
+  if (p->kernel_id != 0) { why = "only kernel_id 0 (Wendland C2) exists"; return SPH_ERR_INVALID_ARG; }
+  return SPH_OK;
+}
+
+// one relaxation step on the handle's stream
+sph_status launch_step(sph_handle* h, int record) {
+  DevState& S = h->S;
+  PassFlags f;
+  f.general_eos = h->par.gamma != 2.0;
+  f.record = record;
+  cudaError_t e = build_cells(S, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "build_cells");
+  const bool f64 = h->prec == SPH_PREC_FP64;
+  if (h->dim == 2) {
+    if (f64) {
+      e = launch_pass_a<2, double>(S, h->Gdw, h->Pd, f, h->stream);
+      if (e == cudaSuccess) e = launch_pass_b<2, double>(S, h->Gdw, h->Pd, h->geod, f, h->stream);
+    } else {
+      e = launch_pass_a<2, float>(S, h->Gf, h->Pf, f, h->stream);
+      if (e == cudaSuccess) e = launch_pass_b<2, float>(S, h->Gf, h->Pf, h->geof, f, h->stream);
+    }
+  } else {
+    if (f64) {
+      e = launch_pass_a<3, double>(S, h->Gdw, h->Pd, f, h->stream);
+      if (e == cudaSuccess) e = launch_pass_b<3, double>(S, h->Gdw, h->Pd, h->geod, f, h->stream);
+    } else {
+      e = launch_pass_a<3, float>(S, h->Gf, h->Pf, f, h->stream);
+      if (e == cudaSuccess) e = launch_pass_b<3, float>(S, h->Gf, h->Pf, h->geof, f, h->stream);
+    }
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "step kernels");
+  return SPH_OK;
+}
+
+sph_status ensure_graph(sph_handle* h, int record) {
+  if (h->gexec && h->graph_record == record) return SPH_OK;
+  if (h->gexec) {
+    cudaGraphExecDestroy(h->gexec);
+    h->gexec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  SPH_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  sph_status s = launch_step(h, record);
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (s != SPH_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  h->graph_record = record;
+  return SPH_OK;
+}
+
+sph_status write_ctl(sph_handle* h) {
+  StepCtl c{h->steps, h->t0, h->t1, h->par.sigma0};
+  SPH_CUDA(h, cudaMemcpyAsync(h->S.ctl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+  return SPH_OK;
+}
+
+sph_status read_flags(sph_handle* h, int* flags) {
+  SPH_CUDA(h, cudaMemcpyAsync(flags, h->S.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SPH_OK;
+}
+
+sph_status do_set_state(sph_handle* h, const double* xyz_dev, const uint8_t* col_dev) {
+  DevState& S = h->S;
+  cudaError_t e;
+  if (h->dim == 2)
+    e = h->prec == SPH_PREC_FP64 ? launch_set_state<2, double>(S, h->Gdw, h->Gd, h->geod, xyz_dev, col_dev, h->stream)
+                                 : launch_set_state<2, float>(S, h->Gf, h->Gd, h->geof, xyz_dev, col_dev, h->stream);
+  else
+    e = h->prec == SPH_PREC_FP64 ? launch_set_state<3, double>(S, h->Gdw, h->Gd, h->geod, xyz_dev, col_dev, h->stream)
+                                 : launch_set_state<3, float>(S, h->Gf, h->Gd, h->geof, xyz_dev, col_dev, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+  h->steps = 0;
+  h->recorded = false;
+  return write_ctl(h);
+}
+
+// temporary device buffer through the handle's allocator, released at scope end
+struct Temp {
+  sph_handle* h;
+  void* p = nullptr;
+  size_t bytes = 0;
+  Temp(sph_handle* hh, size_t b) : h(hh), bytes(std::max<size_t>(b, 16)) { p = h->alloc.alloc(bytes, h->alloc.ctx); }
+  ~Temp() {
+    if (p) {
+      cudaStreamSynchronize(h->stream);
+      h->alloc.free(p, bytes, h->alloc.ctx);
+    }
+  }
+};
+
+}  // namespace
+
+// ================================================================== C ABI ==
+extern "C" {
+
+void sph_destroy(sph_handle* h);
+
+static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_field* field, int64_t n_particles,
+                              int32_t n_colors, const sph_params* params, const sph_alloc* alloc, void* stream) {
+  h->dom = *dom;
+  h->field = *field;
+  h->par = *params;
+  h->dim = dom->dim;
+  h->prec = params->precision;
+  h->n = n_particles;
+  h->ncol = n_colors;
+  h->stream = (cudaStream_t)stream;
+  if (!h->stream) {
+    SPH_CUDA(h, cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+    h->own_stream = true;
+  }
+  if (alloc && alloc->alloc && alloc->free) {
+    h->alloc = *alloc;
+  } else {
+    h->alloc.alloc = default_alloc_fn;
+    h->alloc.free = default_free_fn;
+    h->alloc.ctx = (void*)h->stream;
+    h->default_alloc = true;
+  }
+  const int d = h->dim;
+  const int nn = (int)n_particles;
+
+  // ---- target field: total mass (Eq. total_mass_2) and the range of h ----
+  Geom<double> g1;
+  fill_geom<double>(h->dom, h->field, 1.0, 1.0, g1);
+  const int res = d == 2 ? 2048 : 192;
+  FieldBounds fb{};
+  {
+    Temp scratch(h, sizeof(double) * field_bounds_scratch_doubles());
+    if (!scratch.p) return fail(h, SPH_ERR_OOM, "scratch allocation failed");
+    cudaError_t e = d == 2 ? field_bounds<2>(g1, res, &fb, (double*)scratch.p, h->stream)
+                           : field_bounds<3>(g1, res, &fb, (double*)scratch.p, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "field_bounds");
+  }
+  if (!(fb.sum_w > 0)) return fail(h, SPH_ERR_INVALID_ARG, "the region is empty at the sampling resolution");
+  double cellvol = 1.0;
+  for (int k = 0; k < d; ++k) cellvol *= (h->dom.hi[k] - h->dom.lo[k]) / res;
+  const double mass1 = fb.sum_w * cellvol;  // integral of s^-d (1+P)
+  h->rho_scale = field->rho_scale > 0 ? field->rho_scale : (n_particles > 0 ? (double)n_particles / mass1 : 1.0);
+  const double hfac = h->par.tau * pow(h->rho_scale, -1.0 / d);
+  h->hmin = hfac * fb.min_seff;
+  h->hmax = hfac * fb.max_seff;
+  // field bounds are sampled; widen them by the Lipschitz bound over half a sample cell
+  double diag = 0.0;
+  for (int k = 0; k < d; ++k) diag += pow((h->dom.hi[k] - h->dom.lo[k]) / res, 2);
+  diag = sqrt(diag);
+  h->lip_h = lipschitz_h(h, hfac, fb.max_seff * (1.0 + 1e-6) + fabs(h->field.b) * diag);
+  h->hmin = std::max(0.5 * h->hmin, h->hmin - h->lip_h * diag);
+  h->hmax = h->hmax + h->lip_h * diag;
+  fill_geom<double>(h->dom, h->field, hfac, h->rho_scale, h->geod);
+  fill_geom<float>(h->dom, h->field, hfac, h->rho_scale, h->geof);
+  fill_phys(h, h->Pf);
+  fill_phys(h, h->Pd);
+  SPH_TRY(build_grid(h));
+  fill_grid<float>(h, h->Gf);
+  fill_grid<double>(h, h->Gdw);
+
+  // ---- buffers ----
+  DevState& S = h->S;
+  S.n = nn;
+  S.dim = d;
+  S.fp64 = h->prec == SPH_PREC_FP64;
+  const size_t v4 = S.fp64 ? 32 : 16, t1 = S.fp64 ? 8 : 4;
+  const size_t N = (size_t)std::max<int64_t>(n_particles, 1);
+  uint8_t* tmpb;
+  SPH_TRY(grab(h, tmpb, N * v4)); S.pos4_u = tmpb;
+  SPH_TRY(grab(h, tmpb, N * v4)); S.pos4_s = tmpb;
+  SPH_TRY(grab(h, tmpb, N * v4)); S.acc4 = tmpb;
+  SPH_TRY(grab(h, tmpb, N * v4)); S.visc = tmpb;
+  SPH_TRY(grab(h, tmpb, N * t1)); S.rho = tmpb;
+  SPH_TRY(grab(h, tmpb, N * t1)); S.pc = tmpb;
+  SPH_TRY(grab(h, S.meta_u, N));
+  SPH_TRY(grab(h, S.meta_s, N));
+  SPH_TRY(grab(h, S.key_u, N));
+  SPH_TRY(grab(h, S.key_s, N));
+  SPH_TRY(grab(h, S.pid_u, N));
+  SPH_TRY(grab(h, S.pid_s, N));
+  SPH_TRY(grab(h, S.tmp, N));
+  SPH_TRY(grab(h, S.cnt, (size_t)S.total_cells));
+  SPH_TRY(grab(h, S.cstart, (size_t)S.total_cells + 1));
+  SPH_TRY(grab(h, S.scan_part, (size_t)S.total_cells / 4096 + 2));
+  SPH_TRY(grab(h, S.partials, N / 256 + 2));
+  SPH_TRY(grab(h, S.scal, 2));
+  SPH_TRY(grab(h, S.ctl, 1));
+  SPH_TRY(grab(h, S.tickets, 4));
+  SPH_TRY(grab(h, S.err, 1));
+  SPH_CUDA(h, cudaMemsetAsync(S.cnt, 0, sizeof(uint32_t) * S.total_cells, h->stream));
+  SPH_CUDA(h, cudaMemsetAsync(S.tickets, 0, sizeof(unsigned) * 4, h->stream));
+  SPH_CUDA(h, cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
+  SPH_CUDA(h, cudaMemsetAsync(S.scal, 0, sizeof(Scalars) * 2, h->stream));
+
+  // ---- initial state ----
+  {
+    Temp xyz(h, sizeof(double) * N * d), col(h, N), gens(h, sizeof(double) * 3 * 256);
+    if (!xyz.p || !col.p || !gens.p) return fail(h, SPH_ERR_OOM, "scratch allocation failed");
+    const double wmax = fb.max_w * 1.25;
+    cudaError_t e = d == 2 ? sample_positions<2>(g1, nn, n_colors, params->seed, wmax, (double*)xyz.p,
+                                                 (uint8_t*)col.p, (double*)gens.p, S.err, h->stream)
+                           : sample_positions<3>(g1, nn, n_colors, params->seed, wmax, (double*)xyz.p,
+                                                 (uint8_t*)col.p, (double*)gens.p, S.err, h->stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "sample_positions");
+    SPH_TRY(do_set_state(h, (const double*)xyz.p, (const uint8_t*)col.p));
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  int flags = 0;
+  SPH_TRY(read_flags(h, &flags));
+  return status_from_flags(h, flags);
+}
+
+sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_particles, int32_t n_colors,
+                      const sph_params* params, const sph_alloc* alloc, void* stream, sph_handle** out) {
+  if (!out) return SPH_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  sph_status vs = validate(dom, field, n_particles, n_colors, params, why);
+  if (vs != SPH_OK) {
+    fprintf(stderr, "sph_create: %s\n", why.c_str());
+    return vs;
+  }
+  sph_handle* h = new sph_handle();
+  sph_status s = create_impl(h, dom, field, n_particles, n_colors, params, alloc, stream);
+  if (s != SPH_OK) {
+    fprintf(stderr, "sph_create: %s\n", h->err.c_str());
+    sph_destroy(h);
+    return s;
+  }
+  *out = h;
+  return SPH_OK;
+}
+
+sph_status sph_set_state(sph_handle* h, const double* xyz, const uint8_t* col, int32_t on_device) {
+  if (!h || (h->n > 0 && (!xyz || !col))) return fail(h, SPH_ERR_INVALID_ARG, "null state");
+  const size_t N = (size_t)h->n, d = (size_t)h->dim;
+  SPH_CUDA(h, cudaMemsetAsync(h->S.err, 0, sizeof(int), h->stream));
+  if (on_device) {
+    SPH_TRY(do_set_state(h, xyz, col));
+  } else {
+    Temp tx(h, sizeof(double) * N * d), tc(h, N);
+    if (!tx.p || !tc.p) return fail(h, SPH_ERR_OOM, "scratch allocation failed");
+    SPH_CUDA(h, cudaMemcpyAsync(tx.p, xyz, sizeof(double) * N * d, cudaMemcpyHostToDevice, h->stream));
+    SPH_CUDA(h, cudaMemcpyAsync(tc.p, col, N, cudaMemcpyHostToDevice, h->stream));
+    SPH_TRY(do_set_state(h, (const double*)tx.p, (const uint8_t*)tc.p));
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  int flags = 0;
+  SPH_TRY(read_flags(h, &flags));
+  return status_from_flags(h, flags);
+}
+
+sph_status sph_step(sph_handle* h, int32_t n_steps) {
+  if (!h || n_steps < 0) return fail(h, SPH_ERR_INVALID_ARG, "bad step count");
+  if (h->n == 0 || n_steps == 0) {
+    h->steps += n_steps;
+    return write_ctl(h);
+  }
+  const int record = h->par.record_fields ? 1 : 0;
+  if (h->par.use_graph) {
+    SPH_TRY(ensure_graph(h, record));
+    for (int s = 0; s < n_steps; ++s) SPH_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+  } else {
+    for (int s = 0; s < n_steps; ++s) SPH_TRY(launch_step(h, record));
+  }
+  h->steps += n_steps;
+  h->recorded = record;
+  return SPH_OK;
+}
+
+sph_status sph_step_profiled(sph_handle* h, int32_t n_steps, float* ms_out) {
+  if (!h || n_steps < 0 || !ms_out) return fail(h, SPH_ERR_INVALID_ARG, "bad arguments");
+  ms_out[0] = ms_out[1] = ms_out[2] = 0.0f;
+  if (h->n == 0 || n_steps == 0) return SPH_OK;
+  const int record = h->par.record_fields ? 1 : 0;
+  cudaEvent_t ev[4];
+  for (auto& e : ev) SPH_CUDA(h, cudaEventCreate(&e));
+  DevState& S = h->S;
+  PassFlags f;
+  f.general_eos = h->par.gamma != 2.0;
+  f.record = record;
+  const bool f64 = h->prec == SPH_PREC_FP64;
+  sph_status st = SPH_OK;
+  for (int s = 0; s < n_steps && st == SPH_OK; ++s) {
+    cudaError_t e = cudaEventRecord(ev[0], h->stream);
+    if (e == cudaSuccess) e = build_cells(S, h->stream);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+    if (e == cudaSuccess) {
+      if (h->dim == 2)
+        e = f64 ? launch_pass_a<2, double>(S, h->Gdw, h->Pd, f, h->stream) : launch_pass_a<2, float>(S, h->Gf, h->Pf, f, h->stream);
+      else
+        e = f64 ? launch_pass_a<3, double>(S, h->Gdw, h->Pd, f, h->stream) : launch_pass_a<3, float>(S, h->Gf, h->Pf, f, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+    if (e == cudaSuccess) {
+      if (h->dim == 2)
+        e = f64 ? launch_pass_b<2, double>(S, h->Gdw, h->Pd, h->geod, f, h->stream)
+                : launch_pass_b<2, float>(S, h->Gf, h->Pf, h->geof, f, h->stream);
+      else
+        e = f64 ? launch_pass_b<3, double>(S, h->Gdw, h->Pd, h->geod, f, h->stream)
+                : launch_pass_b<3, float>(S, h->Gf, h->Pf, h->geof, f, h->stream);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    float t;
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+      e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
+      ms_out[k] += t;
+    }
+    if (e != cudaSuccess) st = cuda_fail(h, e, "profiled step");
+    else h->steps += 1;
+  }
+  for (auto& e : ev) cudaEventDestroy(e);
+  h->recorded = record && st == SPH_OK;
+  return st;
+}
+
+sph_status sph_ramp_surface_tension(sph_handle* h, int64_t t0, int64_t t1) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  if (t0 >= 0 && t1 <= t0) return fail(h, SPH_ERR_INVALID_ARG, "ramp needs t1 > t0");
+  h->t0 = t0 < 0 ? -1.0 : (double)t0;
+  h->t1 = t0 < 0 ? -1.0 : (double)t1;
+  return write_ctl(h);
+}
+
+sph_status sph_get_positions(sph_handle* h, double* out, int32_t on_device) {
+  if (!h || (h->n > 0 && !out)) return fail(h, SPH_ERR_INVALID_ARG, "null output");
+  const size_t N = (size_t)h->n, d = (size_t)h->dim;
+  double* dst = out;
+  Temp t(h, on_device ? 0 : sizeof(double) * N * d);
+  if (!on_device) dst = (double*)t.p;
+  cudaError_t e;
+  if (h->dim == 2)
+    e = h->prec == SPH_PREC_FP64 ? launch_get_positions<2, double>(h->S, h->Gd, dst, h->stream)
+                                 : launch_get_positions<2, float>(h->S, h->Gd, dst, h->stream);
+  else
+    e = h->prec == SPH_PREC_FP64 ? launch_get_positions<3, double>(h->S, h->Gd, dst, h->stream)
+                                 : launch_get_positions<3, float>(h->S, h->Gd, dst, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_positions");
+  if (!on_device) SPH_CUDA(h, cudaMemcpyAsync(out, dst, sizeof(double) * N * d, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  int flags = 0;
+  SPH_TRY(read_flags(h, &flags));
+  return status_from_flags(h, flags);
+}
+
+sph_status sph_get_colors(sph_handle* h, uint8_t* out, int32_t on_device) {
+  if (!h || (h->n > 0 && !out)) return fail(h, SPH_ERR_INVALID_ARG, "null output");
+  const size_t N = (size_t)h->n;
+  Temp t(h, on_device ? 0 : N);
+  uint8_t* dst = on_device ? out : (uint8_t*)t.p;
+  cudaError_t e = launch_get_colors(h->S, dst, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_colors");
+  if (!on_device) SPH_CUDA(h, cudaMemcpyAsync(out, dst, N, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SPH_OK;
+}
+
+sph_status sph_get_stats(sph_handle* h, sph_stats* out) {
+  if (!h || !out) return fail(h, SPH_ERR_INVALID_ARG, "null output");
+  Scalars sc{};
+  int flags = 0;
+  SPH_CUDA(h, cudaMemcpyAsync(&sc, h->S.scal, sizeof sc, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync(&flags, h->S.err, sizeof flags, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  memset(out, 0, sizeof *out);
+  out->step = h->steps;
+  out->sigma = sc.sigma;
+  out->dt1 = sc.dt1;
+  out->dt2 = sc.dt2;
+  out->min_rc_over_a = sc.min_rc_a >= DBL_MAX ? INFINITY : sc.min_rc_a;
+  out->max_a = sc.max_a;
+  out->sum_rho = sc.sum_rho;
+  out->err_l2 = sc.err_l2;
+  out->err_max = sc.err_max;
+  out->interface_pairs = sc.ipairs;
+  out->force_pairs = sc.fpairs;
+  out->wall_moved = sc.wall_moved;
+  out->rho_scale = h->rho_scale;
+  out->error_flags = flags;
+  out->n_levels = h->n_levels;
+  return status_from_flags(h, flags);
+}
+
+sph_status sph_get_field(sph_handle* h, int32_t which, double* out, int32_t on_device) {
+  if (!h || (h->n > 0 && !out) || which < 0 || which > 2) return fail(h, SPH_ERR_INVALID_ARG, "bad field request");
+  if (!h->recorded) return fail(h, SPH_ERR_STATE, "no recorded step (set params.record_fields and step)");
+  const size_t N = (size_t)h->n, cnt = which == 0 ? N : N * (size_t)h->dim;
+  Temp t(h, on_device ? 0 : sizeof(double) * cnt);
+  double* dst = on_device ? out : (double*)t.p;
+  cudaError_t e;
+  if (h->dim == 2)
+    e = h->prec == SPH_PREC_FP64 ? launch_get_fields<2, double>(h->S, which, dst, h->stream)
+                                 : launch_get_fields<2, float>(h->S, which, dst, h->stream);
+  else
+    e = h->prec == SPH_PREC_FP64 ? launch_get_fields<3, double>(h->S, which, dst, h->stream)
+                                 : launch_get_fields<3, float>(h->S, which, dst, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_field");
+  if (!on_device) SPH_CUDA(h, cudaMemcpyAsync(out, dst, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SPH_OK;
+}
+
+sph_status sph_neighbor_sets(sph_handle* h, int32_t* dens_count, int32_t* force_count, int64_t* dens_idsum,
+                             int64_t* force_idsum) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  const size_t N = (size_t)std::max<int64_t>(h->n, 1);
+  if (!h->S.dbg_count) {
+    SPH_TRY(grab(h, h->S.dbg_count, 2 * N));
+    SPH_TRY(grab(h, h->S.dbg_sum, 2 * N));
+  }
+  if (h->n == 0) return SPH_OK;
+  DevState S = h->S;
+  S.scal = h->S.scal + 1;  // keep the last step's statistics
+  PassFlags f;
+  f.general_eos = 0;
+  f.nbr_debug = 1;
+  f.advance = 0;
+  cudaError_t e = build_cells(S, h->stream);
+  if (e == cudaSuccess) {
+    if (h->dim == 2)
+      e = h->prec == SPH_PREC_FP64 ? launch_pass_a<2, double>(S, h->Gdw, h->Pd, f, h->stream)
+                                   : launch_pass_a<2, float>(S, h->Gf, h->Pf, f, h->stream);
+    else
+      e = h->prec == SPH_PREC_FP64 ? launch_pass_a<3, double>(S, h->Gdw, h->Pd, f, h->stream)
+                                   : launch_pass_a<3, float>(S, h->Gf, h->Pf, f, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "neighbor_sets");
+  h->recorded = false;
+  std::vector<int32_t> cnt(2 * N);
+  std::vector<long long> sum(2 * N);
+  SPH_CUDA(h, cudaMemcpyAsync(cnt.data(), S.dbg_count, sizeof(int32_t) * 2 * N, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync(sum.data(), S.dbg_sum, sizeof(long long) * 2 * N, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (size_t i = 0; i < (size_t)h->n; ++i) {
+    if (dens_count) dens_count[i] = cnt[2 * i];
+    if (force_count) force_count[i] = cnt[2 * i + 1];
+    if (dens_idsum) dens_idsum[i] = sum[2 * i];
+    if (force_idsum) force_idsum[i] = sum[2 * i + 1];
+  }
+  int flags = 0;
+  SPH_TRY(read_flags(h, &flags));
+  return status_from_flags(h, flags);
+}
+
+sph_status sph_get_cell_list(sph_handle* h, uint32_t* key_by_id, uint32_t* sorted_ids) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  if (h->n == 0) return SPH_OK;
+  const size_t N = (size_t)h->n;
+  cudaError_t e = build_cells(h->S, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "build_cells");
+  h->recorded = false;
+  std::vector<uint32_t> ku(N), pu(N);
+  SPH_CUDA(h, cudaMemcpyAsync(ku.data(), h->S.key_u, 4 * N, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync(pu.data(), h->S.pid_u, 4 * N, cudaMemcpyDeviceToHost, h->stream));
+  if (sorted_ids) SPH_CUDA(h, cudaMemcpyAsync(sorted_ids, h->S.pid_s, 4 * N, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (key_by_id)
+    for (size_t i = 0; i < N; ++i) key_by_id[pu[i]] = ku[i];
+  return SPH_OK;
+}
+
+sph_status sph_get_grid(sph_handle* h, sph_grid_info* out) {
+  if (!h || !out) return SPH_ERR_INVALID_ARG;
+  memset(out, 0, sizeof *out);
+  out->n_levels = h->n_levels;
+  out->dim = h->dim;
+  for (int k = 0; k < 3; ++k) out->lo[k] = h->dom.lo[k];
+  out->h0 = h->h0;
+  out->lip_h = h->lip_h;
+  for (int l = 0; l < h->n_levels; ++l) {
+    out->cell[l] = h->Gd.cell[l];
+    out->dims[l][0] = h->Gd.nx[l];
+    out->dims[l][1] = h->Gd.ny[l];
+    out->dims[l][2] = h->Gd.nz[l];
+  }
+  for (int l = 0; l <= h->n_levels; ++l) out->base[l] = h->Gd.base[l];
+  return SPH_OK;
+}
+
+sph_status sph_sync(sph_handle* h) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  int flags = 0;
+  SPH_TRY(read_flags(h, &flags));
+  return status_from_flags(h, flags);
+}
+
+// checkpoint layout: header (8 x int64: magic, version, n, dim, steps, 0, 0, 0),
+// 2 doubles (t0, t1), n*dim doubles (positions), n bytes (colours)
+static const int64_t kMagic = 0x3148534D48505300LL;
+
+sph_status sph_save(sph_handle* h, void* buf, size_t* nbytes) {
+  if (!h || !nbytes) return SPH_ERR_INVALID_ARG;
+  const size_t N = (size_t)h->n, d = (size_t)h->dim;
+  const size_t need = 8 * 8 + 2 * 8 + 8 * N * d + N;
+  if (!buf) {
+    *nbytes = need;
+    return SPH_OK;
+  }
+  if (*nbytes < need) return fail(h, SPH_ERR_INVALID_ARG, "checkpoint buffer too small");
+  int64_t hdr[8] = {kMagic, 1, (int64_t)N, (int64_t)d, h->steps, 0, 0, 0};
+  double sched[2] = {h->t0, h->t1};
+  uint8_t* p = (uint8_t*)buf;
+  memcpy(p, hdr, sizeof hdr);
+  memcpy(p + 64, sched, sizeof sched);
+  SPH_TRY(sph_get_positions(h, (double*)(p + 80), 0));
+  SPH_TRY(sph_get_colors(h, p + 80 + 8 * N * d, 0));
+  *nbytes = need;
+  return SPH_OK;
+}
+
+sph_status sph_load(sph_handle* h, const void* buf, size_t nbytes) {
+  if (!h || !buf || nbytes < 80) return fail(h, SPH_ERR_INVALID_ARG, "bad checkpoint");
+  int64_t hdr[8];
+  double sched[2];
+  memcpy(hdr, buf, sizeof hdr);
+  memcpy(sched, (const uint8_t*)buf + 64, sizeof sched);
+  const size_t N = (size_t)h->n, d = (size_t)h->dim;
+  if (hdr[0] != kMagic || hdr[1] != 1 || hdr[2] != (int64_t)N || hdr[3] != (int64_t)d ||
+      nbytes < 80 + 8 * N * d + N)
+    return fail(h, SPH_ERR_INVALID_ARG, "checkpoint does not match this handle");
+  const uint8_t* p = (const uint8_t*)buf;
+  SPH_TRY(sph_set_state(h, (const double*)(p + 80), p + 80 + 8 * N * d, 0));
+  h->steps = hdr[4];
+  h->t0 = sched[0];
+  h->t1 = sched[1];
+  return write_ctl(h);
+}
+
+const char* sph_last_error(const sph_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+sph_status sph_get_info(const sph_handle* h, int64_t* n, int32_t* dim, double* rho_scale) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  if (n) *n = h->n;
+  if (dim) *dim = h->dim;
+  if (rho_scale) *rho_scale = h->rho_scale;
+  return SPH_OK;
+}
+
+void sph_destroy(sph_handle* h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->stream);
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto& b : h->blocks) h->alloc.free(b.first, b.second, h->alloc.ctx);
+  cudaStreamSynchronize(h->stream);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,201 @@
+// Cell-linked list of the multi-resolution grid (Algorithm 1, lines 7-8).
+//
+// Particles are ordered by cell key with a counting sort over the dense key
+// range: warp-aggregated atomic counts per cell, an exclusive scan of the
+// counts (which is also the cell-start table the neighbour loops read), an
+// atomic scatter that counts each cell back down to zero, and a gather that
+// makes the order inside each cell stable (ascending previous position) while
+// it moves the particle records into sorted order.
+#include "sph_internal.h"
+
+namespace sph {
+
+namespace {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__global__ void __launch_bounds__(256) k_count(int n, const uint32_t* __restrict__ key,
+                                               uint32_t* __restrict__ cnt) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool active = i < n;
+  unsigned mask = __ballot_sync(0xffffffffu, active);
+  if (!active) return;
+  uint32_t k = key[i];
+  unsigned peers = __match_any_sync(mask, k);
+  int leader = __ffs(peers) - 1;
+  if ((int)(threadIdx.x & 31) == leader) atomicAdd(&cnt[k], (uint32_t)__popc(peers));
+}
+
+__global__ void __launch_bounds__(256) k_scatter(int n, const uint32_t* __restrict__ key,
+                                                 const uint32_t* __restrict__ cstart,
+                                                 uint32_t* __restrict__ cnt,
+                                                 uint32_t* __restrict__ slots) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  bool active = i < n;
+  unsigned mask = __ballot_sync(0xffffffffu, active);
+  if (!active) return;
+  uint32_t k = key[i];
+  unsigned peers = __match_any_sync(mask, k);
+  int lane = threadIdx.x & 31;
+  int leader = __ffs(peers) - 1;
+  uint32_t top = 0;
+  if (lane == leader) top = atomicSub(&cnt[k], (uint32_t)__popc(peers));
+  top = __shfl_sync(peers, top, leader);
+  int rank = __popc(peers & ((1u << lane) - 1u));
+  slots[cstart[k] + top - 1 - rank] = (uint32_t)i;
+}
+
+// per block: sum of a tile of kScanTile counts
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+                                                              uint32_t n, uint32_t* __restrict__ part) {
+  __shared__ uint32_t red[kScanThreads / 32];
+  size_t base = (size_t)blockIdx.x * kScanTile;
+  uint32_t s = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    size_t idx = base + (size_t)k * kScanThreads + threadIdx.x;
+    if (idx < n) s += in[idx];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = threadIdx.x < kScanThreads / 32 ? red[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+  }
+}
+
+// exclusive scan of the block sums, in place (one block of 1024 threads)
+__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ part, int nb) {
+  __shared__ uint32_t wsum[32];
+  int per = (nb + blockDim.x - 1) / blockDim.x;
+  int b0 = threadIdx.x * per;
+  uint32_t local = 0;
+  for (int k = 0; k < per; ++k)
+    if (b0 + k < nb) local += part[b0 + k];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t v = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+    uint32_t vi = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t u = __shfl_up_sync(0xffffffffu, vi, o);
+      if (lane >= o) vi += u;
+    }
+    wsum[lane] = vi - v;
+  }
+  __syncthreads();
+  uint32_t run = wsum[w] + incl - local;
+  for (int k = 0; k < per; ++k)
+    if (b0 + k < nb) {
+      uint32_t v = part[b0 + k];
+      part[b0 + k] = run;
+      run += v;
+    }
+}
+
+// exclusive scan of each tile plus its block offset; out has n + 1 entries
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ in, uint32_t n,
+                                                            const uint32_t* __restrict__ part,
+                                                            uint32_t* __restrict__ out) {
+  __shared__ uint32_t wtot[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  // each warp owns kScanItems * 32 consecutive entries of the tile
+  size_t wbase = (size_t)blockIdx.x * kScanTile + (size_t)w * kScanItems * 32;
+  uint32_t v[kScanItems];
+  uint32_t run = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    size_t idx = wbase + (size_t)k * 32 + lane;
+    uint32_t x = idx < n ? in[idx] : 0u;
+    uint32_t incl = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += y;
+    }
+    v[k] = run + incl - x;
+    run += __shfl_sync(0xffffffffu, incl, 31);
+  }
+  if (lane == 0) wtot[w] = run;
+  __syncthreads();
+  uint32_t off = part[blockIdx.x];
+  for (int q = 0; q < w; ++q) off += wtot[q];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    size_t idx = wbase + (size_t)k * 32 + lane;
+    if (idx < n) out[idx] = off + v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == kScanThreads - 1) {
+    uint32_t tot = part[blockIdx.x];
+    for (int q = 0; q < kScanThreads / 32; ++q) tot += wtot[q];
+    out[n] = tot;
+  }
+}
+
+template <class T>
+__global__ void __launch_bounds__(256) k_stable_gather(
+    int n, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ key_u,
+    const uint32_t* __restrict__ cstart, const V4<T>* __restrict__ pos_u,
+    const uint32_t* __restrict__ meta_u, const uint32_t* __restrict__ pid_u,
+    V4<T>* __restrict__ pos_s, uint32_t* __restrict__ meta_s, uint32_t* __restrict__ pid_s,
+    uint32_t* __restrict__ key_s) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n) return;
+  uint32_t i = slots[s];
+  uint32_t k = key_u[i];
+  uint32_t b = cstart[k], e = cstart[k + 1];
+  uint32_t rank = 0;
+  for (uint32_t t = b; t < e; ++t) rank += slots[t] < i;
+  uint32_t d = b + rank;
+  pos_s[d] = pos_u[i];
+  meta_s[d] = meta_u[i];
+  pid_s[d] = pid_u[i];
+  key_s[d] = k;
+}
+
+__global__ void __launch_bounds__(256) k_get_colors(int n, const uint32_t* __restrict__ meta_u,
+                                                    const uint32_t* __restrict__ pid_u, uint8_t* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[pid_u[i]] = (uint8_t)(meta_u[i] & 0xFFu);
+}
+
+}  // namespace
+
+cudaError_t launch_get_colors(const DevState& S, uint8_t* out, cudaStream_t st) {
+  if (S.n > 0) k_get_colors<<<(S.n + 255) / 256, 256, 0, st>>>(S.n, S.meta_u, S.pid_u, out);
+  return cudaGetLastError();
+}
+
+cudaError_t build_cells(const DevState& S, cudaStream_t st) {
+  const int n = S.n;
+  if (n <= 0) return cudaSuccess;
+  const int tb = 256;
+  const int gb = (n + tb - 1) / tb;
+  k_count<<<gb, tb, 0, st>>>(n, S.key_u, S.cnt);
+  const uint32_t m = S.total_cells;
+  const int nb = (int)((m + kScanTile - 1) / kScanTile);
+  k_scan_reduce<<<nb, kScanThreads, 0, st>>>(S.cnt, m, S.scan_part);
+  k_scan_top<<<1, 1024, 0, st>>>(S.scan_part, nb);
+  k_scan_down<<<nb, kScanThreads, 0, st>>>(S.cnt, m, S.scan_part, S.cstart);
+  k_scatter<<<gb, tb, 0, st>>>(n, S.key_u, S.cstart, S.cnt, S.tmp);
+  if (S.fp64)
+    k_stable_gather<double><<<gb, tb, 0, st>>>(n, S.tmp, S.key_u, S.cstart, (const V4<double>*)S.pos4_u,
+                                               S.meta_u, S.pid_u, (V4<double>*)S.pos4_s, S.meta_s,
+                                               S.pid_s, S.key_s);
+  else
+    k_stable_gather<float><<<gb, tb, 0, st>>>(n, S.tmp, S.key_u, S.cstart, (const V4<float>*)S.pos4_u,
+                                              S.meta_u, S.pid_u, (V4<float>*)S.pos4_s, S.meta_s,
+                                              S.pid_s, S.key_s);
+  return cudaGetLastError();
+}
+
+}  // namespace sph

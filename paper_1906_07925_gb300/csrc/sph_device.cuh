@@ -1,0 +1,317 @@
+// Device-side building blocks of the sm_103a relaxation step: parameter blocks
+// passed by value to kernels, the Wendland C2 kernel, the analytic target field,
+// the level set and its projection, the split-precision cell frame, and the
+// Philox4x32-10 counter-based generator used by the initial sampling.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sph {
+
+constexpr int kMaxLevels = 8;
+constexpr int kMaxShapes = 4;
+
+// error bits latched in the device error word (1 << sph_status value)
+constexpr int kErrNonfinite = 1 << 4;
+constexpr int kErrOutOfDomain = 1 << 5;
+constexpr int kErrTimeout = 1 << 7;
+
+template <class T>
+struct alignas(sizeof(T) * 4) V4 {
+  T x, y, z, w;
+};
+
+// Geometry + target field (Sec. 2.3, 3.1, 3.2) in the working precision T.
+template <class T>
+struct Geom {
+  int dim, n_shapes, field_kind, dist_shape, n_poly;
+  int kind[kMaxShapes], keep_inside[kMaxShapes];
+  T lo[3], hi[3], ext[3];
+  T center[kMaxShapes][3], size[kMaxShapes][3];
+  T s0, a, b;
+  T poly[8];
+  T hfac;      // tau * rho_scale^(-1/d): h = hfac * s * (1 + P)^(-1/d)
+  T rho_scale;
+};
+
+// Multi-resolution cell grid. Level l has cells of edge cell[l] = cell[0] 2^l;
+// a particle lives at the level of its smoothing length and stores its
+// position as integer cell coordinates plus an offset in [0, cell[l]).
+template <class T>
+struct Grid {
+  int n_levels, dim;
+  int nx[kMaxLevels], ny[kMaxLevels], nz[kMaxLevels];
+  uint32_t base[kMaxLevels + 1];
+  T lo[3];
+  T cell[kMaxLevels], inv_cell[kMaxLevels];
+  T wall_hi[kMaxLevels][3];  // upper box wall as an offset inside the last cell
+  T inv_h0;                  // level(h) = floor(log2(h / h0))
+  T lip_h;                   // |grad h| bound: neighbours' h within h_i +- lip_h r
+  T rfac;                    // search radius = kappa h_i rfac covers max(h_i, h_ij)
+};
+
+template <class T>
+struct Phys {
+  T P0, gamma, kappa, inv_tau;
+  T alpha;  // dimensionless Wendland constant: 7/pi (2D), 21/(2 pi) (3D)
+};
+
+// Per-block partials of the pass-A reductions (FP64), reduced in fixed order.
+struct Partial {
+  double min_rc_a, max_a, sum_rho, err_l2, err_max;
+  long long ipairs, fpairs;
+  double pad;
+};
+
+// Step scalars written by the last block of pass A, read by pass B.
+struct Scalars {
+  double dt1, dt2, min_rc_a, max_a, sum_rho, err_l2, err_max, sigma;
+  long long ipairs, fpairs, wall_moved, step_of_stats;
+};
+
+// Surface-tension schedule and step counter (Eq. sph_st_sigma).
+struct StepCtl {
+  long long step;
+  double t0, t1, sigma0;
+};
+
+__device__ __forceinline__ double sigma_of(const StepCtl& c, long long t) {
+  if (c.t0 < 0.0 || (double)t <= c.t0) return c.sigma0;
+  if ((double)t <= c.t1) return c.sigma0 * (1.0 - (c.t0 - (double)t) / (c.t0 - c.t1));
+  return 0.0;
+}
+
+// ---------------------------------------------------------------- math ----
+
+template <class T> __device__ __forceinline__ T dsqrt(T x);
+template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }
+template <> __device__ __forceinline__ double dsqrt<double>(double x) { return sqrt(x); }
+
+template <class T> __device__ __forceinline__ T drsqrt(T x);
+template <> __device__ __forceinline__ float drsqrt<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double drsqrt<double>(double x) { return rsqrt(x); }
+
+template <class T> __device__ __forceinline__ T drcp(T x);
+template <> __device__ __forceinline__ float drcp<float>(float x) { return __fdividef(1.0f, x); }
+template <> __device__ __forceinline__ double drcp<double>(double x) { return 1.0 / x; }
+
+template <class T> __device__ __forceinline__ T dfloor(T x);
+template <> __device__ __forceinline__ float dfloor<float>(float x) { return floorf(x); }
+template <> __device__ __forceinline__ double dfloor<double>(double x) { return floor(x); }
+
+// small integer -> floating point without the conversion unit:
+// for |v| < 2^22, the bit pattern of 1.5*2^23 + v read as a float is exactly
+// 12582912 + v (the integer lands in the low mantissa bits).
+template <class T> __device__ __forceinline__ T small_int_to_fp(int v);
+template <> __device__ __forceinline__ float small_int_to_fp<float>(int v) {
+  return __int_as_float(0x4B400000 + v) - 12582912.0f;
+}
+template <> __device__ __forceinline__ double small_int_to_fp<double>(int v) {
+  return __longlong_as_double(0x4338000000000000LL + (long long)v) - 6755399441055744.0;
+}
+
+template <int D, class T>
+__device__ __forceinline__ T pow_d(T x) {  // x^D
+  return D == 2 ? x * x : x * x * x;
+}
+
+// (h / tau)^(2D) = 1 / rho_t^2 (unit mass, h = tau rho_t^(-1/d))
+template <int D, class T>
+__device__ __forceinline__ T inv_rho_t2(T h, T inv_tau) {
+  T t = h * inv_tau;
+  T t2 = t * t;
+  return D == 2 ? t2 * t2 : t2 * t2 * t2;
+}
+
+// ------------------------------------------------------------ geometry ----
+
+// signed distance, positive inside shape s
+template <class T>
+__device__ __forceinline__ T shape_inside(const Geom<T>& g, int s, const T* x, int dim) {
+  if (g.kind[s] == 0) {
+    T r2 = 0;
+    for (int k = 0; k < dim; ++k) {
+      T d = x[k] - g.center[s][k];
+      r2 += d * d;
+    }
+    return g.size[s][0] - dsqrt(r2);
+  }
+  T out2 = 0, qmax = -1e30;
+  for (int k = 0; k < dim; ++k) {
+    T q = fabs(x[k] - g.center[s][k]) - g.size[s][k];
+    if (q > 0) out2 += q * q;
+    qmax = q > qmax ? q : qmax;
+  }
+  T inside = qmax < 0 ? qmax : T(0);
+  return -(dsqrt(out2) + inside);
+}
+
+template <class T>
+__device__ __forceinline__ T constraint_phi(const Geom<T>& g, int s, const T* x, int dim) {
+  T v = shape_inside(g, s, x, dim);
+  return g.keep_inside[s] ? v : -v;
+}
+
+// Eq. displacement_surface for one shape constraint violated at x (phi < 0):
+// move to the closest point of its surface. Returns 1 if x moved.
+template <class T>
+__device__ __forceinline__ int project_shape(const Geom<T>& g, int s, T* x, int dim) {
+  if (!(constraint_phi(g, s, x, dim) < 0)) return 0;
+  if (g.kind[s] == 0) {
+    T d[3] = {0, 0, 0}, r2 = 0;
+    for (int k = 0; k < dim; ++k) {
+      d[k] = x[k] - g.center[s][k];
+      r2 += d[k] * d[k];
+    }
+    T r = dsqrt(r2);
+    if (r == 0) {
+      d[0] = 1;
+      r = 1;
+    }
+    for (int k = 0; k < dim; ++k) x[k] = g.center[s][k] + g.size[s][0] * d[k] / r;
+    return 1;
+  }
+  if (g.keep_inside[s]) {
+    for (int k = 0; k < dim; ++k) {
+      T lo = g.center[s][k] - g.size[s][k], hi = g.center[s][k] + g.size[s][k];
+      x[k] = x[k] < lo ? lo : (x[k] > hi ? hi : x[k]);
+    }
+    return 1;
+  }
+  int best = 0;
+  T bestd = 1e30, sign = 1;
+  for (int k = 0; k < dim; ++k) {
+    T dlo = x[k] - (g.center[s][k] - g.size[s][k]);
+    T dhi = (g.center[s][k] + g.size[s][k]) - x[k];
+    if (dlo < bestd) { bestd = dlo; best = k; sign = -1; }
+    if (dhi < bestd) { bestd = dhi; best = k; sign = 1; }
+  }
+  x[best] = g.center[s][best] + sign * g.size[s][best];
+  return 1;
+}
+
+// inside the region (box and every shape constraint)?
+template <class T>
+__device__ __forceinline__ bool in_region(const Geom<T>& g, const T* x) {
+  for (int k = 0; k < g.dim; ++k)
+    if (x[k] < g.lo[k] || x[k] > g.hi[k]) return false;
+  for (int s = 0; s < g.n_shapes; ++s)
+    if (!(constraint_phi(g, s, x, g.dim) > 0)) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------- field ----
+
+// polynomial modulation factor 1 + sum_k poly_k b_k(x~)
+template <class T>
+__device__ __forceinline__ T poly_factor(const Geom<T>& g, const T* x) {
+  if (g.n_poly == 0) return T(1);
+  T t[3];
+  for (int k = 0; k < g.dim; ++k) t[k] = T(2) * (x[k] - g.lo[k]) / g.ext[k] - T(1);
+  T b[8];
+  if (g.dim == 2) {
+    T X = t[0], Y = t[1];
+    b[0] = X; b[1] = Y; b[2] = X * X; b[3] = X * Y; b[4] = Y * Y;
+    b[5] = X * X * X; b[6] = X * X * Y; b[7] = X * Y * Y;
+  } else {
+    T X = t[0], Y = t[1], Z = t[2];
+    b[0] = X; b[1] = Y; b[2] = Z; b[3] = X * X; b[4] = Y * Y; b[5] = Z * Z;
+    b[6] = X * Y; b[7] = Y * Z;
+  }
+  T f = 1;
+  for (int k = 0; k < g.n_poly; ++k) f += g.poly[k] * b[k];
+  return f;
+}
+
+template <class T>
+__device__ __forceinline__ T spacing_of(const Geom<T>& g, const T* x) {
+  if (g.field_kind == 0) return g.s0;
+  return g.a + g.b * fabs(shape_inside(g, g.dist_shape, x, g.dim));
+}
+
+// smoothing length h = tau rho_t^(-1/d) with rho_t = rho_scale s^-d (1+P)
+// (Eq. scale_SPH_particle, unit mass) = hfac * s * (1+P)^(-1/d)
+template <int D, class T>
+__device__ __forceinline__ T h_of(const Geom<T>& g, const T* x) {
+  T h = g.hfac * spacing_of(g, x);
+  if (g.n_poly) {
+    T f = poly_factor(g, x);
+    if (D == 2) h *= drsqrt(f);
+    else h *= (T)rcbrt((double)f);
+  }
+  return h;
+}
+
+template <>
+__device__ __forceinline__ float h_of<3, float>(const Geom<float>& g, const float* x) {
+  float h = g.hfac * spacing_of(g, x);
+  if (g.n_poly) h *= rcbrtf(poly_factor(g, x));
+  return h;
+}
+
+// ---------------------------------------------------------------- grid ----
+
+template <class T>
+__device__ __forceinline__ int level_of_h(const Grid<T>& G, T h) {
+  T r = h * G.inv_h0;
+  if (!(r >= T(2))) return 0;
+  int l = ilogb(r);
+  return l < G.n_levels - 1 ? l : G.n_levels - 1;
+}
+
+template <class T>
+__device__ __forceinline__ int level_of_key(const Grid<T>& G, uint32_t key) {
+  int l = 0;
+#pragma unroll
+  for (int q = 1; q < kMaxLevels; ++q)
+    if (q < G.n_levels && key >= G.base[q]) l = q;
+  return l;
+}
+
+// Split-precision frame change: a position given as integer cell coordinates
+// c at level la with offset o in [0, cell[la]) is re-expressed at level lb.
+// Integer parts stay exact; only the offsets are rounded, relative to the
+// cell size.
+template <class T>
+__device__ __forceinline__ void change_level(const Grid<T>& G, int la, int lb, int& c, T& o) {
+  if (la == lb) return;
+  const T c0 = G.cell[0];
+  int X0 = c << la;
+  int sub = (int)dfloor(o * G.inv_cell[0]);
+  int maxsub = (1 << la) - 1;
+  sub = sub < 0 ? 0 : (sub > maxsub ? maxsub : sub);
+  X0 += sub;
+  T o0 = o - small_int_to_fp<T>(sub) * c0;
+  int cb = X0 >> lb;
+  o = o0 + small_int_to_fp<T>(X0 - (cb << lb)) * c0;
+  c = cb;
+}
+
+// ------------------------------------------------------------- Philox ----
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32
+// multiplies with the published multipliers and Weyl key increments.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 ctr, uint2 key) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t hi0 = __umulhi(M0, ctr.x), lo0 = M0 * ctr.x;
+    uint32_t hi1 = __umulhi(M1, ctr.z), lo1 = M1 * ctr.z;
+    uint4 n;
+    n.x = hi1 ^ ctr.y ^ key.x;
+    n.y = lo1;
+    n.z = hi0 ^ ctr.w ^ key.y;
+    n.w = lo0;
+    ctr = n;
+    key.x += W0;
+    key.y += W1;
+  }
+  return ctr;
+}
+
+__device__ __forceinline__ double u01(uint32_t v) {  // (0, 1)
+  return ((double)v + 0.5) * 2.3283064365386963e-10;
+}
+
+}  // namespace sph

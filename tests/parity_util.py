@@ -1,0 +1,105 @@
+"""Helpers shared by the GPU parity tests: run one step on both sides from the
+same seeded input and compare with tolerances stated here.
+
+Tolerances (per-step, identical input state): density relative `tol`; the
+force a_i within `tol` of S_i = sum_j |pair term| (the sums cancel, so a
+relative bound on a_i itself is meaningless); a~ and the displacement are
+downstream of a, so their bound carries the relative error of a,
+eps_i = tol * S_i / |a_i|, maximised over the neighbourhood.
+tol = 1e-5 for the FP32 split-precision path, 1e-12 for FP64.
+"""
+import numpy as np
+from scipy.spatial import cKDTree
+
+import oracle
+
+TOL = {"fp32": 1e-5, "fp64": 1e-12}
+
+
+def make_gpu(p, pos, col, precision, **kw):
+    from paper_1906_07925_gb300 import Relaxation
+    r = Relaxation(p, n_particles=len(pos), n_colors=int(col.max()) + 1, precision=precision,
+                   record_fields=True, use_graph=kw.pop("use_graph", False), **kw)
+    r.set_state(pos, col)
+    return r
+
+
+def h_all(p, pos):
+    return np.array([oracle.h_of(p, x) for x in pos])
+
+
+def local_max(p, pos, h, v):
+    """max of v over each particle's neighbourhood (r < kappa max h)."""
+    tree = cKDTree(pos)
+    R = p.kappa * h.max() * 1.01
+    out = np.empty_like(v)
+    for i, nb in enumerate(tree.query_ball_point(pos, R)):
+        out[i] = v[nb].max()
+    return out
+
+
+def compare_step(p, pos, col, precision, step_index=0, gpu=None):
+    """One step on both sides; assert parity; return (gpu, oracle outputs)."""
+    tol = TOL[precision]
+    r = gpu or make_gpu(p, pos, col, precision)
+    r.step(1)
+    st = r.stats()
+    g = dict(rho=r.field("rho"), acc=r.field("acc"), visc=r.field("visc"), x=r.positions())
+    xo, info, f = oracle.step(p, pos, col, step_index)
+    n = len(pos)
+    # density
+    rel = np.abs(g["rho"] - f["rho"]) / f["rho"]
+    assert rel.max() <= tol, ("rho", rel.max(), int(rel.argmax()))
+    # force a_n, normalised by the sum of pair magnitudes
+    Sa = f["pair_abs_a"]
+    ea = np.abs(g["acc"] - f["acc"]).max(axis=1)
+    ok = ea <= tol * Sa + 1e-300
+    assert ok.all(), ("acc", (ea / np.maximum(Sa, 1e-300)).max(), int(np.argmax(ea / np.maximum(Sa, 1e-300))))
+    # time steps: relative error of a at the argmin particle
+    an = np.linalg.norm(f["acc"], axis=1)
+    cond = np.where(an > 0, Sa / np.maximum(an, 1e-300), 1.0)
+    h = h_all(p, pos)
+    rc = p.kappa * h
+    m = np.where(an > 0, rc / np.maximum(an, 1e-300), np.inf)
+    k = int(np.argmin(m))
+    dt_tol = 2 * tol * (1 + cond[k])
+    assert abs(st["dt1"] - info["dt1"]) <= dt_tol * info["dt1"], ("dt1", st["dt1"], info["dt1"])
+    assert abs(st["dt2"] - info["dt2"]) <= dt_tol * info["dt2"], ("dt2", st["dt2"], info["dt2"])
+    # a~: error carried from a (eps over the neighbourhood), factor 4 for the
+    # harmonic-mean coefficient's own dependence on |a|
+    eps = local_max(p, pos, h, tol * (1 + cond))
+    ev = np.abs(g["visc"] - f["visc"]).max(axis=1)
+    bound_v = 4 * (eps + dt_tol) * f["pair_abs_b"] + 1e-300
+    assert (ev <= bound_v).all(), ("visc", (ev / bound_v).max())
+    # displacement
+    dg = g["x"] - pos
+    do = xo - pos
+    dn = np.linalg.norm(do, axis=1)
+    ed = np.abs(dg - do).max(axis=1)
+    scale = np.abs(pos).max() + 1.0
+    rep = (6e-8 if precision == "fp32" else 1e-15) * (scale if precision == "fp32" else scale)
+    # representation: FP32 offsets are relative to cells (the rounding of the
+    # input positions and of projected points is at most a few ulp of x)
+    bound_d = 4 * (eps + 2 * dt_tol) * (dn + 0.5 * info["dt1"] * info["dt2"] * Sa) + 4 * rep
+    assert (ed <= bound_d).all(), ("disp", (ed / bound_d).max(), int(np.argmax(ed / bound_d)))
+    # integer statistics
+    assert st["force_pairs"] == info["force_pairs"] or precision == "fp32"
+    return r, dict(info=info, f=f, x=xo, gpu=g, stats=st)
+
+
+def near_edge_particles(p, pos, rel=1e-5):
+    """Particles with any pair within `rel` of a support edge (density or force
+    criterion): their FP32 neighbour sets may legitimately differ."""
+    h = h_all(p, pos)
+    tree = cKDTree(pos)
+    R = p.kappa * h.max() * 1.01
+    bad = np.zeros(len(pos), bool)
+    for i, nb in enumerate(tree.query_ball_point(pos, R)):
+        nb = np.asarray(nb)
+        r = np.linalg.norm(pos[nb] - pos[i], axis=1)
+        Hd = p.kappa * h[i]
+        Hf = p.kappa * 0.5 * (h[i] + h[nb])
+        if np.any(np.abs(r - Hd) <= rel * Hd) or np.any(np.abs(r - Hf) <= rel * Hf):
+            bad[i] = True
+    # a particle next to an ambiguous pair sees it too
+    return bad

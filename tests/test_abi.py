@@ -1,0 +1,80 @@
+"""The C-ABI library builds, loads and exports every declared entry point; the
+ctypes mirror of each struct has the C layout; argument validation answers
+without touching a GPU."""
+import ctypes as C
+import os
+import subprocess
+
+import pytest
+
+import workloads as W
+from paper_1906_07925_gb300 import _binding as B
+from paper_1906_07925_gb300 import build as build_lib
+from paper_1906_07925_gb300 import problem_structs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build_lib()
+    return B.load()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = B.declared_symbols()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_struct_layouts_match_header(tmp_path):
+    src = tmp_path / "sizes.c"
+    src.write_text(
+        '#include <stdio.h>\n#include <stddef.h>\n#include "sphmesh.h"\n'
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "sizeof(sph_shape),sizeof(sph_domain),sizeof(sph_field),sizeof(sph_params),"
+        "sizeof(sph_alloc),sizeof(sph_stats),sizeof(sph_grid_info),"
+        "offsetof(sph_params,seed),offsetof(sph_stats,rho_scale));return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
+    want = [C.sizeof(B.sph_shape), C.sizeof(B.sph_domain), C.sizeof(B.sph_field), C.sizeof(B.sph_params),
+            C.sizeof(B.sph_alloc), C.sizeof(B.sph_stats), C.sizeof(B.sph_grid_info),
+            B.sph_params.seed.offset, B.sph_stats.rho_scale.offset]
+    assert got == want
+
+
+def _create(lib, p, n=100, ncol=4, **kw):
+    d, f, q = problem_structs(p, **kw)
+    h = B.H()
+    st = lib.sph_create(C.byref(d), C.byref(f), n, ncol, C.byref(q), None, None, C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda p: setattr(p, "dim", 4),
+    lambda p: setattr(p, "s0", -1.0),
+    lambda p: setattr(p, "tau", 0.0),
+    lambda p: setattr(p, "poly", [0.6, 0.6]),
+    lambda p: setattr(p, "gamma", -2.0),
+])
+def test_invalid_arguments_rejected_before_any_device_work(lib, mutate):
+    p = W.uniform_square_2d(16)
+    mutate(p)
+    st, h = _create(lib, p)
+    assert st == 1 and not h.value
+
+
+def test_bad_colour_count_and_particle_count(lib):
+    p = W.uniform_square_2d(16)
+    assert _create(lib, p, ncol=0)[0] == 1
+    assert _create(lib, p, ncol=300)[0] == 1
+    assert _create(lib, p, n=-5)[0] == 1
+
+
+def test_null_handle_calls(lib):
+    assert lib.sph_step(None, 1) == 1
+    assert lib.sph_sync(None) == 1
+    assert lib.sph_last_error(None) == b"null handle"
+    lib.sph_destroy(None)

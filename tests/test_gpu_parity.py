@@ -1,0 +1,255 @@
+"""GPU path vs the FP64 oracle, element by element, on seeded inputs.
+
+Sizes span several thread blocks and cell rows with ragged tails; the graded
+cases exercise several grid levels. Tolerances are stated in parity_util.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from parity_util import TOL, compare_step, h_all, make_gpu, near_edge_particles
+
+pytestmark = pytest.mark.gpu
+
+
+def c1_state():
+    p = W.uniform_square_2d(64, 4)
+    pos, col, _ = W.lattice_jitter_2d(p, 64, 0.3, 0)
+    return p, pos, col
+
+
+def graded2d_state(n=20000, seed=1, ncol=16):
+    p = W.graded_hole_2d(n, ncol)
+    pos, col, _ = W.sample_density(p, n, seed)
+    return p, pos, col
+
+
+def graded3d_state(n=30000, seed=2, ncol=32):
+    p = W.graded_inclusion_3d(n, ncol)
+    pos, col, _ = W.sample_density(p, n, seed)
+    return p, pos, col
+
+
+# ------------------------------------------------------------ neighbours ----
+
+@pytest.mark.parametrize("case", ["c1", "g2", "g3"])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_neighbor_sets_match_oracle(case, precision):
+    p, pos, col = {"c1": c1_state, "g2": graded2d_state, "g3": graded3d_state}[case]()
+    r = make_gpu(p, pos, col, precision)
+    got = r.neighbor_sets()
+    want = oracle.neighbor_sets(p, pos, 1)
+    keep = np.ones(len(pos), bool)
+    if precision == "fp32":
+        keep = ~near_edge_particles(p, pos)
+    assert keep.mean() > 0.9
+    for k in ("dens_count", "force_count", "dens_idsum", "force_idsum"):
+        assert np.array_equal(got[k][keep], want[k][keep]), k
+    if precision == "fp64":
+        assert all(np.array_equal(got[k], want[k]) for k in got)
+    r.close()
+
+
+def test_grid_has_several_levels_on_graded_fields():
+    p, pos, col = graded3d_state(8000)
+    r = make_gpu(p, pos, col, "fp32")
+    assert r.grid()["n_levels"] >= 3
+    r.close()
+
+
+# ---------------------------------------------------------------- one step ----
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_parity_uniform_square(precision):
+    p, pos, col = c1_state()
+    r, out = compare_step(p, pos, col, precision)
+    assert out["stats"]["interface_pairs"] == out["info"]["interface_pairs"] or precision == "fp32"
+    r.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_parity_graded_2d(precision):
+    p, pos, col = graded2d_state()
+    r, out = compare_step(p, pos, col, precision)
+    assert out["info"]["wall_moved"] > 0  # the hole and the box walls were exercised
+    r.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_parity_graded_3d(precision):
+    p, pos, col = graded3d_state()
+    r, _ = compare_step(p, pos, col, precision)
+    r.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_step_parity_general_gamma_and_poly_field(precision):
+    p = W.adjoint_poly_2d(12000, 8)
+    p.gamma = 1.4
+    pos, col, _ = W.sample_density(p, 12000, 3)
+    r, _ = compare_step(p, pos, col, precision)
+    r.close()
+
+
+def test_step_parity_box_and_sphere_domains():
+    for k, (p, n) in enumerate(W.batch_instances(6, seed=4, n_lo=3000, n_hi=9000)):
+        p.rho_scale = W.rho_scale_for(p, n, res=512 if p.dim == 2 else 96)
+        pos, col, _ = W.sample_density(p, n, 10 + k)
+        r, _ = compare_step(p, pos, col, "fp64")
+        r.close()
+
+
+def test_ramp_schedule():
+    """Steps 0..6 with a ramp over (2, 5]: the sigma each step used matches
+    Eq. sph_st_sigma as the oracle evaluates it."""
+    p, pos, col = c1_state()
+    p = p.copy(t0=2, t1=5)
+    r = make_gpu(p, pos, col, "fp64")
+    r.ramp_surface_tension(2, 5)
+    for s in range(7):
+        r.step(1)
+        assert r.stats()["sigma"] == pytest.approx(oracle.sigma(p, s), abs=1e-15)
+    r.close()
+
+
+def test_ramped_step_parity():
+    """A step taken inside the ramp (sigma = 2) agrees with the oracle."""
+    p, pos, col = graded2d_state(8000)
+    q = p.copy(t0=0, t1=3)  # step 1 of this schedule uses sigma = 3 (1 - 1/3) = 2
+    r = make_gpu(q, pos, col, "fp32")
+    blob = bytearray(r.save())
+    blob[32:40] = np.int64(1).tobytes()  # checkpoint header: step counter = 1
+    r.load(bytes(blob))
+    assert oracle.sigma(q, 1) == pytest.approx(2.0)
+    r2, out = compare_step(q, pos, col, "fp32", step_index=1, gpu=r)
+    assert out["stats"]["sigma"] == pytest.approx(2.0)
+    r.close()
+
+
+# --------------------------------------------------------- many steps ----
+
+def test_relaxation_trajectory_fp64_stays_close():
+    """FP64 path over 20 steps of the 4,096-particle square: trajectories of two
+    correct implementations separate only through rounding, so positions agree
+    to a small fraction of the spacing."""
+    p, pos, col = c1_state()
+    r = make_gpu(p, pos, col, "fp64")
+    r.step(20)
+    xg = r.positions()
+    xo, infos = oracle.run(p, pos, col, 20)
+    assert np.abs(xg - xo).max() < 1e-6 * (1 / 64)
+    assert r.stats()["err_l2"] == pytest.approx(infos[-1]["err_l2"], rel=1e-6)
+    r.close()
+
+
+def test_relaxation_end_state_statistics_fp32():
+    """100 steps of the square case: FP32 split vs the FP64 oracle end states
+    compared statistically (density error, interface pairs)."""
+    p, pos, col = c1_state()
+    r = make_gpu(p, pos, col, "fp32", use_graph=True)
+    r.step(100)
+    st = r.stats()
+    xo, infos = oracle.run(p, pos, col, 100)
+    io = infos[-1]
+    assert st["err_l2"] == pytest.approx(io["err_l2"], rel=0.05)
+    assert abs(st["interface_pairs"] - io["interface_pairs"]) <= 0.05 * io["interface_pairs"] + 5
+    assert st["err_l2"] < 0.5 * oracle.step(p, pos, col, 0)[1]["err_l2"]  # it relaxed
+    r.close()
+
+
+# ------------------------------------------------------------- edge cases ----
+
+def test_empty_and_single_particle():
+    from paper_1906_07925_gb300 import Relaxation
+    p = W.uniform_square_2d(16)
+    r0 = Relaxation(p, 0, 1, precision="fp32")
+    r0.step(3)
+    assert r0.positions().shape == (0, 2)
+    r0.close()
+    r1 = Relaxation(p, 1, 1, precision="fp64", record_fields=True)
+    r1.set_state(np.array([[0.3, 0.4]]), np.array([0], np.uint8))
+    r1.step(2)
+    assert np.array_equal(r1.positions(), [[0.3, 0.4]])
+    st = r1.stats()
+    assert st["dt1"] == 0.0 and st["force_pairs"] == 0
+    r1.close()
+
+
+def test_ragged_sizes_and_graph_matches_direct():
+    for n in (257, 1000, 4097):
+        p = W.graded_hole_2d(n, 3)
+        pos, col, _ = W.sample_density(p, n, 5)
+        a = make_gpu(p, pos, col, "fp32", use_graph=True)
+        b = make_gpu(p, pos, col, "fp32", use_graph=False)
+        a.step(3); b.step(3)
+        assert np.array_equal(a.positions(), b.positions())  # deterministic, same kernels
+        a.close(); b.close()
+
+
+def test_nonfinite_input_is_reported():
+    from paper_1906_07925_gb300 import SphError
+    p, pos, col = c1_state()
+    pos = pos.copy(); pos[5, 0] = np.nan
+    with pytest.raises(SphError) as e:
+        make_gpu(p, pos, col, "fp32")
+    assert e.value.status == 4
+
+
+def test_save_load_roundtrip():
+    p, pos, col = graded2d_state(5000)
+    p = p.copy(t0=3, t1=9)
+    a = make_gpu(p, pos, col, "fp32")
+    a.ramp_surface_tension(3, 9)
+    a.step(4)
+    blob = a.save()
+    b = make_gpu(p, pos, col, "fp32")
+    b.load(blob)
+    assert np.array_equal(a.positions(), b.positions())
+    assert np.array_equal(a.colors(), b.colors())
+    a.step(3); b.step(3)
+    assert np.array_equal(a.positions(), b.positions())
+    assert a.stats()["sigma"] == b.stats()["sigma"]
+    a.close(); b.close()
+
+
+def test_cell_list_sorted_and_stable():
+    p, pos, col = graded3d_state(20000)
+    r = make_gpu(p, pos, col, "fp32")
+    key, order = r.cell_list()
+    ks = key[order]
+    assert np.all(np.diff(ks.astype(np.int64)) >= 0)
+    same = np.diff(ks.astype(np.int64)) == 0
+    assert np.all(np.diff(order.astype(np.int64))[same] > 0)  # ties keep particle-id order
+    assert np.array_equal(np.sort(order), np.arange(len(pos)))
+    g = r.grid()
+    # each key names the cell of its level that holds the particle
+    lv = np.searchsorted(np.array(g["base"][1:]), key, side="right")
+    for l in range(g["n_levels"]):
+        m = lv == l
+        if not m.any():
+            continue
+        c = np.floor((pos[m] - np.array(g["lo"][:3])) / g["cell"][l]).astype(np.int64)
+        dims = np.array(g["dims"][l])
+        c = np.minimum(np.maximum(c, 0), dims - 1)
+        want = g["base"][l] + c[:, 0] + dims[0] * (c[:, 1] + dims[1] * c[:, 2])
+        assert np.mean(want == key[m]) > 0.999  # FP32 offsets may round across a cell face
+    r.close()
+
+
+def test_create_samples_inside_region_with_target_density():
+    from paper_1906_07925_gb300 import Relaxation
+    p = W.graded_hole_2d(200000, 16, rho_scale=0.0)
+    r = Relaxation(p, 200000, 16, precision="fp32", seed=7)
+    x = r.positions(); c = r.colors()
+    assert np.all(W.inside_mask(p, x))
+    assert len(np.unique(c)) == 16
+    rs = r.info()["rho_scale"]
+    assert rs == pytest.approx(oracle.total_mass(p.copy(rho_scale=1.0), 2048) ** -1 * 200000, rel=2e-3)
+    # counts in distance shells follow the target density
+    d = np.abs(np.linalg.norm(x - 0.5, axis=1) - 0.2)
+    near = np.mean(d < 0.05)
+    q = W.sample_density(p.copy(rho_scale=1.0), 100000, 3)[0]
+    want = np.mean(np.abs(np.linalg.norm(q - 0.5, axis=1) - 0.2) < 0.05)
+    assert near == pytest.approx(want, rel=0.03)
+    r.close()

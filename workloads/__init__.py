@@ -164,7 +164,10 @@ def rho_scale_for(p: Problem, n: int, res: int = 0) -> float:
 # ----------------------------------------------------------------------------
 
 def nearest_color(x: np.ndarray, gens: np.ndarray) -> np.ndarray:
-    """Index of the nearest generator (ties: lowest index), as uint8."""
+    """Index of the nearest generator, as uint8."""
+    if x.shape[0] > 200000:
+        from scipy.spatial import cKDTree
+        return cKDTree(gens).query(x)[1].astype(np.uint8)
     best = np.full(x.shape[0], np.inf)
     col = np.zeros(x.shape[0], dtype=np.int64)
     for k in range(gens.shape[0]):
