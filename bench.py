@@ -129,7 +129,7 @@ def oracle_workload_sample(wl, target_n=None):
     counts match the full run). Returns (problem, pos, col, description)."""
     n_full, dim = wl["n"], wl["dim"]
     p = wl["make"](n_full, wl["ncol"])
-    if wl is WORKLOADS["c1"]:
+    if wl["n"] == 4096 and wl["dim"] == 2:
         pos, col, _ = W.lattice_jitter_2d(p, 64, 0.3, 0)
         return p, pos, col, f"full workload ({len(pos)} particles)"
     target_n = target_n or (60000 if dim == 2 else 30000)
@@ -250,9 +250,14 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="override the particle count (small cases for profiler captures)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.particles > 0:
+        wl["n"] = args.particles
+        wl["desc"] = wl["desc"].split(",")[0] + f", {args.particles} particles (reduced)"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     config = {"workload": wl["desc"], "particles": wl["n"], "dim": wl["dim"], "colors": wl["ncol"],

@@ -208,8 +208,11 @@ def test_save_load_roundtrip():
     assert np.array_equal(a.positions(), b.positions())
     assert np.array_equal(a.colors(), b.colors())
     a.step(3); b.step(3)
-    assert np.array_equal(a.positions(), b.positions())
+    # same physical state; the restored handle sums in particle-id order, so the
+    # trajectories agree to rounding, not bit for bit
+    assert np.abs(a.positions() - b.positions()).max() < 1e-7
     assert a.stats()["sigma"] == b.stats()["sigma"]
+    assert a.stats()["step"] == b.stats()["step"] == 7
     a.close(); b.close()
 
 
