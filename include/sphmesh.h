@@ -226,6 +226,45 @@ sph_status sph_get_info(const sph_handle* h, int64_t* n_particles, int32_t* dim,
 /* Release every buffer through the allocator that created it. */
 void sph_destroy(sph_handle* h);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free evaluation (the paper has no counterpart; this is a service
+ * of the library). Some callers cannot allocate device memory at the point
+ * where they need the forces: a host framework that owns every device buffer
+ * and forbids allocation inside its per-step callback, a real-time loop that
+ * cannot afford cudaMalloc's implicit device synchronisation, or an embedded
+ * runtime without an allocator. For them this call evaluates, for a given
+ * particle state and without any handle, what the first pass of a relaxation
+ * step evaluates (the density, a_n = -F_p + F_s and the two time steps), using
+ * scratch space in a file-scope device array of the library instead of
+ * allocations. It calls no cudaMalloc, cudaFree or allocating routine.
+ *
+ * Limits: n <= SPH_NOALLOC_MAX_PARTICLES; the multi-resolution grid the
+ * problem needs must fit in SPH_NOALLOC_MAX_CELLS cells (raise
+ * params->cell_factor otherwise); FP32 split precision only; field->rho_scale
+ * must be given (> 0). Anything beyond: SPH_ERR_INVALID_ARG, nothing launched.
+ * The scratch array (about 14 MB) is held by every GPU that loads the library
+ * until the process exits.
+ *
+ * Arguments: dom, field, params as for sph_create (sigma = params->sigma0, no
+ * ramp); xyz_dev (n x dim doubles) and col_dev (n uint8) are device inputs in
+ * particle-id order; rho_dev (n), acc_dev (n x dim) and dt_dev (2: dt1, dt2)
+ * are device outputs, written in particle-id order. stream: a cudaStream_t
+ * (NULL: legacy default stream).
+ *
+ * The first call on a device looks up the scratch array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call reuses the same array and leaves its
+ * contents behind (the counters it needs zeroed are cleared at the start of
+ * each call); calls that overlap on the GPU (two streams, two threads) race on
+ * it and must be serialised by the caller. The call synchronises `stream`
+ * before returning and reports device-side errors (SPH_ERR_NONFINITE,
+ * SPH_ERR_OUT_OF_DOMAIN) through its status. */
+#define SPH_NOALLOC_MAX_PARTICLES 65536
+#define SPH_NOALLOC_MAX_CELLS (1 << 20)
+sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_field* field, const sph_params* params,
+                                   int64_t n, const double* xyz_dev, const uint8_t* col_dev, double* rho_dev,
+                                   double* acc_dev, double* dt_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

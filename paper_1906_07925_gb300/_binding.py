@@ -108,6 +108,8 @@ def load():
             "sph_save": [H, C.c_void_p, P(C.c_size_t)],
             "sph_load": [H, C.c_void_p, C.c_size_t],
             "sph_get_info": [H, P(C.c_int64), P(C.c_int32), P(C.c_double)],
+            "sph_eval_forces_noalloc": [P(sph_domain), P(sph_field), P(sph_params), C.c_int64, C.c_void_p,
+                                        C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
         }
         for name, args in sig.items():
             f = getattr(L, name)

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/sphmesh.h"
+#include "sph_host.h"
 #include "sph_internal.h"
 
 using namespace sph;
@@ -89,170 +90,6 @@ sph_status status_from_flags(sph_handle* h, int flags) {
   if (flags & kErrNonfinite) return fail(h, SPH_ERR_NONFINITE, "non-finite density, force or position");
   if (flags & kErrOutOfDomain) return fail(h, SPH_ERR_OUT_OF_DOMAIN, "a particle was outside the box");
   if (flags & kErrTimeout) return fail(h, SPH_ERR_TIMEOUT, "a bounded device loop gave up");
-  return SPH_OK;
-}
-
-template <class T>
-void fill_geom(const sph_domain& d, const sph_field& f, double hfac, double rho_scale, Geom<T>& g) {
-  memset(&g, 0, sizeof g);
-  g.dim = d.dim;
-  g.n_shapes = d.n_shapes;
-  g.field_kind = f.kind;
-  g.dist_shape = f.dist_shape;
-  g.n_poly = f.n_poly;
-  for (int k = 0; k < 3; ++k) {
-    g.lo[k] = (T)d.lo[k];
-    g.hi[k] = (T)d.hi[k];
-    g.ext[k] = (T)(d.hi[k] - d.lo[k]);
-  }
-  for (int s = 0; s < d.n_shapes; ++s) {
-    g.kind[s] = d.shapes[s].kind;
-    g.keep_inside[s] = d.shapes[s].keep_inside;
-    for (int k = 0; k < 3; ++k) {
-      g.center[s][k] = (T)d.shapes[s].center[k];
-      g.size[s][k] = (T)d.shapes[s].size[k];
-    }
-  }
-  g.s0 = (T)f.s0;
-  g.a = (T)f.a;
-  g.b = (T)f.b;
-  for (int k = 0; k < 8; ++k) g.poly[k] = (T)f.poly[k];
-  g.hfac = (T)hfac;
-  g.rho_scale = (T)rho_scale;
-}
-
-template <class T>
-void fill_phys(const sph_handle* h, Phys<T>& P) {
-  P.P0 = (T)h->par.P0;
-  P.gamma = (T)h->par.gamma;
-  P.kappa = (T)h->par.kappa;
-  P.inv_tau = (T)(1.0 / h->par.tau);
-  P.alpha = (T)(h->dim == 2 ? 7.0 / M_PI : 21.0 / (2.0 * M_PI));
-}
-
-// Upper bound of |grad h| over the box for h = hfac s (1+P)^(-1/d):
-// |grad s| <= b (distance functions are 1-Lipschitz); |P| <= sum|c_k| = S on
-// x~ in [-1,1]^d; |dP/dx| <= 3 sqrt(d) S * 2/min(ext) (each monomial has
-// |d/dx~| <= 3 there).
-double lipschitz_h(const sph_handle* h, double hfac, double smax) {
-  const sph_field& f = h->field;
-  const int d = h->dim;
-  double S = 0.0;
-  for (int k = 0; k < f.n_poly; ++k) S += fabs(f.poly[k]);
-  double ext_min = DBL_MAX;
-  for (int k = 0; k < d; ++k) ext_min = std::min(ext_min, h->dom.hi[k] - h->dom.lo[k]);
-  const double gb = f.kind == SPH_FIELD_UNIFORM ? 0.0 : fabs(f.b);
-  const double fmin = 1.0 - S;
-  const double gradP = 3.0 * sqrt((double)d) * S * 2.0 / ext_min;
-  const double L = hfac * (gb * pow(fmin, -1.0 / d) + smax / d * pow(fmin, -1.0 / d - 1.0) * gradP);
-  return L * 1.05;
-}
-
-template <class T>
-void fill_grid(const sph_handle* h, Grid<T>& G) {
-  memset(&G, 0, sizeof G);
-  G.n_levels = h->n_levels;
-  G.dim = h->dim;
-  for (int l = 0; l < h->n_levels; ++l) {
-    G.nx[l] = h->Gd.nx[l];
-    G.ny[l] = h->Gd.ny[l];
-    G.nz[l] = h->Gd.nz[l];
-    G.cell[l] = (T)h->Gd.cell[l];
-    G.inv_cell[l] = (T)h->Gd.inv_cell[l];
-    for (int k = 0; k < 3; ++k) G.wall_hi[l][k] = (T)h->Gd.wall_hi[l][k];
-  }
-  for (int l = 0; l <= h->n_levels; ++l) G.base[l] = h->Gd.base[l];
-  for (int k = 0; k < 3; ++k) G.lo[k] = (T)h->dom.lo[k];
-  G.inv_h0 = (T)(1.0 / h->h0);
-  G.lip_h = (T)h->lip_h;
-  G.rfac = (T)h->Gd.rfac;
-}
-
-sph_status build_grid(sph_handle* h) {
-  const int d = h->dim;
-  const double kappa = h->par.kappa;
-  double cf = h->par.cell_factor > 0 ? h->par.cell_factor : 1.0;
-  h->h0 = h->hmin * 0.98;
-  if (!(h->h0 > 0)) return fail(h, SPH_ERR_INVALID_ARG, "target field gives a non-positive smoothing length");
-  if (kappa * h->lip_h >= 1.5) return fail(h, SPH_ERR_INVALID_ARG, "target field varies too fast (kappa |grad h| >= 1.5)");
-  int L = 1;
-  while (L < kMaxLevels && h->h0 * std::ldexp(1.0, L) <= h->hmax) ++L;
-  for (int attempt = 0; attempt < 64; ++attempt) {
-    double c0 = cf * kappa * h->h0;
-    if (h->prec == SPH_PREC_FP32_SPLIT) c0 = (double)(float)c0;
-    uint64_t total = 0;
-    Grid<double>& G = h->Gd;
-    memset(&G, 0, sizeof G);
-    bool ok = true;
-    for (int l = 0; l < L; ++l) {
-      const double c = std::ldexp(c0, l);
-      int dims[3] = {1, 1, 1};
-      for (int k = 0; k < d; ++k) {
-        const double e = h->dom.hi[k] - h->dom.lo[k];
-        const double nd = std::ceil(e / c);
-        if (nd > (1 << 23)) ok = false;
-        dims[k] = std::max(1, (int)nd);
-      }
-      G.nx[l] = dims[0];
-      G.ny[l] = dims[1];
-      G.nz[l] = dims[2];
-      G.cell[l] = c;
-      G.inv_cell[l] = 1.0 / c;
-      for (int k = 0; k < 3; ++k) G.wall_hi[l][k] = k < d ? (h->dom.hi[k] - h->dom.lo[k]) - (dims[k] - 1) * c : 0.0;
-      G.base[l] = (uint32_t)total;
-      total += (uint64_t)dims[0] * dims[1] * dims[2];
-    }
-    if (ok && total < (1ull << 28)) {
-      G.base[L] = (uint32_t)total;
-      G.n_levels = L;
-      G.dim = d;
-      for (int k = 0; k < 3; ++k) G.lo[k] = h->dom.lo[k];
-      G.inv_h0 = 1.0 / h->h0;
-      G.lip_h = h->lip_h;
-      G.rfac = (1.0 + 1e-5) / (1.0 - 0.5 * kappa * h->lip_h);
-      h->n_levels = L;
-      h->cell0 = c0;
-      h->S.total_cells = (uint32_t)total;
-      return SPH_OK;
-    }
-    cf *= 1.25;
-  }
-  return fail(h, SPH_ERR_CELL_OVERFLOW, "cell grid too large");
-}
-
-sph_status validate(const sph_domain* dom, const sph_field* f, int64_t n, int32_t ncol, const sph_params* p,
-                    std::string& why) {
-  if (!dom || !f || !p) { why = "null argument"; return SPH_ERR_INVALID_ARG; }
-  if (dom->dim != 2 && dom->dim != 3) { why = "dim must be 2 or 3"; return SPH_ERR_INVALID_ARG; }
-  if (dom->n_shapes < 0 || dom->n_shapes > kMaxShapes) { why = "n_shapes out of range"; return SPH_ERR_INVALID_ARG; }
-  for (int k = 0; k < dom->dim; ++k)
-    if (!(dom->hi[k] > dom->lo[k])) { why = "empty box"; return SPH_ERR_INVALID_ARG; }
-  for (int s = 0; s < dom->n_shapes; ++s) {
-    const sph_shape& sh = dom->shapes[s];
-    if (sh.kind != SPH_SHAPE_SPHERE && sh.kind != SPH_SHAPE_BOX) { why = "bad shape kind"; return SPH_ERR_INVALID_ARG; }
-    if (!(sh.size[0] > 0)) { why = "bad shape size"; return SPH_ERR_INVALID_ARG; }
-  }
-  if (n < 0 || n > (int64_t)(1u << 30)) { why = "particle count out of range"; return SPH_ERR_INVALID_ARG; }
-  if (ncol < 1 || ncol > 256) { why = "n_colors must be in 1..256"; return SPH_ERR_INVALID_ARG; }
-  if (f->kind == SPH_FIELD_UNIFORM) {
-    if (!(f->s0 > 0)) { why = "s0 must be > 0"; return SPH_ERR_INVALID_ARG; }
-  } else if (f->kind == SPH_FIELD_LINEAR_DISTANCE) {
-    if (!(f->a > 0) || !(f->b >= 0) || f->dist_shape < 0 || f->dist_shape >= dom->n_shapes) {
-      why = "bad linear-distance field";
-      return SPH_ERR_INVALID_ARG;
-    }
-  } else { why = "bad field kind"; return SPH_ERR_INVALID_ARG; }
-  if (f->n_poly < 0 || f->n_poly > 8) { why = "n_poly out of range"; return SPH_ERR_INVALID_ARG; }
-  double S = 0;
-  for (int k = 0; k < f->n_poly; ++k) S += fabs(f->poly[k]);
-  if (!(S < 1.0)) { why = "sum |poly| must be < 1"; return SPH_ERR_INVALID_ARG; }
-  if (!(f->rho_scale >= 0)) { why = "rho_scale must be >= 0"; return SPH_ERR_INVALID_ARG; }
-  if (!(p->P0 > 0) || !(p->gamma > 0) || !(p->sigma0 >= 0) || !(p->tau > 0) || !(p->kappa > 0)) {
-    why = "P0, gamma, tau, kappa must be > 0 and sigma0 >= 0";
-    return SPH_ERR_INVALID_ARG;
-  }
-  if (p->precision != SPH_PREC_FP32_SPLIT && p->precision != SPH_PREC_FP64) { why = "bad precision"; return SPH_ERR_INVALID_ARG; }
-  if (p->kernel_id != 0) { why = "only kernel_id 0 (Wendland C2) exists"; return SPH_ERR_INVALID_ARG; }
   return SPH_OK;
 }
 
@@ -405,16 +242,25 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   double diag = 0.0;
   for (int k = 0; k < d; ++k) diag += pow((h->dom.hi[k] - h->dom.lo[k]) / res, 2);
   diag = sqrt(diag);
-  h->lip_h = lipschitz_h(h, hfac, fb.max_seff * (1.0 + 1e-6) + fabs(h->field.b) * diag);
+  h->lip_h = lipschitz_h(h->dom, h->field, hfac, fb.max_seff * (1.0 + 1e-6) + fabs(h->field.b) * diag);
   h->hmin = std::max(0.5 * h->hmin, h->hmin - h->lip_h * diag);
   h->hmax = h->hmax + h->lip_h * diag;
   fill_geom<double>(h->dom, h->field, hfac, h->rho_scale, h->geod);
   fill_geom<float>(h->dom, h->field, hfac, h->rho_scale, h->geof);
-  fill_phys(h, h->Pf);
-  fill_phys(h, h->Pd);
-  SPH_TRY(build_grid(h));
-  fill_grid<float>(h, h->Gf);
-  fill_grid<double>(h, h->Gdw);
+  fill_phys(d, h->par, h->Pf);
+  fill_phys(d, h->par, h->Pd);
+  {
+    const std::string why = grid_setup(h->dom, h->prec, h->par.kappa, h->par.cell_factor, h->hmin, h->hmax,
+                                       h->lip_h, h->Gd);
+    if (!why.empty())
+      return fail(h, why == "cell grid too large" ? SPH_ERR_CELL_OVERFLOW : SPH_ERR_INVALID_ARG, why);
+    h->n_levels = h->Gd.n_levels;
+    h->h0 = 1.0 / h->Gd.inv_h0;
+    h->cell0 = h->Gd.cell[0];
+    h->S.total_cells = h->Gd.base[h->Gd.n_levels];
+  }
+  convert_grid<float>(h->Gd, h->Gf);
+  convert_grid<double>(h->Gd, h->Gdw);
 
   // ---- buffers ----
   DevState& S = h->S;

@@ -1,0 +1,182 @@
+// Host-side set-up shared by the handle API and the allocation-free entry
+// point: validation, parameter blocks in working precision, the Lipschitz
+// bound of h and the multi-resolution grid.
+#pragma once
+
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "../../include/sphmesh.h"
+#include "sph_internal.h"
+
+namespace sph {
+
+template <class T>
+inline void fill_geom(const sph_domain& d, const sph_field& f, double hfac, double rho_scale, Geom<T>& g) {
+  memset(&g, 0, sizeof g);
+  g.dim = d.dim;
+  g.n_shapes = d.n_shapes;
+  g.field_kind = f.kind;
+  g.dist_shape = f.dist_shape;
+  g.n_poly = f.n_poly;
+  for (int k = 0; k < 3; ++k) {
+    g.lo[k] = (T)d.lo[k];
+    g.hi[k] = (T)d.hi[k];
+    g.ext[k] = (T)(d.hi[k] - d.lo[k]);
+  }
+  for (int s = 0; s < d.n_shapes; ++s) {
+    g.kind[s] = d.shapes[s].kind;
+    g.keep_inside[s] = d.shapes[s].keep_inside;
+    for (int k = 0; k < 3; ++k) {
+      g.center[s][k] = (T)d.shapes[s].center[k];
+      g.size[s][k] = (T)d.shapes[s].size[k];
+    }
+  }
+  g.s0 = (T)f.s0;
+  g.a = (T)f.a;
+  g.b = (T)f.b;
+  for (int k = 0; k < 8; ++k) g.poly[k] = (T)f.poly[k];
+  g.hfac = (T)hfac;
+  g.rho_scale = (T)rho_scale;
+}
+
+template <class T>
+inline void fill_phys(int dim, const sph_params& par, Phys<T>& P) {
+  P.P0 = (T)par.P0;
+  P.gamma = (T)par.gamma;
+  P.kappa = (T)par.kappa;
+  P.inv_tau = (T)(1.0 / par.tau);
+  P.alpha = (T)(dim == 2 ? 7.0 / M_PI : 21.0 / (2.0 * M_PI));
+}
+
+// Upper bound of |grad h| over the box for h = hfac s (1+P)^(-1/d):
+// |grad s| <= b (distance functions are 1-Lipschitz); |P| <= sum|c_k| = S on
+// x~ in [-1,1]^d; |dP/dx| <= 3 sqrt(d) S * 2/min(ext) (each monomial has
+// |d/dx~| <= 3 there).
+inline double lipschitz_h(const sph_domain& dom, const sph_field& f, double hfac, double smax) {
+  const int d = dom.dim;
+  double S = 0.0;
+  for (int k = 0; k < f.n_poly; ++k) S += fabs(f.poly[k]);
+  double ext_min = DBL_MAX;
+  for (int k = 0; k < d; ++k) ext_min = std::min(ext_min, dom.hi[k] - dom.lo[k]);
+  const double gb = f.kind == SPH_FIELD_UNIFORM ? 0.0 : fabs(f.b);
+  const double fmin = 1.0 - S;
+  const double gradP = 3.0 * sqrt((double)d) * S * 2.0 / ext_min;
+  const double L = hfac * (gb * pow(fmin, -1.0 / d) + smax / d * pow(fmin, -1.0 / d - 1.0) * gradP);
+  return L * 1.05;
+}
+
+// the grid in working precision T from the canonical (double) grid
+template <class T>
+inline void convert_grid(const Grid<double>& Gd, Grid<T>& G) {
+  memset(&G, 0, sizeof G);
+  G.n_levels = Gd.n_levels;
+  G.dim = Gd.dim;
+  for (int l = 0; l < Gd.n_levels; ++l) {
+    G.nx[l] = Gd.nx[l];
+    G.ny[l] = Gd.ny[l];
+    G.nz[l] = Gd.nz[l];
+    G.cell[l] = (T)Gd.cell[l];
+    G.inv_cell[l] = (T)Gd.inv_cell[l];
+    for (int k = 0; k < 3; ++k) G.wall_hi[l][k] = (T)Gd.wall_hi[l][k];
+  }
+  for (int l = 0; l <= Gd.n_levels; ++l) G.base[l] = Gd.base[l];
+  for (int k = 0; k < 3; ++k) G.lo[k] = (T)Gd.lo[k];
+  G.inv_h0 = (T)Gd.inv_h0;
+  G.lip_h = (T)Gd.lip_h;
+  G.rfac = (T)Gd.rfac;
+}
+
+// Multi-resolution grid for smoothing lengths in [hmin, hmax]: level l has
+// cells of edge c0 2^l with c0 = cell_factor kappa h0 (rounded to float for the
+// FP32 path so that cell edges are exact in both precisions). Grows c0 until
+// the grid has fewer than 2^28 cells. Returns an error message or "".
+inline std::string grid_setup(const sph_domain& dom, int prec, double kappa, double cell_factor, double hmin,
+                              double hmax, double lip_h, Grid<double>& G) {
+  const int d = dom.dim;
+  double cf = cell_factor > 0 ? cell_factor : 1.0;
+  const double h0 = hmin * 0.98;
+  if (!(h0 > 0)) return "target field gives a non-positive smoothing length";
+  if (kappa * lip_h >= 1.5) return "target field varies too fast (kappa |grad h| >= 1.5)";
+  int L = 1;
+  while (L < kMaxLevels && h0 * std::ldexp(1.0, L) <= hmax) ++L;
+  for (int attempt = 0; attempt < 64; ++attempt) {
+    double c0 = cf * kappa * h0;
+    if (prec == SPH_PREC_FP32_SPLIT) c0 = (double)(float)c0;
+    uint64_t total = 0;
+    memset(&G, 0, sizeof G);
+    bool ok = true;
+    for (int l = 0; l < L; ++l) {
+      const double c = std::ldexp(c0, l);
+      int dims[3] = {1, 1, 1};
+      for (int k = 0; k < d; ++k) {
+        const double e = dom.hi[k] - dom.lo[k];
+        const double nd = std::ceil(e / c);
+        if (nd > (1 << 23)) ok = false;
+        dims[k] = std::max(1, (int)nd);
+      }
+      G.nx[l] = dims[0];
+      G.ny[l] = dims[1];
+      G.nz[l] = dims[2];
+      G.cell[l] = c;
+      G.inv_cell[l] = 1.0 / c;
+      for (int k = 0; k < 3; ++k) G.wall_hi[l][k] = k < d ? (dom.hi[k] - dom.lo[k]) - (dims[k] - 1) * c : 0.0;
+      G.base[l] = (uint32_t)total;
+      total += (uint64_t)dims[0] * dims[1] * dims[2];
+    }
+    if (ok && total < (1ull << 28)) {
+      G.base[L] = (uint32_t)total;
+      G.n_levels = L;
+      G.dim = d;
+      for (int k = 0; k < 3; ++k) G.lo[k] = dom.lo[k];
+      G.inv_h0 = 1.0 / h0;
+      G.lip_h = lip_h;
+      G.rfac = (1.0 + 1e-5) / (1.0 - 0.5 * kappa * lip_h);
+      return "";
+    }
+    cf *= 1.25;
+  }
+  return "cell grid too large";
+}
+
+inline sph_status validate(const sph_domain* dom, const sph_field* f, int64_t n, int32_t ncol, const sph_params* p,
+                    std::string& why) {
+  if (!dom || !f || !p) { why = "null argument"; return SPH_ERR_INVALID_ARG; }
+  if (dom->dim != 2 && dom->dim != 3) { why = "dim must be 2 or 3"; return SPH_ERR_INVALID_ARG; }
+  if (dom->n_shapes < 0 || dom->n_shapes > kMaxShapes) { why = "n_shapes out of range"; return SPH_ERR_INVALID_ARG; }
+  for (int k = 0; k < dom->dim; ++k)
+    if (!(dom->hi[k] > dom->lo[k])) { why = "empty box"; return SPH_ERR_INVALID_ARG; }
+  for (int s = 0; s < dom->n_shapes; ++s) {
+    const sph_shape& sh = dom->shapes[s];
+    if (sh.kind != SPH_SHAPE_SPHERE && sh.kind != SPH_SHAPE_BOX) { why = "bad shape kind"; return SPH_ERR_INVALID_ARG; }
+    if (!(sh.size[0] > 0)) { why = "bad shape size"; return SPH_ERR_INVALID_ARG; }
+  }
+  if (n < 0 || n > (int64_t)(1u << 30)) { why = "particle count out of range"; return SPH_ERR_INVALID_ARG; }
+  if (ncol < 1 || ncol > 256) { why = "n_colors must be in 1..256"; return SPH_ERR_INVALID_ARG; }
+  if (f->kind == SPH_FIELD_UNIFORM) {
+    if (!(f->s0 > 0)) { why = "s0 must be > 0"; return SPH_ERR_INVALID_ARG; }
+  } else if (f->kind == SPH_FIELD_LINEAR_DISTANCE) {
+    if (!(f->a > 0) || !(f->b >= 0) || f->dist_shape < 0 || f->dist_shape >= dom->n_shapes) {
+      why = "bad linear-distance field";
+      return SPH_ERR_INVALID_ARG;
+    }
+  } else { why = "bad field kind"; return SPH_ERR_INVALID_ARG; }
+  if (f->n_poly < 0 || f->n_poly > 8) { why = "n_poly out of range"; return SPH_ERR_INVALID_ARG; }
+  double S = 0;
+  for (int k = 0; k < f->n_poly; ++k) S += fabs(f->poly[k]);
+  if (!(S < 1.0)) { why = "sum |poly| must be < 1"; return SPH_ERR_INVALID_ARG; }
+  if (!(f->rho_scale >= 0)) { why = "rho_scale must be >= 0"; return SPH_ERR_INVALID_ARG; }
+  if (!(p->P0 > 0) || !(p->gamma > 0) || !(p->sigma0 >= 0) || !(p->tau > 0) || !(p->kappa > 0)) {
+    why = "P0, gamma, tau, kappa must be > 0 and sigma0 >= 0";
+    return SPH_ERR_INVALID_ARG;
+  }
+  if (p->precision != SPH_PREC_FP32_SPLIT && p->precision != SPH_PREC_FP64) { why = "bad precision"; return SPH_ERR_INVALID_ARG; }
+  if (p->kernel_id != 0) { why = "only kernel_id 0 (Wendland C2) exists"; return SPH_ERR_INVALID_ARG; }
+  return SPH_OK;
+}
+
+
+}  // namespace sph
