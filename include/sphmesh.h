@@ -101,7 +101,10 @@ typedef struct {
   int32_t block_size;  /* threads per block of the neighbour kernels; 0 -> auto */
   int32_t use_graph;   /* 1: sph_step replays a captured CUDA graph of one step */
   int32_t record_fields; /* 1: keep rho, a_n and a~ of the last step for sph_get_field */
-  int32_t reserved;
+  int32_t list_capacity; /* neighbour-list entries per particle; 0 -> auto */
+  double skin;           /* neighbour-list skin as a fraction of the support kappa h;
+                            0 -> 0.3; the list is rebuilt when a particle has moved
+                            half its skin (results do not depend on it) */
 } sph_params;
 
 typedef struct {
@@ -242,8 +245,9 @@ void sph_destroy(sph_handle* h);
  * problem needs must fit in SPH_NOALLOC_MAX_CELLS cells (raise
  * params->cell_factor otherwise); FP32 split precision only; field->rho_scale
  * must be given (> 0). Anything beyond: SPH_ERR_INVALID_ARG, nothing launched.
- * The scratch array (about 14 MB) is held by every GPU that loads the library
- * until the process exits.
+ * The scratch array (about 22 MB) is held by every GPU that loads the library
+ * until the process exits. A particle with more than 95 neighbours inside its
+ * support makes the call fail with SPH_ERR_CELL_OVERFLOW.
  *
  * Arguments: dom, field, params as for sph_create (sigma = params->sigma0, no
  * ramp); xyz_dev (n x dim doubles) and col_dev (n uint8) are device inputs in
@@ -259,8 +263,8 @@ void sph_destroy(sph_handle* h);
  * it and must be serialised by the caller. The call synchronises `stream`
  * before returning and reports device-side errors (SPH_ERR_NONFINITE,
  * SPH_ERR_OUT_OF_DOMAIN) through its status. */
-#define SPH_NOALLOC_MAX_PARTICLES 65536
-#define SPH_NOALLOC_MAX_CELLS (1 << 20)
+#define SPH_NOALLOC_MAX_PARTICLES 32768
+#define SPH_NOALLOC_MAX_CELLS (1 << 19)
 sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_field* field, const sph_params* params,
                                    int64_t n, const double* xyz_dev, const uint8_t* col_dev, double* rho_dev,
                                    double* acc_dev, double* dt_dev, void* stream);

@@ -35,7 +35,8 @@ def load_library():
     return B.load()
 
 
-def problem_structs(p, precision="fp32", seed=0, cell_factor=0.0, use_graph=True, record_fields=False):
+def problem_structs(p, precision="fp32", seed=0, cell_factor=0.0, use_graph=True, record_fields=False, skin=0.0,
+                    list_capacity=0):
     """Marshal a problem description (attributes: dim, lo, hi, shapes, field_kind,
     s0, a, b, dist_shape, poly, rho_scale, P0, gamma, sigma0, tau, kappa) into
     the C structs."""
@@ -67,6 +68,8 @@ def problem_structs(p, precision="fp32", seed=0, cell_factor=0.0, use_graph=True
     q.cell_factor = float(cell_factor)
     q.use_graph = 1 if use_graph else 0
     q.record_fields = 1 if record_fields else 0
+    q.skin = float(skin)
+    q.list_capacity = int(list_capacity)
     return d, f, q
 
 
@@ -79,7 +82,7 @@ class Relaxation:
     """
 
     def __init__(self, problem, n_particles, n_colors=None, precision="fp32", seed=0, cell_factor=0.0,
-                 use_graph=True, record_fields=False, device=None):
+                 use_graph=True, record_fields=False, device=None, skin=0.0, list_capacity=0):
         import torch
         self._torch = torch
         self.lib = B.load()
@@ -90,7 +93,8 @@ class Relaxation:
         self.dim = int(problem.dim)
         self.n = int(n_particles)
         ncol = int(n_colors if n_colors is not None else getattr(problem, "n_colors", 1))
-        dom, fld, par = problem_structs(problem, precision, seed, cell_factor, use_graph, record_fields)
+        dom, fld, par = problem_structs(problem, precision, seed, cell_factor, use_graph, record_fields, skin,
+                                        list_capacity)
         dev, stream = self.device, self.stream
 
         def _alloc(nbytes, ctx):

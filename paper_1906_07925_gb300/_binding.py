@@ -38,7 +38,8 @@ class sph_params(C.Structure):
     _fields_ = [("P0", C.c_double), ("gamma", C.c_double), ("sigma0", C.c_double), ("tau", C.c_double),
                 ("kappa", C.c_double), ("precision", C.c_int32), ("kernel_id", C.c_int32),
                 ("seed", C.c_uint64), ("cell_factor", C.c_double), ("block_size", C.c_int32),
-                ("use_graph", C.c_int32), ("record_fields", C.c_int32), ("reserved", C.c_int32)]
+                ("use_graph", C.c_int32), ("record_fields", C.c_int32), ("list_capacity", C.c_int32),
+                ("skin", C.c_double)]
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)

@@ -1,12 +1,14 @@
-// Host side of the C ABI (include/sphmesh.h): handle, validation, grid set-up,
-// buffer ownership through the caller's allocator, step orchestration (direct
-// launches or a replayed CUDA graph of one step), accessors, checkpoints.
+// Host side of the C ABI (include/sphmesh.h): handle, validation, grid and
+// frame set-up, buffer ownership through the caller's allocator, step
+// orchestration (direct launches or a replayed CUDA graph of one step),
+// accessors, checkpoints.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/sphmesh.h"
@@ -22,14 +24,14 @@ struct sph_handle {
   sph_field field{};
   sph_params par{};
   sph_alloc alloc{};
-  bool default_alloc = false;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
-  double rho_scale = 1.0, h0 = 0.0, lip_h = 0.0, cell0 = 0.0, hmin = 0.0, hmax = 0.0;
-  int n_levels = 1;
+  double rho_scale = 1.0, lip_h = 0.0, hmin = 0.0, hmax = 0.0;
+  HostGrid hg{};
   Grid<float> Gf{};
-  Grid<double> Gd{};     // canonical grid (cell edges exactly those of the working precision)
-  Grid<double> Gdw{};    // grid in the working precision when it is double
+  Grid<double> Gdw{};
+  Frame<float> Ff{};
+  Frame<double> Fd{};
   Geom<float> geof{};
   Geom<double> geod{};
   Phys<float> Pf{};
@@ -63,10 +65,16 @@ sph_status cuda_fail(sph_handle* h, cudaError_t e, const char* where) {
   return fail(h, SPH_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
 
-#define SPH_CUDA(h, expr)                                   \
-  do {                                                      \
-    cudaError_t e_ = (expr);                                \
+#define SPH_CUDA(h, expr)                                    \
+  do {                                                       \
+    cudaError_t e_ = (expr);                                 \
     if (e_ != cudaSuccess) return cuda_fail((h), e_, #expr); \
+  } while (0)
+
+#define SPH_TRY(expr)            \
+  do {                           \
+    sph_status s_ = (expr);      \
+    if (s_ != SPH_OK) return s_; \
   } while (0)
 
 template <class P>
@@ -80,46 +88,106 @@ sph_status grab(sph_handle* h, P*& out, size_t count) {
   return SPH_OK;
 }
 
-#define SPH_TRY(expr)                 \
-  do {                                \
-    sph_status s_ = (expr);           \
-    if (s_ != SPH_OK) return s_;      \
-  } while (0)
-
 sph_status status_from_flags(sph_handle* h, int flags) {
   if (flags & kErrNonfinite) return fail(h, SPH_ERR_NONFINITE, "non-finite density, force or position");
   if (flags & kErrOutOfDomain) return fail(h, SPH_ERR_OUT_OF_DOMAIN, "a particle was outside the box");
+  if (flags & kErrListOverflow)
+    return fail(h, SPH_ERR_CELL_OVERFLOW, "a neighbour list exceeded its capacity (raise params.list_capacity)");
   if (flags & kErrTimeout) return fail(h, SPH_ERR_TIMEOUT, "a bounded device loop gave up");
   return SPH_OK;
 }
 
+// position frames and kernel grids (make_frames in sph_host.h)
+void setup_frames(sph_handle* h) {
+  Frames fr;
+  make_frames(h->dom, h->par.kappa, h->par.skin > 0 ? h->par.skin : 0.3, h->hg, fr);
+  h->Ff = fr.f;
+  h->Fd = fr.d;
+  h->Gf = fr.gf;
+  h->Gdw = fr.gd;
+}
+
+// expected list length for a support kappa h and a skin: the ball of radius
+// kappa h (1 + skin) holds about V_d (kappa tau (1 + skin))^d particles
+int auto_capacity(const sph_handle* h) {
+  const double skin = h->par.skin > 0 ? h->par.skin : 0.3;
+  const double r = h->par.kappa * h->par.tau * (1.0 + skin) * 1.05;
+  const double e = h->dim == 2 ? M_PI * r * r : 4.0 / 3.0 * M_PI * r * r * r;
+  int cap = (int)std::ceil(2.0 * e + 16.0);
+  return (cap + 7) & ~7;
+}
+
 // one relaxation step on the handle's stream
-sph_status launch_step(sph_handle* h, int record) {
+sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEvent_t* ev = nullptr) {
   DevState& S = h->S;
   PassFlags f;
   f.general_eos = h->par.gamma != 2.0;
   f.record = record;
-  cudaError_t e = build_cells(S, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "build_cells");
   const bool f64 = h->prec == SPH_PREC_FP64;
-  if (h->dim == 2) {
-    if (f64) {
-      e = launch_pass_a<2, double>(S, h->Gdw, h->Pd, f, h->stream);
-      if (e == cudaSuccess) e = launch_pass_b<2, double>(S, h->Gdw, h->Pd, h->geod, f, h->stream);
-    } else {
-      e = launch_pass_a<2, float>(S, h->Gf, h->Pf, f, h->stream);
-      if (e == cudaSuccess) e = launch_pass_b<2, float>(S, h->Gf, h->Pf, h->geof, f, h->stream);
-    }
-  } else {
-    if (f64) {
-      e = launch_pass_a<3, double>(S, h->Gdw, h->Pd, f, h->stream);
-      if (e == cudaSuccess) e = launch_pass_b<3, double>(S, h->Gdw, h->Pd, h->geod, f, h->stream);
-    } else {
-      e = launch_pass_a<3, float>(S, h->Gf, h->Pf, f, h->stream);
-      if (e == cudaSuccess) e = launch_pass_b<3, float>(S, h->Gf, h->Pf, h->geof, f, h->stream);
-    }
+  cudaError_t e = cudaSuccess;
+  if (ev) e = cudaEventRecord(ev[0], h->stream);
+  if (e == cudaSuccess) e = launch_gate(S, force_rebuild, h->stream);
+  if (e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+              : launch_rebuild<2, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
+    else
+      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+              : launch_rebuild<3, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
   }
+  if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
+  if (e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_pass_a<2, double>(S, h->Fd, h->Pd, f, h->stream)
+              : launch_pass_a<2, float>(S, h->Ff, h->Pf, f, h->stream);
+    else
+      e = f64 ? launch_pass_a<3, double>(S, h->Fd, h->Pd, f, h->stream)
+              : launch_pass_a<3, float>(S, h->Ff, h->Pf, f, h->stream);
+  }
+  if (ev && e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
+  if (e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_pass_b<2, double>(S, h->Fd, h->Pd, h->geod, f, h->stream)
+              : launch_pass_b<2, float>(S, h->Ff, h->Pf, h->geof, f, h->stream);
+    else
+      e = f64 ? launch_pass_b<3, double>(S, h->Fd, h->Pd, h->geod, f, h->stream)
+              : launch_pass_b<3, float>(S, h->Ff, h->Pf, h->geof, f, h->stream);
+  }
+  if (ev && e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "step kernels");
+  return SPH_OK;
+}
+
+// a list rebuild plus pass A without advancing (diagnostics); the next step
+// rebuilds again so that its views are fresh
+sph_status launch_evaluate(sph_handle* h, int nbr_debug) {
+  DevState S = h->S;
+  S.scal = h->S.scal + 1;  // keep the last step's statistics
+  PassFlags f;
+  f.general_eos = h->par.gamma != 2.0;
+  f.nbr_debug = nbr_debug;
+  f.advance = 0;
+  const bool f64 = h->prec == SPH_PREC_FP64;
+  cudaError_t e = launch_gate(S, 1, h->stream);
+  if (e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+              : launch_rebuild<2, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
+    else
+      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+              : launch_rebuild<3, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
+  }
+  if (e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_pass_a<2, double>(S, h->Fd, h->Pd, f, h->stream)
+              : launch_pass_a<2, float>(S, h->Ff, h->Pf, f, h->stream);
+    else
+      e = f64 ? launch_pass_a<3, double>(S, h->Fd, h->Pd, f, h->stream)
+              : launch_pass_a<3, float>(S, h->Ff, h->Pf, f, h->stream);
+  }
+  if (e == cudaSuccess) e = launch_request_rebuild(S, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "evaluate");
+  h->recorded = false;
   return SPH_OK;
 }
 
@@ -145,9 +213,31 @@ sph_status ensure_graph(sph_handle* h, int record) {
   return SPH_OK;
 }
 
-sph_status write_ctl(sph_handle* h) {
-  StepCtl c{h->steps, h->t0, h->t1, h->par.sigma0};
+// whole control block (set-up / set_state: the next step rebuilds the list)
+sph_status write_ctl_all(sph_handle* h) {
+  StepCtl c{};
+  c.step = h->steps;
+  c.t0 = h->t0;
+  c.t1 = h->t1;
+  c.sigma0 = h->par.sigma0;
+  c.buf = 0;
+  c.vp = 0;
+  c.rebuild = 0;
+  c.need_rebuild = 1;
+  c.rebuilds = 0;
   SPH_CUDA(h, cudaMemcpyAsync(h->S.ctl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+  return SPH_OK;
+}
+
+// only the schedule and the counter (the list bookkeeping stays on the device)
+sph_status write_ctl_sched(sph_handle* h) {
+  const double sched[2] = {h->t0, h->t1};
+  const long long step = h->steps;
+  SPH_CUDA(h, cudaMemcpyAsync((char*)h->S.ctl + offsetof(StepCtl, step), &step, sizeof step,
+                              cudaMemcpyHostToDevice, h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync((char*)h->S.ctl + offsetof(StepCtl, t0), sched, sizeof sched,
+                              cudaMemcpyHostToDevice, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   return SPH_OK;
 }
 
@@ -160,16 +250,17 @@ sph_status read_flags(sph_handle* h, int* flags) {
 sph_status do_set_state(sph_handle* h, const double* xyz_dev, const uint8_t* col_dev) {
   DevState& S = h->S;
   cudaError_t e;
+  const bool f64 = h->prec == SPH_PREC_FP64;
   if (h->dim == 2)
-    e = h->prec == SPH_PREC_FP64 ? launch_set_state<2, double>(S, h->Gdw, h->Gd, h->geod, xyz_dev, col_dev, h->stream)
-                                 : launch_set_state<2, float>(S, h->Gf, h->Gd, h->geof, xyz_dev, col_dev, h->stream);
+    e = f64 ? launch_set_state<2, double>(S, h->Fd, xyz_dev, col_dev, h->stream)
+            : launch_set_state<2, float>(S, h->Ff, xyz_dev, col_dev, h->stream);
   else
-    e = h->prec == SPH_PREC_FP64 ? launch_set_state<3, double>(S, h->Gdw, h->Gd, h->geod, xyz_dev, col_dev, h->stream)
-                                 : launch_set_state<3, float>(S, h->Gf, h->Gd, h->geof, xyz_dev, col_dev, h->stream);
+    e = f64 ? launch_set_state<3, double>(S, h->Fd, xyz_dev, col_dev, h->stream)
+            : launch_set_state<3, float>(S, h->Ff, xyz_dev, col_dev, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
   h->steps = 0;
   h->recorded = false;
-  return write_ctl(h);
+  return write_ctl_all(h);
 }
 
 // temporary device buffer through the handle's allocator, released at scope end
@@ -213,7 +304,6 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
     h->alloc.alloc = default_alloc_fn;
     h->alloc.free = default_free_fn;
     h->alloc.ctx = (void*)h->stream;
-    h->default_alloc = true;
   }
   const int d = h->dim;
   const int nn = (int)n_particles;
@@ -236,53 +326,49 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   const double mass1 = fb.sum_w * cellvol;  // integral of s^-d (1+P)
   h->rho_scale = field->rho_scale > 0 ? field->rho_scale : (n_particles > 0 ? (double)n_particles / mass1 : 1.0);
   const double hfac = h->par.tau * pow(h->rho_scale, -1.0 / d);
-  h->hmin = hfac * fb.min_seff;
-  h->hmax = hfac * fb.max_seff;
-  // field bounds are sampled; widen them by the Lipschitz bound over half a sample cell
+  // sampled bounds of h, widened by the Lipschitz bound over half a sample cell
   double diag = 0.0;
   for (int k = 0; k < d; ++k) diag += pow((h->dom.hi[k] - h->dom.lo[k]) / res, 2);
   diag = sqrt(diag);
   h->lip_h = lipschitz_h(h->dom, h->field, hfac, fb.max_seff * (1.0 + 1e-6) + fabs(h->field.b) * diag);
-  h->hmin = std::max(0.5 * h->hmin, h->hmin - h->lip_h * diag);
-  h->hmax = h->hmax + h->lip_h * diag;
+  h->hmin = std::max(0.5 * hfac * fb.min_seff, hfac * fb.min_seff - h->lip_h * diag);
+  h->hmax = hfac * fb.max_seff + h->lip_h * diag;
   fill_geom<double>(h->dom, h->field, hfac, h->rho_scale, h->geod);
   fill_geom<float>(h->dom, h->field, hfac, h->rho_scale, h->geof);
   fill_phys(d, h->par, h->Pf);
   fill_phys(d, h->par, h->Pd);
   {
-    const std::string why = grid_setup(h->dom, h->prec, h->par.kappa, h->par.cell_factor, h->hmin, h->hmax,
-                                       h->lip_h, h->Gd);
+    const std::string why = grid_setup(h->dom, h->par.kappa, h->par.cell_factor, h->hmin, h->hmax, h->lip_h, h->hg);
     if (!why.empty())
       return fail(h, why == "cell grid too large" ? SPH_ERR_CELL_OVERFLOW : SPH_ERR_INVALID_ARG, why);
-    h->n_levels = h->Gd.n_levels;
-    h->h0 = 1.0 / h->Gd.inv_h0;
-    h->cell0 = h->Gd.cell[0];
-    h->S.total_cells = h->Gd.base[h->Gd.n_levels];
+    h->S.total_cells = h->hg.base[h->hg.n_levels];
   }
-  convert_grid<float>(h->Gd, h->Gf);
-  convert_grid<double>(h->Gd, h->Gdw);
+  setup_frames(h);
 
   // ---- buffers ----
   DevState& S = h->S;
   S.n = nn;
   S.dim = d;
   S.fp64 = h->prec == SPH_PREC_FP64;
+  S.cap = h->par.list_capacity > 0 ? h->par.list_capacity : auto_capacity(h);
   const size_t v4 = S.fp64 ? 32 : 16, t1 = S.fp64 ? 8 : 4;
   const size_t N = (size_t)std::max<int64_t>(n_particles, 1);
   uint8_t* tmpb;
-  SPH_TRY(grab(h, tmpb, N * v4)); S.pos4_u = tmpb;
-  SPH_TRY(grab(h, tmpb, N * v4)); S.pos4_s = tmpb;
+  for (int b = 0; b < 2; ++b) {
+    SPH_TRY(grab(h, tmpb, N * 32)); S.X[b] = tmpb;
+    SPH_TRY(grab(h, S.meta[b], N));
+    SPH_TRY(grab(h, S.pid[b], N));
+    SPH_TRY(grab(h, tmpb, N * v4)); S.view[b] = tmpb;
+  }
+  SPH_TRY(grab(h, tmpb, N * v4)); S.vbuild = tmpb;
   SPH_TRY(grab(h, tmpb, N * v4)); S.acc4 = tmpb;
   SPH_TRY(grab(h, tmpb, N * v4)); S.visc = tmpb;
   SPH_TRY(grab(h, tmpb, N * t1)); S.rho = tmpb;
   SPH_TRY(grab(h, tmpb, N * t1)); S.pc = tmpb;
-  SPH_TRY(grab(h, S.meta_u, N));
-  SPH_TRY(grab(h, S.meta_s, N));
-  SPH_TRY(grab(h, S.key_u, N));
-  SPH_TRY(grab(h, S.key_s, N));
-  SPH_TRY(grab(h, S.pid_u, N));
-  SPH_TRY(grab(h, S.pid_s, N));
+  SPH_TRY(grab(h, S.key, N));
   SPH_TRY(grab(h, S.tmp, N));
+  SPH_TRY(grab(h, S.list, N * (size_t)S.cap));
+  SPH_TRY(grab(h, S.lcount, N));
   SPH_TRY(grab(h, S.cnt, (size_t)S.total_cells));
   SPH_TRY(grab(h, S.cstart, (size_t)S.total_cells + 1));
   SPH_TRY(grab(h, S.scan_part, (size_t)S.total_cells / 4096 + 2));
@@ -295,6 +381,7 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   SPH_CUDA(h, cudaMemsetAsync(S.tickets, 0, sizeof(unsigned) * 4, h->stream));
   SPH_CUDA(h, cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
   SPH_CUDA(h, cudaMemsetAsync(S.scal, 0, sizeof(Scalars) * 2, h->stream));
+  SPH_CUDA(h, cudaMemsetAsync(S.lcount, 0, sizeof(uint32_t) * N, h->stream));
 
   // ---- initial state ----
   {
@@ -320,6 +407,14 @@ sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_p
   *out = nullptr;
   std::string why;
   sph_status vs = validate(dom, field, n_particles, n_colors, params, why);
+  if (vs == SPH_OK && n_particles > (int64_t)(1 << 24)) {
+    why = "at most 2^24 particles per instance";
+    vs = SPH_ERR_INVALID_ARG;
+  }
+  if (vs == SPH_OK && (params->skin < 0 || params->list_capacity < 0)) {
+    why = "skin and list_capacity must be >= 0";
+    vs = SPH_ERR_INVALID_ARG;
+  }
   if (vs != SPH_OK) {
     fprintf(stderr, "sph_create: %s\n", why.c_str());
     return vs;
@@ -358,7 +453,7 @@ sph_status sph_step(sph_handle* h, int32_t n_steps) {
   if (!h || n_steps < 0) return fail(h, SPH_ERR_INVALID_ARG, "bad step count");
   if (h->n == 0 || n_steps == 0) {
     h->steps += n_steps;
-    return write_ctl(h);
+    return write_ctl_sched(h);
   }
   const int record = h->par.record_fields ? 1 : 0;
   if (h->par.use_graph) {
@@ -379,33 +474,11 @@ sph_status sph_step_profiled(sph_handle* h, int32_t n_steps, float* ms_out) {
   const int record = h->par.record_fields ? 1 : 0;
   cudaEvent_t ev[4];
   for (auto& e : ev) SPH_CUDA(h, cudaEventCreate(&e));
-  DevState& S = h->S;
-  PassFlags f;
-  f.general_eos = h->par.gamma != 2.0;
-  f.record = record;
-  const bool f64 = h->prec == SPH_PREC_FP64;
   sph_status st = SPH_OK;
   for (int s = 0; s < n_steps && st == SPH_OK; ++s) {
-    cudaError_t e = cudaEventRecord(ev[0], h->stream);
-    if (e == cudaSuccess) e = build_cells(S, h->stream);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
-    if (e == cudaSuccess) {
-      if (h->dim == 2)
-        e = f64 ? launch_pass_a<2, double>(S, h->Gdw, h->Pd, f, h->stream) : launch_pass_a<2, float>(S, h->Gf, h->Pf, f, h->stream);
-      else
-        e = f64 ? launch_pass_a<3, double>(S, h->Gdw, h->Pd, f, h->stream) : launch_pass_a<3, float>(S, h->Gf, h->Pf, f, h->stream);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
-    if (e == cudaSuccess) {
-      if (h->dim == 2)
-        e = f64 ? launch_pass_b<2, double>(S, h->Gdw, h->Pd, h->geod, f, h->stream)
-                : launch_pass_b<2, float>(S, h->Gf, h->Pf, h->geof, f, h->stream);
-      else
-        e = f64 ? launch_pass_b<3, double>(S, h->Gdw, h->Pd, h->geod, f, h->stream)
-                : launch_pass_b<3, float>(S, h->Gf, h->Pf, h->geof, f, h->stream);
-    }
-    if (e == cudaSuccess) e = cudaEventRecord(ev[3], h->stream);
-    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    st = launch_step(h, record, 0, ev);
+    if (st != SPH_OK) break;
+    cudaError_t e = cudaEventSynchronize(ev[3]);
     float t;
     for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
       e = cudaEventElapsedTime(&t, ev[k], ev[k + 1]);
@@ -422,9 +495,10 @@ sph_status sph_step_profiled(sph_handle* h, int32_t n_steps, float* ms_out) {
 sph_status sph_ramp_surface_tension(sph_handle* h, int64_t t0, int64_t t1) {
   if (!h) return SPH_ERR_INVALID_ARG;
   if (t0 >= 0 && t1 <= t0) return fail(h, SPH_ERR_INVALID_ARG, "ramp needs t1 > t0");
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   h->t0 = t0 < 0 ? -1.0 : (double)t0;
   h->t1 = t0 < 0 ? -1.0 : (double)t1;
-  return write_ctl(h);
+  return write_ctl_sched(h);
 }
 
 sph_status sph_get_positions(sph_handle* h, double* out, int32_t on_device) {
@@ -434,12 +508,13 @@ sph_status sph_get_positions(sph_handle* h, double* out, int32_t on_device) {
   Temp t(h, on_device ? 0 : sizeof(double) * N * d);
   if (!on_device) dst = (double*)t.p;
   cudaError_t e;
+  const bool f64 = h->prec == SPH_PREC_FP64;
   if (h->dim == 2)
-    e = h->prec == SPH_PREC_FP64 ? launch_get_positions<2, double>(h->S, h->Gd, dst, h->stream)
-                                 : launch_get_positions<2, float>(h->S, h->Gd, dst, h->stream);
+    e = f64 ? launch_get_positions<2, double>(h->S, h->Fd, dst, h->stream)
+            : launch_get_positions<2, float>(h->S, h->Ff, dst, h->stream);
   else
-    e = h->prec == SPH_PREC_FP64 ? launch_get_positions<3, double>(h->S, h->Gd, dst, h->stream)
-                                 : launch_get_positions<3, float>(h->S, h->Gd, dst, h->stream);
+    e = f64 ? launch_get_positions<3, double>(h->S, h->Fd, dst, h->stream)
+            : launch_get_positions<3, float>(h->S, h->Ff, dst, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_positions");
   if (!on_device) SPH_CUDA(h, cudaMemcpyAsync(out, dst, sizeof(double) * N * d, cudaMemcpyDeviceToHost, h->stream));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -482,7 +557,7 @@ sph_status sph_get_stats(sph_handle* h, sph_stats* out) {
   out->wall_moved = sc.wall_moved;
   out->rho_scale = h->rho_scale;
   out->error_flags = flags;
-  out->n_levels = h->n_levels;
+  out->n_levels = h->hg.n_levels;
   return status_from_flags(h, flags);
 }
 
@@ -493,12 +568,13 @@ sph_status sph_get_field(sph_handle* h, int32_t which, double* out, int32_t on_d
   Temp t(h, on_device ? 0 : sizeof(double) * cnt);
   double* dst = on_device ? out : (double*)t.p;
   cudaError_t e;
+  const bool f64 = h->prec == SPH_PREC_FP64;
   if (h->dim == 2)
-    e = h->prec == SPH_PREC_FP64 ? launch_get_fields<2, double>(h->S, which, dst, h->stream)
-                                 : launch_get_fields<2, float>(h->S, which, dst, h->stream);
+    e = f64 ? launch_get_fields<2, double>(h->S, which, dst, h->stream)
+            : launch_get_fields<2, float>(h->S, which, dst, h->stream);
   else
-    e = h->prec == SPH_PREC_FP64 ? launch_get_fields<3, double>(h->S, which, dst, h->stream)
-                                 : launch_get_fields<3, float>(h->S, which, dst, h->stream);
+    e = f64 ? launch_get_fields<3, double>(h->S, which, dst, h->stream)
+            : launch_get_fields<3, float>(h->S, which, dst, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "get_field");
   if (!on_device) SPH_CUDA(h, cudaMemcpyAsync(out, dst, sizeof(double) * cnt, cudaMemcpyDeviceToHost, h->stream));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
@@ -514,27 +590,13 @@ sph_status sph_neighbor_sets(sph_handle* h, int32_t* dens_count, int32_t* force_
     SPH_TRY(grab(h, h->S.dbg_sum, 2 * N));
   }
   if (h->n == 0) return SPH_OK;
-  DevState S = h->S;
-  S.scal = h->S.scal + 1;  // keep the last step's statistics
-  PassFlags f;
-  f.general_eos = 0;
-  f.nbr_debug = 1;
-  f.advance = 0;
-  cudaError_t e = build_cells(S, h->stream);
-  if (e == cudaSuccess) {
-    if (h->dim == 2)
-      e = h->prec == SPH_PREC_FP64 ? launch_pass_a<2, double>(S, h->Gdw, h->Pd, f, h->stream)
-                                   : launch_pass_a<2, float>(S, h->Gf, h->Pf, f, h->stream);
-    else
-      e = h->prec == SPH_PREC_FP64 ? launch_pass_a<3, double>(S, h->Gdw, h->Pd, f, h->stream)
-                                   : launch_pass_a<3, float>(S, h->Gf, h->Pf, f, h->stream);
-  }
-  if (e != cudaSuccess) return cuda_fail(h, e, "neighbor_sets");
-  h->recorded = false;
+  SPH_TRY(launch_evaluate(h, 1));
   std::vector<int32_t> cnt(2 * N);
   std::vector<long long> sum(2 * N);
-  SPH_CUDA(h, cudaMemcpyAsync(cnt.data(), S.dbg_count, sizeof(int32_t) * 2 * N, cudaMemcpyDeviceToHost, h->stream));
-  SPH_CUDA(h, cudaMemcpyAsync(sum.data(), S.dbg_sum, sizeof(long long) * 2 * N, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync(cnt.data(), h->S.dbg_count, sizeof(int32_t) * 2 * N, cudaMemcpyDeviceToHost,
+                              h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync(sum.data(), h->S.dbg_sum, sizeof(long long) * 2 * N, cudaMemcpyDeviceToHost,
+                              h->stream));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   for (size_t i = 0; i < (size_t)h->n; ++i) {
     if (dens_count) dens_count[i] = cnt[2 * i];
@@ -551,13 +613,15 @@ sph_status sph_get_cell_list(sph_handle* h, uint32_t* key_by_id, uint32_t* sorte
   if (!h) return SPH_ERR_INVALID_ARG;
   if (h->n == 0) return SPH_OK;
   const size_t N = (size_t)h->n;
-  cudaError_t e = build_cells(h->S, h->stream);
-  if (e != cudaSuccess) return cuda_fail(h, e, "build_cells");
-  h->recorded = false;
+  SPH_TRY(launch_evaluate(h, 0));
+  // after the rebuild: keys were computed in the old order (buffer 1 - buf)
+  StepCtl c{};
+  SPH_CUDA(h, cudaMemcpyAsync(&c, h->S.ctl, sizeof c, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   std::vector<uint32_t> ku(N), pu(N);
-  SPH_CUDA(h, cudaMemcpyAsync(ku.data(), h->S.key_u, 4 * N, cudaMemcpyDeviceToHost, h->stream));
-  SPH_CUDA(h, cudaMemcpyAsync(pu.data(), h->S.pid_u, 4 * N, cudaMemcpyDeviceToHost, h->stream));
-  if (sorted_ids) SPH_CUDA(h, cudaMemcpyAsync(sorted_ids, h->S.pid_s, 4 * N, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync(ku.data(), h->S.key, 4 * N, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync(pu.data(), h->S.pid[1 - c.buf], 4 * N, cudaMemcpyDeviceToHost, h->stream));
+  if (sorted_ids) SPH_CUDA(h, cudaMemcpyAsync(sorted_ids, h->S.pid[c.buf], 4 * N, cudaMemcpyDeviceToHost, h->stream));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   if (key_by_id)
     for (size_t i = 0; i < N; ++i) key_by_id[pu[i]] = ku[i];
@@ -567,18 +631,18 @@ sph_status sph_get_cell_list(sph_handle* h, uint32_t* key_by_id, uint32_t* sorte
 sph_status sph_get_grid(sph_handle* h, sph_grid_info* out) {
   if (!h || !out) return SPH_ERR_INVALID_ARG;
   memset(out, 0, sizeof *out);
-  out->n_levels = h->n_levels;
+  out->n_levels = h->hg.n_levels;
   out->dim = h->dim;
   for (int k = 0; k < 3; ++k) out->lo[k] = h->dom.lo[k];
-  out->h0 = h->h0;
+  out->h0 = h->hg.h0;
   out->lip_h = h->lip_h;
-  for (int l = 0; l < h->n_levels; ++l) {
-    out->cell[l] = h->Gd.cell[l];
-    out->dims[l][0] = h->Gd.nx[l];
-    out->dims[l][1] = h->Gd.ny[l];
-    out->dims[l][2] = h->Gd.nz[l];
+  for (int l = 0; l < h->hg.n_levels; ++l) {
+    out->cell[l] = h->hg.cell[l];
+    out->dims[l][0] = h->hg.nx[l];
+    out->dims[l][1] = h->hg.ny[l];
+    out->dims[l][2] = h->hg.nz[l];
   }
-  for (int l = 0; l <= h->n_levels; ++l) out->base[l] = h->Gd.base[l];
+  for (int l = 0; l <= h->hg.n_levels; ++l) out->base[l] = h->hg.base[l];
   return SPH_OK;
 }
 
@@ -628,7 +692,7 @@ sph_status sph_load(sph_handle* h, const void* buf, size_t nbytes) {
   h->steps = hdr[4];
   h->t0 = sched[0];
   h->t1 = sched[1];
-  return write_ctl(h);
+  return write_ctl_sched(h);
 }
 
 const char* sph_last_error(const sph_handle* h) { return h ? h->err.c_str() : "null handle"; }
@@ -643,10 +707,10 @@ sph_status sph_get_info(const sph_handle* h, int64_t* n, int32_t* dim, double* r
 
 void sph_destroy(sph_handle* h) {
   if (!h) return;
-  cudaStreamSynchronize(h->stream);
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   for (auto& b : h->blocks) h->alloc.free(b.first, b.second, h->alloc.ctx);
-  cudaStreamSynchronize(h->stream);
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_stream) cudaStreamDestroy(h->stream);
   delete h;
 }

@@ -1,11 +1,13 @@
 // Cell-linked list of the multi-resolution grid (Algorithm 1, lines 7-8).
 //
-// Particles are ordered by cell key with a counting sort over the dense key
-// range: warp-aggregated atomic counts per cell, an exclusive scan of the
-// counts (which is also the cell-start table the neighbour loops read), an
-// atomic scatter that counts each cell back down to zero, and a gather that
-// makes the order inside each cell stable (ascending previous position) while
-// it moves the particle records into sorted order.
+// At a neighbour-list rebuild, particles are ordered by cell key with a
+// counting sort over the dense key range: warp-aggregated atomic counts per
+// cell, an exclusive scan of the counts (which is also the cell-start table the
+// list build reads), an atomic scatter that counts each cell back down to zero,
+// and a gather that makes the order inside each cell stable (ascending previous
+// position) while it moves the particle state into the other buffer. Every
+// kernel here returns at once on steps without a rebuild (ctl->rebuild == 0),
+// so one captured graph serves every step.
 #include "sph_internal.h"
 
 namespace sph {
@@ -16,8 +18,25 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
-__global__ void __launch_bounds__(256) k_count(int n, const uint32_t* __restrict__ key,
+__global__ void k_gate(StepCtl* __restrict__ ctl, int force) {
+  StepCtl c = *ctl;
+  c.vp ^= 1;
+  if (c.need_rebuild || force) {
+    c.rebuild = 1;
+    c.buf ^= 1;
+    c.need_rebuild = 0;
+    c.rebuilds += 1;
+  } else {
+    c.rebuild = 0;
+  }
+  *ctl = c;
+}
+
+__global__ void k_request_rebuild(StepCtl* __restrict__ ctl) { ctl->need_rebuild = 1; }
+
+__global__ void __launch_bounds__(256) k_count(int n, const StepCtl* __restrict__ ctl, const uint32_t* __restrict__ key,
                                                uint32_t* __restrict__ cnt) {
+  if (!ctl->rebuild) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool active = i < n;
   unsigned mask = __ballot_sync(0xffffffffu, active);
@@ -28,10 +47,12 @@ __global__ void __launch_bounds__(256) k_count(int n, const uint32_t* __restrict
   if ((int)(threadIdx.x & 31) == leader) atomicAdd(&cnt[k], (uint32_t)__popc(peers));
 }
 
-__global__ void __launch_bounds__(256) k_scatter(int n, const uint32_t* __restrict__ key,
+__global__ void __launch_bounds__(256) k_scatter(int n, const StepCtl* __restrict__ ctl,
+                                                 const uint32_t* __restrict__ key,
                                                  const uint32_t* __restrict__ cstart,
                                                  uint32_t* __restrict__ cnt,
                                                  uint32_t* __restrict__ slots) {
+  if (!ctl->rebuild) return;
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   bool active = i < n;
   unsigned mask = __ballot_sync(0xffffffffu, active);
@@ -48,8 +69,10 @@ __global__ void __launch_bounds__(256) k_scatter(int n, const uint32_t* __restri
 }
 
 // per block: sum of a tile of kScanTile counts
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const StepCtl* __restrict__ ctl,
+                                                              const uint32_t* __restrict__ in,
                                                               uint32_t n, uint32_t* __restrict__ part) {
+  if (!ctl->rebuild) return;
   __shared__ uint32_t red[kScanThreads / 32];
   size_t base = (size_t)blockIdx.x * kScanTile;
   uint32_t s = 0;
@@ -69,7 +92,9 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __
 }
 
 // exclusive scan of the block sums, in place (one block of 1024 threads)
-__global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ part, int nb) {
+__global__ void __launch_bounds__(1024) k_scan_top(const StepCtl* __restrict__ ctl, uint32_t* __restrict__ part,
+                                                   int nb) {
+  if (!ctl->rebuild) return;
   __shared__ uint32_t wsum[32];
   int per = (nb + blockDim.x - 1) / blockDim.x;
   int b0 = threadIdx.x * per;
@@ -104,9 +129,11 @@ __global__ void __launch_bounds__(1024) k_scan_top(uint32_t* __restrict__ part, 
 }
 
 // exclusive scan of each tile plus its block offset; out has n + 1 entries
-__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ in, uint32_t n,
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const StepCtl* __restrict__ ctl,
+                                                            const uint32_t* __restrict__ in, uint32_t n,
                                                             const uint32_t* __restrict__ part,
                                                             uint32_t* __restrict__ out) {
+  if (!ctl->rebuild) return;
   __shared__ uint32_t wtot[kScanThreads / 32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   // each warp owns kScanItems * 32 consecutive entries of the tile
@@ -141,37 +168,55 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __re
   }
 }
 
-template <class T>
+struct alignas(32) State64 {
+  long long x, y, z, w;
+};
+
+// slot s of the scatter holds old index i; its rank among the cell's members by
+// old index gives the stable destination, where the state is copied
 __global__ void __launch_bounds__(256) k_stable_gather(
-    int n, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ key_u,
-    const uint32_t* __restrict__ cstart, const V4<T>* __restrict__ pos_u,
-    const uint32_t* __restrict__ meta_u, const uint32_t* __restrict__ pid_u,
-    V4<T>* __restrict__ pos_s, uint32_t* __restrict__ meta_s, uint32_t* __restrict__ pid_s,
-    uint32_t* __restrict__ key_s) {
+    int n, const StepCtl* __restrict__ ctl, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ key,
+    const uint32_t* __restrict__ cstart, State64* __restrict__ X0, State64* __restrict__ X1,
+    uint32_t* __restrict__ m0, uint32_t* __restrict__ m1, uint32_t* __restrict__ p0, uint32_t* __restrict__ p1) {
+  if (!ctl->rebuild) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
+  const int nb = ctl->buf;  // new buffer; the old order lives in the other one
   uint32_t i = slots[s];
-  uint32_t k = key_u[i];
+  uint32_t k = key[i];
   uint32_t b = cstart[k], e = cstart[k + 1];
   uint32_t rank = 0;
   for (uint32_t t = b; t < e; ++t) rank += slots[t] < i;
   uint32_t d = b + rank;
-  pos_s[d] = pos_u[i];
-  meta_s[d] = meta_u[i];
-  pid_s[d] = pid_u[i];
-  key_s[d] = k;
+  (nb ? X1 : X0)[d] = (nb ? X0 : X1)[i];
+  (nb ? m1 : m0)[d] = (nb ? m0 : m1)[i];
+  (nb ? p1 : p0)[d] = (nb ? p0 : p1)[i];
 }
 
-__global__ void __launch_bounds__(256) k_get_colors(int n, const uint32_t* __restrict__ meta_u,
-                                                    const uint32_t* __restrict__ pid_u, uint8_t* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_get_colors(int n, const StepCtl* __restrict__ ctl,
+                                                    const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
+                                                    const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
+                                                    uint8_t* __restrict__ out) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[pid_u[i]] = (uint8_t)(meta_u[i] & 0xFFu);
+  const int buf = ctl->buf;
+  if (i < n) out[(buf ? p1 : p0)[i]] = (uint8_t)((buf ? m1 : m0)[i] & 0xFFu);
 }
 
 }  // namespace
 
+cudaError_t launch_gate(const DevState& S, int force, cudaStream_t st) {
+  k_gate<<<1, 1, 0, st>>>(S.ctl, force);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_request_rebuild(const DevState& S, cudaStream_t st) {
+  k_request_rebuild<<<1, 1, 0, st>>>(S.ctl);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_get_colors(const DevState& S, uint8_t* out, cudaStream_t st) {
-  if (S.n > 0) k_get_colors<<<(S.n + 255) / 256, 256, 0, st>>>(S.n, S.meta_u, S.pid_u, out);
+  if (S.n > 0)
+    k_get_colors<<<(S.n + 255) / 256, 256, 0, st>>>(S.n, S.ctl, S.meta[0], S.meta[1], S.pid[0], S.pid[1], out);
   return cudaGetLastError();
 }
 
@@ -180,21 +225,15 @@ cudaError_t build_cells(const DevState& S, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int tb = 256;
   const int gb = (n + tb - 1) / tb;
-  k_count<<<gb, tb, 0, st>>>(n, S.key_u, S.cnt);
+  k_count<<<gb, tb, 0, st>>>(n, S.ctl, S.key, S.cnt);
   const uint32_t m = S.total_cells;
   const int nb = (int)((m + kScanTile - 1) / kScanTile);
-  k_scan_reduce<<<nb, kScanThreads, 0, st>>>(S.cnt, m, S.scan_part);
-  k_scan_top<<<1, 1024, 0, st>>>(S.scan_part, nb);
-  k_scan_down<<<nb, kScanThreads, 0, st>>>(S.cnt, m, S.scan_part, S.cstart);
-  k_scatter<<<gb, tb, 0, st>>>(n, S.key_u, S.cstart, S.cnt, S.tmp);
-  if (S.fp64)
-    k_stable_gather<double><<<gb, tb, 0, st>>>(n, S.tmp, S.key_u, S.cstart, (const V4<double>*)S.pos4_u,
-                                               S.meta_u, S.pid_u, (V4<double>*)S.pos4_s, S.meta_s,
-                                               S.pid_s, S.key_s);
-  else
-    k_stable_gather<float><<<gb, tb, 0, st>>>(n, S.tmp, S.key_u, S.cstart, (const V4<float>*)S.pos4_u,
-                                              S.meta_u, S.pid_u, (V4<float>*)S.pos4_s, S.meta_s,
-                                              S.pid_s, S.key_s);
+  k_scan_reduce<<<nb, kScanThreads, 0, st>>>(S.ctl, S.cnt, m, S.scan_part);
+  k_scan_top<<<1, 1024, 0, st>>>(S.ctl, S.scan_part, nb);
+  k_scan_down<<<nb, kScanThreads, 0, st>>>(S.ctl, S.cnt, m, S.scan_part, S.cstart);
+  k_scatter<<<gb, tb, 0, st>>>(n, S.ctl, S.key, S.cstart, S.cnt, S.tmp);
+  k_stable_gather<<<gb, tb, 0, st>>>(n, S.ctl, S.tmp, S.key, S.cstart, (State64*)S.X[0], (State64*)S.X[1],
+                                     S.meta[0], S.meta[1], S.pid[0], S.pid[1]);
   return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@ constexpr int kMaxShapes = 4;
 // error bits latched in the device error word (1 << sph_status value)
 constexpr int kErrNonfinite = 1 << 4;
 constexpr int kErrOutOfDomain = 1 << 5;
+constexpr int kErrListOverflow = 1 << 6;
 constexpr int kErrTimeout = 1 << 7;
 
 template <class T>
@@ -35,21 +36,46 @@ struct Geom {
   T rho_scale;
 };
 
-// Multi-resolution cell grid. Level l has cells of edge cell[l] = cell[0] 2^l;
-// a particle lives at the level of its smoothing length and stores its
-// position as integer cell coordinates plus an offset in [0, cell[l]).
+// Multi-resolution cell grid. Level l has cells of edge c0 2^l; a particle is
+// filed at the level of its smoothing length. Positions are integers (see
+// Frame), so the level-l cell index of a coordinate X is X >> (cshift + l).
 template <class T>
 struct Grid {
-  int n_levels, dim;
+  int n_levels, dim, cshift;
   int nx[kMaxLevels], ny[kMaxLevels], nz[kMaxLevels];
   uint32_t base[kMaxLevels + 1];
-  T lo[3];
-  T cell[kMaxLevels], inv_cell[kMaxLevels];
-  T wall_hi[kMaxLevels][3];  // upper box wall as an offset inside the last cell
-  T inv_h0;                  // level(h) = floor(log2(h / h0))
-  T lip_h;                   // |grad h| bound: neighbours' h within h_i +- lip_h r
-  T rfac;                    // search radius = kappa h_i rfac covers max(h_i, h_ij)
+  T cellv[kMaxLevels];   // cell edge in view units
+  T inv_h0;              // level(h) = floor(log2(h / h0)), h physical
+  T lip_h;               // |grad h| bound: neighbours' h within h_i +- lip_h r
+  T rfac;                // kappa h_i rfac covers r < kappa max(h_i, h_ij)
 };
+
+// Position frames. The state of a particle is an int64 coordinate per axis,
+// X = (x - lo) / q64, exact and independent of the level. Pair arithmetic
+// uses a "view" refreshed every step: for FP32, the low 32 bits of X >> sv
+// (differences taken modulo 2^32 are exact for nearby particles, whatever the
+// domain size); for FP64, physical coordinates relative to lo.
+template <class T>
+struct Frame {
+  double q64, inv_q64;   // physical length of one state unit and its inverse
+  double s2v;            // state units -> view units (2^-cshift)
+  double lod[3];         // box origin
+  long long xmax[3];     // state coordinate of the upper box face
+  int sv;                // FP32 view integer = round(X / 2^sv) = 2^-kViewBits c0
+  int mbits;             // FP32: bits of 1.5 * 2^(23 - kCoarseBits); adding d encodes d 2^-kCoarseBits
+  float mbias;           // FP32: 1.5 * 2^(23 - kCoarseBits)
+  float vscale;          // FP32: 2^-kViewBits, one view integer in view units
+  T qv, inv_qv;          // physical length of one view unit (the finest cell edge c0)
+  T q64t, inv_q64t;
+  T lo[3];
+  T skin;                // list skin as a fraction of kappa h
+};
+
+// The view unit is the level-0 cell edge c0. FP32 view integers are 2^-24 c0;
+// the coarse inside/outside test of a listed pair uses them shifted down to
+// 2^-20 c0, whose differences convert exactly without the conversion unit.
+constexpr int kViewBits = 24;
+constexpr int kCoarseBits = 20;
 
 template <class T>
 struct Phys {
@@ -70,10 +96,15 @@ struct Scalars {
   long long ipairs, fpairs, wall_moved, step_of_stats;
 };
 
-// Surface-tension schedule and step counter (Eq. sph_st_sigma).
+// Surface-tension schedule (Eq. sph_st_sigma), step counter and the
+// neighbour-list bookkeeping. `buf` selects the buffer holding the state in its
+// current order, `vp` the current view buffer; `need_rebuild` is raised by
+// pass B when a particle has moved half its skin since the list was built.
 struct StepCtl {
   long long step;
   double t0, t1, sigma0;
+  int buf, vp, rebuild, need_rebuild;
+  long long rebuilds;
 };
 
 __device__ __forceinline__ double sigma_of(const StepCtl& c, long long t) {
@@ -267,25 +298,6 @@ __device__ __forceinline__ int level_of_key(const Grid<T>& G, uint32_t key) {
   for (int q = 1; q < kMaxLevels; ++q)
     if (q < G.n_levels && key >= G.base[q]) l = q;
   return l;
-}
-
-// Split-precision frame change: a position given as integer cell coordinates
-// c at level la with offset o in [0, cell[la]) is re-expressed at level lb.
-// Integer parts stay exact; only the offsets are rounded, relative to the
-// cell size.
-template <class T>
-__device__ __forceinline__ void change_level(const Grid<T>& G, int la, int lb, int& c, T& o) {
-  if (la == lb) return;
-  const T c0 = G.cell[0];
-  int X0 = c << la;
-  int sub = (int)dfloor(o * G.inv_cell[0]);
-  int maxsub = (1 << la) - 1;
-  sub = sub < 0 ? 0 : (sub > maxsub ? maxsub : sub);
-  X0 += sub;
-  T o0 = o - small_int_to_fp<T>(sub) * c0;
-  int cb = X0 >> lb;
-  o = o0 + small_int_to_fp<T>(X0 - (cb << lb)) * c0;
-  c = cb;
 }
 
 // ------------------------------------------------------------- Philox ----

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <type_traits>
 
 #include "../../include/sphmesh.h"
 #include "sph_internal.h"
@@ -69,77 +70,131 @@ inline double lipschitz_h(const sph_domain& dom, const sph_field& f, double hfac
   return L * 1.05;
 }
 
-// the grid in working precision T from the canonical (double) grid
+// Host description of the multi-resolution grid. Integer positions: one state
+// unit q64 = 2^-62 L (L the power of two at or above the largest box extent),
+// so coordinates stay below 2^62; the level-0 cell edge is 2^cshift units.
+struct HostGrid {
+  int n_levels = 1, dim = 2, cshift = 0;
+  int nx[kMaxLevels], ny[kMaxLevels], nz[kMaxLevels];
+  uint32_t base[kMaxLevels + 1];
+  double cell[kMaxLevels];  // cell edge per level (physical)
+  double q64, h0, lip_h, rfac;
+};
+
+// the grid for kernels in working precision T (cell edges in view units)
 template <class T>
-inline void convert_grid(const Grid<double>& Gd, Grid<T>& G) {
+inline void convert_grid(const HostGrid& H, double view_unit, Grid<T>& G) {
   memset(&G, 0, sizeof G);
-  G.n_levels = Gd.n_levels;
-  G.dim = Gd.dim;
-  for (int l = 0; l < Gd.n_levels; ++l) {
-    G.nx[l] = Gd.nx[l];
-    G.ny[l] = Gd.ny[l];
-    G.nz[l] = Gd.nz[l];
-    G.cell[l] = (T)Gd.cell[l];
-    G.inv_cell[l] = (T)Gd.inv_cell[l];
-    for (int k = 0; k < 3; ++k) G.wall_hi[l][k] = (T)Gd.wall_hi[l][k];
+  G.n_levels = H.n_levels;
+  G.dim = H.dim;
+  G.cshift = H.cshift;
+  for (int l = 0; l < H.n_levels; ++l) {
+    G.nx[l] = H.nx[l];
+    G.ny[l] = H.ny[l];
+    G.nz[l] = H.nz[l];
+    G.cellv[l] = (T)(H.cell[l] / view_unit);
   }
-  for (int l = 0; l <= Gd.n_levels; ++l) G.base[l] = Gd.base[l];
-  for (int k = 0; k < 3; ++k) G.lo[k] = (T)Gd.lo[k];
-  G.inv_h0 = (T)Gd.inv_h0;
-  G.lip_h = (T)Gd.lip_h;
-  G.rfac = (T)Gd.rfac;
+  for (int l = 0; l <= H.n_levels; ++l) G.base[l] = H.base[l];
+  G.inv_h0 = (T)(1.0 / H.h0);
+  G.lip_h = (T)H.lip_h;
+  G.rfac = (T)H.rfac;
 }
 
 // Multi-resolution grid for smoothing lengths in [hmin, hmax]: level l has
-// cells of edge c0 2^l with c0 = cell_factor kappa h0 (rounded to float for the
-// FP32 path so that cell edges are exact in both precisions). Grows c0 until
-// the grid has fewer than 2^28 cells. Returns an error message or "".
-inline std::string grid_setup(const sph_domain& dom, int prec, double kappa, double cell_factor, double hmin,
-                              double hmax, double lip_h, Grid<double>& G) {
+// cells of edge c0 2^l, c0 the power-of-two multiple of the state unit nearest
+// to cell_factor kappa h0 (h0 = 0.98 hmin), doubled until the grid has fewer
+// than 2^28 cells. Returns an error message or "".
+inline std::string grid_setup(const sph_domain& dom, double kappa, double cell_factor, double hmin, double hmax,
+                              double lip_h, HostGrid& G) {
   const int d = dom.dim;
-  double cf = cell_factor > 0 ? cell_factor : 1.0;
+  const double cf = cell_factor > 0 ? cell_factor : 1.0;
   const double h0 = hmin * 0.98;
   if (!(h0 > 0)) return "target field gives a non-positive smoothing length";
   if (kappa * lip_h >= 1.5) return "target field varies too fast (kappa |grad h| >= 1.5)";
+  double ext = 0.0;
+  for (int k = 0; k < d; ++k) ext = std::max(ext, dom.hi[k] - dom.lo[k]);
+  const double q64 = std::ldexp(std::exp2(std::ceil(std::log2(ext))), -62);
   int L = 1;
   while (L < kMaxLevels && h0 * std::ldexp(1.0, L) <= hmax) ++L;
-  for (int attempt = 0; attempt < 64; ++attempt) {
-    double c0 = cf * kappa * h0;
-    if (prec == SPH_PREC_FP32_SPLIT) c0 = (double)(float)c0;
+  int m = (int)std::lround(std::log2(cf * kappa * h0 / q64));
+  m = std::max(m, kViewBits + 1);
+  for (; m < 62; ++m) {
+    const double c0 = std::ldexp(q64, m);
     uint64_t total = 0;
-    memset(&G, 0, sizeof G);
-    bool ok = true;
+    G = HostGrid{};
     for (int l = 0; l < L; ++l) {
       const double c = std::ldexp(c0, l);
       int dims[3] = {1, 1, 1};
-      for (int k = 0; k < d; ++k) {
-        const double e = dom.hi[k] - dom.lo[k];
-        const double nd = std::ceil(e / c);
-        if (nd > (1 << 23)) ok = false;
-        dims[k] = std::max(1, (int)nd);
-      }
+      for (int k = 0; k < d; ++k) dims[k] = std::max(1, (int)std::min(std::ceil((dom.hi[k] - dom.lo[k]) / c), 1e9));
       G.nx[l] = dims[0];
       G.ny[l] = dims[1];
       G.nz[l] = dims[2];
       G.cell[l] = c;
-      G.inv_cell[l] = 1.0 / c;
-      for (int k = 0; k < 3; ++k) G.wall_hi[l][k] = k < d ? (dom.hi[k] - dom.lo[k]) - (dims[k] - 1) * c : 0.0;
-      G.base[l] = (uint32_t)total;
+      G.base[l] = (uint32_t)std::min<uint64_t>(total, 0xFFFFFFFFu);
       total += (uint64_t)dims[0] * dims[1] * dims[2];
     }
-    if (ok && total < (1ull << 28)) {
+    if (total < (1ull << 28)) {
       G.base[L] = (uint32_t)total;
       G.n_levels = L;
       G.dim = d;
-      for (int k = 0; k < 3; ++k) G.lo[k] = dom.lo[k];
-      G.inv_h0 = 1.0 / h0;
+      G.cshift = m;
+      G.q64 = q64;
+      G.h0 = h0;
       G.lip_h = lip_h;
       G.rfac = (1.0 + 1e-5) / (1.0 - 0.5 * kappa * lip_h);
       return "";
     }
-    cf *= 1.25;
   }
   return "cell grid too large";
+}
+
+// Position frames. The integer state unit q64 divides the level-0 cell edge by
+// 2^kCellShift, so cell coordinates are shifts. The FP32 view drops sv low bits
+// so that every pair the passes look at spans less than 2^22 view units.
+struct Frames {
+  Frame<float> f;
+  Frame<double> d;
+  Grid<float> gf;
+  Grid<double> gd;
+};
+
+inline void make_frames(const sph_domain& dom, double kappa, double skin, const HostGrid& hg, Frames& out) {
+  const int dim = dom.dim;
+  const double c0 = hg.cell[0];
+  const double q64 = hg.q64;
+  const int sv = hg.cshift - kViewBits;
+  auto fill = [&](auto& F) {
+    using T = std::remove_reference_t<decltype(F.qv)>;
+    memset(&F, 0, sizeof F);
+    F.q64 = q64;
+    F.inv_q64 = 1.0 / q64;
+    for (int k = 0; k < 3; ++k) {
+      F.lod[k] = dom.lo[k];
+      F.lo[k] = (T)dom.lo[k];
+      F.xmax[k] = k < dim ? (long long)std::llround((dom.hi[k] - dom.lo[k]) / q64) : 0;
+    }
+    F.q64t = (T)q64;
+    F.inv_q64t = (T)(1.0 / q64);
+    F.s2v = std::ldexp(1.0, -hg.cshift);
+    F.skin = (T)(skin * kappa);
+  };
+  fill(out.f);
+  fill(out.d);
+  // view unit = c0 for both precisions (lengths of order one in the pair math)
+  out.f.qv = (float)c0;
+  out.f.inv_qv = (float)(1.0 / c0);
+  out.d.qv = c0;
+  out.d.inv_qv = 1.0 / c0;
+  out.f.sv = out.d.sv = sv;
+  // 1.5 * 2^(23 - kCoarseBits): its low mantissa bit is one coarse view integer
+  const float bias = (float)std::ldexp(1.5, 23 - kCoarseBits);
+  int bits;
+  memcpy(&bits, &bias, sizeof bits);
+  out.f.mbits = bits;
+  out.f.mbias = bias;
+  out.f.vscale = (float)std::ldexp(1.0, -kViewBits);
+  convert_grid<float>(hg, c0, out.gf);
+  convert_grid<double>(hg, c0, out.gd);
 }
 
 inline sph_status validate(const sph_domain* dom, const sph_field* f, int64_t n, int32_t ncol, const sph_params* p,

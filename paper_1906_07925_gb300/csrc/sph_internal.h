@@ -9,39 +9,48 @@
 
 namespace sph {
 
-// Raw device pointers of one relaxation instance. "_u" arrays hold the state
-// in the order the previous step left it (the next sort's input); "_s" arrays
-// hold the same records sorted by cell key (the neighbour loops' input).
+// Raw device pointers of one relaxation instance. The particle state (integer
+// positions, colours, ids) is double-buffered: ctl->buf names the buffer that
+// holds it in the current (cell-sorted at the last list build) order; the list
+// rebuild gathers it into the other buffer. Views are double-buffered by
+// ctl->vp (pass B writes the next step's views while pass A/B read the current).
 struct DevState {
-  int n = 0, dim = 2, fp64 = 0, block = 256;
-  void* pos4_u = nullptr;  // V4<T>: offsets in the particle's cell + h
-  void* pos4_s = nullptr;
-  uint32_t* meta_u = nullptr;  // (x cell coordinate << 8) | colour
-  uint32_t* meta_s = nullptr;
-  uint32_t* key_u = nullptr;   // cell key (level base + linear cell id)
-  uint32_t* key_s = nullptr;
-  uint32_t* pid_u = nullptr;   // original particle id
-  uint32_t* pid_s = nullptr;
-  uint32_t* cnt = nullptr;     // per-cell counters (all zero between steps)
-  uint32_t* cstart = nullptr;  // exclusive prefix of cell counts, total+1 entries
-  uint32_t* tmp = nullptr;     // scatter slots
+  int n = 0, dim = 2, fp64 = 0, cap = 0;
+  void* X[2] = {nullptr, nullptr};       // int64 x, y, z (+ pad) per particle
+  uint32_t* meta[2] = {nullptr, nullptr};  // colour
+  uint32_t* pid[2] = {nullptr, nullptr};   // particle id
+  void* view[2] = {nullptr, nullptr};    // int4 (FP32) or double4 (FP64)
+  void* vbuild = nullptr;                // view at the list build, w = half skin
+  uint32_t* key = nullptr;               // cell key (old order, rebuild only)
+  uint32_t* tmp = nullptr;               // scatter slots
+  uint32_t* cnt = nullptr;               // per-cell counters (all zero between rebuilds)
+  uint32_t* cstart = nullptr;            // exclusive prefix of cell counts, total+1 entries
   uint32_t* scan_part = nullptr;
   uint32_t total_cells = 0;
-  void* acc4 = nullptr;        // V4<T>: a_n and g = 0.05 rho_t r_c |a| (sorted order)
-  void* rho = nullptr;         // T: density (sorted order)
-  void* visc = nullptr;        // V4<T>: a~ (sorted order; recorded steps only)
-  void* pc = nullptr;          // T: p/rho^2 (general EOS only)
+  uint32_t* list = nullptr;              // cap x n entries (j << 8 | colour_j), column per particle
+  uint32_t* lcount = nullptr;
+  void* acc4 = nullptr;   // V4<T>: a_n and g = 0.05 rho_t r_c |a|
+  void* rho = nullptr;    // T
+  void* visc = nullptr;   // V4<T>: a~ (recorded steps only)
+  void* pc = nullptr;     // T: p/rho^2 (general EOS only)
   Partial* partials = nullptr;
   Scalars* scal = nullptr;
   StepCtl* ctl = nullptr;
-  unsigned* tickets = nullptr;  // [0] pass A
+  unsigned* tickets = nullptr;
   int* err = nullptr;
-  int* dbg_count = nullptr;         // 2n: density / force set sizes by particle id
-  long long* dbg_sum = nullptr;     // 2n: sums of member ids
+  int* dbg_count = nullptr;        // 2n: density / force set sizes by particle id
+  long long* dbg_sum = nullptr;    // 2n: sums of member ids
 };
 
-// cell list: count -> scan -> scatter -> stable gather into the _s arrays
+// per-step gate: flip the view buffer; start a list rebuild (flip the state
+// buffer) when pass B asked for one or `force` is set
+cudaError_t launch_gate(const DevState& S, int force, cudaStream_t st);
+// the next step rebuilds the list (after set-up or a diagnostic evaluation)
+cudaError_t launch_request_rebuild(const DevState& S, cudaStream_t st);
+// cell list of the old order -> gather into the new order (predicated on ctl->rebuild)
 cudaError_t build_cells(const DevState& S, cudaStream_t st);
+// colours by particle id
+cudaError_t launch_get_colors(const DevState& S, uint8_t* out, cudaStream_t st);
 
 struct PassFlags {
   int general_eos = 0;  // gamma != 2: density pass first, pressure p/rho^2
@@ -51,18 +60,18 @@ struct PassFlags {
 };
 
 template <int D, class T>
-cudaError_t launch_pass_a(const DevState& S, const Grid<T>& G, const Phys<T>& P, PassFlags f,
+cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& F, const Geom<T>& g, T kappa,
+                           cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P, PassFlags f, cudaStream_t st);
+template <int D, class T>
+cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& g, PassFlags f,
                           cudaStream_t st);
 template <int D, class T>
-cudaError_t launch_pass_b(const DevState& S, const Grid<T>& G, const Phys<T>& P, const Geom<T>& g,
-                          PassFlags f, cudaStream_t st);
-template <int D, class T>
-cudaError_t launch_set_state(const DevState& S, const Grid<T>& G, const Grid<double>& Gd,
-                             const Geom<T>& g, const double* xyz, const uint8_t* col,
+cudaError_t launch_set_state(const DevState& S, const Frame<T>& F, const double* xyz, const uint8_t* col,
                              cudaStream_t st);
 template <int D, class T>
-cudaError_t launch_get_positions(const DevState& S, const Grid<double>& Gd, double* out,
-                                 cudaStream_t st);
+cudaError_t launch_get_positions(const DevState& S, const Frame<T>& F, double* out, cudaStream_t st);
 template <int D, class T>
 cudaError_t launch_get_fields(const DevState& S, int which, double* out, cudaStream_t st);
 
@@ -74,8 +83,6 @@ template <int D>
 cudaError_t field_bounds(const Geom<double>& g, int res, FieldBounds* host_out, double* scratch,
                          cudaStream_t st);
 int field_bounds_scratch_doubles();
-// colours by particle id from the "_u" arrays
-cudaError_t launch_get_colors(const DevState& S, uint8_t* out, cudaStream_t st);
 template <int D>
 cudaError_t sample_positions(const Geom<double>& g, int n, int n_colors, uint64_t seed, double wmax,
                              double* xyz, uint8_t* col, double* gens, int* err, cudaStream_t st);

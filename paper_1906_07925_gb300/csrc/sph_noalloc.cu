@@ -2,9 +2,9 @@
 // (sph_eval_forces_noalloc in include/sphmesh.h).
 //
 // For callers that cannot allocate device memory: every scratch buffer the
-// cell list and pass A need lives in one file-scope device array of fixed
-// size, carved into segments below. The kernels are the same ones the handle
-// path launches; only the origin of their scratch pointers differs.
+// cell sort, the neighbour list and pass A need lives in one file-scope device
+// array of fixed size, carved into segments below. The kernels are the same
+// ones the handle path launches; only the origin of their pointers differs.
 #include <cstdio>
 #include <mutex>
 
@@ -17,23 +17,28 @@ namespace {
 
 constexpr size_t kN = SPH_NOALLOC_MAX_PARTICLES;
 constexpr size_t kC = SPH_NOALLOC_MAX_CELLS;
+constexpr size_t kCap = 96;  // list entries per particle (exact neighbour sets, no skin)
 
 constexpr size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 
 // segment offsets (bytes) inside the scratch array
-constexpr size_t kPos4U = 0;
-constexpr size_t kPos4S = kPos4U + al(16 * kN);
-constexpr size_t kAcc4 = kPos4S + al(16 * kN);
+constexpr size_t kX0 = 0;
+constexpr size_t kX1 = kX0 + al(32 * kN);
+constexpr size_t kM0 = kX1 + al(32 * kN);
+constexpr size_t kM1 = kM0 + al(4 * kN);
+constexpr size_t kP0 = kM1 + al(4 * kN);
+constexpr size_t kP1 = kP0 + al(4 * kN);
+constexpr size_t kV0 = kP1 + al(4 * kN);
+constexpr size_t kV1 = kV0 + al(16 * kN);
+constexpr size_t kVb = kV1 + al(16 * kN);
+constexpr size_t kKey = kVb + al(16 * kN);
+constexpr size_t kTmp = kKey + al(4 * kN);
+constexpr size_t kList = kTmp + al(4 * kN);
+constexpr size_t kLcount = kList + al(4 * kCap * kN);
+constexpr size_t kAcc4 = kLcount + al(4 * kN);
 constexpr size_t kRho = kAcc4 + al(16 * kN);
 constexpr size_t kPc = kRho + al(4 * kN);
-constexpr size_t kMetaU = kPc + al(4 * kN);
-constexpr size_t kMetaS = kMetaU + al(4 * kN);
-constexpr size_t kKeyU = kMetaS + al(4 * kN);
-constexpr size_t kKeyS = kKeyU + al(4 * kN);
-constexpr size_t kPidU = kKeyS + al(4 * kN);
-constexpr size_t kPidS = kPidU + al(4 * kN);
-constexpr size_t kTmp = kPidS + al(4 * kN);
-constexpr size_t kCnt = kTmp + al(4 * kN);
+constexpr size_t kCnt = kPc + al(4 * kN);
 constexpr size_t kCstart = kCnt + al(4 * kC);
 constexpr size_t kScanPart = kCstart + al(4 * (kC + 1));
 constexpr size_t kPartials = kScanPart + al(4 * (kC / 4096 + 2));
@@ -121,20 +126,20 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
   const double hmin = hfac * smin * std::pow(1.0 + S, -1.0 / d);
   const double hmax = hfac * smax * std::pow(1.0 - S, -1.0 / d);
   const double lip = lipschitz_h(*dom, *field, hfac, smax);
-  Grid<double> Gd;
-  why = grid_setup(*dom, SPH_PREC_FP32_SPLIT, params->kappa, params->cell_factor, hmin, hmax, lip, Gd);
+  HostGrid hg;
+  why = grid_setup(*dom, params->kappa, params->cell_factor, hmin, hmax, lip, hg);
   if (!why.empty()) {
     fprintf(stderr, "sph_eval_forces_noalloc: %s\n", why.c_str());
     return SPH_ERR_INVALID_ARG;
   }
-  const uint32_t cells = Gd.base[Gd.n_levels];
+  const uint32_t cells = hg.base[hg.n_levels];
   if (cells > kC) {
     fprintf(stderr, "sph_eval_forces_noalloc: the grid needs %u cells, above the limit of %d (raise cell_factor)\n",
             cells, SPH_NOALLOC_MAX_CELLS);
     return SPH_ERR_INVALID_ARG;
   }
-  Grid<float> Gf;
-  convert_grid<float>(Gd, Gf);
+  Frames fr;
+  make_frames(*dom, params->kappa, 0.0, hg, fr);  // one evaluation: no skin
   Geom<float> geof;
   fill_geom<float>(*dom, *field, hfac, field->rho_scale, geof);
   Phys<float> Pf;
@@ -150,18 +155,23 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
   Sd.n = (int)n;
   Sd.dim = d;
   Sd.fp64 = 0;
-  Sd.pos4_u = base + kPos4U;
-  Sd.pos4_s = base + kPos4S;
+  Sd.cap = (int)kCap;
+  Sd.X[0] = base + kX0;
+  Sd.X[1] = base + kX1;
+  Sd.meta[0] = (uint32_t*)(base + kM0);
+  Sd.meta[1] = (uint32_t*)(base + kM1);
+  Sd.pid[0] = (uint32_t*)(base + kP0);
+  Sd.pid[1] = (uint32_t*)(base + kP1);
+  Sd.view[0] = base + kV0;
+  Sd.view[1] = base + kV1;
+  Sd.vbuild = base + kVb;
+  Sd.key = (uint32_t*)(base + kKey);
+  Sd.tmp = (uint32_t*)(base + kTmp);
+  Sd.list = (uint32_t*)(base + kList);
+  Sd.lcount = (uint32_t*)(base + kLcount);
   Sd.acc4 = base + kAcc4;
   Sd.rho = base + kRho;
   Sd.pc = base + kPc;
-  Sd.meta_u = (uint32_t*)(base + kMetaU);
-  Sd.meta_s = (uint32_t*)(base + kMetaS);
-  Sd.key_u = (uint32_t*)(base + kKeyU);
-  Sd.key_s = (uint32_t*)(base + kKeyS);
-  Sd.pid_u = (uint32_t*)(base + kPidU);
-  Sd.pid_s = (uint32_t*)(base + kPidS);
-  Sd.tmp = (uint32_t*)(base + kTmp);
   Sd.cnt = (uint32_t*)(base + kCnt);
   Sd.cstart = (uint32_t*)(base + kCstart);
   Sd.scan_part = (uint32_t*)(base + kScanPart);
@@ -173,15 +183,20 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
   Sd.err = (int*)(base + kErr);
 
   // state that must start at zero: cell counters, the last-block ticket, the
-  // error word; the step control block (step 0, no ramp)
-  const StepCtl ctl{0, -1.0, -1.0, params->sigma0};
-#define NA_CUDA(expr)                                                                    \
-  do {                                                                                   \
-    cudaError_t e_ = (expr);                                                             \
-    if (e_ != cudaSuccess) {                                                             \
+  // error word, the statistics; the control block (step 0, no ramp; the gate
+  // below moves the state set here from buffer 0 into buffer 1)
+  StepCtl ctl{};
+  ctl.step = 0;
+  ctl.t0 = ctl.t1 = -1.0;
+  ctl.sigma0 = params->sigma0;
+  ctl.need_rebuild = 1;
+#define NA_CUDA(expr)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (expr);                                                               \
+    if (e_ != cudaSuccess) {                                                               \
       fprintf(stderr, "sph_eval_forces_noalloc: %s: %s\n", #expr, cudaGetErrorString(e_)); \
-      return SPH_ERR_CUDA;                                                               \
-    }                                                                                    \
+      return SPH_ERR_CUDA;                                                                 \
+    }                                                                                      \
   } while (0)
   NA_CUDA(cudaMemsetAsync(Sd.cnt, 0, sizeof(uint32_t) * cells, st));
   NA_CUDA(cudaMemsetAsync(Sd.tickets, 0, 16, st));
@@ -192,16 +207,19 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
     PassFlags f;
     f.general_eos = params->gamma != 2.0;
     f.advance = 0;
+    const float kappa = (float)params->kappa;
     if (d == 2) {
-      NA_CUDA((launch_set_state<2, float>(Sd, Gf, Gd, geof, xyz_dev, col_dev, st)));
-      NA_CUDA(build_cells(Sd, st));
-      NA_CUDA((launch_pass_a<2, float>(Sd, Gf, Pf, f, st)));
+      NA_CUDA((launch_set_state<2, float>(Sd, fr.f, xyz_dev, col_dev, st)));
+      NA_CUDA(launch_gate(Sd, 1, st));
+      NA_CUDA((launch_rebuild<2, float>(Sd, fr.gf, fr.f, geof, kappa, st)));
+      NA_CUDA((launch_pass_a<2, float>(Sd, fr.f, Pf, f, st)));
       NA_CUDA((launch_get_fields<2, float>(Sd, 0, rho_dev, st)));
       NA_CUDA((launch_get_fields<2, float>(Sd, 1, acc_dev, st)));
     } else {
-      NA_CUDA((launch_set_state<3, float>(Sd, Gf, Gd, geof, xyz_dev, col_dev, st)));
-      NA_CUDA(build_cells(Sd, st));
-      NA_CUDA((launch_pass_a<3, float>(Sd, Gf, Pf, f, st)));
+      NA_CUDA((launch_set_state<3, float>(Sd, fr.f, xyz_dev, col_dev, st)));
+      NA_CUDA(launch_gate(Sd, 1, st));
+      NA_CUDA((launch_rebuild<3, float>(Sd, fr.gf, fr.f, geof, kappa, st)));
+      NA_CUDA((launch_pass_a<3, float>(Sd, fr.f, Pf, f, st)));
       NA_CUDA((launch_get_fields<3, float>(Sd, 0, rho_dev, st)));
       NA_CUDA((launch_get_fields<3, float>(Sd, 1, acc_dev, st)));
     }
@@ -214,5 +232,6 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
 #undef NA_CUDA
   if (flags & kErrNonfinite) return SPH_ERR_NONFINITE;
   if (flags & kErrOutOfDomain) return SPH_ERR_OUT_OF_DOMAIN;
+  if (flags & kErrListOverflow) return SPH_ERR_CELL_OVERFLOW;
   return SPH_OK;
 }

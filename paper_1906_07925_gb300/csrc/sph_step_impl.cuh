@@ -1,110 +1,120 @@
 // Relaxation-step kernels (Algorithm 1, lines 6-16), templated on the
-// dimension D and the working precision T (float with split-precision
-// positions, or double). Instantiated per dimension in sph_step_2d.cu /
-// sph_step_3d.cu.
+// dimension D and the working precision T. Instantiated per dimension in
+// sph_step_2d.cu / sph_step_3d.cu.
 //
-// Positions are never stored as absolute coordinates: a particle is an integer
-// cell (level from its smoothing length, coordinates in that level's grid) plus
-// an offset inside the cell. Pair vectors are formed as (offset difference) +
-// (cell difference) * cell edge, so their rounding error is relative to the
-// cell size, not to the domain size.
+// State. Each particle is an int64 coordinate per axis (Frame). Pair vectors
+// come from a per-step view: FP32 keeps the low 32 bits of X >> sv and forms
+// differences modulo 2^32 (exact for nearby particles) converted without the
+// conversion unit; FP64 keeps physical coordinates. Either way the rounding of
+// a pair vector is relative to the pair distance, not to the domain size.
+//
+// Neighbour list (Algorithm 1, line 8). The list of particle i holds every j
+// (itself included) that can come within kappa max(h_i, h_ij) before some
+// particle has moved half its skin; it is rebuilt, on the device, only then.
+// Passes A and B re-test the exact criteria of the current step for every
+// listed pair, so the list only saves the search, never changes a result.
 #pragma once
 
 #include <cfloat>
+#include <type_traits>
 
 #include "sph_internal.h"
 
 namespace sph {
 
-// ------------------------------------------------------------------------
-// Candidate enumeration. For target i (level li, cell (cx,cy,cz), offsets o)
-// visit every particle j that can satisfy r_ij < kappa max(h_i, h_ij). The
-// levels searched cover h_j in h_i +- lip_h R; in each level the ball of
-// radius R is cut into rows of cells along x, each row a contiguous range of
-// the cell-sorted arrays, trimmed to the ball's x-extent at the row.
-// ------------------------------------------------------------------------
-template <int D, class T, class F>
-__device__ __forceinline__ void for_each_candidate(const Grid<T>& G, const V4<T>* __restrict__ pos4,
-                                                   const uint32_t* __restrict__ meta,
-                                                   const uint32_t* __restrict__ cstart, int li,
-                                                   int cx, int cy, int cz, T ox, T oy, T oz, T hi,
-                                                   T R, F&& body) {
-  const T R2 = R * R;
-  const T slack = hi * T(1e-5);
-  const int l0 = level_of_h(G, hi - slack - G.lip_h * R);
-  const int l1 = level_of_h(G, hi + slack + G.lip_h * R);
-  for (int l = l0; l <= l1; ++l) {
-    int cxl = cx, cyl = cy, czl = cz;
-    T fx = ox, fy = oy, fz = oz;
-    change_level(G, li, l, cxl, fx);
-    change_level(G, li, l, cyl, fy);
-    if (D == 3) change_level(G, li, l, czl, fz);
-    const T c = G.cell[l], ic = G.inv_cell[l];
-    const int nx = G.nx[l], ny = G.ny[l], nz = G.nz[l];
-    const uint32_t base = G.base[l];
-    int zlo = 0, zhi = 0;
-    if (D == 3) {
-      zlo = (int)dfloor((fz - R) * ic);
-      zhi = (int)dfloor((fz + R) * ic);
-    }
-    const int ylo = (int)dfloor((fy - R) * ic), yhi = (int)dfloor((fy + R) * ic);
-    for (int dz = zlo; dz <= zhi; ++dz) {
-      const int czz = czl + dz;
-      if (D == 3 && (czz < 0 || czz >= nz)) continue;
-      T zrel = 0, dzp = 0;
-      if (D == 3) {
-        zrel = fz - small_int_to_fp<T>(dz) * c;
-        dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
-      }
-      for (int dy = ylo; dy <= yhi; ++dy) {
-        const int cyy = cyl + dy;
-        if (cyy < 0 || cyy >= ny) continue;
-        const T yrel = fy - small_int_to_fp<T>(dy) * c;
-        const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
-        const T dp2 = dyp * dyp + dzp * dzp;
-        if (dp2 >= R2) continue;
-        const T half = dsqrt(R2 - dp2);
-        int x0 = cxl + (int)dfloor((fx - half) * ic);
-        int x1 = cxl + (int)dfloor((fx + half) * ic);
-        x0 = x0 < 0 ? 0 : x0;
-        x1 = x1 > nx - 1 ? nx - 1 : x1;
-        if (x0 > x1) continue;
-        const uint32_t krow = base + (uint32_t)nx * ((uint32_t)cyy + (uint32_t)ny * (uint32_t)(D == 3 ? czz : 0));
-        const int jb = (int)cstart[krow + x0], je = (int)cstart[krow + x1 + 1];
-        for (int j = jb; j < je; ++j) {
-          const V4<T> pj = pos4[j];
-          const uint32_t mj = meta[j];
-          const T dx = (fx - pj.x) - small_int_to_fp<T>((int)(mj >> 8) - cxl) * c;
-          const T ddy = yrel - pj.y;
-          const T ddz = D == 3 ? zrel - pj.z : T(0);
-          const T r2 = dx * dx + ddy * ddy + ddz * ddz;
-          body(j, dx, ddy, ddz, r2, pj, mj);
-        }
-      }
-    }
+// ---------------------------------------------------------------- views ----
+template <class T> struct ViewOf;
+template <> struct ViewOf<float> { using type = int4; };
+template <> struct ViewOf<double> { using type = V4<double>; };
+
+// Difference of two view coordinates, in view units (finest cell edges).
+// Precise (FAST = false): the exact integer difference, rounded once to float.
+// Coarse (FAST = true, the inside/outside test of a listed pair): the view
+// integers are dropped to 2^-kCoarseBits c0 and their difference d (|d| < 2^22,
+// certified per particle by the list build) is added to the bits of
+// 1.5 * 2^(23 - kCoarseBits), whose low mantissa bit weighs 2^-kCoarseBits: the
+// float is then bias + d 2^-kCoarseBits exactly, converted by one integer add
+// and one float subtract instead of the conversion unit.
+template <bool FAST>
+__device__ __forceinline__ float vd(const Frame<float>& F, int a, int b) {
+  if (FAST) {
+    // the modular difference is exact; shift it, not the (wrapped) operands
+    constexpr int s = kViewBits - kCoarseBits;
+    return __int_as_float(F.mbits + ((a - b) >> s)) - F.mbias;
   }
+  return (float)(a - b) * F.vscale;
+}
+template <bool FAST>
+__device__ __forceinline__ double vd(const Frame<double>&, double a, double b) {
+  return a - b;
+}
+__device__ __forceinline__ float view_h(const int4& v) { return __int_as_float(v.w); }
+__device__ __forceinline__ double view_h(const V4<double>& v) { return v.w; }
+
+// the list count of particle i; bit 31 certifies that every listed pair stays
+// within the exact range of the FP32 fast conversion until the next rebuild
+constexpr uint32_t kFastBit = 0x80000000u;
+
+struct alignas(32) LL4 {
+  long long x, y, z, w;
+};
+
+// physical position (relative to lo) of an integer coordinate
+template <class T>
+__device__ __forceinline__ T coord_phys(const Frame<T>& F, long long X) {
+  return (T)X * F.q64t;
 }
 
-// decode target i: level and cell coordinates from its key and meta word
-template <int D, class T>
-__device__ __forceinline__ void decode_cell(const Grid<T>& G, uint32_t key, uint32_t meta, int& l, int& cx,
-                                            int& cy, int& cz) {
-  l = level_of_key(G, key);
-  const uint32_t loc = key - G.base[l];
-  cx = (int)(meta >> 8);
-  const uint32_t row = loc / (uint32_t)G.nx[l];
-  if (D == 3) {
-    cy = (int)(row % (uint32_t)G.ny[l]);
-    cz = (int)(row / (uint32_t)G.ny[l]);
-  } else {
-    cy = (int)row;
-    cz = 0;
+// view of a particle at integer position X with smoothing length h (physical):
+// FP32 integers of 2^-kViewBits c0 (rounded; the low 32 bits suffice because
+// only differences of nearby particles are used), FP64 c0 units; w = h / c0
+template <int D>
+__device__ __forceinline__ int4 make_view(const Frame<float>& F, const LL4& X, float h) {
+  const long long half = 1LL << (F.sv - 1);
+  return make_int4((int)((X.x + half) >> F.sv), (int)((X.y + half) >> F.sv), D == 3 ? (int)((X.z + half) >> F.sv) : 0,
+                   __float_as_int(h * F.inv_qv));
+}
+template <int D>
+__device__ __forceinline__ V4<double> make_view(const Frame<double>& F, const LL4& X, double h) {
+  return V4<double>{(double)X.x * F.s2v, (double)X.y * F.s2v, D == 3 ? (double)X.z * F.s2v : 0.0, h * F.inv_qv};
+}
+__device__ __forceinline__ int4 with_w(int4 v, float w) { return make_int4(v.x, v.y, v.z, __float_as_int(w)); }
+__device__ __forceinline__ V4<double> with_w(V4<double> v, double w) { return V4<double>{v.x, v.y, v.z, w}; }
+
+// Visit the cnt listed entries of particle i (column i of the list) in
+// batches of four: the four list words, then the four neighbour views, are
+// loaded before any is used, so each warp keeps several independent gathers in
+// flight. List words are streamed (read once per pass).
+template <class VT, class Fn>
+__device__ __forceinline__ void for_list(const uint32_t* __restrict__ list, const VT* __restrict__ view, int n, int i,
+                                         int cnt, Fn&& pair) {
+  int k = 0;
+  for (; k + 4 <= cnt; k += 4) {
+    uint32_t e[4];
+    VT v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[q] = __ldcs(list + (size_t)(k + q) * n + i);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = view[e[q] >> 8];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) pair(e[q], v[q]);
+  }
+  for (; k < cnt; ++k) {
+    const uint32_t e = __ldcs(list + (size_t)k * n + i);
+    pair(e, view[e >> 8]);
   }
 }
 
 template <class T> __device__ __forceinline__ T pair_r(T r2);
 template <> __device__ __forceinline__ float pair_r<float>(float r2) { return r2 * rsqrtf(r2); }
 template <> __device__ __forceinline__ double pair_r<double>(double r2) { return sqrt(r2); }
+
+template <int D, class T>
+__device__ __forceinline__ void abs_pos(const Frame<T>& F, const LL4& X, T* x) {
+  x[0] = F.lo[0] + coord_phys(F, X.x);
+  x[1] = F.lo[1] + coord_phys(F, X.y);
+  x[2] = D == 3 ? F.lo[2] + coord_phys(F, X.z) : T(0);
+}
 
 // ---------------------------------------------------------- reductions ----
 __device__ __forceinline__ double warp_min(double v) {
@@ -124,7 +134,7 @@ __device__ __forceinline__ long long warp_sum(long long v) {
   return v;
 }
 
-// fixed-order block reduction of a Partial (deterministic)
+// fixed-order block reduction of a Partial (deterministic); valid in warp 0
 __device__ __forceinline__ Partial block_reduce(Partial p, Partial* sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   p.min_rc_a = warp_min(p.min_rc_a);
@@ -150,7 +160,164 @@ __device__ __forceinline__ Partial block_reduce(Partial p, Partial* sm) {
     p = q;
   }
   __syncthreads();
-  return p;  // valid in warp 0
+  return p;
+}
+
+// ------------------------------------------------------------------------
+// List rebuild (runs only when ctl->rebuild). Old order: buffer 1 - buf.
+// ------------------------------------------------------------------------
+
+// cell key of each particle in the old order: level from h at its position,
+// cell coordinates X >> (cshift + level)
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_rekey(int n, const StepCtl* __restrict__ ctl, const LL4* __restrict__ X0,
+                                               const LL4* __restrict__ X1, Frame<T> F, Grid<T> G, Geom<T> geo,
+                                               uint32_t* __restrict__ key) {
+  if (!ctl->rebuild) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const LL4 X = (ctl->buf ? X0 : X1)[i];
+  T x[3];
+  abs_pos<D, T>(F, X, x);
+  const int l = level_of_h(G, h_of<D, T>(geo, x));
+  const int sh = G.cshift + l;
+  const int c[3] = {(int)min((long long)G.nx[l] - 1, X.x >> sh), (int)min((long long)G.ny[l] - 1, X.y >> sh),
+                    D == 3 ? (int)min((long long)G.nz[l] - 1, X.z >> sh) : 0};
+  key[i] = G.base[l] + (uint32_t)c[0] + (uint32_t)G.nx[l] * ((uint32_t)c[1] + (uint32_t)G.ny[l] * (uint32_t)c[2]);
+}
+
+// views of the (new) current order and the reference view for the skin test
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_make_view(int n, const StepCtl* __restrict__ ctl, int force,
+                                                   const LL4* __restrict__ X0, const LL4* __restrict__ X1,
+                                                   Frame<T> F, Geom<T> geo, typename ViewOf<T>::type* __restrict__ v0,
+                                                   typename ViewOf<T>::type* __restrict__ v1,
+                                                   typename ViewOf<T>::type* __restrict__ vbuild) {
+  if (!force && !ctl->rebuild) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const LL4 X = (ctl->buf ? X1 : X0)[i];
+  T x[3];
+  abs_pos<D, T>(F, X, x);
+  const T h = h_of<D, T>(geo, x);
+  const auto v = make_view<D>(F, X, h);
+  (ctl->vp ? v1 : v0)[i] = v;
+  vbuild[i] = with_w(v, T(0.5) * F.skin * view_h(v));  // half the skin, view units (kappa folded in by the host)
+}
+
+// Neighbour list of each particle: every j (itself included) with
+//   r < kappa max(h_i, h_ij) (1 + 1e-5) + kappa lip_h s_max / 2 + s_max,
+// s = skin (kappa folded) of i and j: after both moved at most half their skin
+// (and h changed by at most lip_h times that), any pair inside the exact
+// criteria is still listed. Candidates come from rows of cells of every level
+// that can hold such a j.
+template <int D, class T>
+__global__ void __launch_bounds__(256) k_list_build(int n, const StepCtl* __restrict__ ctl,
+                                                    const LL4* __restrict__ X0, const LL4* __restrict__ X1,
+                                                    const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
+                                                    const typename ViewOf<T>::type* __restrict__ v0,
+                                                    const typename ViewOf<T>::type* __restrict__ v1,
+                                                    const typename ViewOf<T>::type* __restrict__ vbuild,
+                                                    const uint32_t* __restrict__ cstart, Frame<T> F, Grid<T> G,
+                                                    T kappa, int cap, uint32_t* __restrict__ list,
+                                                    uint32_t* __restrict__ lcount, int* __restrict__ err) {
+  using VT = typename ViewOf<T>::type;
+  if (!ctl->rebuild) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int buf = ctl->buf;
+  const LL4 X = (buf ? X1 : X0)[i];
+  const VT* __restrict__ view = ctl->vp ? v1 : v0;
+  const uint32_t* __restrict__ meta = buf ? m1 : m0;
+  const VT vi = view[i];
+  const T hv = view_h(vi);                 // view units
+  const T sk = view_h(vbuild[i]) * T(2);   // skin of i, view units
+  const T lip = G.lip_h;
+  // search radius: bound h_j by Lipschitz continuity, iterate twice
+  T hhi = hv, Rs = kappa * hv * G.rfac + sk * (T(1) + T(0.5) * kappa * lip);
+  for (int it = 0; it < 2; ++it) {
+    hhi = hv * T(1.00001) + lip * Rs;
+    const T shi = sk * hhi / hv;
+    Rs = kappa * T(0.5) * (hv + hhi) * G.rfac + shi * (T(1) + T(0.5) * kappa * lip);
+    Rs = Rs > kappa * hv * G.rfac ? Rs : kappa * hv * G.rfac;
+  }
+  const T hlo = hv * T(0.99999) - lip * Rs;
+  const T qv = F.qv;
+  const int l0 = level_of_h(G, hlo * qv), l1 = level_of_h(G, hhi * qv);
+  const T R2 = Rs * Rs;
+  int cnt = 0;
+  bool over = false;
+  T reach = 0;
+  for (int l = l0; l <= l1; ++l) {
+    const int sh = G.cshift + l;
+    const long long cxl = min((long long)G.nx[l] - 1, X.x >> sh);
+    const long long cyl = min((long long)G.ny[l] - 1, X.y >> sh);
+    const long long czl = D == 3 ? min((long long)G.nz[l] - 1, X.z >> sh) : 0;
+    const T c = G.cellv[l], ic = T(1) / c;
+    // target position inside its level-l cell, view units
+    const T fx = (T)((double)(X.x - (cxl << sh)) * F.s2v);
+    const T fy = (T)((double)(X.y - (cyl << sh)) * F.s2v);
+    const T fz = D == 3 ? (T)((double)(X.z - (czl << sh)) * F.s2v) : T(0);
+    const int nx = G.nx[l], ny = G.ny[l], nz = G.nz[l];
+    const uint32_t base = G.base[l];
+    int zlo = 0, zhi = 0;
+    if (D == 3) {
+      zlo = (int)dfloor((fz - Rs) * ic);
+      zhi = (int)dfloor((fz + Rs) * ic);
+    }
+    const int ylo = (int)dfloor((fy - Rs) * ic), yhi = (int)dfloor((fy + Rs) * ic);
+    for (int dz = zlo; dz <= zhi; ++dz) {
+      const long long czz = czl + dz;
+      if (D == 3 && (czz < 0 || czz >= nz)) continue;
+      T dzp = 0;
+      if (D == 3) {
+        const T zrel = fz - (T)dz * c;
+        dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
+      }
+      for (int dy = ylo; dy <= yhi; ++dy) {
+        const long long cyy = cyl + dy;
+        if (cyy < 0 || cyy >= ny) continue;
+        const T yrel = fy - (T)dy * c;
+        const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
+        const T dp2 = dyp * dyp + dzp * dzp;
+        if (dp2 >= R2) continue;
+        const T half = dsqrt(R2 - dp2);
+        long long x0 = cxl + (long long)dfloor((fx - half) * ic);
+        long long x1 = cxl + (long long)dfloor((fx + half) * ic);
+        x0 = x0 < 0 ? 0 : x0;
+        x1 = x1 > nx - 1 ? nx - 1 : x1;
+        if (x0 > x1) continue;
+        const uint32_t krow = base + (uint32_t)nx * ((uint32_t)cyy + (uint32_t)ny * (uint32_t)(D == 3 ? czz : 0));
+        const int jb = (int)cstart[krow + (uint32_t)x0], je = (int)cstart[krow + (uint32_t)x1 + 1];
+        for (int j = jb; j < je; ++j) {
+          const VT vj = view[j];
+          const T dx = vd<false>(F, vi.x, vj.x), dy2 = vd<false>(F, vi.y, vj.y);
+          const T dz2 = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+          const T r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+          if (r2 >= R2) continue;
+          const T hj = view_h(vj);
+          const T skj = sk * hj / hv;
+          const T smax = sk > skj ? sk : skj;
+          const T hm = hv > T(0.5) * (hv + hj) ? hv : T(0.5) * (hv + hj);
+          // h_j is known here: only rounding and the h change over the skin need a margin
+          const T Rl = kappa * hm * T(1.00001) + smax * (T(1) + T(0.5) * kappa * lip);
+          if (r2 < Rl * Rl) {
+            if (cnt < cap) list[(size_t)cnt * n + i] = ((uint32_t)j << 8) | (meta[j] & 0xFFu);
+            else over = true;
+            ++cnt;
+            // largest axis separation this pair can reach before the next rebuild
+            const T ax = fabs(dx) > fabs(dy2) ? fabs(dx) : fabs(dy2);
+            const T am = (ax > fabs(dz2) ? ax : fabs(dz2)) + smax;
+            reach = reach > am ? reach : am;
+          }
+        }
+      }
+    }
+  }
+  // the coarse FP32 conversion is exact below 2^22 coarse integers = 2^(22 - kCoarseBits) c0
+  const bool fast = reach < T(0.999) * T(1 << (22 - kCoarseBits));
+  lcount[i] = (uint32_t)(cnt < cap ? cnt : cap) | (fast ? kFastBit : 0u);
+  if (over) atomicOr(err, kErrListOverflow);
 }
 
 // --------------------------------------------------------------------------
@@ -158,44 +325,62 @@ __device__ __forceinline__ Partial block_reduce(Partial p, Partial* sm) {
 // p = P0 (rho/rho_t)^gamma (Eq. EOS_current), needed by the neighbours' forces.
 // --------------------------------------------------------------------------
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_density(int n, const V4<T>* __restrict__ pos4,
-                                                 const uint32_t* __restrict__ meta,
-                                                 const uint32_t* __restrict__ key,
-                                                 const uint32_t* __restrict__ cstart, Grid<T> G,
-                                                 Phys<T> P, T* __restrict__ rho_out, T* __restrict__ pc_out) {
+__global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restrict__ ctl,
+                                                 const typename ViewOf<T>::type* __restrict__ v0,
+                                                 const typename ViewOf<T>::type* __restrict__ v1,
+                                                 const uint32_t* __restrict__ list,
+                                                 const uint32_t* __restrict__ lcount, Frame<T> F, Phys<T> P,
+                                                 T* __restrict__ rho_out, T* __restrict__ pc_out) {
+  using VT = typename ViewOf<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const V4<T> pi = pos4[i];
-  const uint32_t mi = meta[i];
-  int li, cx, cy, cz;
-  decode_cell<D, T>(G, key[i], mi, li, cx, cy, cz);
-  const T hi = pi.w;
-  const T Hd = P.kappa * hi, Hd2 = Hd * Hd, invHd = T(1) / Hd;
+  const VT* __restrict__ view = ctl->vp ? v1 : v0;
+  const VT vi = view[i];
+  const T hv = view_h(vi);
+  const T Hd = P.kappa * hv, Hd2 = Hd * Hd, invHd = T(1) / Hd;
+  const uint32_t lc = lcount[i];
+  const int cnt = (int)(lc & ~kFastBit);
   T acc = 0;
-  for_each_candidate<D, T>(G, pos4, meta, cstart, li, cx, cy, cz, pi.x, pi.y, pi.z, hi, Hd * (T(1) + T(1e-5)),
-                           [&](int j, T, T, T, T r2, const V4<T>&, uint32_t) {
-                             if (r2 < Hd2) {
-                               const T q = r2 > T(0) ? pair_r<T>(r2) * invHd : T(0);
-                               const T u = T(1) - q, u2 = u * u;
-                               acc += u2 * u2 * (T(1) + T(4) * q);
-                             }
-                           });
-  const T rho = acc * P.alpha * (D == 2 ? invHd * invHd : invHd * invHd * invHd);
-  const T irt2 = inv_rho_t2<D, T>(hi, P.inv_tau);  // 1/rho_t^2
+  auto loop = [&](auto fastc) {
+    constexpr bool FAST = decltype(fastc)::value;
+    for (int k = 0; k < cnt; ++k) {
+      const uint32_t e = list[(size_t)k * n + i];
+      const VT vj = view[e >> 8];
+      T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
+      T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
+      T r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < Hd2) {
+        if (FAST) {
+          dx = vd<false>(F, vi.x, vj.x);
+          dy = vd<false>(F, vi.y, vj.y);
+          dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+          r2 = dx * dx + dy * dy + dz * dz;
+        }
+        const T q = r2 > T(0) ? pair_r<T>(r2) * invHd : T(0);
+        const T u = T(1) - q, u2 = u * u;
+        acc += u2 * u2 * (T(1) + T(4) * q);
+      }
+    }
+  };
+  if (lc & kFastBit) loop(std::true_type{});
+  else loop(std::false_type{});
+  const T Hphys = Hd * F.qv;
+  const T rho = acc * P.alpha / (D == 2 ? Hphys * Hphys : Hphys * Hphys * Hphys);
+  const T irt2 = inv_rho_t2<D, T>(hv * F.qv, P.inv_tau);
   const T rt = T(1) / dsqrt(irt2);
   rho_out[i] = rho;
   pc_out[i] = P.P0 * (T)pow((double)(rho / rt), (double)P.gamma) / (rho * rho);
 }
 
 // --------------------------------------------------------------------------
-// Pass A (Algorithm 1, lines 9-13): per target i
+// Pass A (Algorithm 1, lines 9-13): per target i, over its listed j
 //   rho_i = sum_j W(r_ij, h_i)                                 (Eq. density_sum)
 //   a_i   = -sum_j [(P_i + P_j) + beta_ij P0 (1/rho_t,i^2 + 1/rho_t,j^2)]
 //                  dW(r_ij, h_ij)/dr e_ij                      (Eqs. sph_pressure_force_2,
 //                                                                   sph_st_force, sph_st_beta)
 // with P = P0/rho_t^2 at gamma = 2 (Eq. EOS_2) or p/rho^2 otherwise;
-// e_ij = (r_i - r_j)/r_ij, h_ij = (h_i + h_j)/2, dW/dr e_ij = -20 alpha / H^(D+2)
-// (1 - q)^3 (r_i - r_j) for the Wendland C2 kernel of support H.
+// e_ij = (r_i - r_j)/r_ij, h_ij = (h_i + h_j)/2, and for the Wendland C2 kernel
+// of support H: dW/dr e_ij = -20 alpha (1 - q)^3 (r_i - r_j) / H^(D+2).
 // Writes a_i and g_i = 0.05 rho_t,i r_c,i |a_i| (eta_i = dt1 g_i, Eq.
 // viscosity_coefficient with v~ = a dt1 / 2); FP64 block partials of
 // min r_c/|a|, max |a|, sum rho, sum (rho/rho_t - 1)^2, max |rho/rho_t - 1|,
@@ -203,77 +388,106 @@ __global__ void __launch_bounds__(256) k_density(int n, const V4<T>* __restrict_
 // (Eq. time_step_size, see below).
 // --------------------------------------------------------------------------
 template <int D, class T, bool GENERAL, bool DBG>
-__global__ void __launch_bounds__(256) k_pass_a(int n, const V4<T>* __restrict__ pos4,
-                                                const uint32_t* __restrict__ meta,
-                                                const uint32_t* __restrict__ key,
-                                                const uint32_t* __restrict__ cstart,
-                                                const uint32_t* __restrict__ pid, Grid<T> G, Phys<T> P,
+__global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
+                                                const typename ViewOf<T>::type* __restrict__ v0,
+                                                const typename ViewOf<T>::type* __restrict__ v1,
+                                                const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
+                                                const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
+                                                const uint32_t* __restrict__ list,
+                                                const uint32_t* __restrict__ lcount, Frame<T> F, Phys<T> P,
                                                 const T* __restrict__ pc, V4<T>* __restrict__ acc_out,
                                                 T* __restrict__ rho_out, Partial* __restrict__ partials,
-                                                Scalars* __restrict__ scal, StepCtl* __restrict__ ctl,
-                                                unsigned* __restrict__ ticket, int* __restrict__ err,
-                                                int advance, int* __restrict__ dbg_count,
+                                                Scalars* __restrict__ scal, unsigned* __restrict__ ticket,
+                                                int* __restrict__ err, int advance, int* __restrict__ dbg_count,
                                                 long long* __restrict__ dbg_sum) {
+  using VT = typename ViewOf<T>::type;
   __shared__ Partial sm[8];
   __shared__ bool last;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const long long step = ctl->step;
-  const T sigma = (T)sigma_of(*ctl, step);
+  const StepCtl cc = *ctl;
+  const long long step = cc.step;
+  const int buf = cc.buf;
+  const VT* __restrict__ view = cc.vp ? v1 : v0;
+  const T sigma = (T)sigma_of(cc, step);
   Partial part{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0.0};
   if (i < n) {
-    const V4<T> pi = pos4[i];
-    const uint32_t mi = meta[i];
-    const uint32_t ci = mi & 0xFFu;
-    int li, cx, cy, cz;
-    decode_cell<D, T>(G, key[i], mi, li, cx, cy, cz);
-    const T hi = pi.w;
-    const T Hd = P.kappa * hi, Hd2 = Hd * Hd, invHd = T(1) / Hd;
-    const T qi = inv_rho_t2<D, T>(hi, P.inv_tau);  // 1/rho_t,i^2
+    const uint32_t* __restrict__ pid = buf ? p1 : p0;
+    const VT vi = view[i];
+    const uint32_t ci = (buf ? m1 : m0)[i] & 0xFFu;
+    const T hv = view_h(vi);
+    const T qv = F.qv;
+    const T Hd = P.kappa * hv, Hd2 = Hd * Hd, invHd = T(1) / Hd;
+    const T inv_tau_v = P.inv_tau * qv;           // h in view units -> (h/tau)
+    const T qi = inv_rho_t2<D, T>(hv, inv_tau_v);  // 1/rho_t,i^2
     const T Pi = GENERAL ? pc[i] : P.P0 * qi;
+    const T sP0 = sigma * P.P0;
     const T half_kappa = T(0.5) * P.kappa;
     T dsum = 0, ax = 0, ay = 0, az = 0;
     int nf = 0, ni = 0, nd = 0;
     long long sd = 0, sf = 0;
-    for_each_candidate<D, T>(
-        G, pos4, meta, cstart, li, cx, cy, cz, pi.x, pi.y, pi.z, hi, Hd * G.rfac,
-        [&](int j, T dx, T dy, T dz, T r2, const V4<T>& pj, uint32_t mj) {
-          if (!GENERAL && r2 < Hd2) {
-            const T q = r2 > T(0) ? pair_r<T>(r2) * invHd : T(0);
-            const T u = T(1) - q, u2 = u * u;
-            dsum += u2 * u2 * (T(1) + T(4) * q);
-            if (DBG) {
-              ++nd;
-              sd += pid[j];
-            }
+    const uint32_t lc = lcount[i];
+    const int cnt = (int)(lc & ~kFastBit);
+    auto loop = [&](auto fastc) {
+      constexpr bool FAST = decltype(fastc)::value;
+      for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+        const int j = (int)(e >> 8);
+        T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
+        T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
+        T r2 = dx * dx + dy * dy + dz * dz;
+        const T hj = view_h(vj);
+        const T Hf = half_kappa * (hv + hj);
+        const bool inD = !GENERAL && r2 < Hd2;
+        const bool inF = r2 < Hf * Hf && j != i;
+        if (!(inD || inF)) return;
+        if (FAST) {
+          dx = vd<false>(F, vi.x, vj.x);
+          dy = vd<false>(F, vi.y, vj.y);
+          dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+          r2 = dx * dx + dy * dy + dz * dz;
+        }
+        const T r = r2 > T(0) ? pair_r<T>(r2) : T(0);
+        if (inD) {
+          const T q = r * invHd;
+          const T u = T(1) - q, u2 = u * u;
+          dsum += u2 * u2 * (T(1) + T(4) * q);
+          if (DBG) {
+            ++nd;
+            sd += pid[j];
           }
-          const T Hf = half_kappa * (hi + pj.w);
-          if (r2 < Hf * Hf && j != i) {
-            const T invH = drcp<T>(Hf);
-            const T q = pair_r<T>(r2) * invH;
-            const T u = T(1) - q;
-            const T invH2 = invH * invH;
-            const T w = u * u * u * (D == 2 ? invH2 * invH2 : invH2 * invH2 * invH);
-            const T qj = inv_rho_t2<D, T>(pj.w, P.inv_tau);
-            const T Pj = GENERAL ? pc[j] : P.P0 * qj;
-            const bool other = (mj & 0xFFu) != ci;
-            const T coef = (Pi + Pj) + (other ? sigma * P.P0 * (qi + qj) : T(0));
-            const T s = coef * w;
-            ax += s * dx;
-            ay += s * dy;
-            az += s * dz;
-            ++nf;
-            ni += other;
-            if (DBG) sf += pid[j];
-          }
-        });
-    const T rho = GENERAL ? rho_out[i] : dsum * P.alpha * (D == 2 ? invHd * invHd : invHd * invHd * invHd);
-    const T k20 = T(20) * P.alpha;
+        }
+        if (inF) {
+          const T invH = drcp<T>(Hf);
+          const T q = r * invH;
+          const T u = T(1) - q;
+          const T invH2 = invH * invH;
+          const T w = u * u * u * (D == 2 ? invH2 * invH2 : invH2 * invH2 * invH);
+          const T qj = inv_rho_t2<D, T>(hj, inv_tau_v);
+          const T Pj = GENERAL ? pc[j] : P.P0 * qj;
+          const bool other = (e & 0xFFu) != ci;
+          const T coef = (Pi + Pj) + (other ? sP0 * (qi + qj) : T(0));
+          const T s = coef * w;
+          ax += s * dx;
+          ay += s * dy;
+          az += s * dz;
+          ++nf;
+          ni += other;
+          if (DBG) sf += pid[j];
+        }
+      });
+    };
+    if (lc & kFastBit) loop(std::true_type{});
+    else loop(std::false_type{});
+    // back to physical units: rho ~ 1/H^D, a ~ (view length)^-(D+1)
+    const T Hphys = Hd * qv;
+    const T rho = GENERAL ? rho_out[i] : dsum * P.alpha / (D == 2 ? Hphys * Hphys : Hphys * Hphys * Hphys);
+    const T iq = F.inv_qv;
+    const T k20 = T(20) * P.alpha * (D == 2 ? iq * iq * iq : iq * iq * iq * iq);
     ax *= k20;
     ay *= k20;
     az *= k20;
     const T an = dsqrt(ax * ax + ay * ay + az * az);
     const T rt = T(1) / dsqrt(qi);
-    const T rc = Hd;
+    const T rc = Hphys;
     const T g = T(0.05) * rt * rc * an;
     acc_out[i] = V4<T>{ax, ay, az, g};
     if (!GENERAL && rho_out) rho_out[i] = rho;
@@ -303,28 +517,19 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, const V4<T>* __restrict__
   }
   __syncthreads();
   if (!last) return;
-  // last block: fixed-order reduction of every block partial
+  // last block: fixed-order reduction of every block partial (L2 reads)
   __threadfence();
   Partial acc{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0.0};
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    // L2 reads: the partials were written by other blocks of this launch
     const double* qd = (const double*)&partials[b];
     const long long* ql = (const long long*)&partials[b];
-    Partial q;
-    q.min_rc_a = __ldcg(qd + 0);
-    q.max_a = __ldcg(qd + 1);
-    q.sum_rho = __ldcg(qd + 2);
-    q.err_l2 = __ldcg(qd + 3);
-    q.err_max = __ldcg(qd + 4);
-    q.ipairs = __ldcg(ql + 5);
-    q.fpairs = __ldcg(ql + 6);
-    acc.min_rc_a = fmin(acc.min_rc_a, q.min_rc_a);
-    acc.max_a = fmax(acc.max_a, q.max_a);
-    acc.sum_rho += q.sum_rho;
-    acc.err_l2 += q.err_l2;
-    acc.err_max = fmax(acc.err_max, q.err_max);
-    acc.ipairs += q.ipairs;
-    acc.fpairs += q.fpairs;
+    acc.min_rc_a = fmin(acc.min_rc_a, __ldcg(qd + 0));
+    acc.max_a = fmax(acc.max_a, __ldcg(qd + 1));
+    acc.sum_rho += __ldcg(qd + 2);
+    acc.err_l2 += __ldcg(qd + 3);
+    acc.err_max = fmax(acc.err_max, __ldcg(qd + 4));
+    acc.ipairs += __ldcg(ql + 5);
+    acc.fpairs += __ldcg(ql + 6);
   }
   acc = block_reduce(acc, sm);
   if (threadIdx.x == 0) {
@@ -364,55 +569,74 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, const V4<T>* __restrict__
 //   a~_i = (dt1^2 / 2) B_i,
 //   B_i  = sum_j HM(g_i, g_j) (1/rho_t,i^2 + 1/rho_t,j^2) (dW/dr / r)(a_i - a_j),
 //   v_i  = dt1 a_i / 2 + dt2 a~_i / 2,   r_i += v_i dt2.
-// Then the particle is re-expressed in its (possibly new) cell and level and
-// its next sort key is written; records go to the "_u" arrays.
+// The new view goes to the other view buffer; a particle that moved half its
+// skin since the list was built raises need_rebuild.
 // --------------------------------------------------------------------------
 template <int D, class T, bool RECORD>
-__global__ void __launch_bounds__(256) k_pass_b(int n, const V4<T>* __restrict__ pos4,
-                                                const uint32_t* __restrict__ meta,
-                                                const uint32_t* __restrict__ key,
-                                                const uint32_t* __restrict__ cstart,
-                                                const uint32_t* __restrict__ pid_s,
-                                                const V4<T>* __restrict__ acc, Grid<T> G, Phys<T> P,
-                                                Geom<T> geo, const Scalars* __restrict__ scal,
-                                                V4<T>* __restrict__ pos_u, uint32_t* __restrict__ meta_u,
-                                                uint32_t* __restrict__ key_u, uint32_t* __restrict__ pid_u,
-                                                V4<T>* __restrict__ visc_out, int* __restrict__ err,
-                                                unsigned long long* __restrict__ wall_moved) {
+__global__ void __launch_bounds__(256) k_pass_b(int n, StepCtl* __restrict__ ctl,
+                                                const typename ViewOf<T>::type* __restrict__ v0,
+                                                const typename ViewOf<T>::type* __restrict__ v1,
+                                                typename ViewOf<T>::type* __restrict__ w0,
+                                                typename ViewOf<T>::type* __restrict__ w1,
+                                                const typename ViewOf<T>::type* __restrict__ vbuild,
+                                                LL4* __restrict__ X0, LL4* __restrict__ X1,
+                                                const uint32_t* __restrict__ list,
+                                                const uint32_t* __restrict__ lcount,
+                                                const V4<T>* __restrict__ acc, Frame<T> F, Phys<T> P, Geom<T> geo,
+                                                const Scalars* __restrict__ scal, V4<T>* __restrict__ visc_out,
+                                                int* __restrict__ err, unsigned long long* __restrict__ wall_moved) {
+  using VT = typename ViewOf<T>::type;
   __shared__ int moved_sm[8];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  int moved = 0;
+  const int vp = ctl->vp, buf = ctl->buf;
+  int moved = 0, far = 0;
   if (i < n) {
-    const V4<T> pi = pos4[i];
-    const uint32_t mi = meta[i];
-    int li, cx, cy, cz;
-    decode_cell<D, T>(G, key[i], mi, li, cx, cy, cz);
-    const T hi = pi.w;
-    const T qi = inv_rho_t2<D, T>(hi, P.inv_tau);
+    const VT* __restrict__ view = vp ? v1 : v0;
+    const VT vi = view[i];
+    const T hv = view_h(vi);
+    const T qv = F.qv;
+    const T inv_tau_v = P.inv_tau * qv;
+    const T qi = inv_rho_t2<D, T>(hv, inv_tau_v);
     const V4<T> ai = acc[i];
     const T half_kappa = T(0.5) * P.kappa;
     T bx = 0, by = 0, bz = 0;
-    for_each_candidate<D, T>(G, pos4, meta, cstart, li, cx, cy, cz, pi.x, pi.y, pi.z, hi,
-                             P.kappa * hi * G.rfac,
-                             [&](int j, T, T, T, T r2, const V4<T>& pj, uint32_t) {
-                               const T Hf = half_kappa * (hi + pj.w);
-                               if (r2 < Hf * Hf && j != i) {
-                                 const V4<T> aj = acc[j];
-                                 const T gs = ai.w + aj.w;
-                                 const T hm = gs > T(0) ? T(2) * ai.w * aj.w * drcp<T>(gs) : T(0);
-                                 const T invH = drcp<T>(Hf);
-                                 const T q = pair_r<T>(r2) * invH;
-                                 const T u = T(1) - q;
-                                 const T invH2 = invH * invH;
-                                 const T w = u * u * u * (D == 2 ? invH2 * invH2 : invH2 * invH2 * invH);
-                                 const T s = hm * (qi + inv_rho_t2<D, T>(pj.w, P.inv_tau)) * w;
-                                 bx += s * (ai.x - aj.x);
-                                 by += s * (ai.y - aj.y);
-                                 bz += s * (ai.z - aj.z);
-                               }
-                             });
-    // dW/dr / r = -20 alpha (1-q)^3 / H^(D+2)
-    const T km = T(-20) * P.alpha;
+    const uint32_t lc = lcount[i];
+    const int cnt = (int)(lc & ~kFastBit);
+    auto loop = [&](auto fastc) {
+      constexpr bool FAST = decltype(fastc)::value;
+      for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+        const int j = (int)(e >> 8);
+        T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
+        T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
+        T r2 = dx * dx + dy * dy + dz * dz;
+        const T hj = view_h(vj);
+        const T Hf = half_kappa * (hv + hj);
+        if (!(r2 < Hf * Hf && j != i)) return;
+        if (FAST) {
+          dx = vd<false>(F, vi.x, vj.x);
+          dy = vd<false>(F, vi.y, vj.y);
+          dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+          r2 = dx * dx + dy * dy + dz * dz;
+        }
+        const V4<T> aj = acc[j];
+        const T gs = ai.w + aj.w;
+        const T hm = gs > T(0) ? T(2) * ai.w * aj.w * drcp<T>(gs) : T(0);
+        const T invH = drcp<T>(Hf);
+        const T q = r2 > T(0) ? pair_r<T>(r2) * invH : T(0);
+        const T u = T(1) - q;
+        const T invH2 = invH * invH;
+        const T w = u * u * u * (D == 2 ? invH2 * invH2 : invH2 * invH2 * invH);
+        const T s = hm * (qi + inv_rho_t2<D, T>(hj, inv_tau_v)) * w;
+        bx += s * (ai.x - aj.x);
+        by += s * (ai.y - aj.y);
+        bz += s * (ai.z - aj.z);
+      });
+    };
+    if (lc & kFastBit) loop(std::true_type{});
+    else loop(std::false_type{});
+    // dW/dr / r = -20 alpha (1-q)^3 / H^(D+2); view lengths -> physical
+    const T iq = F.inv_qv;
+    const T km = T(-20) * P.alpha * (D == 2 ? iq * iq * iq * iq : iq * iq * iq * iq * iq);
     bx *= km;
     by *= km;
     bz *= km;
@@ -423,77 +647,49 @@ __global__ void __launch_bounds__(256) k_pass_b(int n, const V4<T>* __restrict__
     d[0] = (T(0.5) * dt1 * ai.x + T(0.5) * dt2 * kv * bx) * dt2;
     d[1] = (T(0.5) * dt1 * ai.y + T(0.5) * dt2 * kv * by) * dt2;
     d[2] = D == 3 ? (T(0.5) * dt1 * ai.z + T(0.5) * dt2 * kv * bz) * dt2 : T(0);
-    int c[3] = {cx, cy, cz};
-    T o[3] = {pi.x, pi.y, pi.z};
+    LL4* __restrict__ Xs = buf ? X1 : X0;
+    LL4 X = Xs[i];
     const bool finite = isfinite((double)d[0]) && isfinite((double)d[1]) && isfinite((double)d[2]);
     if (!finite) atomicOr(err, kErrNonfinite);
-    int l = li;
     if (finite) {
-      const T cl = G.cell[l], icl = G.inv_cell[l];
-      const int dims[3] = {G.nx[l], G.ny[l], G.nz[l]};
-      // drift and re-normalise into the cell grid of level l
+      long long* Xc[3] = {&X.x, &X.y, &X.z};
       for (int k = 0; k < D; ++k) {
-        o[k] += d[k];
-        const int sh = (int)dfloor(o[k] * icl);
-        if (sh) {
-          c[k] += sh;
-          o[k] -= (T)sh * cl;
-        }
-      }
-      // bounding box (first constraint): clamp, which is the closest point
-      for (int k = 0; k < D; ++k) {
-        if (c[k] < 0 || (c[k] == 0 && o[k] < T(0))) {
-          c[k] = 0;
-          o[k] = T(0);
-          moved = 1;
-        } else if (c[k] > dims[k] - 1 || (c[k] == dims[k] - 1 && o[k] > G.wall_hi[l][k])) {
-          c[k] = dims[k] - 1;
-          o[k] = G.wall_hi[l][k];
-          moved = 1;
-        }
+        long long v = *Xc[k] + (long long)llrint((double)(d[k] * F.inv_q64t));
+        // bounding box (first constraint): clamp, the closest point
+        if (v < 0) { v = 0; moved = 1; }
+        if (v > F.xmax[k]) { v = F.xmax[k]; moved = 1; }
+        *Xc[k] = v;
       }
       // shape constraints, in order, at the absolute position
-      T xa[3] = {0, 0, 0};
-      for (int k = 0; k < D; ++k) xa[k] = G.lo[k] + (T)c[k] * cl + o[k];
+      T xa[3];
+      abs_pos<D, T>(F, X, xa);
       int mv = 0;
       for (int s = 0; s < geo.n_shapes; ++s) mv |= project_shape(geo, s, xa, D);
       if (mv) {
         moved = 1;
         for (int k = 0; k < D; ++k) {
-          const T rel = xa[k] - G.lo[k];
-          int cc = (int)dfloor(rel * icl);
-          cc = cc < 0 ? 0 : (cc > dims[k] - 1 ? dims[k] - 1 : cc);
-          c[k] = cc;
-          o[k] = rel - (T)cc * cl;
+          long long v = (long long)llrint((double)((xa[k] - F.lo[k]) * F.inv_q64t));
+          v = v < 0 ? 0 : (v > F.xmax[k] ? F.xmax[k] : v);
+          *Xc[k] = v;
         }
+        abs_pos<D, T>(F, X, xa);
       }
+      Xs[i] = X;
       // smoothing length at the new position (Algorithm 1, line 6 of the next step)
       const T hn = h_of<D, T>(geo, xa);
-      const int ln = level_of_h(G, hn);
-      if (ln != l) {
-        for (int k = 0; k < D; ++k) {
-          change_level(G, l, ln, c[k], o[k]);
-          const int dn = k == 0 ? G.nx[ln] : (k == 1 ? G.ny[ln] : G.nz[ln]);
-          if (c[k] > dn - 1) {
-            o[k] += (T)(c[k] - (dn - 1)) * G.cell[ln];
-            c[k] = dn - 1;
-          }
-        }
-        l = ln;
-      }
-      const uint32_t kk = G.base[l] + (uint32_t)c[0] +
-                          (uint32_t)G.nx[l] * ((uint32_t)c[1] + (uint32_t)G.ny[l] * (uint32_t)(D == 3 ? c[2] : 0));
-      pos_u[i] = V4<T>{o[0], o[1], D == 3 ? o[2] : T(0), hn};
-      meta_u[i] = ((uint32_t)c[0] << 8) | (mi & 0xFFu);
-      key_u[i] = kk;
+      const VT vn = make_view<D>(F, X, hn);
+      (vp ? w0 : w1)[i] = vn;
+      // skin test against the view at list build
+      const VT vb = vbuild[i];
+      const T ex = vd<false>(F, vn.x, vb.x), ey = vd<false>(F, vn.y, vb.y);
+      const T ez = D == 3 ? vd<false>(F, vn.z, vb.z) : T(0);
+      const T lim = view_h(vb);
+      far = (ex * ex + ey * ey + ez * ez) >= lim * lim;
     } else {
-      pos_u[i] = pi;
-      meta_u[i] = mi;
-      key_u[i] = key[i];
+      (vp ? w0 : w1)[i] = vi;
     }
-    pid_u[i] = pid_s[i];
   }
-  // count of projected particles (integer atomics: deterministic)
+  if (__syncthreads_or(far) && threadIdx.x == 0) ctl->need_rebuild = 1;
   int v = moved;
   for (int s = 16; s > 0; s >>= 1) v += __shfl_xor_sync(0xffffffffu, v, s);
   if ((threadIdx.x & 31) == 0) moved_sm[threadIdx.x >> 5] = v;
@@ -510,70 +706,54 @@ __global__ void __launch_bounds__(256) k_pass_b(int n, const V4<T>* __restrict__
 // --------------------------------------------------------------------------
 template <int D, class T>
 __global__ void __launch_bounds__(256) k_set_state(int n, const double* __restrict__ xyz,
-                                                   const uint8_t* __restrict__ col, Geom<T> geo, Grid<T> G,
-                                                   Grid<double> Gd, V4<T>* __restrict__ pos_u,
-                                                   uint32_t* __restrict__ meta_u, uint32_t* __restrict__ key_u,
-                                                   uint32_t* __restrict__ pid_u, int* __restrict__ err) {
+                                                   const uint8_t* __restrict__ col, Frame<T> F,
+                                                   LL4* __restrict__ X0, uint32_t* __restrict__ meta0,
+                                                   uint32_t* __restrict__ pid0, int* __restrict__ err) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double x[3] = {0, 0, 0};
-  bool ok = true;
+  long long v[3] = {0, 0, 0};
   for (int k = 0; k < D; ++k) {
-    x[k] = xyz[(size_t)i * D + k];
-    ok = ok && isfinite(x[k]);
+    const double x = xyz[(size_t)i * D + k];
+    if (!isfinite(x)) {
+      atomicOr(err, kErrNonfinite);
+      continue;
+    }
+    const double u = (x - F.lod[k]) * F.inv_q64;
+    if (u < 0.0 || u > (double)F.xmax[k] + 0.5) atomicOr(err, kErrOutOfDomain);
+    long long w = (long long)llrint(u < 0.0 ? 0.0 : (u > (double)F.xmax[k] ? (double)F.xmax[k] : u));
+    v[k] = w;
   }
-  if (!ok) {
-    atomicOr(err, kErrNonfinite);
-    for (int k = 0; k < D; ++k) x[k] = Gd.lo[k];
-  }
-  T xt[3] = {0, 0, 0};
-  for (int k = 0; k < D; ++k) xt[k] = (T)x[k];
-  const T h = h_of<D, T>(geo, xt);
-  const int l = level_of_h(G, h);
-  int c[3] = {0, 0, 0};
-  T o[3] = {0, 0, 0};
-  const int dims[3] = {G.nx[l], G.ny[l], G.nz[l]};
-  for (int k = 0; k < D; ++k) {
-    const double rel = x[k] - Gd.lo[k];
-    int cc = (int)floor(rel * Gd.inv_cell[l]);
-    if (rel < 0.0 || cc > dims[k] - 1 || (cc == dims[k] - 1 && rel - cc * Gd.cell[l] > (double)Gd.wall_hi[l][k]))
-      atomicOr(err, kErrOutOfDomain);
-    cc = cc < 0 ? 0 : (cc > dims[k] - 1 ? dims[k] - 1 : cc);
-    c[k] = cc;
-    o[k] = (T)(rel - (double)cc * Gd.cell[l]);
-  }
-  pos_u[i] = V4<T>{o[0], o[1], o[2], h};
-  meta_u[i] = ((uint32_t)c[0] << 8) | (uint32_t)col[i];
-  key_u[i] = G.base[l] + (uint32_t)c[0] + (uint32_t)G.nx[l] * ((uint32_t)c[1] + (uint32_t)G.ny[l] * (uint32_t)c[2]);
-  pid_u[i] = (uint32_t)i;
+  X0[i] = LL4{v[0], v[1], v[2], 0};
+  meta0[i] = (uint32_t)col[i];
+  pid0[i] = (uint32_t)i;
 }
 
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_get_positions(int n, const V4<T>* __restrict__ pos_u,
-                                                       const uint32_t* __restrict__ meta_u,
-                                                       const uint32_t* __restrict__ key_u,
-                                                       const uint32_t* __restrict__ pid_u, Grid<double> Gd,
+__global__ void __launch_bounds__(256) k_get_positions(int n, const StepCtl* __restrict__ ctl,
+                                                       const LL4* __restrict__ X0, const LL4* __restrict__ X1,
+                                                       const uint32_t* __restrict__ p0,
+                                                       const uint32_t* __restrict__ p1, Frame<T> F,
                                                        double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int l, cx, cy, cz;
-  decode_cell<D, double>(Gd, key_u[i], meta_u[i], l, cx, cy, cz);
-  const V4<T> p = pos_u[i];
-  const uint32_t id = pid_u[i];
-  const double cl = Gd.cell[l];
-  out[(size_t)id * D + 0] = Gd.lo[0] + ((double)cx * cl + (double)p.x);
-  out[(size_t)id * D + 1] = Gd.lo[1] + ((double)cy * cl + (double)p.y);
-  if (D == 3) out[(size_t)id * D + 2] = Gd.lo[2] + ((double)cz * cl + (double)p.z);
+  const int buf = ctl->buf;
+  const LL4 X = (buf ? X1 : X0)[i];
+  const uint32_t id = (buf ? p1 : p0)[i];
+  out[(size_t)id * D + 0] = F.lod[0] + (double)X.x * F.q64;
+  out[(size_t)id * D + 1] = F.lod[1] + (double)X.y * F.q64;
+  if (D == 3) out[(size_t)id * D + 2] = F.lod[2] + (double)X.z * F.q64;
 }
 
-// which: 0 rho (n), 1 acc (n x D), 2 visc (n x D); source arrays in sorted order
+// which: 0 rho (n), 1 acc (n x D), 2 visc (n x D); source arrays in the current order
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_get_fields(int n, int which, const uint32_t* __restrict__ pid_s,
-                                                    const T* __restrict__ rho, const V4<T>* __restrict__ acc,
-                                                    const V4<T>* __restrict__ visc, double* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_get_fields(int n, int which, const StepCtl* __restrict__ ctl,
+                                                    const uint32_t* __restrict__ p0,
+                                                    const uint32_t* __restrict__ p1, const T* __restrict__ rho,
+                                                    const V4<T>* __restrict__ acc, const V4<T>* __restrict__ visc,
+                                                    double* __restrict__ out) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const uint32_t id = pid_s[i];
+  const uint32_t id = (ctl->buf ? p1 : p0)[i];
   if (which == 0) {
     out[id] = (double)rho[i];
     return;
@@ -590,19 +770,37 @@ __global__ void __launch_bounds__(256) k_get_fields(int n, int which, const uint
 inline int grid_for(int n, int tb) { return (n + tb - 1) / tb; }
 
 template <int D, class T>
-cudaError_t launch_pass_a(const DevState& S, const Grid<T>& G, const Phys<T>& P, PassFlags f,
-                          cudaStream_t st) {
+cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& F, const Geom<T>& g, T kappa,
+                           cudaStream_t st) {
+  using VT = typename ViewOf<T>::type;
   const int tb = 256, gb = grid_for(S.n, tb);
-  const V4<T>* pos = (const V4<T>*)S.pos4_s;
+  const LL4* X0 = (const LL4*)S.X[0];
+  const LL4* X1 = (const LL4*)S.X[1];
+  k_rekey<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, F, G, g, S.key);
+  cudaError_t e = build_cells(S, st);
+  if (e != cudaSuccess) return e;
+  k_make_view<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, 0, X0, X1, F, g, (VT*)S.view[0], (VT*)S.view[1],
+                                       (VT*)S.vbuild);
+  k_list_build<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const VT*)S.view[0],
+                                        (const VT*)S.view[1], (const VT*)S.vbuild, S.cstart, F, G, kappa, S.cap,
+                                        S.list, S.lcount, S.err);
+  return cudaGetLastError();
+}
+
+template <int D, class T>
+cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P, PassFlags f, cudaStream_t st) {
+  using VT = typename ViewOf<T>::type;
+  const int tb = 256, gb = grid_for(S.n, tb);
   T* rho = (T*)S.rho;
   T* pc = (T*)S.pc;
-  if (f.general_eos) {
-    k_density<D, T><<<gb, tb, 0, st>>>(S.n, pos, S.meta_s, S.key_s, S.cstart, G, P, rho, pc);
-  }
-#define SPH_PASS_A(GEN, DBG)                                                                          \
-  k_pass_a<D, T, GEN, DBG><<<gb, tb, 0, st>>>(S.n, pos, S.meta_s, S.key_s, S.cstart, S.pid_s, G, P, pc, \
-                                              (V4<T>*)S.acc4, rho, S.partials, S.scal, S.ctl,         \
-                                              S.tickets, S.err, f.advance, S.dbg_count, S.dbg_sum)
+  if (f.general_eos)
+    k_density<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1], S.list, S.lcount,
+                                       F, P, rho, pc);
+#define SPH_PASS_A(GEN, DBG)                                                                                    \
+  k_pass_a<D, T, GEN, DBG><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],           \
+                                              S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount, F, P, \
+                                              pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
+                                              f.advance, S.dbg_count, S.dbg_sum)
   if (f.general_eos) {
     if (f.nbr_debug) SPH_PASS_A(true, true);
     else SPH_PASS_A(true, false);
@@ -615,38 +813,39 @@ cudaError_t launch_pass_a(const DevState& S, const Grid<T>& G, const Phys<T>& P,
 }
 
 template <int D, class T>
-cudaError_t launch_pass_b(const DevState& S, const Grid<T>& G, const Phys<T>& P, const Geom<T>& g,
-                          PassFlags f, cudaStream_t st) {
+cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& g, PassFlags f,
+                          cudaStream_t st) {
+  using VT = typename ViewOf<T>::type;
   const int tb = 256, gb = grid_for(S.n, tb);
   unsigned long long* wm = (unsigned long long*)&S.scal->wall_moved;
   if (f.record)
-    k_pass_b<D, T, true><<<gb, tb, 0, st>>>(S.n, (const V4<T>*)S.pos4_s, S.meta_s, S.key_s, S.cstart,
-                                            S.pid_s, (const V4<T>*)S.acc4, G, P, g, S.scal,
-                                            (V4<T>*)S.pos4_u, S.meta_u, S.key_u, S.pid_u, (V4<T>*)S.visc,
-                                            S.err, wm);
+    k_pass_b<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
+                                            (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0],
+                                            (LL4*)S.X[1], S.list, S.lcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
+                                            (V4<T>*)S.visc, S.err, wm);
   else
-    k_pass_b<D, T, false><<<gb, tb, 0, st>>>(S.n, (const V4<T>*)S.pos4_s, S.meta_s, S.key_s, S.cstart,
-                                             S.pid_s, (const V4<T>*)S.acc4, G, P, g, S.scal,
-                                             (V4<T>*)S.pos4_u, S.meta_u, S.key_u, S.pid_u, (V4<T>*)S.visc,
-                                             S.err, wm);
+    k_pass_b<D, T, false><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
+                                             (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0],
+                                             (LL4*)S.X[1], S.list, S.lcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
+                                             (V4<T>*)S.visc, S.err, wm);
   return cudaGetLastError();
 }
 
 template <int D, class T>
-cudaError_t launch_set_state(const DevState& S, const Grid<T>& G, const Grid<double>& Gd, const Geom<T>& g,
-                             const double* xyz, const uint8_t* col, cudaStream_t st) {
+cudaError_t launch_set_state(const DevState& S, const Frame<T>& F, const double* xyz, const uint8_t* col,
+                             cudaStream_t st) {
   const int tb = 256, gb = grid_for(S.n, tb);
   if (S.n > 0)
-    k_set_state<D, T><<<gb, tb, 0, st>>>(S.n, xyz, col, g, G, Gd, (V4<T>*)S.pos4_u, S.meta_u, S.key_u, S.pid_u,
-                                         S.err);
+    k_set_state<D, T><<<gb, tb, 0, st>>>(S.n, xyz, col, F, (LL4*)S.X[0], S.meta[0], S.pid[0], S.err);
   return cudaGetLastError();
 }
 
 template <int D, class T>
-cudaError_t launch_get_positions(const DevState& S, const Grid<double>& Gd, double* out, cudaStream_t st) {
+cudaError_t launch_get_positions(const DevState& S, const Frame<T>& F, double* out, cudaStream_t st) {
   const int tb = 256, gb = grid_for(S.n, tb);
   if (S.n > 0)
-    k_get_positions<D, T><<<gb, tb, 0, st>>>(S.n, (const V4<T>*)S.pos4_u, S.meta_u, S.key_u, S.pid_u, Gd, out);
+    k_get_positions<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, (const LL4*)S.X[0], (const LL4*)S.X[1], S.pid[0],
+                                             S.pid[1], F, out);
   return cudaGetLastError();
 }
 
@@ -654,20 +853,21 @@ template <int D, class T>
 cudaError_t launch_get_fields(const DevState& S, int which, double* out, cudaStream_t st) {
   const int tb = 256, gb = grid_for(S.n, tb);
   if (S.n > 0)
-    k_get_fields<D, T><<<gb, tb, 0, st>>>(S.n, which, S.pid_s, (const T*)S.rho, (const V4<T>*)S.acc4,
-                                          (const V4<T>*)S.visc, out);
+    k_get_fields<D, T><<<gb, tb, 0, st>>>(S.n, which, S.ctl, S.pid[0], S.pid[1], (const T*)S.rho,
+                                          (const V4<T>*)S.acc4, (const V4<T>*)S.visc, out);
   return cudaGetLastError();
 }
 
-#define SPH_INSTANTIATE_STEP(D, T)                                                                        \
-  template cudaError_t launch_pass_a<D, T>(const DevState&, const Grid<T>&, const Phys<T>&, PassFlags,   \
-                                           cudaStream_t);                                                \
-  template cudaError_t launch_pass_b<D, T>(const DevState&, const Grid<T>&, const Phys<T>&,              \
-                                           const Geom<T>&, PassFlags, cudaStream_t);                     \
-  template cudaError_t launch_set_state<D, T>(const DevState&, const Grid<T>&, const Grid<double>&,      \
-                                              const Geom<T>&, const double*, const uint8_t*, cudaStream_t); \
-  template cudaError_t launch_get_positions<D, T>(const DevState&, const Grid<double>&, double*,         \
-                                                  cudaStream_t);                                         \
+#define SPH_INSTANTIATE_STEP(D, T)                                                                             \
+  template cudaError_t launch_rebuild<D, T>(const DevState&, const Grid<T>&, const Frame<T>&, const Geom<T>&, \
+                                            T, cudaStream_t);                                                 \
+  template cudaError_t launch_pass_a<D, T>(const DevState&, const Frame<T>&, const Phys<T>&, PassFlags,       \
+                                           cudaStream_t);                                                     \
+  template cudaError_t launch_pass_b<D, T>(const DevState&, const Frame<T>&, const Phys<T>&, const Geom<T>&,  \
+                                           PassFlags, cudaStream_t);                                          \
+  template cudaError_t launch_set_state<D, T>(const DevState&, const Frame<T>&, const double*, const uint8_t*, \
+                                              cudaStream_t);                                                  \
+  template cudaError_t launch_get_positions<D, T>(const DevState&, const Frame<T>&, double*, cudaStream_t);   \
   template cudaError_t launch_get_fields<D, T>(const DevState&, int, double*, cudaStream_t);
 
 }  // namespace sph

@@ -72,7 +72,7 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
     lib = load_library()
     p = W.uniform_square_2d(64)
     d, f, q = problem_structs(p, precision="fp32")
-    n = 65537
+    n = 32769
     x = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
     c = torch.zeros(n, dtype=torch.uint8, device="cuda")
     o = torch.zeros((n, 2), dtype=torch.float64, device="cuda")
