@@ -175,7 +175,8 @@ def run_gpu(args, wl, rank, world):
     p = wl["make"](wl["n"], wl["ncol"])
     n = wl["n"]
     t_setup = time.perf_counter()
-    r = Relaxation(p, n, wl["ncol"], precision=wl["precision"], seed=wl["seed"] + 1000 * rank, use_graph=True)
+    r = Relaxation(p, n, wl["ncol"], precision=wl["precision"], seed=wl["seed"] + 1000 * rank, use_graph=True,
+                   skin=args.skin)
     torch.cuda.synchronize()
     log(f"[rank {rank}] create {time.perf_counter() - t_setup:.2f}s, grid {r.grid()['n_levels']} levels")
     stream = r.stream
@@ -250,6 +251,7 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skin", type=float, default=0.0, help="neighbour-list skin / (kappa h); 0: library default")
     ap.add_argument("--particles", type=int, default=0,
                     help="override the particle count (small cases for profiler captures)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)

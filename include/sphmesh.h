@@ -245,7 +245,7 @@ void sph_destroy(sph_handle* h);
  * problem needs must fit in SPH_NOALLOC_MAX_CELLS cells (raise
  * params->cell_factor otherwise); FP32 split precision only; field->rho_scale
  * must be given (> 0). Anything beyond: SPH_ERR_INVALID_ARG, nothing launched.
- * The scratch array (about 22 MB) is held by every GPU that loads the library
+ * The scratch array (about 35 MB) is held by every GPU that loads the library
  * until the process exits. A particle with more than 95 neighbours inside its
  * support makes the call fail with SPH_ERR_CELL_OVERFLOW.
  *

@@ -369,6 +369,8 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   SPH_TRY(grab(h, S.tmp, N));
   SPH_TRY(grab(h, S.list, N * (size_t)S.cap));
   SPH_TRY(grab(h, S.lcount, N));
+  SPH_TRY(grab(h, S.plist, N * (size_t)S.cap));
+  SPH_TRY(grab(h, S.pcount, N));
   SPH_TRY(grab(h, S.cnt, (size_t)S.total_cells));
   SPH_TRY(grab(h, S.cstart, (size_t)S.total_cells + 1));
   SPH_TRY(grab(h, S.scan_part, (size_t)S.total_cells / 4096 + 2));

@@ -28,7 +28,9 @@ struct DevState {
   uint32_t* scan_part = nullptr;
   uint32_t total_cells = 0;
   uint32_t* list = nullptr;              // cap x n entries (j << 8 | colour_j), column per particle
-  uint32_t* lcount = nullptr;
+  uint32_t* lcount = nullptr;            // entries per particle; bit 31: FP32 coarse test exact
+  uint32_t* plist = nullptr;             // cap x n: the force pairs of the current step (pass A -> B)
+  uint32_t* pcount = nullptr;
   void* acc4 = nullptr;   // V4<T>: a_n and g = 0.05 rho_t r_c |a|
   void* rho = nullptr;    // T
   void* visc = nullptr;   // V4<T>: a~ (recorded steps only)

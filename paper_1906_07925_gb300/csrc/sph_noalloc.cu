@@ -35,7 +35,9 @@ constexpr size_t kKey = kVb + al(16 * kN);
 constexpr size_t kTmp = kKey + al(4 * kN);
 constexpr size_t kList = kTmp + al(4 * kN);
 constexpr size_t kLcount = kList + al(4 * kCap * kN);
-constexpr size_t kAcc4 = kLcount + al(4 * kN);
+constexpr size_t kPlist = kLcount + al(4 * kN);
+constexpr size_t kPcount = kPlist + al(4 * kCap * kN);
+constexpr size_t kAcc4 = kPcount + al(4 * kN);
 constexpr size_t kRho = kAcc4 + al(16 * kN);
 constexpr size_t kPc = kRho + al(4 * kN);
 constexpr size_t kCnt = kPc + al(4 * kN);
@@ -169,6 +171,8 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
   Sd.tmp = (uint32_t*)(base + kTmp);
   Sd.list = (uint32_t*)(base + kList);
   Sd.lcount = (uint32_t*)(base + kLcount);
+  Sd.plist = (uint32_t*)(base + kPlist);
+  Sd.pcount = (uint32_t*)(base + kPcount);
   Sd.acc4 = base + kAcc4;
   Sd.rho = base + kRho;
   Sd.pc = base + kPc;

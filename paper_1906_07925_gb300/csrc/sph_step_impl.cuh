@@ -48,6 +48,14 @@ template <bool FAST>
 __device__ __forceinline__ double vd(const Frame<double>&, double a, double b) {
   return a - b;
 }
+// radius H widened for a screening test on coarse vectors: each coarse component
+// is the exact one floored to 2^-kCoarseBits c0, so |r_coarse - r| < sqrt(3) 2^-kCoarseBits;
+// the relative term covers FP32 rounding of r^2. A pair that passes is tested
+// again on the exact vectors, so the slack only admits a few extra candidates.
+template <class T>
+__device__ __forceinline__ T screen_radius(T H) {
+  return H * T(1.0 + 1.0 / (1 << 20)) + T(1.0 / (1 << (kCoarseBits - 2)));
+}
 __device__ __forceinline__ float view_h(const int4& v) { return __int_as_float(v.w); }
 __device__ __forceinline__ double view_h(const V4<double>& v) { return v.w; }
 
@@ -340,6 +348,7 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
   const T Hd = P.kappa * hv, Hd2 = Hd * Hd, invHd = T(1) / Hd;
   const uint32_t lc = lcount[i];
   const int cnt = (int)(lc & ~kFastBit);
+  const T Hs = (lc & kFastBit) ? screen_radius<T>(Hd) : Hd, Hs2 = Hs * Hs;
   T acc = 0;
   auto loop = [&](auto fastc) {
     constexpr bool FAST = decltype(fastc)::value;
@@ -349,12 +358,13 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
       T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
       T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
       T r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < Hd2) {
+      if (r2 < Hs2) {
         if (FAST) {
           dx = vd<false>(F, vi.x, vj.x);
           dy = vd<false>(F, vi.y, vj.y);
           dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
           r2 = dx * dx + dy * dy + dz * dz;
+          if (!(r2 < Hd2)) continue;
         }
         const T q = r2 > T(0) ? pair_r<T>(r2) * invHd : T(0);
         const T u = T(1) - q, u2 = u * u;
@@ -399,7 +409,8 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
                                                 T* __restrict__ rho_out, Partial* __restrict__ partials,
                                                 Scalars* __restrict__ scal, unsigned* __restrict__ ticket,
                                                 int* __restrict__ err, int advance, int* __restrict__ dbg_count,
-                                                long long* __restrict__ dbg_sum) {
+                                                long long* __restrict__ dbg_sum, uint32_t* __restrict__ plist,
+                                                uint32_t* __restrict__ pcount) {
   using VT = typename ViewOf<T>::type;
   __shared__ Partial sm[8];
   __shared__ bool last;
@@ -427,24 +438,36 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
     long long sd = 0, sf = 0;
     const uint32_t lc = lcount[i];
     const int cnt = (int)(lc & ~kFastBit);
-    auto loop = [&](auto fastc) {
+    // 1) this step's pairs: a cheap test of every skin-list entry, the pairs
+    //    inside either support compacted into column i of plist (the expensive
+    //    pair arithmetic then runs only for them, with all lanes busy)
+    int np = 0;
+    auto scan = [&](auto fastc) {
       constexpr bool FAST = decltype(fastc)::value;
       for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+        const T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
+        const T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
+        const T r2 = dx * dx + dy * dy + dz * dz;
+        const T Hf = half_kappa * (hv + view_h(vj));
+        const T Hm = screen_radius<T>(GENERAL || Hf > Hd ? Hf : Hd);
+        if (r2 < Hm * Hm) plist[(size_t)np++ * n + i] = e;
+      });
+    };
+    if (lc & kFastBit) scan(std::true_type{});
+    else scan(std::false_type{});
+    if (pcount) pcount[i] = (uint32_t)np;
+    // 2) density, pressure and surface tension over those pairs (exact criteria)
+    {
+      for_list(plist, view, n, i, np, [&](uint32_t e, const VT& vj) {
         const int j = (int)(e >> 8);
-        T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
-        T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
-        T r2 = dx * dx + dy * dy + dz * dz;
+        const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
+        const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+        const T r2 = dx * dx + dy * dy + dz * dz;
         const T hj = view_h(vj);
         const T Hf = half_kappa * (hv + hj);
         const bool inD = !GENERAL && r2 < Hd2;
         const bool inF = r2 < Hf * Hf && j != i;
         if (!(inD || inF)) return;
-        if (FAST) {
-          dx = vd<false>(F, vi.x, vj.x);
-          dy = vd<false>(F, vi.y, vj.y);
-          dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
-          r2 = dx * dx + dy * dy + dz * dz;
-        }
         const T r = r2 > T(0) ? pair_r<T>(r2) : T(0);
         if (inD) {
           const T q = r * invHd;
@@ -474,9 +497,7 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
           if (DBG) sf += pid[j];
         }
       });
-    };
-    if (lc & kFastBit) loop(std::true_type{});
-    else loop(std::false_type{});
+    }
     // back to physical units: rho ~ 1/H^D, a ~ (view length)^-(D+1)
     const T Hphys = Hd * qv;
     const T rho = GENERAL ? rho_out[i] : dsum * P.alpha / (D == 2 ? Hphys * Hphys : Hphys * Hphys * Hphys);
@@ -580,8 +601,8 @@ __global__ void __launch_bounds__(256) k_pass_b(int n, StepCtl* __restrict__ ctl
                                                 typename ViewOf<T>::type* __restrict__ w1,
                                                 const typename ViewOf<T>::type* __restrict__ vbuild,
                                                 LL4* __restrict__ X0, LL4* __restrict__ X1,
-                                                const uint32_t* __restrict__ list,
-                                                const uint32_t* __restrict__ lcount,
+                                                const uint32_t* __restrict__ plist,
+                                                const uint32_t* __restrict__ pcount,
                                                 const V4<T>* __restrict__ acc, Frame<T> F, Phys<T> P, Geom<T> geo,
                                                 const Scalars* __restrict__ scal, V4<T>* __restrict__ visc_out,
                                                 int* __restrict__ err, unsigned long long* __restrict__ wall_moved) {
@@ -600,40 +621,30 @@ __global__ void __launch_bounds__(256) k_pass_b(int n, StepCtl* __restrict__ ctl
     const V4<T> ai = acc[i];
     const T half_kappa = T(0.5) * P.kappa;
     T bx = 0, by = 0, bz = 0;
-    const uint32_t lc = lcount[i];
-    const int cnt = (int)(lc & ~kFastBit);
-    auto loop = [&](auto fastc) {
-      constexpr bool FAST = decltype(fastc)::value;
-      for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
-        const int j = (int)(e >> 8);
-        T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
-        T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
-        T r2 = dx * dx + dy * dy + dz * dz;
-        const T hj = view_h(vj);
-        const T Hf = half_kappa * (hv + hj);
-        if (!(r2 < Hf * Hf && j != i)) return;
-        if (FAST) {
-          dx = vd<false>(F, vi.x, vj.x);
-          dy = vd<false>(F, vi.y, vj.y);
-          dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
-          r2 = dx * dx + dy * dy + dz * dz;
-        }
-        const V4<T> aj = acc[j];
-        const T gs = ai.w + aj.w;
-        const T hm = gs > T(0) ? T(2) * ai.w * aj.w * drcp<T>(gs) : T(0);
-        const T invH = drcp<T>(Hf);
-        const T q = r2 > T(0) ? pair_r<T>(r2) * invH : T(0);
-        const T u = T(1) - q;
-        const T invH2 = invH * invH;
-        const T w = u * u * u * (D == 2 ? invH2 * invH2 : invH2 * invH2 * invH);
-        const T s = hm * (qi + inv_rho_t2<D, T>(hj, inv_tau_v)) * w;
-        bx += s * (ai.x - aj.x);
-        by += s * (ai.y - aj.y);
-        bz += s * (ai.z - aj.z);
-      });
-    };
-    if (lc & kFastBit) loop(std::true_type{});
-    else loop(std::false_type{});
+    // this step's pairs as pass A compacted them (same positions); the force
+    // support is tested again on the exact vectors
+    const int cnt = (int)pcount[i];
+    for_list(plist, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+      const int j = (int)(e >> 8);
+      const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
+      const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+      const T r2 = dx * dx + dy * dy + dz * dz;
+      const T hj = view_h(vj);
+      const T Hf = half_kappa * (hv + hj);
+      if (!(r2 < Hf * Hf) || j == i) return;
+      const V4<T> aj = acc[j];
+      const T gs = ai.w + aj.w;
+      const T hm = gs > T(0) ? T(2) * ai.w * aj.w * drcp<T>(gs) : T(0);
+      const T invH = drcp<T>(Hf);
+      const T q = r2 > T(0) ? pair_r<T>(r2) * invH : T(0);
+      const T u = T(1) - q;
+      const T invH2 = invH * invH;
+      const T w = u * u * u * (D == 2 ? invH2 * invH2 : invH2 * invH2 * invH);
+      const T s = hm * (qi + inv_rho_t2<D, T>(hj, inv_tau_v)) * w;
+      bx += s * (ai.x - aj.x);
+      by += s * (ai.y - aj.y);
+      bz += s * (ai.z - aj.z);
+    });
     // dW/dr / r = -20 alpha (1-q)^3 / H^(D+2); view lengths -> physical
     const T iq = F.inv_qv;
     const T km = T(-20) * P.alpha * (D == 2 ? iq * iq * iq * iq : iq * iq * iq * iq * iq);
@@ -800,7 +811,7 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
   k_pass_a<D, T, GEN, DBG><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],           \
                                               S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount, F, P, \
                                               pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
-                                              f.advance, S.dbg_count, S.dbg_sum)
+                                              f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount)
   if (f.general_eos) {
     if (f.nbr_debug) SPH_PASS_A(true, true);
     else SPH_PASS_A(true, false);
@@ -821,12 +832,12 @@ cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P
   if (f.record)
     k_pass_b<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
                                             (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0],
-                                            (LL4*)S.X[1], S.list, S.lcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
+                                            (LL4*)S.X[1], S.plist, S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
                                             (V4<T>*)S.visc, S.err, wm);
   else
     k_pass_b<D, T, false><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
                                              (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0],
-                                             (LL4*)S.X[1], S.list, S.lcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
+                                             (LL4*)S.X[1], S.plist, S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
                                              (V4<T>*)S.visc, S.err, wm);
   return cudaGetLastError();
 }
