@@ -100,6 +100,16 @@ def lib():
             L.orc_step.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int,
                                    C.POINTER(StepInfo), C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_void_p, C.c_void_p]
+            L.orc_step_fixed_dt.restype = C.c_int
+            L.orc_step_fixed_dt.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int,
+                                            _dp, C.POINTER(StepInfo)]
+            L.orc_objective.restype = C.c_int
+            L.orc_objective.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_double,
+                                        C.POINTER(C.c_double)]
+            L.orc_backward.restype = C.c_int
+            L.orc_backward.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int32,
+                                       C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                       C.POINTER(C.c_double), _dp, _dp]
             L.orc_num_threads.restype = C.c_int
             L.orc_num_threads.argtypes = []
             _lib = L
@@ -220,3 +230,50 @@ def run(p, pos, col, n_steps, start_step=0, mode=1):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+def run_fixed_dt(p, pos, col, dts, start_step=0, mode=1):
+    """len(dts) steps with prescribed (dt1, dt2) per step; returns the end state."""
+    pos = np.array(pos, dtype=np.float64, order="C", copy=True)
+    col = np.ascontiguousarray(col, dtype=np.uint8)
+    pc = to_c(p)
+    info = StepInfo()
+    for s, dt in enumerate(np.asarray(dts, dtype=np.float64).reshape(-1, 2)):
+        rc = lib().orc_step_fixed_dt(C.byref(pc), pos.shape[0], pos, col, int(start_step + s), int(mode),
+                                     np.ascontiguousarray(dt), C.byref(info))
+        if rc != 0:
+            raise RuntimeError("oracle step failed")
+    return pos
+
+
+def objective(p, pos, col, lam):
+    """L = sum_i (rho_i/rho_t,i - 1)^2 + lam * sum_{i<j, C_i != C_j} W(r_ij, kappa h_ij)."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    col = np.ascontiguousarray(col, dtype=np.uint8)
+    out = C.c_double()
+    if lib().orc_objective(C.byref(to_c(p)), pos.shape[0], pos, col, float(lam), C.byref(out)) != 0:
+        raise RuntimeError("oracle objective failed")
+    return out.value
+
+
+GRAD_NAMES = ("sigma0", "gamma", "P0") + tuple(f"poly{m}" for m in range(8))
+
+
+def backward(p, pos0, col, n_steps, lam, dt=None, seed=None, start_step=0):
+    """Sensitivities of L after n_steps steps from pos0 (see orc_backward).
+    dt: None (step sizes recomputed and differentiated) or (n_steps, 2) prescribed.
+    Returns dict(L, dpos0, grads {name: value}, dt (n_steps, 2))."""
+    pos0 = np.ascontiguousarray(pos0, dtype=np.float64)
+    col = np.ascontiguousarray(col, dtype=np.uint8)
+    n, d = pos0.shape
+    dt_in = None if dt is None else np.ascontiguousarray(np.asarray(dt, dtype=np.float64).reshape(-1))
+    dt_out = np.zeros(2 * n_steps)
+    sd = None if seed is None else np.ascontiguousarray(seed, dtype=np.float64).reshape(-1)
+    L = C.c_double()
+    dpos = np.zeros((n, d))
+    g = np.zeros(11)
+    rc = lib().orc_backward(C.byref(to_c(p)), n, pos0, col, int(start_step), int(n_steps), _ptr(dt_in),
+                            _ptr(dt_out), float(lam), _ptr(sd), C.byref(L), dpos, g)
+    if rc != 0:
+        raise RuntimeError("oracle backward failed")
+    return dict(L=L.value, dpos0=dpos, grads=dict(zip(GRAD_NAMES, g)), dt=dt_out.reshape(-1, 2))

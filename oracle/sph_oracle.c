@@ -409,9 +409,9 @@ int orc_neighbor_sets(const orc_problem* p, int64_t n, const double* pos, int mo
 /* ------------------------------------------------------------------------ */
 /* One relaxation step (Algorithm 1, lines 6-16).                            */
 /* ------------------------------------------------------------------------ */
-int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,
-             int mode, orc_step_info* info, double* rho_out, double* acc_out, double* visc_out,
-             double* pair_abs_a, double* pair_abs_b) {
+static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,
+                     int mode, const double* dt_fixed, orc_step_info* info, double* rho_out,
+                     double* acc_out, double* visc_out, double* pair_abs_a, double* pair_abs_b) {
   const int d = p->dim;
   const double kappa = p->kappa, P0 = p->P0, gamma = p->gamma;
   const double sigma = orc_sigma(p, (double)step);
@@ -503,6 +503,7 @@ int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, i
     }
   }
   if (!(dt1 < INFINITY)) dt1 = 0.0;
+  if (dt_fixed) dt1 = dt_fixed[0];  /* prescribed step sizes (frozen-step sensitivities) */
   /* Eq. time_int_01: v~ = v_n + a_n dt1 / 2 with v_n = 0 */
   for (size_t q = 0; q < nd; ++q) vt[q] = 0.5 * a[q] * dt1;
 
@@ -524,6 +525,7 @@ int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, i
       if (t2 < dt2) dt2 = t2;
     }
   }
+  if (dt_fixed) dt2 = dt_fixed[1];
 
   /* line 14: Eq. sph_viscous_force with rho := rho_t (Eq. sph_viscous_force_2):
    * a~_i = sum_j 2 eta_i eta_j/(eta_i + eta_j) (1/rho_t,i^2 + 1/rho_t,j^2)
@@ -580,5 +582,522 @@ int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, i
 
   free_sets(&S);
   free(h); free(rt); free(rho); free(Pc); free(a); free(vt); free(at); free(eta);
+  return 0;
+}
+
+int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,
+             int mode, orc_step_info* info, double* rho_out, double* acc_out, double* visc_out,
+             double* pair_abs_a, double* pair_abs_b) {
+  return step_core(p, n, pos, col, step, mode, NULL, info, rho_out, acc_out, visc_out, pair_abs_a,
+                   pair_abs_b);
+}
+
+int orc_step_fixed_dt(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,
+                      int mode, const double* dt, orc_step_info* info) {
+  return step_core(p, n, pos, col, step, mode, dt, info, NULL, NULL, NULL, NULL, NULL);
+}
+
+/* ======================================================================== */
+/* Sensitivities of a relaxation run (reverse mode, written by hand).        */
+/*                                                                          */
+/* The paper tunes nothing by gradient; this part differentiates the step of */
+/* Algorithm 1 (lines 6-16) as the forward code above computes it, for the   */
+/* objective                                                                 */
+/*   L = sum_i (rho_i/rho_t,i - 1)^2 + lambda sum_{i<j, C_i != C_j} W(r_ij, kappa h_ij) */
+/* after K steps, with respect to the initial positions, sigma0, gamma, P0    */
+/* and the coefficients of the polynomial density factor (rho_scale fixed).  */
+/* Two modes: the step sizes recomputed from the state (the min over         */
+/* particles differentiated at its argmin), or prescribed ("frozen").        */
+/* Pair sums are visited as unordered pairs and scattered to both ends.      */
+/* ======================================================================== */
+
+/* partial derivatives of the kernel functions (Wendland C2, support H):
+ *   W = c_d H^-d f(q), f = (1-q)^4 (1+4q), f' = -20 q (1-q)^3, q = r/H
+ *   dW/dH = -c_d H^-(d+1) (d f + q f')
+ *   F = (dW/dr)/r = -20 c_d H^-(d+2) (1-q)^3
+ *   dF/dr = 60 c_d H^-(d+3) (1-q)^2,  dF/dH = 20 c_d H^-(d+3) (1-q)^2 ((d+2)(1-q) - 3q) */
+static double kernel_c(int dim) { return dim == 2 ? 7.0 / PI : 21.0 / (2.0 * PI); }
+
+static double dW_dH(double r, double H, int dim) {
+  double q = r / H;
+  if (q >= 1.0) return 0.0;
+  double u = 1.0 - q, f = u * u * u * u * (1.0 + 4.0 * q), fp = -20.0 * q * u * u * u;
+  return -kernel_c(dim) * pow(H, -(double)(dim + 1)) * (dim * f + q * fp);
+}
+
+static void force_kernel(double r, double H, int dim, double* F, double* F_r, double* F_H) {
+  double q = r / H;
+  *F = *F_r = *F_H = 0.0;
+  if (q >= 1.0) return;
+  double u = 1.0 - q, c = kernel_c(dim);
+  double Hm = pow(H, -(double)(dim + 3));
+  *F = -20.0 * c * Hm * H * u * u * u;
+  *F_r = 60.0 * c * Hm * u * u;
+  *F_H = 20.0 * c * Hm * u * u * ((dim + 2) * u - 3.0 * q);
+}
+
+/* gradient of the signed inside distance of a shape (the branch the value takes) */
+static void inside_distance_grad(const orc_shape* s, const double* x, int dim, double* g) {
+  for (int k = 0; k < 3; ++k) g[k] = 0.0;
+  if (s->kind == ORC_SPHERE) {
+    double r2 = 0.0;
+    for (int k = 0; k < dim; ++k) r2 += (x[k] - s->center[k]) * (x[k] - s->center[k]);
+    double r = sqrt(r2);
+    if (r > 0.0)
+      for (int k = 0; k < dim; ++k) g[k] = -(x[k] - s->center[k]) / r;
+    return;
+  }
+  double outside2 = 0.0, qmax = -INFINITY, q[3] = {0, 0, 0};
+  int kmax = 0;
+  for (int k = 0; k < dim; ++k) {
+    q[k] = fabs(x[k] - s->center[k]) - s->size[k];
+    if (q[k] > 0) outside2 += q[k] * q[k];
+    if (q[k] > qmax) { qmax = q[k]; kmax = k; }
+  }
+  if (outside2 > 0.0) {
+    double o = sqrt(outside2);
+    for (int k = 0; k < dim; ++k)
+      if (q[k] > 0) g[k] = -q[k] * (x[k] >= s->center[k] ? 1.0 : -1.0) / o;
+  } else if (qmax < 0) {
+    g[kmax] = -(x[kmax] >= s->center[kmax] ? 1.0 : -1.0);
+  }
+}
+
+/* the polynomial basis b_m(x~) of the density factor and d b_m / d x_k */
+static void poly_basis(const orc_problem* p, const double* x, double* b, double db[8][3]) {
+  double t[3] = {0, 0, 0}, dt[3] = {0, 0, 0};
+  for (int k = 0; k < p->dim; ++k) {
+    t[k] = 2.0 * (x[k] - p->lo[k]) / (p->hi[k] - p->lo[k]) - 1.0;
+    dt[k] = 2.0 / (p->hi[k] - p->lo[k]);
+  }
+  memset(db, 0, sizeof(double) * 24);
+  if (p->dim == 2) {
+    double X = t[0], Y = t[1];
+    b[0] = X; b[1] = Y; b[2] = X * X; b[3] = X * Y; b[4] = Y * Y;
+    b[5] = X * X * X; b[6] = X * X * Y; b[7] = X * Y * Y;
+    double dX[8] = {1, 0, 2 * X, Y, 0, 3 * X * X, 2 * X * Y, Y * Y};
+    double dY[8] = {0, 1, 0, X, 2 * Y, 0, X * X, 2 * X * Y};
+    for (int m = 0; m < 8; ++m) { db[m][0] = dX[m] * dt[0]; db[m][1] = dY[m] * dt[1]; }
+  } else {
+    double X = t[0], Y = t[1], Z = t[2];
+    b[0] = X; b[1] = Y; b[2] = Z; b[3] = X * X; b[4] = Y * Y; b[5] = Z * Z;
+    b[6] = X * Y; b[7] = Y * Z;
+    double dX[8] = {1, 0, 0, 2 * X, 0, 0, Y, 0};
+    double dY[8] = {0, 1, 0, 0, 2 * Y, 0, X, Z};
+    double dZ[8] = {0, 0, 1, 0, 0, 2 * Z, 0, Y};
+    for (int m = 0; m < 8; ++m) { db[m][0] = dX[m] * dt[0]; db[m][1] = dY[m] * dt[1]; db[m][2] = dZ[m] * dt[2]; }
+  }
+}
+
+/* rho_t = rho_scale s^-d P(x): its gradient in x and its derivatives in the
+ * polynomial coefficients */
+static double rho_t_grad(const orc_problem* p, const double* x, double* grad, double* dcoef) {
+  int d = p->dim;
+  double s = spacing(p, x), Pf = poly_factor(p, x);
+  double base = p->rho_scale * pow(s, -(double)d);
+  double rt = base * Pf;
+  double gs[3] = {0, 0, 0};
+  if (p->field_kind != ORC_FIELD_UNIFORM) {
+    const orc_shape* sh = &p->shapes[p->dist_shape];
+    double dist = shape_inside_distance(sh, x, d), gd[3];
+    inside_distance_grad(sh, x, d, gd);
+    double sg = dist >= 0.0 ? 1.0 : -1.0;
+    for (int k = 0; k < d; ++k) gs[k] = p->b * sg * gd[k];
+  }
+  double b[8], db[8][3], gP[3] = {0, 0, 0};
+  for (int m = 0; m < 8; ++m) dcoef[m] = 0.0;
+  if (p->n_poly > 0) {
+    poly_basis(p, x, b, db);
+    for (int m = 0; m < p->n_poly && m < 8; ++m) {
+      dcoef[m] = base * b[m];
+      for (int k = 0; k < d; ++k) gP[k] += p->poly[m] * db[m][k];
+    }
+  }
+  for (int k = 0; k < 3; ++k) grad[k] = 0.0;
+  for (int k = 0; k < d; ++k) grad[k] = rt * (-(double)d * gs[k] / s) + base * gP[k];
+  return rt;
+}
+
+/* vector-Jacobian product of orc_project at y: g holds the adjoint of the
+ * projected point on entry and that of y on return. The constraints act in
+ * order (box first); each violated one is a map whose Jacobian is taken at the
+ * point it received. */
+static void project_vjp(const orc_problem* p, const double* y, double* g) {
+  int d = p->dim;
+  orc_shape cons[5];
+  int nc = 0;
+  cons[nc++] = box_shape(p);
+  for (int s = 0; s < p->n_shapes; ++s) cons[nc++] = p->shapes[s];
+  double z[6][3];
+  for (int k = 0; k < 3; ++k) z[0][k] = k < d ? y[k] : 0.0;
+  for (int c = 0; c < nc; ++c) {
+    memcpy(z[c + 1], z[c], sizeof z[c]);
+    project_one(&cons[c], z[c + 1], d);
+  }
+  for (int c = nc - 1; c >= 0; --c) {
+    const orc_shape* s = &cons[c];
+    const double* x = z[c];
+    if (!(constraint_phi(s, x, d) < 0.0)) continue;
+    if (s->kind == ORC_SPHERE) {
+      double dv[3] = {0, 0, 0}, r2 = 0.0;
+      for (int k = 0; k < d; ++k) { dv[k] = x[k] - s->center[k]; r2 += dv[k] * dv[k]; }
+      double r = sqrt(r2);
+      if (r == 0.0) { for (int k = 0; k < d; ++k) g[k] = 0.0; continue; }
+      double ng = 0.0;
+      for (int k = 0; k < d; ++k) ng += dv[k] / r * g[k];
+      for (int k = 0; k < d; ++k) g[k] = s->size[0] / r * (g[k] - dv[k] / r * ng);
+    } else if (s->keep_inside) {
+      for (int k = 0; k < d; ++k) {
+        double lo = s->center[k] - s->size[k], hi = s->center[k] + s->size[k];
+        if (x[k] < lo || x[k] > hi) g[k] = 0.0;
+      }
+    } else {
+      int best = 0; double bestd = INFINITY;
+      for (int k = 0; k < d; ++k) {
+        double dlo = x[k] - (s->center[k] - s->size[k]);
+        double dhi = (s->center[k] + s->size[k]) - x[k];
+        if (dlo < bestd) { bestd = dlo; best = k; }
+        if (dhi < bestd) { bestd = dhi; best = k; }
+      }
+      g[best] = 0.0;
+    }
+  }
+}
+
+/* adjoints of the per-particle target quantities -> positions and coefficients:
+ * rtb (rho_t), hb (h = tau rho_t^-1/d) and Tb (T = 1/rho_t^2) at particle i */
+static void local_field_vjp(const orc_problem* p, const double* x, double rtb, double hb, double Tb,
+                            double* xb, double* dpoly) {
+  double grad[3], dc[8];
+  double rt = rho_t_grad(p, x, grad, dc);
+  double h = p->tau * pow(1.0 / rt, 1.0 / p->dim);
+  double T = 1.0 / (rt * rt);
+  double tot = rtb + hb * (-h / (p->dim * rt)) + Tb * (-2.0 * T / rt);
+  for (int k = 0; k < p->dim; ++k) xb[k] += tot * grad[k];
+  for (int m = 0; m < 8; ++m) dpoly[m] += tot * dc[m];
+}
+
+typedef struct {
+  double sigma0, gamma, P0, poly[8];
+} param_bar;
+
+/* density reverse: rho_i = sum_{j in D_i} W(r_ij, kappa h_i); adds to xb and hb */
+static void density_vjp(const orc_problem* p, int64_t n, const double* pos, const double* h,
+                        const nbr_sets* S, const double* rhob, double* xb, double* hb) {
+  int d = p->dim;
+  for (int64_t i = 0; i < n; ++i) {
+    if (rhob[i] == 0.0) continue;
+    double H = p->kappa * h[i];
+    for (int64_t t = S->dstart[i]; t < S->dstart[i + 1]; ++t) {
+      int64_t j = S->dlist[t];
+      double r = sqrt(dist2(pos + i * d, pos + j * d, d));
+      hb[i] += rhob[i] * dW_dH(r, H, d) * p->kappa;
+      if (j == i || r == 0.0) continue;
+      double c = rhob[i] * orc_dW(r, H, d) / r;
+      for (int k = 0; k < d; ++k) {
+        double e = pos[i * d + k] - pos[j * d + k];
+        xb[i * d + k] += c * e;
+        xb[j * d + k] -= c * e;
+      }
+    }
+  }
+}
+
+static double ramp_of(const orc_problem* p, int64_t step) {
+  orc_problem q = *p;
+  q.sigma0 = 1.0;
+  return orc_sigma(&q, (double)step);
+}
+
+/* One step in reverse. pos is the state the step starts from; g holds the
+ * adjoint of the state it produced on entry and that of pos on return. */
+static int step_vjp(const orc_problem* p, int64_t n, const double* pos, const uint8_t* col,
+                    int64_t step, const double* dt_fixed, double* g, param_bar* pb) {
+  const int d = p->dim;
+  const double kappa = p->kappa, P0 = p->P0, gamma = p->gamma;
+  const double sigma = orc_sigma(p, (double)step);
+  const int dens_free = (gamma == 2.0 && !p->eos_general);
+  size_t nd = (size_t)n * (size_t)d;
+  double *h = calloc(n, 8), *rt = calloc(n, 8), *T = calloc(n, 8), *rho = calloc(n, 8), *Q = calloc(n, 8);
+  double *a = calloc(nd, 8), *vt = calloc(nd, 8), *at = calloc(nd, 8), *eta = calloc(n, 8), *y = calloc(nd, 8);
+  double *xb = calloc(nd, 8), *ab = calloc(nd, 8), *vtb = calloc(nd, 8), *atb = calloc(nd, 8);
+  double *hb = calloc(n, 8), *rtb = calloc(n, 8), *Tb = calloc(n, 8), *Qb = calloc(n, 8), *etab = calloc(n, 8),
+         *rhob = calloc(n, 8);
+  if (!h || !rt || !T || !rho || !Q || !a || !vt || !at || !eta || !y || !xb || !ab || !vtb || !atb || !hb ||
+      !rtb || !Tb || !Qb || !etab || !rhob)
+    return -1;
+  /* forward quantities of this step (as step_core computes them) */
+  for (int64_t i = 0; i < n; ++i) {
+    rt[i] = orc_rho_t(p, pos + i * d);
+    h[i] = p->tau * pow(1.0 / rt[i], 1.0 / d);
+    T[i] = 1.0 / (rt[i] * rt[i]);
+  }
+  nbr_sets S; memset(&S, 0, sizeof S);
+  if (build_sets(p, n, pos, h, 1, &S) != 0) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    double s = 0.0;
+    for (int64_t t = S.dstart[i]; t < S.dstart[i + 1]; ++t) {
+      int64_t j = S.dlist[t];
+      s += orc_W(sqrt(dist2(pos + i * d, pos + j * d, d)), kappa * h[i], d);
+    }
+    rho[i] = s;
+    Q[i] = dens_free ? P0 * T[i] : P0 * pow(rho[i] / rt[i], gamma) / (rho[i] * rho[i]);
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
+      int64_t j = S.flist[t];
+      double r = sqrt(dist2(pos + i * d, pos + j * d, d));
+      double F, Fr, FH;
+      force_kernel(r, kappa * 0.5 * (h[i] + h[j]), d, &F, &Fr, &FH);
+      double beta = (col[i] != col[j]) ? sigma : 0.0;
+      double coef = Q[i] + Q[j] + beta * P0 * (T[i] + T[j]);
+      for (int k = 0; k < d; ++k) a[i * d + k] -= coef * F * (pos[i * d + k] - pos[j * d + k]);
+    }
+  double mmin = INFINITY; int64_t kmin = -1;
+  for (int64_t i = 0; i < n; ++i) {
+    double an = 0.0;
+    for (int k = 0; k < d; ++k) an += a[i * d + k] * a[i * d + k];
+    an = sqrt(an);
+    if (an > 0.0 && kappa * h[i] / an < mmin) { mmin = kappa * h[i] / an; kmin = i; }
+  }
+  double dt1 = kmin >= 0 ? 0.25 * sqrt(mmin) : 0.0, dt2;
+  if (dt_fixed) dt1 = dt_fixed[0];
+  for (size_t q = 0; q < nd; ++q) vt[q] = 0.5 * a[q] * dt1;
+  dt2 = dt1;
+  for (int64_t i = 0; i < n; ++i) {
+    double vn = 0.0;
+    for (int k = 0; k < d; ++k) vn += vt[i * d + k] * vt[i * d + k];
+    vn = sqrt(vn);
+    double rc = kappa * h[i], nu = 0.1 * rc * vn;
+    eta[i] = rt[i] * nu;
+    if (vn > 0.0) {
+      if (rc / (40.0 * vn) < dt2) dt2 = rc / (40.0 * vn);
+      if (0.125 * rc * rc / nu < dt2) dt2 = 0.125 * rc * rc / nu;
+    }
+  }
+  if (dt_fixed) dt2 = dt_fixed[1];
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
+      int64_t j = S.flist[t];
+      double r = sqrt(dist2(pos + i * d, pos + j * d, d));
+      double F, Fr, FH;
+      force_kernel(r, kappa * 0.5 * (h[i] + h[j]), d, &F, &Fr, &FH);
+      double es = eta[i] + eta[j], hm = es > 0.0 ? 2.0 * eta[i] * eta[j] / es : 0.0;
+      double K = hm * (T[i] + T[j]) * F;
+      for (int k = 0; k < d; ++k) at[i * d + k] += K * (vt[i * d + k] - vt[j * d + k]);
+    }
+  for (size_t q = 0; q < nd; ++q) y[q] = pos[q] + dt2 * (vt[q] + 0.5 * dt2 * at[q]);
+
+  /* reverse: projection (line 16), drift and kicks (Eqs. time_int_01..03) */
+  double dt1b = 0.0, dt2b = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double gi[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) gi[k] = g[i * d + k];
+    project_vjp(p, y + i * d, gi);
+    for (int k = 0; k < d; ++k) {
+      size_t q = (size_t)i * d + k;
+      xb[q] += gi[k];
+      vtb[q] += dt2 * gi[k];
+      atb[q] += 0.5 * dt2 * dt2 * gi[k];
+      dt2b += gi[k] * (vt[q] + dt2 * at[q]);
+    }
+  }
+  /* viscous pairs: a~_i = sum_j K_ij (v~_i - v~_j), K = hm (T_i + T_j) F */
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
+      int64_t j = S.flist[t];
+      if (j < i) continue;
+      double e[3] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) e[k] = pos[i * d + k] - pos[j * d + k];
+      double r = sqrt(dist2(pos + i * d, pos + j * d, d));
+      double F, Fr, FH;
+      force_kernel(r, kappa * 0.5 * (h[i] + h[j]), d, &F, &Fr, &FH);
+      double es = eta[i] + eta[j], hm = es > 0.0 ? 2.0 * eta[i] * eta[j] / es : 0.0;
+      double dhi = es > 0.0 ? 2.0 * eta[j] * eta[j] / (es * es) : 0.0;
+      double dhj = es > 0.0 ? 2.0 * eta[i] * eta[i] / (es * es) : 0.0;
+      double Ts = T[i] + T[j], K = hm * Ts * F, Kb = 0.0;
+      for (int k = 0; k < d; ++k) {
+        double dab = atb[i * d + k] - atb[j * d + k];
+        vtb[i * d + k] += K * dab;
+        vtb[j * d + k] -= K * dab;
+        Kb += dab * (vt[i * d + k] - vt[j * d + k]);
+      }
+      etab[i] += Kb * Ts * F * dhi;
+      etab[j] += Kb * Ts * F * dhj;
+      Tb[i] += Kb * hm * F;
+      Tb[j] += Kb * hm * F;
+      double Fb = Kb * hm * Ts;
+      for (int k = 0; k < d; ++k) {
+        xb[i * d + k] += Fb * Fr * e[k] / r;
+        xb[j * d + k] -= Fb * Fr * e[k] / r;
+      }
+      hb[i] += Fb * FH * 0.5 * kappa;
+      hb[j] += Fb * FH * 0.5 * kappa;
+    }
+  /* eta_i = rho_t,i 0.1 kappa h_i |v~_i|; v~ = a dt1/2 */
+  for (int64_t i = 0; i < n; ++i) {
+    double vn = 0.0;
+    for (int k = 0; k < d; ++k) vn += vt[i * d + k] * vt[i * d + k];
+    vn = sqrt(vn);
+    if (vn > 0.0) {
+      rtb[i] += etab[i] * 0.1 * kappa * h[i] * vn;
+      hb[i] += etab[i] * 0.1 * rt[i] * kappa * vn;
+      for (int k = 0; k < d; ++k) vtb[i * d + k] += etab[i] * 0.1 * rt[i] * kappa * h[i] * vt[i * d + k] / vn;
+    }
+    for (int k = 0; k < d; ++k) {
+      ab[i * d + k] += 0.5 * dt1 * vtb[i * d + k];
+      dt1b += 0.5 * a[i * d + k] * vtb[i * d + k];
+    }
+  }
+  /* recomputed step sizes: dt1 = 0.25 sqrt(m), dt2 = 0.2 sqrt(m) (both minima
+   * sit at the argmin of m = r_c,k/|a_k|) */
+  if (!dt_fixed && kmin >= 0) {
+    double mb = dt1b * 0.125 / sqrt(mmin) + dt2b * 0.1 / sqrt(mmin);
+    double an = 0.0;
+    for (int k = 0; k < d; ++k) an += a[kmin * d + k] * a[kmin * d + k];
+    an = sqrt(an);
+    hb[kmin] += mb * kappa / an;
+    for (int k = 0; k < d; ++k) ab[kmin * d + k] -= mb * kappa * h[kmin] * a[kmin * d + k] / (an * an * an);
+  }
+  /* pressure and surface-tension pairs: a_i = sum_j S_ij (x_i - x_j), S = -coef F */
+  double sigb = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
+      int64_t j = S.flist[t];
+      if (j < i) continue;
+      double e[3] = {0, 0, 0};
+      for (int k = 0; k < d; ++k) e[k] = pos[i * d + k] - pos[j * d + k];
+      double r = sqrt(dist2(pos + i * d, pos + j * d, d));
+      double F, Fr, FH;
+      force_kernel(r, kappa * 0.5 * (h[i] + h[j]), d, &F, &Fr, &FH);
+      int other = col[i] != col[j];
+      double beta = other ? sigma : 0.0;
+      double coef = Q[i] + Q[j] + beta * P0 * (T[i] + T[j]);
+      double Sij = -coef * F, Sb = 0.0;
+      for (int k = 0; k < d; ++k) {
+        double dab = ab[i * d + k] - ab[j * d + k];
+        xb[i * d + k] += Sij * dab;
+        xb[j * d + k] -= Sij * dab;
+        Sb += dab * e[k];
+      }
+      double cb = -Sb * F;
+      Qb[i] += cb; Qb[j] += cb;
+      Tb[i] += cb * beta * P0; Tb[j] += cb * beta * P0;
+      if (other) sigb += cb * P0 * (T[i] + T[j]);
+      pb->P0 += cb * beta * (T[i] + T[j]);
+      double Fb = -Sb * coef;
+      for (int k = 0; k < d; ++k) {
+        xb[i * d + k] += Fb * Fr * e[k] / r;
+        xb[j * d + k] -= Fb * Fr * e[k] / r;
+      }
+      hb[i] += Fb * FH * 0.5 * kappa;
+      hb[j] += Fb * FH * 0.5 * kappa;
+    }
+  pb->sigma0 += sigb * ramp_of(p, step);
+  /* equation of state: Q = p/rho^2 = P0 (rho/rho_t)^gamma / rho^2 (P0 T at gamma = 2) */
+  for (int64_t i = 0; i < n; ++i) {
+    double lr = log(rho[i] / rt[i]);
+    pb->gamma += Qb[i] * Q[i] * lr;
+    if (dens_free) {
+      Tb[i] += Qb[i] * P0;
+      pb->P0 += Qb[i] * T[i];
+    } else {
+      rhob[i] += Qb[i] * (gamma - 2.0) * Q[i] / rho[i];
+      rtb[i] += -gamma * Qb[i] * Q[i] / rt[i];
+      pb->P0 += Qb[i] * pow(rho[i] / rt[i], gamma) / (rho[i] * rho[i]);
+    }
+  }
+  density_vjp(p, n, pos, h, &S, rhob, xb, hb);
+  for (int64_t i = 0; i < n; ++i) local_field_vjp(p, pos + i * d, rtb[i], hb[i], Tb[i], xb + i * d, pb->poly);
+  memcpy(g, xb, sizeof(double) * nd);
+  free_sets(&S);
+  free(h); free(rt); free(T); free(rho); free(Q); free(a); free(vt); free(at); free(eta); free(y);
+  free(xb); free(ab); free(vtb); free(atb); free(hb); free(rtb); free(Tb); free(Qb); free(etab); free(rhob);
+  return 0;
+}
+
+/* objective at pos; with g non-NULL also adds dL/dpos to g and dL/dcoef to dpoly */
+static int objective_core(const orc_problem* p, int64_t n, const double* pos, const uint8_t* col,
+                          double lambda, double* L, double* g, double* dpoly) {
+  const int d = p->dim;
+  const double kappa = p->kappa;
+  double *h = calloc(n, 8), *rt = calloc(n, 8), *rhob = calloc(n, 8), *hb = calloc(n, 8), *rtb = calloc(n, 8);
+  if (!h || !rt || !rhob || !hb || !rtb) return -1;
+  for (int64_t i = 0; i < n; ++i) {
+    rt[i] = orc_rho_t(p, pos + i * d);
+    h[i] = p->tau * pow(1.0 / rt[i], 1.0 / d);
+  }
+  nbr_sets S; memset(&S, 0, sizeof S);
+  if (build_sets(p, n, pos, h, 1, &S) != 0) return -1;
+  double Ld = 0.0, Li = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double rho = 0.0;
+    for (int64_t t = S.dstart[i]; t < S.dstart[i + 1]; ++t)
+      rho += orc_W(sqrt(dist2(pos + i * d, pos + S.dlist[t] * d, d)), kappa * h[i], d);
+    double e = rho / rt[i] - 1.0;
+    Ld += e * e;
+    rhob[i] = 2.0 * e / rt[i];
+    rtb[i] = -2.0 * e * rho / (rt[i] * rt[i]);
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
+      int64_t j = S.flist[t];
+      if (j < i || col[i] == col[j]) continue;
+      double r = sqrt(dist2(pos + i * d, pos + j * d, d));
+      double H = kappa * 0.5 * (h[i] + h[j]);
+      Li += orc_W(r, H, d);
+      if (!g) continue;
+      double c = lambda * orc_dW(r, H, d) / r;
+      for (int k = 0; k < d; ++k) {
+        double e = pos[i * d + k] - pos[j * d + k];
+        g[i * d + k] += c * e;
+        g[j * d + k] -= c * e;
+      }
+      double wh = lambda * dW_dH(r, H, d) * 0.5 * kappa;
+      hb[i] += wh; hb[j] += wh;
+    }
+  *L = Ld + lambda * Li;
+  if (g) {
+    density_vjp(p, n, pos, h, &S, rhob, g, hb);
+    for (int64_t i = 0; i < n; ++i) local_field_vjp(p, pos + i * d, rtb[i], hb[i], 0.0, g + i * d, dpoly);
+  }
+  free_sets(&S);
+  free(h); free(rt); free(rhob); free(hb); free(rtb);
+  return 0;
+}
+
+int orc_objective(const orc_problem* p, int64_t n, const double* pos, const uint8_t* col, double lambda,
+                  double* L) {
+  return objective_core(p, n, pos, col, lambda, L, NULL, NULL);
+}
+
+int orc_backward(const orc_problem* p, int64_t n, const double* pos0, const uint8_t* col, int64_t step0,
+                 int32_t K, const double* dt_in, double* dt_out, double lambda, const double* seed,
+                 double* L, double* dpos0, double* grads) {
+  const int d = p->dim;
+  size_t nd = (size_t)n * (size_t)d;
+  double* traj = (double*)malloc(sizeof(double) * nd * (size_t)(K + 1));
+  if (!traj) return -1;
+  memcpy(traj, pos0, sizeof(double) * nd);
+  for (int32_t s = 0; s < K; ++s) {
+    double* x = traj + nd * (size_t)(s + 1);
+    memcpy(x, traj + nd * (size_t)s, sizeof(double) * nd);
+    orc_step_info info;
+    if (step_core(p, n, x, col, step0 + s, 1, dt_in ? dt_in + 2 * s : NULL, &info, NULL, NULL, NULL, NULL,
+                  NULL) != 0) { free(traj); return -1; }
+    if (dt_out) { dt_out[2 * s] = info.dt1; dt_out[2 * s + 1] = info.dt2; }
+  }
+  param_bar pb; memset(&pb, 0, sizeof pb);
+  memset(dpos0, 0, sizeof(double) * nd);
+  if (objective_core(p, n, traj + nd * (size_t)K, col, lambda, L, dpos0, pb.poly) != 0) { free(traj); return -1; }
+  if (seed)
+    for (size_t q = 0; q < nd; ++q) dpos0[q] += seed[q];
+  for (int32_t s = K - 1; s >= 0; --s)
+    if (step_vjp(p, n, traj + nd * (size_t)s, col, step0 + s, dt_in ? dt_in + 2 * s : NULL, dpos0, &pb) != 0) {
+      free(traj); return -1;
+    }
+  grads[0] = pb.sigma0; grads[1] = pb.gamma; grads[2] = pb.P0;
+  for (int m = 0; m < 8; ++m) grads[3 + m] = pb.poly[m];
+  free(traj);
   return 0;
 }

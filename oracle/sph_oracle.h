@@ -101,6 +101,29 @@ int orc_step(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, i
              int mode, orc_step_info* info, double* rho, double* acc, double* visc,
              double* pair_abs_a, double* pair_abs_b);
 
+/* orc_step with prescribed step sizes dt = {dt1, dt2} instead of the ones
+ * Eq. time_step_size gives (for finite-difference checks of frozen-step
+ * sensitivities). */
+int orc_step_fixed_dt(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,
+                      int mode, const double* dt, orc_step_info* info);
+
+/* Objective of the sensitivity runs (not in the paper): the density error and
+ * an interface energy,
+ *   L = sum_i (rho_i/rho_t,i - 1)^2 + lambda sum_{i<j, C_i != C_j} W(r_ij, kappa h_ij). */
+int orc_objective(const orc_problem* p, int64_t n, const double* pos, const uint8_t* col, double lambda,
+                  double* L);
+
+/* K steps from pos0 (step counter step0), then L at the end state, then the
+ * hand-written reverse pass. dt_in (2K: dt1, dt2 per step) prescribes the step
+ * sizes ("frozen"); NULL recomputes them from the state and differentiates
+ * that choice too. dt_out (2K, may be NULL) receives the sizes used. seed
+ * (n*dim, may be NULL) is added to dL/dx_K. Outputs: L, dpos0 = dL/dx_0
+ * (n*dim), grads = {dL/dsigma0, dL/dgamma, dL/dP0, dL/dpoly[0..7]} (11), with
+ * rho_scale held fixed. */
+int orc_backward(const orc_problem* p, int64_t n, const double* pos0, const uint8_t* col, int64_t step0,
+                 int32_t K, const double* dt_in, double* dt_out, double lambda, const double* seed,
+                 double* L, double* dpos0, double* grads);
+
 /* Number of OpenMP threads the oracle uses. */
 int orc_num_threads(void);
 
