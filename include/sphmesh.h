@@ -129,6 +129,8 @@ typedef struct {
   double rho_scale;        /* rho_scale in use */
   int32_t error_flags;     /* latched device error bits (1 << sph_status) */
   int32_t n_levels;        /* cell levels of the multi-resolution grid */
+  int64_t list_entries;    /* neighbour-list entries scanned by the last step (sum over i) */
+  int64_t list_rebuilds;   /* neighbour-list builds so far */
 } sph_stats;
 
 typedef struct {
@@ -219,6 +221,53 @@ sph_status sph_sync(sph_handle* h);
  * the size needed. Synchronises. */
 sph_status sph_save(sph_handle* h, void* buf, size_t* nbytes);
 sph_status sph_load(sph_handle* h, const void* buf, size_t nbytes);
+
+/* ---------------------------------------------------------------------------
+ * Sensitivities of a relaxation run (reverse mode). The paper tunes nothing by
+ * gradient; this differentiates K steps of Algorithm 1 (lines 6-16) as the
+ * library computes them, for the objective
+ *   L = w sum_i (rho_i/rho_t,i - 1)^2 + lambda sum_{i<j, C_i != C_j} W(r_ij, kappa h_ij)
+ * at the end state (rho from Eq. density_sum, W the kernel), plus seed . x_K
+ * when a seed (dL/dx_K of an outer loss) is given.
+ *
+ * Step sizes (Eq. time_step_size): with frozen_dt = 0 they are recomputed from
+ * the state and their dependence is differentiated (the global minimum at its
+ * argmin particle); with frozen_dt = 1 they are constants: those of dt_in when
+ * given, else those this run chose.
+ *
+ * Memory: the run keeps a checkpoint of the positions every ckpt_every steps
+ * and recomputes the steps in between during the reverse sweep (FP64, by
+ * particle id: ceil(K / ckpt_every) + ckpt_every + 3 arrays of n x dim
+ * doubles, through the handle's allocator, released before returning).
+ * --------------------------------------------------------------------------- */
+typedef struct {
+  double density_weight; /* w: weight of the density-error term */
+  double lambda;       /* weight of the interface term */
+  int32_t frozen_dt;   /* 1: step sizes are constants; 0: recomputed and differentiated */
+  int32_t ckpt_every;  /* checkpoint interval in steps (>= 1) */
+} sph_objective;
+
+typedef struct {
+  double L;            /* objective at the end state (without the seed term) */
+  double d_sigma0;     /* dL/dsigma0 (through the ramp, if any) */
+  double d_gamma;      /* dL/dgamma (of the general equation of state p = P0 (rho/rho_t)^gamma) */
+  double d_P0;         /* dL/dP0 (0 up to rounding when step sizes are recomputed: the run is P0-free) */
+  double d_poly[8];    /* dL/dpoly[m], rho_scale held fixed */
+} sph_grad;
+
+/* From the handle's current state x_0 (step counter t), run K steps, evaluate
+ * L at x_K and return the gradient: dpos0 (n x dim doubles, particle-id
+ * order) = dL/dx_0 and *grad. The handle is left at x_K with counter t + K, as
+ * after sph_step(h, K).
+ *
+ * Arguments: obj (not NULL); seed (n x dim, particle-id order) or NULL;
+ * dt_in (2K doubles: dt1, dt2 per step) or NULL; dt_out (2K) or NULL receives
+ * the step sizes used. seed, dt_in, dt_out and dpos0 live in device memory
+ * when on_device = 1, else in host memory. Errors: INVALID_ARG (K < 0,
+ * ckpt_every < 1, null obj/dpos0/grad, dt_in with frozen_dt = 0), OOM, and the
+ * device errors of sph_step. Synchronises. */
+sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, const double* seed,
+                        const double* dt_in, double* dt_out, double* dpos0, int32_t on_device, sph_grad* grad);
 
 /* Message of the last failing call on this handle (never NULL). */
 const char* sph_last_error(const sph_handle* h);

@@ -175,6 +175,29 @@ class Relaxation:
         self._check(self.lib.sph_get_positions(self.h, x.ctypes.data, 0))
         return x
 
+    GRAD_NAMES = ("sigma0", "gamma", "P0") + tuple(f"poly{m}" for m in range(8))
+
+    def backward(self, n_steps, lam=1.0, frozen_dt=False, ckpt_every=5, seed=None, dt=None, density_weight=1.0):
+        """Sensitivities of L (density_weight * density error + lam * interface
+        energy) after n_steps steps from the current state; the handle ends at
+        the final state.
+        seed: optional (n, dim) dL/dx_K of an outer loss; dt: optional (n_steps, 2)
+        prescribed step sizes (implies frozen_dt). Returns dict(L, dpos0 (n, dim),
+        grads {name: value}, dt (n_steps, 2))."""
+        obj = B.sph_objective(float(density_weight), float(lam), 1 if (frozen_dt or dt is not None) else 0,
+                              int(ckpt_every))
+        g = B.sph_grad()
+        dpos = np.zeros((self.n, self.dim), np.float64)
+        dt_out = np.zeros((max(int(n_steps), 0), 2), np.float64)
+        sd = None if seed is None else np.ascontiguousarray(seed, dtype=np.float64)
+        di = None if dt is None else np.ascontiguousarray(dt, dtype=np.float64)
+        self._check(self.lib.sph_backward(self.h, int(n_steps), C.byref(obj),
+                                          None if sd is None else sd.ctypes.data,
+                                          None if di is None else di.ctypes.data,
+                                          dt_out.ctypes.data, dpos.ctypes.data, 0, C.byref(g)))
+        grads = dict(zip(self.GRAD_NAMES, [g.d_sigma0, g.d_gamma, g.d_P0] + list(g.d_poly)))
+        return dict(L=g.L, dpos0=dpos, grads=grads, dt=dt_out)
+
     def colors(self):
         c = np.empty(self.n, np.uint8)
         self._check(self.lib.sph_get_colors(self.h, c.ctypes.data, 0))
@@ -230,3 +253,34 @@ class Relaxation:
         n = C.c_int64(); d = C.c_int32(); rs = C.c_double()
         self._check(self.lib.sph_get_info(self.h, C.byref(n), C.byref(d), C.byref(rs)))
         return dict(n=n.value, dim=d.value, rho_scale=rs.value)
+
+
+def relax_fn(relaxation, n_steps, frozen_dt=True, ckpt_every=5):
+    """A torch.autograd function x0 -> x_K (n_steps steps of `relaxation`):
+    forward runs the steps from x0 (a CUDA float64 (n, dim) tensor, colours
+    kept), backward returns dL/dx0 for the incoming dL/dx_K through
+    sph_backward with both objective weights 0 (the seed alone)."""
+    import torch
+
+    class _Relax(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x0):
+            col = torch.from_numpy(relaxation.colors()).to(x0.device)
+            ctx.save_for_backward(x0.detach().clone(), col)
+            relaxation.set_state(x0.detach().to(torch.float64).contiguous(), col)
+            relaxation.step(n_steps)
+            out = torch.empty_like(x0, dtype=torch.float64)
+            relaxation.positions(out=out)
+            torch.cuda.current_stream().wait_stream(relaxation.stream)
+            return out
+
+        @staticmethod
+        def backward(ctx, gout):
+            x0, col = ctx.saved_tensors
+            relaxation.set_state(x0.to(torch.float64).contiguous(), col)
+            seed = gout.detach().to(torch.float64).contiguous().cpu().numpy()
+            r = relaxation.backward(n_steps, lam=0.0, density_weight=0.0, frozen_dt=frozen_dt,
+                                    ckpt_every=ckpt_every, seed=seed)
+            return torch.from_numpy(r["dpos0"]).to(gout.device, gout.dtype)
+
+    return _Relax.apply

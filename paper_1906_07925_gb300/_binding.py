@@ -55,7 +55,8 @@ class sph_stats(C.Structure):
                 ("min_rc_over_a", C.c_double), ("max_a", C.c_double), ("sum_rho", C.c_double),
                 ("err_l2", C.c_double), ("err_max", C.c_double), ("interface_pairs", C.c_int64),
                 ("force_pairs", C.c_int64), ("wall_moved", C.c_int64), ("rho_scale", C.c_double),
-                ("error_flags", C.c_int32), ("n_levels", C.c_int32)]
+                ("error_flags", C.c_int32), ("n_levels", C.c_int32),
+                ("list_entries", C.c_int64), ("list_rebuilds", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -65,6 +66,16 @@ class sph_grid_info(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("dim", C.c_int32), ("lo", C.c_double * 3), ("h0", C.c_double),
                 ("lip_h", C.c_double), ("cell", C.c_double * 8), ("dims", (C.c_int32 * 3) * 8),
                 ("base", C.c_uint32 * 9)]
+
+
+class sph_objective(C.Structure):
+    _fields_ = [("density_weight", C.c_double), ("lambda_", C.c_double), ("frozen_dt", C.c_int32),
+                ("ckpt_every", C.c_int32)]
+
+
+class sph_grad(C.Structure):
+    _fields_ = [("L", C.c_double), ("d_sigma0", C.c_double), ("d_gamma", C.c_double), ("d_P0", C.c_double),
+                ("d_poly", C.c_double * 8)]
 
 
 H = C.c_void_p
@@ -109,6 +120,8 @@ def load():
             "sph_save": [H, C.c_void_p, P(C.c_size_t)],
             "sph_load": [H, C.c_void_p, C.c_size_t],
             "sph_get_info": [H, P(C.c_int64), P(C.c_int32), P(C.c_double)],
+            "sph_backward": [H, C.c_int32, P(sph_objective), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                             C.c_int32, P(sph_grad)],
             "sph_eval_forces_noalloc": [P(sph_domain), P(sph_field), P(sph_params), C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
         }

@@ -1,0 +1,7 @@
+// 2D instantiations of the reverse-pass kernels (float, double).
+#include "sph_adjoint_impl.cuh"
+
+namespace sph {
+SPH_INSTANTIATE_ADJOINT(2, float)
+SPH_INSTANTIATE_ADJOINT(2, double)
+}  // namespace sph

@@ -43,6 +43,15 @@ struct sph_handle {
   bool recorded = false;
   cudaGraphExec_t gexec = nullptr;
   int graph_record = -1;
+  // reverse-pass buffers (allocated by the first sph_backward)
+  struct {
+    bool ready = false;
+    void *xb = nullptr, *atb = nullptr, *ab = nullptr, *hb = nullptr, *Tb = nullptr, *rtb = nullptr,
+         *rhob = nullptr;
+    double *part = nullptr, *acc = nullptr, *g[2] = {nullptr, nullptr};
+    unsigned* ticket = nullptr;
+    uint8_t* col = nullptr;  // colours by particle id
+  } adj;
   std::string err;
 };
 
@@ -117,12 +126,16 @@ int auto_capacity(const sph_handle* h) {
   return (cap + 7) & ~7;
 }
 
-// one relaxation step on the handle's stream
-sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEvent_t* ev = nullptr) {
+// one relaxation step on the handle's stream; dt_fix (device, may be null)
+// prescribes {dt1, dt2}, dt_rec (device, may be null) receives them
+sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEvent_t* ev = nullptr,
+                       const double* dt_fix = nullptr, double* dt_rec = nullptr) {
   DevState& S = h->S;
   PassFlags f;
   f.general_eos = h->par.gamma != 2.0;
   f.record = record;
+  f.dt_fix = dt_fix;
+  f.dt_rec = dt_rec;
   const bool f64 = h->prec == SPH_PREC_FP64;
   cudaError_t e = cudaSuccess;
   if (ev) e = cudaEventRecord(ev[0], h->stream);
@@ -276,6 +289,163 @@ struct Temp {
     }
   }
 };
+
+// ------------------------------------------------------- reverse pass --
+// state from positions by id (device) at step counter `step`; the next gate
+// rebuilds the list
+sph_status set_state_at(sph_handle* h, const double* xyz_dev, const uint8_t* col_dev, int64_t step) {
+  const bool f64 = h->prec == SPH_PREC_FP64;
+  cudaError_t e;
+  if (h->dim == 2)
+    e = f64 ? launch_set_state<2, double>(h->S, h->Fd, xyz_dev, col_dev, h->stream)
+            : launch_set_state<2, float>(h->S, h->Ff, xyz_dev, col_dev, h->stream);
+  else
+    e = f64 ? launch_set_state<3, double>(h->S, h->Fd, xyz_dev, col_dev, h->stream)
+            : launch_set_state<3, float>(h->S, h->Ff, xyz_dev, col_dev, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
+  h->steps = step;
+  h->recorded = false;
+  return write_ctl_all(h);
+}
+
+sph_status positions_to(sph_handle* h, double* dst_dev) {
+  const bool f64 = h->prec == SPH_PREC_FP64;
+  cudaError_t e;
+  if (h->dim == 2)
+    e = f64 ? launch_get_positions<2, double>(h->S, h->Fd, dst_dev, h->stream)
+            : launch_get_positions<2, float>(h->S, h->Ff, dst_dev, h->stream);
+  else
+    e = f64 ? launch_get_positions<3, double>(h->S, h->Fd, dst_dev, h->stream)
+            : launch_get_positions<3, float>(h->S, h->Ff, dst_dev, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "get_positions");
+  return SPH_OK;
+}
+
+// list rebuild at the current state (then the forward quantities of the step
+// when `forward`: pass A without advancing, pass B recording a~ without moving)
+sph_status reverse_setup(sph_handle* h, bool forward, const double* dt_fix) {
+  DevState& S = h->S;
+  PassFlags f;
+  f.general_eos = h->par.gamma != 2.0;
+  f.record = 1;
+  f.advance = 0;
+  f.move = 0;
+  f.dt_fix = dt_fix;
+  const bool f64 = h->prec == SPH_PREC_FP64;
+  cudaError_t e = launch_gate(S, 1, h->stream);
+  if (e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+              : launch_rebuild<2, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
+    else
+      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+              : launch_rebuild<3, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
+  }
+  if (forward && e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_pass_a<2, double>(S, h->Fd, h->Pd, f, h->stream)
+              : launch_pass_a<2, float>(S, h->Ff, h->Pf, f, h->stream);
+    else
+      e = f64 ? launch_pass_a<3, double>(S, h->Fd, h->Pd, f, h->stream)
+              : launch_pass_a<3, float>(S, h->Ff, h->Pf, f, h->stream);
+  }
+  if (forward && e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_pass_b<2, double>(S, h->Fd, h->Pd, h->geod, f, h->stream)
+              : launch_pass_b<2, float>(S, h->Ff, h->Pf, h->geof, f, h->stream);
+    else
+      e = f64 ? launch_pass_b<3, double>(S, h->Fd, h->Pd, h->geod, f, h->stream)
+              : launch_pass_b<3, float>(S, h->Ff, h->Pf, h->geof, f, h->stream);
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "reverse set-up");
+  return SPH_OK;
+}
+
+sph_status ensure_adj(sph_handle* h) {
+  if (h->adj.ready) return SPH_OK;
+  const size_t N = (size_t)h->n, d = (size_t)h->dim;
+  const size_t t1 = h->prec == SPH_PREC_FP64 ? 8 : 4, v4 = 4 * t1;
+  const size_t nb = N / 256 + 2;
+  auto& a = h->adj;
+  uint8_t* p = nullptr;
+  SPH_TRY(grab(h, p, N * 32)); a.xb = p;
+  SPH_TRY(grab(h, p, N * v4)); a.atb = p;
+  SPH_TRY(grab(h, p, N * v4)); a.ab = p;
+  SPH_TRY(grab(h, p, N * t1)); a.hb = p;
+  SPH_TRY(grab(h, p, N * t1)); a.Tb = p;
+  SPH_TRY(grab(h, p, N * t1)); a.rtb = p;
+  SPH_TRY(grab(h, p, N * t1)); a.rhob = p;
+  SPH_TRY(grab(h, a.part, nb * kAdjPartials));
+  SPH_TRY(grab(h, a.acc, (size_t)kAdjSlots));
+  SPH_TRY(grab(h, a.g[0], N * d));
+  SPH_TRY(grab(h, a.g[1], N * d));
+  SPH_TRY(grab(h, a.ticket, 4));
+  SPH_TRY(grab(h, a.col, N));
+  SPH_CUDA(h, cudaMemsetAsync(a.ticket, 0, 16, h->stream));
+  a.ready = true;
+  return SPH_OK;
+}
+
+template <class T>
+AdjBufs<T> adj_bufs(sph_handle* h, const double* gin, double* gout) {
+  AdjBufs<T> B;
+  auto& a = h->adj;
+  B.gin = gin;
+  B.gout = gout;
+  B.xb = (V4<double>*)a.xb;
+  B.atb = (V4<T>*)a.atb;
+  B.ab = (V4<T>*)a.ab;
+  B.hb = (T*)a.hb;
+  B.Tb = (T*)a.Tb;
+  B.rtb = (T*)a.rtb;
+  B.rhob = (T*)a.rhob;
+  B.part = a.part;
+  B.acc = a.acc;
+  B.ticket = a.ticket;
+  return B;
+}
+
+sph_status run_objective(sph_handle* h, double wd, double lambda, const double* seed, double* gout) {
+  cudaError_t e;
+  const bool f64 = h->prec == SPH_PREC_FP64;
+  if (h->dim == 2)
+    e = f64 ? launch_objective<2, double>(h->S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, seed, gout), wd,
+                                          lambda, h->stream)
+            : launch_objective<2, float>(h->S, h->Ff, h->Pf, h->geod, adj_bufs<float>(h, seed, gout), wd,
+                                         lambda, h->stream);
+  else
+    e = f64 ? launch_objective<3, double>(h->S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, seed, gout), wd,
+                                          lambda, h->stream)
+            : launch_objective<3, float>(h->S, h->Ff, h->Pf, h->geod, adj_bufs<float>(h, seed, gout), wd,
+                                         lambda, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "objective");
+  return SPH_OK;
+}
+
+sph_status run_bwd_step(sph_handle* h, const double* gin, double* gout, int recomputed, double ramp) {
+  cudaError_t e;
+  const bool f64 = h->prec == SPH_PREC_FP64;
+  const int gen = h->par.gamma != 2.0;
+  if (h->dim == 2)
+    e = f64 ? launch_bwd_step<2, double>(h->S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, gin, gout), recomputed,
+                                         gen, ramp, h->stream)
+            : launch_bwd_step<2, float>(h->S, h->Ff, h->Pf, h->geod, adj_bufs<float>(h, gin, gout), recomputed, gen,
+                                        ramp, h->stream);
+  else
+    e = f64 ? launch_bwd_step<3, double>(h->S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, gin, gout), recomputed,
+                                         gen, ramp, h->stream)
+            : launch_bwd_step<3, float>(h->S, h->Ff, h->Pf, h->geod, adj_bufs<float>(h, gin, gout), recomputed, gen,
+                                        ramp, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "reverse step");
+  return SPH_OK;
+}
+
+// sigma(t)/sigma0 (Eq. sph_st_sigma with sigma0 = 1)
+double ramp_at(const sph_handle* h, int64_t t) {
+  if (h->t0 < 0.0 || (double)t <= h->t0) return 1.0;
+  if ((double)t <= h->t1) return 1.0 - (h->t0 - (double)t) / (h->t0 - h->t1);
+  return 0.0;
+}
 
 }  // namespace
 
@@ -543,6 +713,8 @@ sph_status sph_get_stats(sph_handle* h, sph_stats* out) {
   int flags = 0;
   SPH_CUDA(h, cudaMemcpyAsync(&sc, h->S.scal, sizeof sc, cudaMemcpyDeviceToHost, h->stream));
   SPH_CUDA(h, cudaMemcpyAsync(&flags, h->S.err, sizeof flags, cudaMemcpyDeviceToHost, h->stream));
+  StepCtl ctl{};
+  SPH_CUDA(h, cudaMemcpyAsync(&ctl, h->S.ctl, sizeof ctl, cudaMemcpyDeviceToHost, h->stream));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   memset(out, 0, sizeof *out);
   out->step = h->steps;
@@ -560,6 +732,8 @@ sph_status sph_get_stats(sph_handle* h, sph_stats* out) {
   out->rho_scale = h->rho_scale;
   out->error_flags = flags;
   out->n_levels = h->hg.n_levels;
+  out->list_entries = sc.lentries;
+  out->list_rebuilds = ctl.rebuilds;
   return status_from_flags(h, flags);
 }
 
@@ -695,6 +869,100 @@ sph_status sph_load(sph_handle* h, const void* buf, size_t nbytes) {
   h->t0 = sched[0];
   h->t1 = sched[1];
   return write_ctl_sched(h);
+}
+
+sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, const double* seed,
+                        const double* dt_in, double* dt_out, double* dpos0, int32_t on_device, sph_grad* grad) {
+  if (!h || !obj || !grad || (h->n > 0 && !dpos0)) return fail(h, SPH_ERR_INVALID_ARG, "null argument");
+  if (K < 0 || obj->ckpt_every < 1) return fail(h, SPH_ERR_INVALID_ARG, "K < 0 or ckpt_every < 1");
+  if (dt_in && !obj->frozen_dt) return fail(h, SPH_ERR_INVALID_ARG, "dt_in needs frozen_dt = 1");
+  memset(grad, 0, sizeof *grad);
+  const size_t N = (size_t)h->n, d = (size_t)h->dim, nd = N * d;
+  const int64_t t0 = h->steps;
+  if (N == 0) {
+    h->steps += K;
+    return write_ctl_sched(h);
+  }
+  SPH_TRY(ensure_adj(h));
+  auto& a = h->adj;
+  const int c = obj->ckpt_every;
+  const int nck = K > 0 ? (K + c - 1) / c : 0;
+  const size_t nseg = (size_t)std::min(c, std::max(K, 1));
+  // device scratch: checkpoints, the segment being reversed, x_K, step sizes, host-side inputs
+  Temp tck(h, sizeof(double) * nd * (size_t)std::max(nck, 1)), tseg(h, sizeof(double) * nd * nseg),
+      txk(h, sizeof(double) * nd), tdt(h, sizeof(double) * 2 * (size_t)std::max(K, 1)),
+      tseed(h, (seed && !on_device) ? sizeof(double) * nd : 0);
+  if (!tck.p || !tseg.p || !txk.p || !tdt.p || !tseed.p)
+    return fail(h, SPH_ERR_OOM, "reverse-pass scratch allocation failed");
+  double* ck = (double*)tck.p;
+  double* sg = (double*)tseg.p;
+  double* xk = (double*)txk.p;
+  double* dts = (double*)tdt.p;
+  const double* seed_d = seed;
+  if (seed && !on_device) {
+    SPH_CUDA(h, cudaMemcpyAsync(tseed.p, seed, sizeof(double) * nd, cudaMemcpyHostToDevice, h->stream));
+    seed_d = (const double*)tseed.p;
+  }
+  if (dt_in) {
+    SPH_CUDA(h, cudaMemcpyAsync(dts, dt_in, sizeof(double) * 2 * (size_t)K,
+                                on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  }
+  SPH_CUDA(h, cudaMemsetAsync(h->S.err, 0, sizeof(int), h->stream));
+  SPH_CUDA(h, cudaMemsetAsync(a.acc, 0, sizeof(double) * kAdjSlots, h->stream));
+  if (launch_get_colors(h->S, a.col, h->stream) != cudaSuccess) return fail(h, SPH_ERR_CUDA, "colours");
+  // forward run with checkpoints; the step sizes are recorded (or prescribed)
+  for (int s = 0; s < K; ++s) {
+    if (s % c == 0) SPH_TRY(positions_to(h, ck + nd * (size_t)(s / c)));
+    SPH_TRY(launch_step(h, 0, 0, nullptr, dt_in ? dts + 2 * s : nullptr, dt_in ? nullptr : dts + 2 * s));
+    h->steps += 1;
+  }
+  SPH_TRY(positions_to(h, xk));
+  // objective at x_K: the gradient seed
+  int cur = 0;
+  SPH_TRY(reverse_setup(h, false, nullptr));
+  SPH_TRY(run_objective(h, obj->density_weight, obj->lambda, seed_d, a.g[cur]));
+  // reverse sweep, segment by segment
+  for (int seg = nck - 1; seg >= 0; --seg) {
+    const int s0 = seg * c, s1 = std::min(K, s0 + c);
+    SPH_CUDA(h, cudaMemcpyAsync(sg, ck + nd * (size_t)seg, sizeof(double) * nd, cudaMemcpyDeviceToDevice,
+                                h->stream));
+    if (s1 - s0 > 1) {
+      SPH_TRY(set_state_at(h, sg, a.col, t0 + s0));
+      for (int s = s0; s < s1 - 1; ++s) {
+        SPH_TRY(launch_step(h, 0, 0, nullptr, dts + 2 * s, nullptr));
+        SPH_TRY(positions_to(h, sg + nd * (size_t)(s - s0 + 1)));
+      }
+    }
+    for (int s = s1 - 1; s >= s0; --s) {
+      SPH_TRY(set_state_at(h, sg + nd * (size_t)(s - s0), a.col, t0 + s));
+      SPH_TRY(reverse_setup(h, true, obj->frozen_dt ? dts + 2 * s : nullptr));
+      SPH_TRY(run_bwd_step(h, a.g[cur], a.g[1 - cur], !obj->frozen_dt, ramp_at(h, t0 + s)));
+      cur = 1 - cur;
+    }
+  }
+  // results
+  double acc[kAdjSlots];
+  SPH_CUDA(h, cudaMemcpyAsync(acc, a.acc, sizeof acc, cudaMemcpyDeviceToHost, h->stream));
+  if (on_device) {
+    SPH_CUDA(h, cudaMemcpyAsync(dpos0, a.g[cur], sizeof(double) * nd, cudaMemcpyDeviceToDevice, h->stream));
+    if (dt_out && K > 0)
+      SPH_CUDA(h, cudaMemcpyAsync(dt_out, dts, sizeof(double) * 2 * (size_t)K, cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    SPH_CUDA(h, cudaMemcpyAsync(dpos0, a.g[cur], sizeof(double) * nd, cudaMemcpyDeviceToHost, h->stream));
+    if (dt_out && K > 0)
+      SPH_CUDA(h, cudaMemcpyAsync(dt_out, dts, sizeof(double) * 2 * (size_t)K, cudaMemcpyDeviceToHost, h->stream));
+  }
+  // leave the handle at x_K
+  SPH_TRY(set_state_at(h, xk, a.col, t0 + K));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  grad->L = acc[kAdjL];
+  grad->d_sigma0 = acc[kAdjSigma0];
+  grad->d_gamma = acc[kAdjGamma];
+  grad->d_P0 = acc[kAdjP0];
+  for (int m = 0; m < 8; ++m) grad->d_poly[m] = acc[kAdjPoly + m];
+  int flags = 0;
+  SPH_TRY(read_flags(h, &flags));
+  return status_from_flags(h, flags);
 }
 
 const char* sph_last_error(const sph_handle* h) { return h ? h->err.c_str() : "null handle"; }

@@ -47,7 +47,7 @@ struct Grid {
   T cellv[kMaxLevels];   // cell edge in view units
   T inv_h0;              // level(h) = floor(log2(h / h0)), h physical
   T lip_h;               // |grad h| bound: neighbours' h within h_i +- lip_h r
-  T rfac;                // kappa h_i rfac covers r < kappa max(h_i, h_ij)
+  T rfac;                // kappa h_i rfac covers r < kappa max(h_i, h_j)
 };
 
 // Position frames. The state of a particle is an int64 coordinate per axis,
@@ -87,13 +87,16 @@ struct Phys {
 struct Partial {
   double min_rc_a, max_a, sum_rho, err_l2, err_max;
   long long ipairs, fpairs;
-  double pad;
+  long long lentries;  // neighbour-list entries scanned
+  long long amin;      // index (current order) of min_rc_a; -1: none
 };
 
 // Step scalars written by the last block of pass A, read by pass B.
 struct Scalars {
   double dt1, dt2, min_rc_a, max_a, sum_rho, err_l2, err_max, sigma;
   long long ipairs, fpairs, wall_moved, step_of_stats;
+  long long lentries;
+  long long argmin;  // particle (current order) where min r_c/|a| sits; -1: none
 };
 
 // Surface-tension schedule (Eq. sph_st_sigma), step counter and the

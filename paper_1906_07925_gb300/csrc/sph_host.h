@@ -110,7 +110,7 @@ inline std::string grid_setup(const sph_domain& dom, double kappa, double cell_f
   const double cf = cell_factor > 0 ? cell_factor : 1.0;
   const double h0 = hmin * 0.98;
   if (!(h0 > 0)) return "target field gives a non-positive smoothing length";
-  if (kappa * lip_h >= 1.5) return "target field varies too fast (kappa |grad h| >= 1.5)";
+  if (kappa * lip_h >= 0.75) return "target field varies too fast (kappa |grad h| >= 0.75)";
   double ext = 0.0;
   for (int k = 0; k < d; ++k) ext = std::max(ext, dom.hi[k] - dom.lo[k]);
   const double q64 = std::ldexp(std::exp2(std::ceil(std::log2(ext))), -62);
@@ -141,7 +141,8 @@ inline std::string grid_setup(const sph_domain& dom, double kappa, double cell_f
       G.q64 = q64;
       G.h0 = h0;
       G.lip_h = lip_h;
-      G.rfac = (1.0 + 1e-5) / (1.0 - 0.5 * kappa * lip_h);
+      // r < kappa h_j <= kappa (h_i + lip_h r)  =>  r < kappa h_i / (1 - kappa lip_h)
+      G.rfac = (1.0 + 1e-5) / (1.0 - kappa * lip_h);
       return "";
     }
   }

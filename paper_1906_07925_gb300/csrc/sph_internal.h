@@ -59,6 +59,9 @@ struct PassFlags {
   int record = 0;       // keep rho and a~ for output
   int nbr_debug = 0;    // write neighbour-set sizes and id sums by particle id
   int advance = 1;      // count this pass as a step (sigma schedule, counter)
+  int move = 1;         // pass B: integrate (0: only a~, for the reverse pass)
+  const double* dt_fix = nullptr;  // pass A: prescribed {dt1, dt2} (device)
+  double* dt_rec = nullptr;        // pass A: record {dt1, dt2} (device)
 };
 
 template <int D, class T>
@@ -76,6 +79,48 @@ template <int D, class T>
 cudaError_t launch_get_positions(const DevState& S, const Frame<T>& F, double* out, cudaStream_t st);
 template <int D, class T>
 cudaError_t launch_get_fields(const DevState& S, int which, double* out, cudaStream_t st);
+
+// accumulated results (double slots of AdjBufs::acc)
+enum AdjSlot : int {
+  kAdjL = 0,       // objective value
+  kAdjSigma0 = 1,  // dL/dsigma0
+  kAdjGamma = 2,
+  kAdjP0 = 3,
+  kAdjPoly = 4,    // 8 slots: dL/dpoly[m]
+  kAdjDt1b = 12,   // per step: adjoint of dt1 (reset by k_bwd_out)
+  kAdjDt2b = 13,   // per step: adjoint of dt2
+  kAdjMbar = 14,   // per step: adjoint of m = min r_c/|a|
+  kAdjSlots = 16
+};
+constexpr int kAdjPartials = 12;  // doubles per block partial
+
+template <class T>
+struct AdjBufs {
+  const double* gin = nullptr;  // n x D by id: adjoint of the state the step produced (or the seed)
+  double* gout = nullptr;       // n x D by id: adjoint of the state it started from
+  V4<double>* xb = nullptr;     // current order: adjoint of x (accumulating)
+  V4<T>* atb = nullptr;         // adjoint of a~
+  V4<T>* ab = nullptr;          // adjoint of a
+  T* hb = nullptr;              // adjoint of h
+  T* Tb = nullptr;              // adjoint of T = 1/rho_t^2
+  T* rtb = nullptr;             // adjoint of rho_t
+  T* rhob = nullptr;            // adjoint of rho
+  double* part = nullptr;       // kAdjPartials per block
+  double* acc = nullptr;        // kAdjSlots
+  unsigned* ticket = nullptr;
+};
+
+// reverse pass of one step: the step's state, list and forward quantities
+// (pass A with advance = 0, pass B with move = 0 and record = 1) in place;
+// B.gin -> B.gout. ramp = sigma(t)/sigma0 of the step.
+template <int D, class T>
+cudaError_t launch_bwd_step(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<double>& geo,
+                            const AdjBufs<T>& B, int recomputed_dt, int general_eos, double ramp, cudaStream_t st);
+// objective at the current state (list in place) and its gradient -> B.gout;
+// B.gin (may be null) is an extra seed added to dL/dx
+template <int D, class T>
+cudaError_t launch_objective(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<double>& geo,
+                             const AdjBufs<T>& B, double wd, double lambda, cudaStream_t st);
 
 // initial sampling (create)
 struct FieldBounds {

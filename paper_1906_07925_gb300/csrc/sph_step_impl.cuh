@@ -9,8 +9,10 @@
 // a pair vector is relative to the pair distance, not to the domain size.
 //
 // Neighbour list (Algorithm 1, line 8). The list of particle i holds every j
-// (itself included) that can come within kappa max(h_i, h_ij) before some
+// (itself included) that can come within kappa max(h_i, h_j) before some
 // particle has moved half its skin; it is rebuilt, on the device, only then.
+// The criterion is symmetric, so i also finds every j whose own support
+// reaches i (the reverse pass gathers over such pairs).
 // Passes A and B re-test the exact criteria of the current step for every
 // listed pair, so the list only saves the search, never changes a result.
 #pragma once
@@ -19,6 +21,11 @@
 #include <type_traits>
 
 #include "sph_internal.h"
+
+// resident 256-thread blocks per SM asked of the pair passes (caps registers)
+#ifndef SPH_PASS_MIN_BLOCKS
+#define SPH_PASS_MIN_BLOCKS 5
+#endif
 
 namespace sph {
 
@@ -141,30 +148,46 @@ __device__ __forceinline__ long long warp_sum(long long v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+// minimum and where it sits; ties go to the smaller index (order-independent)
+__device__ __forceinline__ void argmin_merge(double& v, long long& k, double ov, long long ok) {
+  if (ov < v || (ov == v && ok < k)) {
+    v = ov;
+    k = ok;
+  }
+}
+__device__ __forceinline__ void warp_argmin(double& v, long long& k) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const long long ok = __shfl_xor_sync(0xffffffffu, k, o);
+    argmin_merge(v, k, ov, ok);
+  }
+}
 
 // fixed-order block reduction of a Partial (deterministic); valid in warp 0
 __device__ __forceinline__ Partial block_reduce(Partial p, Partial* sm) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  p.min_rc_a = warp_min(p.min_rc_a);
+  warp_argmin(p.min_rc_a, p.amin);
   p.max_a = warp_max(p.max_a);
   p.sum_rho = warp_sum(p.sum_rho);
   p.err_l2 = warp_sum(p.err_l2);
   p.err_max = warp_max(p.err_max);
   p.ipairs = warp_sum(p.ipairs);
   p.fpairs = warp_sum(p.fpairs);
+  p.lentries = warp_sum(p.lentries);
   if (lane == 0) sm[w] = p;
   __syncthreads();
   if (w == 0) {
     Partial q;
     if (lane < nw) q = sm[lane];
-    else q = Partial{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0.0};
-    q.min_rc_a = warp_min(q.min_rc_a);
+    else q = Partial{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, -1};
+    warp_argmin(q.min_rc_a, q.amin);
     q.max_a = warp_max(q.max_a);
     q.sum_rho = warp_sum(q.sum_rho);
     q.err_l2 = warp_sum(q.err_l2);
     q.err_max = warp_max(q.err_max);
     q.ipairs = warp_sum(q.ipairs);
     q.fpairs = warp_sum(q.fpairs);
+    q.lentries = warp_sum(q.lentries);
     p = q;
   }
   __syncthreads();
@@ -214,7 +237,7 @@ __global__ void __launch_bounds__(256) k_make_view(int n, const StepCtl* __restr
 }
 
 // Neighbour list of each particle: every j (itself included) with
-//   r < kappa max(h_i, h_ij) (1 + 1e-5) + kappa lip_h s_max / 2 + s_max,
+//   r < kappa max(h_i, h_j) (1 + 1e-5) + kappa lip_h s_max / 2 + s_max,
 // s = skin (kappa folded) of i and j: after both moved at most half their skin
 // (and h changed by at most lip_h times that), any pair inside the exact
 // criteria is still listed. Candidates come from rows of cells of every level
@@ -246,7 +269,7 @@ __global__ void __launch_bounds__(256) k_list_build(int n, const StepCtl* __rest
   for (int it = 0; it < 2; ++it) {
     hhi = hv * T(1.00001) + lip * Rs;
     const T shi = sk * hhi / hv;
-    Rs = kappa * T(0.5) * (hv + hhi) * G.rfac + shi * (T(1) + T(0.5) * kappa * lip);
+    Rs = kappa * hhi * G.rfac + shi * (T(1) + T(0.5) * kappa * lip);
     Rs = Rs > kappa * hv * G.rfac ? Rs : kappa * hv * G.rfac;
   }
   const T hlo = hv * T(0.99999) - lip * Rs;
@@ -306,7 +329,7 @@ __global__ void __launch_bounds__(256) k_list_build(int n, const StepCtl* __rest
           const T hj = view_h(vj);
           const T skj = sk * hj / hv;
           const T smax = sk > skj ? sk : skj;
-          const T hm = hv > T(0.5) * (hv + hj) ? hv : T(0.5) * (hv + hj);
+          const T hm = hv > hj ? hv : hj;  // symmetric: j lists i whenever i lists j
           // h_j is known here: only rounding and the h change over the skin need a margin
           const T Rl = kappa * hm * T(1.00001) + smax * (T(1) + T(0.5) * kappa * lip);
           if (r2 < Rl * Rl) {
@@ -398,7 +421,7 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
 // (Eq. time_step_size, see below).
 // --------------------------------------------------------------------------
 template <int D, class T, bool GENERAL, bool DBG>
-__global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
+__global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, StepCtl* ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
@@ -410,7 +433,8 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
                                                 Scalars* __restrict__ scal, unsigned* __restrict__ ticket,
                                                 int* __restrict__ err, int advance, int* __restrict__ dbg_count,
                                                 long long* __restrict__ dbg_sum, uint32_t* __restrict__ plist,
-                                                uint32_t* __restrict__ pcount) {
+                                                uint32_t* __restrict__ pcount, const double* __restrict__ dt_fix,
+                                                double* __restrict__ dt_rec) {
   using VT = typename ViewOf<T>::type;
   __shared__ Partial sm[8];
   __shared__ bool last;
@@ -420,7 +444,7 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
   const int buf = cc.buf;
   const VT* __restrict__ view = cc.vp ? v1 : v0;
   const T sigma = (T)sigma_of(cc, step);
-  Partial part{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0.0};
+  Partial part{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, -1};
   if (i < n) {
     const uint32_t* __restrict__ pid = buf ? p1 : p0;
     const VT vi = view[i];
@@ -438,33 +462,26 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
     long long sd = 0, sf = 0;
     const uint32_t lc = lcount[i];
     const int cnt = (int)(lc & ~kFastBit);
-    // 1) this step's pairs: a cheap test of every skin-list entry, the pairs
-    //    inside either support compacted into column i of plist (the expensive
-    //    pair arithmetic then runs only for them, with all lanes busy)
-    int np = 0;
-    auto scan = [&](auto fastc) {
+    // Every skin-list entry: a screening test on the coarse vectors (when the
+    // list build certified them), then the exact vectors and criteria for the
+    // pairs that pass. This step's force pairs go to column i of plist.
+    auto loop = [&](auto fastc) {
       constexpr bool FAST = decltype(fastc)::value;
       for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
-        const T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
-        const T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
-        const T r2 = dx * dx + dy * dy + dz * dz;
-        const T Hf = half_kappa * (hv + view_h(vj));
-        const T Hm = screen_radius<T>(GENERAL || Hf > Hd ? Hf : Hd);
-        if (r2 < Hm * Hm) plist[(size_t)np++ * n + i] = e;
-      });
-    };
-    if (lc & kFastBit) scan(std::true_type{});
-    else scan(std::false_type{});
-    if (pcount) pcount[i] = (uint32_t)np;
-    // 2) density, pressure and surface tension over those pairs (exact criteria)
-    {
-      for_list(plist, view, n, i, np, [&](uint32_t e, const VT& vj) {
         const int j = (int)(e >> 8);
-        const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
-        const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
-        const T r2 = dx * dx + dy * dy + dz * dz;
+        T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
+        T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
+        T r2 = dx * dx + dy * dy + dz * dz;
         const T hj = view_h(vj);
         const T Hf = half_kappa * (hv + hj);
+        if (FAST) {
+          const T Hm = screen_radius<T>(GENERAL || Hf > Hd ? Hf : Hd);
+          if (!(r2 < Hm * Hm)) return;
+          dx = vd<false>(F, vi.x, vj.x);
+          dy = vd<false>(F, vi.y, vj.y);
+          dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+          r2 = dx * dx + dy * dy + dz * dz;
+        }
         const bool inD = !GENERAL && r2 < Hd2;
         const bool inF = r2 < Hf * Hf && j != i;
         if (!(inD || inF)) return;
@@ -492,12 +509,16 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
           ax += s * dx;
           ay += s * dy;
           az += s * dz;
+          plist[(size_t)nf * n + i] = e;  // this step's force pairs, for pass B
           ++nf;
           ni += other;
           if (DBG) sf += pid[j];
         }
       });
-    }
+    };
+    if (lc & kFastBit) loop(std::true_type{});
+    else loop(std::false_type{});
+    pcount[i] = (uint32_t)nf;
     // back to physical units: rho ~ 1/H^D, a ~ (view length)^-(D+1)
     const T Hphys = Hd * qv;
     const T rho = GENERAL ? rho_out[i] : dsum * P.alpha / (D == 2 ? Hphys * Hphys : Hphys * Hphys * Hphys);
@@ -514,12 +535,14 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
     if (!GENERAL && rho_out) rho_out[i] = rho;
     const double e = (double)rho / (double)rt - 1.0;
     part.min_rc_a = an > T(0) ? (double)rc / (double)an : DBL_MAX;
+    part.amin = an > T(0) ? (long long)i : -1;
     part.max_a = (double)an;
     part.sum_rho = (double)rho;
     part.err_l2 = e * e;
     part.err_max = fabs(e);
     part.ipairs = ni;
     part.fpairs = nf;
+    part.lentries = cnt;
     if (!(isfinite((double)an) && isfinite((double)rho))) atomicOr(err, kErrNonfinite);
     if (DBG) {
       const uint32_t id = pid[i];
@@ -540,17 +563,18 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
   if (!last) return;
   // last block: fixed-order reduction of every block partial (L2 reads)
   __threadfence();
-  Partial acc{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0.0};
+  Partial acc{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, -1};
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
     const double* qd = (const double*)&partials[b];
     const long long* ql = (const long long*)&partials[b];
-    acc.min_rc_a = fmin(acc.min_rc_a, __ldcg(qd + 0));
+    argmin_merge(acc.min_rc_a, acc.amin, __ldcg(qd + 0), __ldcg(ql + 8));
     acc.max_a = fmax(acc.max_a, __ldcg(qd + 1));
     acc.sum_rho += __ldcg(qd + 2);
     acc.err_l2 += __ldcg(qd + 3);
     acc.err_max = fmax(acc.err_max, __ldcg(qd + 4));
     acc.ipairs += __ldcg(ql + 5);
     acc.fpairs += __ldcg(ql + 6);
+    acc.lentries += __ldcg(ql + 7);
   }
   acc = block_reduce(acc, sm);
   if (threadIdx.x == 0) {
@@ -565,9 +589,18 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
       dt1 = 0.25 * sqrt(m);
       dt2 = fmin(dt1, fmin(m / (20.0 * dt1), 2.5 * m / dt1));
     }
+    if (dt_fix) {  // prescribed step sizes
+      dt1 = dt_fix[0];
+      dt2 = dt_fix[1];
+    }
+    if (dt_rec) {
+      dt_rec[0] = dt1;
+      dt_rec[1] = dt2;
+    }
     scal->dt1 = dt1;
     scal->dt2 = dt2;
     scal->min_rc_a = m;
+    scal->argmin = acc.amin;
     scal->max_a = acc.max_a;
     scal->sum_rho = acc.sum_rho;
     scal->err_l2 = acc.err_l2;
@@ -575,6 +608,7 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
     scal->sigma = (double)sigma;
     scal->ipairs = acc.ipairs / 2;
     scal->fpairs = acc.fpairs / 2;
+    scal->lentries = acc.lentries;
     scal->wall_moved = 0;
     scal->step_of_stats = step;
     if (advance) ctl->step = step + 1;
@@ -594,7 +628,7 @@ __global__ void __launch_bounds__(256) k_pass_a(int n, StepCtl* ctl,
 // skin since the list was built raises need_rebuild.
 // --------------------------------------------------------------------------
 template <int D, class T, bool RECORD>
-__global__ void __launch_bounds__(256) k_pass_b(int n, StepCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_b(int n, StepCtl* __restrict__ ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 typename ViewOf<T>::type* __restrict__ w0,
@@ -605,7 +639,8 @@ __global__ void __launch_bounds__(256) k_pass_b(int n, StepCtl* __restrict__ ctl
                                                 const uint32_t* __restrict__ pcount,
                                                 const V4<T>* __restrict__ acc, Frame<T> F, Phys<T> P, Geom<T> geo,
                                                 const Scalars* __restrict__ scal, V4<T>* __restrict__ visc_out,
-                                                int* __restrict__ err, unsigned long long* __restrict__ wall_moved) {
+                                                int* __restrict__ err, unsigned long long* __restrict__ wall_moved,
+                                                int move) {
   using VT = typename ViewOf<T>::type;
   __shared__ int moved_sm[8];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -654,6 +689,7 @@ __global__ void __launch_bounds__(256) k_pass_b(int n, StepCtl* __restrict__ ctl
     const T dt1 = (T)scal->dt1, dt2 = (T)scal->dt2;
     const T kv = T(0.5) * dt1 * dt1;  // a~ = kv B
     if (RECORD) visc_out[i] = V4<T>{kv * bx, kv * by, kv * bz, T(0)};
+    if (move) {
     T d[3];
     d[0] = (T(0.5) * dt1 * ai.x + T(0.5) * dt2 * kv * bx) * dt2;
     d[1] = (T(0.5) * dt1 * ai.y + T(0.5) * dt2 * kv * by) * dt2;
@@ -699,6 +735,7 @@ __global__ void __launch_bounds__(256) k_pass_b(int n, StepCtl* __restrict__ ctl
     } else {
       (vp ? w0 : w1)[i] = vi;
     }
+    }  // move
   }
   if (__syncthreads_or(far) && threadIdx.x == 0) ctl->need_rebuild = 1;
   int v = moved;
@@ -811,7 +848,8 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
   k_pass_a<D, T, GEN, DBG><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],           \
                                               S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount, F, P, \
                                               pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
-                                              f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount)
+                                              f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix,     \
+                                              f.dt_rec)
   if (f.general_eos) {
     if (f.nbr_debug) SPH_PASS_A(true, true);
     else SPH_PASS_A(true, false);
@@ -833,12 +871,12 @@ cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P
     k_pass_b<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
                                             (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0],
                                             (LL4*)S.X[1], S.plist, S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
-                                            (V4<T>*)S.visc, S.err, wm);
+                                            (V4<T>*)S.visc, S.err, wm, f.move);
   else
     k_pass_b<D, T, false><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
                                              (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0],
                                              (LL4*)S.X[1], S.plist, S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
-                                             (V4<T>*)S.visc, S.err, wm);
+                                             (V4<T>*)S.visc, S.err, wm, f.move);
   return cudaGetLastError();
 }
 
