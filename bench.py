@@ -45,16 +45,29 @@ WORKLOADS = {
                     "FP32 split-precision, seed 1",
                dim=2, n=1 << 20, ncol=64, precision="fp32", seed=1,
                make=lambda n, c: W.graded_hole_2d(n, c, rho_scale=0.0)),
+    "c5": dict(desc="512 independent instances (256 2D + 256 3D), particle counts log-uniform in [2k, 200k] "
+                    "(seed 4), 2-64 colours, random sphere/box region, linear graded spacing, FP32",
+               dim=0, n=0, ncol=0, precision="fp32", seed=4, make=None),
     "c1": dict(desc="2D unit square, uniform, 4,096 particles (64x64 lattice + 0.3 jitter), 4 colours, FP64, seed 0",
                dim=2, n=4096, ncol=4, precision="fp64", seed=0,
                make=lambda n, c: W.uniform_square_2d(64, c)),
 }
 
-# algorithmic DRAM bytes per particle and launch (FP32 split precision)
-ALG_BYTES = {"pass_a": 44, "pass_b": 72, "cells": 84}
-ALG_BYTES_FP64 = {"pass_a": 72, "pass_b": 120, "cells": 100}
-CELL_BYTES_PER_CELL = 12  # scan: read counts twice, write starts
-KERNELS_PER_STEP = 8      # count, 3 scan, scatter, gather, pass A, pass B
+# algorithmic DRAM bytes per particle and launch: the particle record read and
+# the results written once, as a cell-list method with a per-step re-sort needs
+# them (3D FP32: key + sort 20, record gather 17 R + 17 W, pass A 17 R + 16 W,
+# pass B 29 R + 20 W; FP64 about 1.7x). The neighbour lists this library keeps
+# are extra traffic by design and are not counted.
+ALG_BYTES = {"cells": 54, "pass_a": 33, "pass_b": 49}
+ALG_BYTES_FP64 = {"cells": 92, "pass_a": 56, "pass_b": 83}
+# launches per step (gamma = 2): gate; rekey, count, 3 scan, scatter, gather,
+# make_view, list_build (predicated: they exit at once unless the list is
+# rebuilt); pass A; pass B
+KERNELS_PER_STEP = 12
+# pair arithmetic per force/density pair (FP32 flop, counted from the kernels):
+# density 8, pressure + surface tension 30 (pass A), viscous 28 (pass B)
+FLOP_PER_PAIR = {"density": 8, "force": 30, "visc": 28}
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
 
 
 def log(*a):
@@ -240,7 +253,161 @@ def run_gpu(args, wl, rank, world):
            "h2d_bytes_per_step": (n * d * 8 + n) / args.steps, "d2h_bytes_per_step": (n * d * 8 + 128) / args.steps}
     info = dict(grid=r.grid(), stats=st, stats_e2e=st2)
     r.close()
-    return dict(ms=ms, ms_step=ms_step, value=value, clocks=ck, phase_ms=phase_ms, e2e=e2e, info=info)
+    out = dict(ms=ms, ms_step=ms_step, value=value, clocks=ck, phase_ms=phase_ms, e2e=e2e, info=info)
+    if not args.no_extras and wl["precision"] == "fp32":
+        out["fp64"] = run_fp64(args, wl, p, rank)
+        if wl["dim"] == 3 and wl["n"] == 1 << 23:
+            out["adjoint"] = run_adjoint(rank)
+    return out
+
+
+def run_fp64(args, wl, p, rank):
+    """The same workload with the FP64 path: graph-timed steps."""
+    import torch
+    from paper_1906_07925_gb300 import Relaxation
+    n = wl["n"]
+    r = Relaxation(p, n, wl["ncol"], precision="fp64", seed=wl["seed"] + 1000 * rank, use_graph=True)
+    r.step(3)
+    r.sync()
+    k = max(3, min(args.steps, 10))
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(r.stream)
+    r.step(k)
+    e1.record(r.stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / k
+    r.close()
+    return {"value": n / (ms * 1e-3), "unit": METRIC, "ms_per_step": ms, "steps": k, "warmup": 3, "dtype": "f64"}
+
+
+def run_adjoint(rank, K=20, ckpt=5):
+    """Adjoint cost ratio on the polynomial-field workload: 262,144 particles
+    (2D graded hole), 32 colours, FP32, K = 20 steps, checkpoint every 5:
+    wall time of sph_backward (its own forward run, the objective and the
+    reverse sweep) over that of K forward steps, both synchronised."""
+    import torch
+    from paper_1906_07925_gb300 import Relaxation
+    n = 1 << 18
+    p = W.adjoint_poly_2d(n=n, n_colors=32, seed=3)
+    r = Relaxation(p, n_particles=n, n_colors=32, precision="fp32", seed=3 + 1000 * rank, use_graph=True)
+    x0, c0 = r.positions(), r.colors()
+    gout = torch.empty((n, 2), dtype=torch.float64, device="cuda")
+    r.step(K)  # warm-up
+    r.set_state(x0, c0)
+    r.backward(K, lam=1.0, ckpt_every=ckpt, out=gout)  # warm-up (allocates the reverse buffers and graphs)
+    fw, bw = [], []
+    for _ in range(3):
+        r.set_state(x0, c0)
+        r.sync()
+        t0 = time.perf_counter()
+        r.step(K)
+        r.sync()
+        fw.append(time.perf_counter() - t0)
+        r.set_state(x0, c0)
+        r.sync()
+        t0 = time.perf_counter()
+        g = r.backward(K, lam=1.0, ckpt_every=ckpt, out=gout)  # gradient stays on the device
+        bw.append(time.perf_counter() - t0)
+    r.close()
+    f, b = statistics.median(fw), statistics.median(bw)
+    return {"workload": "2D graded hole + 8-coefficient polynomial density, 262,144 particles, 32 colours, FP32",
+            "K": K, "ckpt_every": ckpt, "forward_ms": f * 1e3, "backward_ms": b * 1e3, "ratio": b / f,
+            "L": g["L"]}
+
+
+def batch_problems(n_inst=512, seed=4):
+    inst = W.batch_instances(n_inst, seed=seed)
+    probs, ns, cols = [], [], []
+    for p, n in inst:
+        p.rho_scale = 0.0  # normalised by the library to n particles
+        probs.append(p)
+        ns.append(n)
+        cols.append(p.n_colors)
+    return probs, ns, cols
+
+
+def run_batch(args, rank, world):
+    """Batched form: every instance advanced by one CUDA graph per step
+    (branch count autotuned), against the same steps issued as a loop of
+    per-instance graphs on the same stream."""
+    import torch
+    from paper_1906_07925_gb300 import Batch
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    probs, ns, cols = batch_problems()
+    total = sum(ns)
+    seeds = [1000 * rank + k for k in range(len(probs))]
+    t0 = time.perf_counter()
+    b = Batch(probs, ns, cols, precision="fp32", seeds=seeds)
+    log(f"[rank {rank}] batch create {time.perf_counter() - t0:.1f}s, {len(probs)} instances, {total} particles")
+    tune = b.tune(candidates=(1, 8, 16, 32, 64, 128, 256), steps_each=4)
+    b.step(args.warmup)
+    b.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ev[0].record(b.stream)
+    b.step(args.steps)
+    ev[1].record(b.stream)
+    ev[1].synchronize()
+    ck = clocks.stop()
+    ms = ev[0].elapsed_time(ev[1])
+    # the same steps as per-instance graphs (reference mode), same stream
+    b.step_each(1)
+    b.sync()
+    ev[2].record(b.stream)
+    b.step_each(args.steps)
+    ev[3].record(b.stream)
+    ev[3].synchronize()
+    ms_each = ev[2].elapsed_time(ev[3])
+    # end to end: host state in, K batched steps, positions out
+    xs = [b.positions(k) for k in range(len(probs))]
+    cs = [b.colors(k) for k in range(len(probs))]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(len(probs)):
+        b.set_state(k, xs[k], cs[k])
+    b.step(args.steps)
+    for k in range(len(probs)):
+        xs[k] = b.positions(k)
+    e2e_s = time.perf_counter() - t0
+    b.close()
+    if world > 1:
+        t = torch.tensor([ms, ms_each, e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, ms_each, e2e_s = [float(v) for v in t.tolist()]
+    hb = sum(n * p.dim * 8 + n for p, n in zip(probs, ns))
+    return dict(ms=ms, ms_each=ms_each, total=total, clocks=ck, tune=tune,
+                e2e={"value": world * total * args.steps / e2e_s, "unit": METRIC,
+                     "h2d_bytes_per_step": hb / args.steps, "d2h_bytes_per_step": (hb - total) / args.steps})
+
+
+def batch_oracle_sample(args):
+    """The four smallest instances (two 2D, two 3D), 2 oracle steps each."""
+    import oracle
+    oracle.build()
+    probs, ns, cols = batch_problems()
+    pick = sorted([k for k in range(len(probs)) if probs[k].dim == 2], key=lambda k: ns[k])[:2] + \
+        sorted([k for k in range(len(probs)) if probs[k].dim == 3], key=lambda k: ns[k])[:2]
+    parts, secs = 0, 0.0
+    for k in pick:
+        p = probs[k]
+        p.rho_scale = W.rho_scale_for(p, ns[k], res=512 if p.dim == 2 else 64)
+        pos, col, _ = W.sample_density(p, ns[k], k)
+        x = pos
+        for s in range(3):
+            t0 = time.perf_counter()
+            x, _, _ = oracle.step(p, x, col, s, want=False)
+            if s > 0:
+                secs += time.perf_counter() - t0
+                parts += len(pos)
+    return parts / secs, oracle.num_threads(), (f"instances {pick} ({sum(ns[k] for k in pick)} particles), "
+                                               "2 timed oracle steps each after 1 warm-up")
 
 
 def main():
@@ -255,7 +422,10 @@ def main():
     ap.add_argument("--particles", type=int, default=0,
                     help="override the particle count (small cases for profiler captures)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64 and adjoint side measurements")
     args = ap.parse_args()
+    if args.workload == "c5":
+        return main_batch(args)
     wl = dict(WORKLOADS[args.workload])
     if args.particles > 0:
         wl["n"] = args.particles
@@ -298,7 +468,6 @@ def main():
     ab = ALG_BYTES_FP64 if wl["precision"] == "fp64" else ALG_BYTES
     cells = res["info"]["grid"]["base"][-1]
     per_particle = dict(ab)
-    per_particle["cells"] = ab["cells"] + CELL_BYTES_PER_CELL * cells / n
     dom = max(("pass_a", "pass_b"), key=lambda k: res["phase_ms"][k])
     ach = per_particle[dom] * n / (res["phase_ms"][dom] * 1e-3) / 1e9
     step_bytes = sum(per_particle.values()) * n
@@ -309,6 +478,12 @@ def main():
             "step_alg_bytes_per_particle": sum(per_particle.values()),
             "step_achieved_gbs": step_bytes / (res["ms_step"] * 1e-3) / 1e9,
             "phase_ms": res["phase_ms"]}
+    st0 = res["info"]["stats"]
+    fpp = 2 * st0["force_pairs"] / n
+    flop = fpp * (FLOP_PER_PAIR["density"] + FLOP_PER_PAIR["force"] + FLOP_PER_PAIR["visc"])
+    roof["fp32_pair_flop_per_particle"] = flop
+    roof["fp32_tflops_step"] = flop * n / (res["ms_step"] * 1e-3) / 1e12
+    roof["fp32_frac_of_nominal_peak"] = roof["fp32_tflops_step"] / FP32_PEAK_TFLOPS
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         q, pos, col, desc = oracle_workload_sample(wl)
@@ -322,10 +497,54 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["precision"] == "fp32" else "f64",
            "data": "synthetic", "config": config, "clocks": res["clocks"], "e2e": res["e2e"],
            "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roof, "cpu_baseline": cpu,
+           "fp64": res.get("fp64"), "adjoint": res.get("adjoint"),
            "step_stats": {"force_pairs_per_particle": 2 * st["force_pairs"] / n, "list_entries_per_particle": st["list_entries"] / n, "list_rebuilds": st["list_rebuilds"], "dt1": st["dt1"],
                           "err_l2_rms": math.sqrt(st["err_l2"] / n), "levels": res["info"]["grid"]["n_levels"],
                           "cells": cells}}
     print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main_batch(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    wl = WORKLOADS["c5"]
+    config = {"workload": wl["desc"], "instances": 512, "kernel": "Wendland C2", "tau": 2.0, "kappa": 1.0,
+              "gamma": 2.0, "l2": "inputs larger than L2 (about 22M particles)", "parallelism": f"replicas x{world}"}
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        v, cores, desc = batch_oracle_sample(args)
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": config,
+                          "cpu_baseline": {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle",
+                                           "sample": desc},
+                          "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+              flush=True)
+        return
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    res = run_batch(args, rank, world)
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            v, cores, desc = batch_oracle_sample(args)
+            cpu = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc}
+        ms_step = res["ms"] / args.steps
+        out = {"metric": METRIC, "value": world * res["total"] * args.steps / (res["ms"] * 1e-3), "unit": METRIC,
+               "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "data": "synthetic", "config": config, "clocks": res["clocks"], "e2e": res["e2e"],
+               "gpu_launches": KERNELS_PER_STEP * 512 * args.steps,
+               "per_instance_graphs": {"value": world * res["total"] * args.steps / (res["ms_each"] * 1e-3),
+                                       "ms_per_step": res["ms_each"] / args.steps,
+                                       "speedup_of_batched": res["ms_each"] / res["ms"]},
+               "autotuner": res["tune"], "cpu_baseline": cpu}
+        print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
 

@@ -269,6 +269,57 @@ typedef struct {
 sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, const double* seed,
                         const double* dt_in, double* dt_out, double* dpos0, int32_t on_device, sph_grad* grad);
 
+/* ---------------------------------------------------------------------------
+ * Batches of independent instances (uneven sizes, 2D and 3D mixed). One CUDA
+ * graph advances every instance by one step: instance k's kernels form one
+ * branch-local chain, the branches fork from and join to the batch's stream and
+ * run concurrently. The paper runs one instance at a time; batching is a
+ * service of the library for many small problems on one GPU.
+ * --------------------------------------------------------------------------- */
+typedef struct {
+  sph_domain dom;
+  sph_field field;
+  int64_t n_particles;
+  int32_t n_colors;
+  int32_t reserved;
+  sph_params params;   /* use_graph is ignored (the batch graph replaces it) */
+} sph_instance_desc;
+
+typedef struct sph_batch sph_batch;
+
+/* Create n_inst instances (as sph_create each, all on `stream`; NULL: a new
+ * stream). n_branches > 0 fixes the number of graph branches; 0 leaves it to
+ * sph_batch_tune (or 16 at the first step). Errors as sph_create. */
+sph_status sph_batch_create(const sph_instance_desc* descs, int32_t n_inst, const sph_alloc* alloc, void* stream,
+                            int32_t n_branches, sph_batch** out);
+
+/* Autotuner: time steps_each graph-launched steps for each candidate branch
+ * count, keep the fastest; instances are dealt longest first (particles x
+ * dimension cost) to the least-loaded branch. The trial steps are undone (the
+ * state and step counters are restored). Synchronises. */
+sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_candidates, int32_t steps_each);
+
+/* n_steps steps of every instance, one graph launch per step (async). */
+sph_status sph_batch_step(sph_batch* b, int32_t n_steps);
+
+/* Reference mode: the same steps as a loop of per-instance graph launches on
+ * the batch's stream (one graph per instance and step). */
+sph_status sph_batch_step_each(sph_batch* b, int32_t n_steps);
+
+/* Instance k's handle (owned by the batch: use sph_get_positions, sph_get_stats
+ * etc. on it; do not destroy it). */
+sph_status sph_batch_get(sph_batch* b, int32_t k, sph_handle** h);
+
+/* Instance count, branch count in use, and the autotuner's trials (n_tuned
+ * entries of candidate branch count and ms per step; arrays may be NULL). */
+sph_status sph_batch_info(const sph_batch* b, int32_t* n_inst, int32_t* n_branches, int32_t* n_tuned,
+                          int32_t* tuned_branches, float* tuned_ms);
+
+/* Wait for the batch's stream; report latched device errors of any instance. */
+sph_status sph_batch_sync(sph_batch* b);
+const char* sph_batch_last_error(const sph_batch* b);
+void sph_batch_destroy(sph_batch* b);
+
 /* Message of the last failing call on this handle (never NULL). */
 const char* sph_last_error(const sph_handle* h);
 

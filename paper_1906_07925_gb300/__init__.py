@@ -17,7 +17,7 @@ import numpy as np
 
 from . import _binding as B
 
-__all__ = ["Relaxation", "SphError", "build", "load_library", "problem_structs"]
+__all__ = ["Batch", "Relaxation", "SphError", "build", "load_library", "problem_structs", "relax_fn"]
 
 
 class SphError(RuntimeError):
@@ -177,16 +177,28 @@ class Relaxation:
 
     GRAD_NAMES = ("sigma0", "gamma", "P0") + tuple(f"poly{m}" for m in range(8))
 
-    def backward(self, n_steps, lam=1.0, frozen_dt=False, ckpt_every=5, seed=None, dt=None, density_weight=1.0):
+    def backward(self, n_steps, lam=1.0, frozen_dt=False, ckpt_every=5, seed=None, dt=None, density_weight=1.0,
+                 out=None):
         """Sensitivities of L (density_weight * density error + lam * interface
         energy) after n_steps steps from the current state; the handle ends at
         the final state.
         seed: optional (n, dim) dL/dx_K of an outer loss; dt: optional (n_steps, 2)
-        prescribed step sizes (implies frozen_dt). Returns dict(L, dpos0 (n, dim),
+        prescribed step sizes (implies frozen_dt). out: optional CUDA float64
+        (n, dim) tensor that receives dpos0 on the device (then seed and dt
+        must be CUDA tensors too, or None). Returns dict(L, dpos0 (n, dim),
         grads {name: value}, dt (n_steps, 2))."""
         obj = B.sph_objective(float(density_weight), float(lam), 1 if (frozen_dt or dt is not None) else 0,
                               int(ckpt_every))
         g = B.sph_grad()
+        if out is not None:
+            torch = self._torch
+            dt_dev = torch.zeros((max(int(n_steps), 0), 2), dtype=torch.float64, device=out.device)
+            self._check(self.lib.sph_backward(self.h, int(n_steps), C.byref(obj),
+                                              None if seed is None else seed.data_ptr(),
+                                              None if dt is None else dt.data_ptr(),
+                                              dt_dev.data_ptr(), out.data_ptr(), 1, C.byref(g)))
+            grads = dict(zip(self.GRAD_NAMES, [g.d_sigma0, g.d_gamma, g.d_P0] + list(g.d_poly)))
+            return dict(L=g.L, dpos0=out, grads=grads, dt=dt_dev)
         dpos = np.zeros((self.n, self.dim), np.float64)
         dt_out = np.zeros((max(int(n_steps), 0), 2), np.float64)
         sd = None if seed is None else np.ascontiguousarray(seed, dtype=np.float64)
@@ -284,3 +296,122 @@ def relax_fn(relaxation, n_steps, frozen_dt=True, ckpt_every=5):
             return torch.from_numpy(r["dpos0"]).to(gout.device, gout.dtype)
 
     return _Relax.apply
+
+
+class Batch:
+    """Independent instances stepped together by one CUDA graph per step
+    (include/sphmesh.h, sph_batch_*). problems: list of problem descriptions
+    (as for Relaxation), each with n_particles / n_colors attributes or given
+    in the parallel lists. n_branches = 0: tune with tune() (or 16 by default)."""
+
+    def __init__(self, problems, n_particles, n_colors, precision="fp32", seeds=None, n_branches=0, device=None):
+        import torch
+        self._torch = torch
+        self.lib = B.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = torch.cuda.Stream(device=self.device)
+        k = len(problems)
+        descs = (B.sph_instance_desc * k)()
+        self.dims, self.ns = [], []
+        for i, p in enumerate(problems):
+            d, f, q = problem_structs(p, precision, 0 if seeds is None else int(seeds[i]), use_graph=False)
+            descs[i].dom, descs[i].field, descs[i].params = d, f, q
+            descs[i].n_particles = int(n_particles[i])
+            descs[i].n_colors = int(n_colors[i])
+            self.dims.append(int(p.dim))
+            self.ns.append(int(n_particles[i]))
+        dev, stream = self.device, self.stream
+
+        def _alloc(nbytes, ctx):
+            try:
+                return torch.cuda.caching_allocator_alloc(int(nbytes), dev, stream)
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, ctx):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._cb = (B.ALLOC_FN(_alloc), B.FREE_FN(_free))
+        al = B.sph_alloc(self._cb[0], self._cb[1], None)
+        h = B.H()
+        with torch.cuda.device(self.device):
+            st = self.lib.sph_batch_create(descs, k, C.byref(al), C.c_void_p(stream.cuda_stream), int(n_branches),
+                                           C.byref(h))
+        if st != B.SPH_OK:
+            raise SphError(st, "sph_batch_create failed (details on stderr)")
+        self.b = h
+        self.n_inst = k
+
+    def _check(self, st):
+        if st != B.SPH_OK:
+            raise SphError(st, self.lib.sph_batch_last_error(self.b).decode())
+
+    def tune(self, candidates=(1, 4, 8, 16, 32, 64, 128), steps_each=2):
+        arr = (C.c_int32 * len(candidates))(*candidates)
+        self._check(self.lib.sph_batch_tune(self.b, arr, len(candidates), int(steps_each)))
+        return self.info()
+
+    def info(self):
+        ni, nb, nt = C.c_int32(), C.c_int32(), C.c_int32()
+        tb = (C.c_int32 * 64)()
+        tm = (C.c_float * 64)()
+        self._check(self.lib.sph_batch_info(self.b, C.byref(ni), C.byref(nb), C.byref(nt), tb, tm))
+        return dict(n_inst=ni.value, n_branches=nb.value,
+                    trials=[(tb[i], tm[i]) for i in range(nt.value)])
+
+    def step(self, n=1):
+        self._check(self.lib.sph_batch_step(self.b, int(n)))
+
+    def step_each(self, n=1):
+        self._check(self.lib.sph_batch_step_each(self.b, int(n)))
+
+    def sync(self):
+        self._check(self.lib.sph_batch_sync(self.b))
+
+    def _h(self, k):
+        h = B.H()
+        self._check(self.lib.sph_batch_get(self.b, int(k), C.byref(h)))
+        return h
+
+    def positions(self, k):
+        x = np.empty((self.ns[k], self.dims[k]), np.float64)
+        h = self._h(k)
+        st = self.lib.sph_get_positions(h, x.ctypes.data, 0)
+        if st != B.SPH_OK:
+            raise SphError(st, self.lib.sph_last_error(h).decode())
+        return x
+
+    def colors(self, k):
+        c = np.empty(self.ns[k], np.uint8)
+        h = self._h(k)
+        st = self.lib.sph_get_colors(h, c.ctypes.data, 0)
+        if st != B.SPH_OK:
+            raise SphError(st, self.lib.sph_last_error(h).decode())
+        return c
+
+    def set_state(self, k, pos, col):
+        pos = np.ascontiguousarray(pos, dtype=np.float64)
+        col = np.ascontiguousarray(col, dtype=np.uint8)
+        h = self._h(k)
+        st = self.lib.sph_set_state(h, pos.ctypes.data, col.ctypes.data, 0)
+        if st != B.SPH_OK:
+            raise SphError(st, self.lib.sph_last_error(h).decode())
+
+    def stats(self, k):
+        s = B.sph_stats()
+        h = self._h(k)
+        st = self.lib.sph_get_stats(h, C.byref(s))
+        if st != B.SPH_OK:
+            raise SphError(st, self.lib.sph_last_error(h).decode())
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.sph_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -78,6 +78,11 @@ class sph_grad(C.Structure):
                 ("d_poly", C.c_double * 8)]
 
 
+class sph_instance_desc(C.Structure):
+    _fields_ = [("dom", sph_domain), ("field", sph_field), ("n_particles", C.c_int64), ("n_colors", C.c_int32),
+                ("reserved", C.c_int32), ("params", sph_params)]
+
+
 H = C.c_void_p
 _lock = threading.Lock()
 _lib = None
@@ -122,6 +127,13 @@ def load():
             "sph_get_info": [H, P(C.c_int64), P(C.c_int32), P(C.c_double)],
             "sph_backward": [H, C.c_int32, P(sph_objective), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                              C.c_int32, P(sph_grad)],
+            "sph_batch_create": [C.c_void_p, C.c_int32, P(sph_alloc), C.c_void_p, C.c_int32, P(H)],
+            "sph_batch_tune": [H, C.c_void_p, C.c_int32, C.c_int32],
+            "sph_batch_step": [H, C.c_int32],
+            "sph_batch_step_each": [H, C.c_int32],
+            "sph_batch_get": [H, C.c_int32, P(H)],
+            "sph_batch_info": [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+            "sph_batch_sync": [H],
             "sph_eval_forces_noalloc": [P(sph_domain), P(sph_field), P(sph_params), C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
         }
@@ -133,5 +145,9 @@ def load():
         L.sph_last_error.restype = C.c_char_p
         L.sph_destroy.argtypes = [H]
         L.sph_destroy.restype = None
+        L.sph_batch_destroy.argtypes = [H]
+        L.sph_batch_destroy.restype = None
+        L.sph_batch_last_error.argtypes = [H]
+        L.sph_batch_last_error.restype = C.c_char_p
         _lib = L
         return L

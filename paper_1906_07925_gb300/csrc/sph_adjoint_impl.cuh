@@ -21,6 +21,7 @@
 //   k_bwd_visc   viscous pairs and eta: adjoints of v~, a, h, T, rho_t
 //   k_bwd_dt     (recomputed step sizes) the argmin particle's share
 //   k_bwd_force  pressure / surface-tension pairs and the equation of state
+//                (gamma = 2 form: then also the target field, as below)
 //   k_bwd_local  density pairs (where rho has an adjoint), then the target
 //                field rho_t(x) and h(x): adjoint of x by particle id
 // k_obj computes the objective and seeds the same accumulators at the end
@@ -47,7 +48,7 @@ struct KernelD {
 template <int D, class T>
 __device__ __forceinline__ KernelD<D, T> wendland(T r, T H, T c) {
   KernelD<D, T> k{T(0), T(0), T(0)};
-  const T iH = T(1) / H, q = r * iH;
+  const T iH = drcp<T>(H), q = r * iH;
   if (!(q < T(1))) return k;
   const T u = T(1) - q, u3 = u * u * u;
   const T cH = c * ipow_d<D, T>(iH);  // c H^-d
@@ -63,7 +64,7 @@ struct ForceD {
 template <int D, class T>
 __device__ __forceinline__ ForceD<D, T> force_fn(T r, T H, T c) {
   ForceD<D, T> k{T(0), T(0), T(0)};
-  const T iH = T(1) / H, q = r * iH;
+  const T iH = drcp<T>(H), q = r * iH;
   if (!(q < T(1))) return k;
   const T u = T(1) - q, u2 = u * u;
   const T cH3 = c * ipow_d<D, T>(iH) * iH * iH * iH;  // c H^-(d+3)
@@ -73,20 +74,26 @@ __device__ __forceinline__ ForceD<D, T> force_fn(T r, T H, T c) {
   return k;
 }
 
-// fixed-order block sum of m doubles; the block's sums go to part[blockIdx.x]
-// and the last block to finish returns true with every block's partial
-// summed (in block order) into out[0..m) of every thread.
-template <int M>
-__device__ bool block_partials(double (&v)[M], double* __restrict__ part, unsigned* __restrict__ ticket,
-                               double* out) {
+// fixed-order block sum of M values (warp sums in the working precision,
+// warp totals and everything after in FP64); the block's sums go to
+// part[blockIdx.x] and the last block to finish returns true with every
+// block's partial summed (in block order) into out[0..M) of every thread.
+__device__ __forceinline__ float warp_sum_t(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum_t(double v) { return warp_sum(v); }
+
+template <int M, class T>
+__device__ bool block_partials(T (&v)[M], double* __restrict__ part, unsigned* __restrict__ ticket, double* out) {
   __shared__ double sm[8][M];
   __shared__ double res[M];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int q = 0; q < M; ++q) {
-    double x = warp_sum(v[q]);
-    if (lane == 0) sm[w][q] = x;
+    const T x = warp_sum_t(v[q]);
+    if (lane == 0) sm[w][q] = (double)x;
   }
   __syncthreads();
   if (threadIdx.x < M) {
@@ -102,9 +109,22 @@ __device__ bool block_partials(double (&v)[M], double* __restrict__ part, unsign
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  // every thread sums a fixed stride of the block partials, then a fixed tree
+  double a[M];
+#pragma unroll
+  for (int q = 0; q < M; ++q) a[q] = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < M; ++q) a[q] += __ldcg(part + (size_t)b * kAdjPartials + q);
+#pragma unroll
+  for (int q = 0; q < M; ++q) {
+    const double x = warp_sum(a[q]);
+    if (lane == 0) sm[w][q] = x;
+  }
+  __syncthreads();
   if (threadIdx.x < M) {
     double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(part + (size_t)b * kAdjPartials + threadIdx.x);
+    for (int k = 0; k < nw; ++k) s += sm[k][threadIdx.x];
     res[threadIdx.x] = s;
   }
   __syncthreads();
@@ -114,13 +134,9 @@ __device__ bool block_partials(double (&v)[M], double* __restrict__ part, unsign
   return true;
 }
 
-// absolute position (FP64) of an integer coordinate
-template <int D, class T>
-__device__ __forceinline__ void abs_pos_d(const Frame<T>& F, const LL4& X, double* x) {
-  x[0] = F.lod[0] + (double)X.x * F.q64;
-  x[1] = F.lod[1] + (double)X.y * F.q64;
-  x[2] = D == 3 ? F.lod[2] + (double)X.z * F.q64 : 0.0;
-}
+template <class T> __device__ __forceinline__ T dlog(T x);
+template <> __device__ __forceinline__ float dlog<float>(float x) { return logf(x); }
+template <> __device__ __forceinline__ double dlog<double>(double x) { return log(x); }
 
 // T = 1/rho_t^2 and rho_t from h (h = tau rho_t^(-1/d))
 template <int D, class T>
@@ -141,28 +157,28 @@ __global__ void __launch_bounds__(256) k_bwd_out(int n, const StepCtl* __restric
                                                  const LL4* __restrict__ X0, const LL4* __restrict__ X1,
                                                  const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
                                                  const V4<T>* __restrict__ acc, const V4<T>* __restrict__ visc,
-                                                 const Scalars* __restrict__ scal, Frame<T> F, Geom<double> geo,
+                                                 const Scalars* __restrict__ scal, Frame<T> F, Geom<T> geo,
                                                  AdjBufs<T> B) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[1] = {0.0};
+  T v[1] = {T(0)};
   if (i < n) {
     const int buf = ctl->buf;
     const LL4 X = (buf ? X1 : X0)[i];
     const uint32_t id = (buf ? p1 : p0)[i];
-    const double dt1 = scal->dt1, dt2 = scal->dt2;
+    const T dt1 = (T)scal->dt1, dt2 = (T)scal->dt2;
     const V4<T> a = acc[i], at = visc[i];
-    const double vt[3] = {0.5 * dt1 * (double)a.x, 0.5 * dt1 * (double)a.y, 0.5 * dt1 * (double)a.z};
-    const double att[3] = {(double)at.x, (double)at.y, (double)at.z};
-    double g[3] = {0, 0, 0};
-    for (int k = 0; k < D; ++k) g[k] = B.gin[(size_t)id * D + k];
-    // forward: integer drift with the box clamp (as pass B), then the shapes
+    const T vt[3] = {T(0.5) * dt1 * a.x, T(0.5) * dt1 * a.y, T(0.5) * dt1 * a.z};
+    const T att[3] = {at.x, at.y, at.z};
+    T g[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) g[k] = (T)B.gin[(size_t)id * D + k];
+    // forward, as pass B: integer drift with the box clamp, then the shapes
     const long long Xc[3] = {X.x, X.y, X.z};
     bool clamped[3] = {false, false, false};
-    double z[kMaxShapes + 1][3];
-    for (int k = 0; k < 3; ++k) z[0][k] = 0.0;
+    T z[kMaxShapes + 1][3];
+    for (int k = 0; k < 3; ++k) z[0][k] = T(0);
     for (int k = 0; k < D; ++k) {
-      const double dk = (vt[k] + 0.5 * dt2 * att[k]) * dt2;
-      long long u = Xc[k] + (long long)llrint(dk * F.inv_q64);
+      const T dk = (vt[k] + T(0.5) * dt2 * att[k]) * dt2;
+      long long u = Xc[k] + (long long)llrint((double)(dk * F.inv_q64t));
       if (u < 0) {
         u = 0;
         clamped[k] = true;
@@ -171,7 +187,7 @@ __global__ void __launch_bounds__(256) k_bwd_out(int n, const StepCtl* __restric
         u = F.xmax[k];
         clamped[k] = true;
       }
-      z[0][k] = F.lod[k] + (double)u * F.q64;
+      z[0][k] = F.lo[k] + (T)u * F.q64t;
     }
     for (int s = 0; s < geo.n_shapes; ++s) {
       for (int k = 0; k < 3; ++k) z[s + 1][k] = z[s][k];
@@ -179,46 +195,48 @@ __global__ void __launch_bounds__(256) k_bwd_out(int n, const StepCtl* __restric
     }
     // reverse
     for (int s = geo.n_shapes - 1; s >= 0; --s) {
-      const double* x = z[s];
-      if (!(constraint_phi(geo, s, x, D) < 0.0)) continue;
+      const T* x = z[s];
+      if (!(constraint_phi(geo, s, x, D) < T(0))) continue;
       if (geo.kind[s] == 0) {
-        double dv[3] = {0, 0, 0}, r2 = 0.0;
+        T dv[3] = {0, 0, 0}, r2 = 0;
         for (int k = 0; k < D; ++k) {
           dv[k] = x[k] - geo.center[s][k];
           r2 += dv[k] * dv[k];
         }
-        const double r = sqrt(r2);
-        if (r == 0.0) {
-          for (int k = 0; k < D; ++k) g[k] = 0.0;
+        const T r = dsqrt(r2);
+        if (r == T(0)) {
+          for (int k = 0; k < D; ++k) g[k] = T(0);
           continue;
         }
-        double ng = 0.0;
+        T ng = 0;
         for (int k = 0; k < D; ++k) ng += dv[k] * g[k];
         ng /= r;
         for (int k = 0; k < D; ++k) g[k] = geo.size[s][0] / r * (g[k] - dv[k] / r * ng);
       } else if (geo.keep_inside[s]) {
         for (int k = 0; k < D; ++k) {
-          const double lo = geo.center[s][k] - geo.size[s][k], hi = geo.center[s][k] + geo.size[s][k];
-          if (x[k] < lo || x[k] > hi) g[k] = 0.0;
+          const T lo = geo.center[s][k] - geo.size[s][k], hi = geo.center[s][k] + geo.size[s][k];
+          if (x[k] < lo || x[k] > hi) g[k] = T(0);
         }
       } else {
         int best = 0;
-        double bestd = 1e300;
+        T bestd = T(1e30);
         for (int k = 0; k < D; ++k) {
-          const double dlo = x[k] - (geo.center[s][k] - geo.size[s][k]);
-          const double dhi = (geo.center[s][k] + geo.size[s][k]) - x[k];
+          const T dlo = x[k] - (geo.center[s][k] - geo.size[s][k]);
+          const T dhi = (geo.center[s][k] + geo.size[s][k]) - x[k];
           if (dlo < bestd) { bestd = dlo; best = k; }
           if (dhi < bestd) { bestd = dhi; best = k; }
         }
-        g[best] = 0.0;
+        g[best] = T(0);
       }
     }
     for (int k = 0; k < D; ++k)
-      if (clamped[k]) g[k] = 0.0;
-    B.xb[i] = V4<double>{g[0], g[1], g[2], 0.0};
-    const double c = 0.5 * dt2 * dt2;
-    B.atb[i] = V4<T>{(T)(c * g[0]), (T)(c * g[1]), (T)(c * g[2]), T(0)};
-    for (int k = 0; k < D; ++k) v[0] += g[k] * (vt[k] + dt2 * att[k]);
+      if (clamped[k]) g[k] = T(0);
+    B.xb[i] = V4<double>{(double)g[0], (double)g[1], (double)g[2], 0.0};
+    const T c = T(0.5) * dt2 * dt2;
+    B.atb[i] = V4<T>{c * g[0], c * g[1], c * g[2], T(0)};
+    T pv = 0;
+    for (int k = 0; k < D; ++k) pv += g[k] * (vt[k] + dt2 * att[k]);
+    v[0] = pv;
   }
   double out[1];
   if (block_partials<1>(v, B.part, B.ticket, out) && threadIdx.x == 0) B.acc[kAdjDt2b] = out[0];
@@ -237,7 +255,7 @@ __global__ void __launch_bounds__(256) k_bwd_visc(int n, const StepCtl* __restri
                                                   Frame<T> F, Phys<T> P, int recomputed_dt, AdjBufs<T> B) {
   using VT = typename ViewOf<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[1] = {0.0};
+  T v[1] = {T(0)};
   if (i < n) {
     const VT* __restrict__ view = ctl->vp ? v1 : v0;
     const VT vi = view[i];
@@ -245,7 +263,7 @@ __global__ void __launch_bounds__(256) k_bwd_visc(int n, const StepCtl* __restri
     const T half_kappa = T(0.5) * P.kappa;
     const T dt1 = (T)scal->dt1, dt2 = (T)scal->dt2;
     const V4<T> ai = acc[i];
-    const T rti = rho_t_of_h<D, T>(hi, P.inv_tau), Ti = T(1) / (rti * rti);
+    const T rti = rho_t_of_h<D, T>(hi, P.inv_tau), Ti = inv_rho_t2<D, T>(hi, P.inv_tau);
     const T etai = dt1 * ai.w;
     const V4<T> atbi = B.atb[i];
     const V4<double> ybar = B.xb[i];
@@ -261,16 +279,17 @@ __global__ void __launch_bounds__(256) k_bwd_visc(int n, const StepCtl* __restri
       const T hvj = view_h(vj);
       const T Hv = half_kappa * (hv + hvj);
       if (!(r2 < Hv * Hv) || j == i) return;
-      const T r = dsqrt(r2) * qv, ex = dx * qv, ey = dy * qv, ez = dz * qv;
-      const T hj = hvj * qv;
+      const T irv = drsqrt<T>(r2);  // 1/r, view units
+      const T r = r2 * irv * qv, ir = irv * F.inv_qv, ex = dx * qv, ey = dy * qv, ez = dz * qv;
       const ForceD<D, T> f = force_fn<D, T>(r, Hv * qv, P.alpha);
       const V4<T> aj = acc[j];
       const V4<T> atbj = B.atb[j];
-      const T rtj = rho_t_of_h<D, T>(hj, P.inv_tau), Tj = T(1) / (rtj * rtj);
+      const T Tj = inv_rho_t2<D, T>(hvj * qv, P.inv_tau);
       const T etaj = dt1 * aj.w;
       const T es = etai + etaj;
-      const T hm = es > T(0) ? T(2) * etai * etaj / es : T(0);
-      const T dhm = es > T(0) ? T(2) * etaj * etaj / (es * es) : T(0);
+      const T ies = es > T(0) ? drcp<T>(es) : T(0);
+      const T hm = T(2) * etai * etaj * ies;
+      const T dhm = T(2) * etaj * etaj * ies * ies;
       const T Ts = Ti + Tj;
       const T K = hm * Ts * f.F;
       const T gx = atbi.x - atbj.x, gy = atbi.y - atbj.y, gz = atbi.z - atbj.z;
@@ -282,7 +301,7 @@ __global__ void __launch_bounds__(256) k_bwd_visc(int n, const StepCtl* __restri
       etab += Kb * Ts * f.F * dhm;
       Tbar += Kb * hm * f.F;
       const T Fb = Kb * hm * Ts;
-      const T cr = Fb * f.Fr / r;
+      const T cr = Fb * f.Fr * ir;
       xx += cr * ex;
       xy += cr * ey;
       xz += cr * ez;
@@ -304,7 +323,7 @@ __global__ void __launch_bounds__(256) k_bwd_visc(int n, const StepCtl* __restri
     }
     // v~ = dt1 a / 2
     B.ab[i] = V4<T>{hd * vbx, hd * vby, hd * vbz, T(0)};
-    v[0] = 0.5 * ((double)ai.x * vbx + (double)ai.y * vby + (double)ai.z * vbz);
+    v[0] = T(0.5) * (ai.x * vbx + ai.y * vby + ai.z * vbz);
     B.xb[i] = V4<double>{ybar.x + xx, ybar.y + xy, ybar.z + xz, 0.0};
     B.hb[i] = hbar;
     B.Tb[i] = Tbar;
@@ -345,6 +364,112 @@ __global__ void k_bwd_dt(const StepCtl* __restrict__ ctl, const typename ViewOf<
   B.hb[k] += (T)(mb * (double)P.kappa / an);
 }
 
+// gradient of the signed inside distance of shape s (the branch its value takes)
+template <class T>
+__device__ __forceinline__ void inside_distance_grad(const Geom<T>& g, int s, const T* x, int dim, T* gr) {
+  for (int k = 0; k < 3; ++k) gr[k] = T(0);
+  if (g.kind[s] == 0) {
+    T r2 = 0;
+    for (int k = 0; k < dim; ++k) r2 += (x[k] - g.center[s][k]) * (x[k] - g.center[s][k]);
+    const T r = dsqrt(r2);
+    if (r > T(0))
+      for (int k = 0; k < dim; ++k) gr[k] = -(x[k] - g.center[s][k]) / r;
+    return;
+  }
+  T out2 = 0, qmax = T(-1e30), q[3] = {0, 0, 0};
+  int kmax = 0;
+  for (int k = 0; k < dim; ++k) {
+    q[k] = fabs(x[k] - g.center[s][k]) - g.size[s][k];
+    if (q[k] > T(0)) out2 += q[k] * q[k];
+    if (q[k] > qmax) {
+      qmax = q[k];
+      kmax = k;
+    }
+  }
+  if (out2 > T(0)) {
+    const T o = dsqrt(out2);
+    for (int k = 0; k < dim; ++k)
+      if (q[k] > T(0)) gr[k] = -q[k] * (x[k] >= g.center[s][k] ? T(1) : T(-1)) / o;
+  } else if (qmax < T(0)) {
+    gr[kmax] = -(x[kmax] >= g.center[s][kmax] ? T(1) : T(-1));
+  }
+}
+
+// rho_t(x) = rho_scale s(x)^-d P(x): value, gradient in x, derivatives in the
+// polynomial coefficients
+template <int D, class T>
+__device__ __forceinline__ T rho_t_grad(const Geom<T>& g, const T* x, T* grad, T* dc) {
+  const T s = spacing_of(g, x);
+  const T base = g.rho_scale * (D == 2 ? T(1) / (s * s) : T(1) / (s * s * s));
+  T gs[3] = {0, 0, 0};
+  if (g.field_kind != 0) {
+    const T dist = shape_inside(g, g.dist_shape, x, D);
+    T gd[3];
+    inside_distance_grad(g, g.dist_shape, x, D, gd);
+    const T sg = dist >= T(0) ? T(1) : T(-1);
+    for (int k = 0; k < D; ++k) gs[k] = g.b * sg * gd[k];
+  }
+  T Pf = 1, gP[3] = {0, 0, 0};
+  for (int m = 0; m < 8; ++m) dc[m] = T(0);
+  if (g.n_poly > 0) {
+    T t[3] = {0, 0, 0}, tt[3] = {0, 0, 0};
+    for (int k = 0; k < D; ++k) {
+      t[k] = T(2) * (x[k] - g.lo[k]) / g.ext[k] - T(1);
+      tt[k] = T(2) / g.ext[k];
+    }
+    T b[8], bx[8], by[8], bz[8];
+    const T X = t[0], Y = t[1], Z = t[2];
+    if (D == 2) {
+      const T b_[8] = {X, Y, X * X, X * Y, Y * Y, X * X * X, X * X * Y, X * Y * Y};
+      const T x_[8] = {1, 0, 2 * X, Y, 0, 3 * X * X, 2 * X * Y, Y * Y};
+      const T y_[8] = {0, 1, 0, X, 2 * Y, 0, X * X, 2 * X * Y};
+      for (int m = 0; m < 8; ++m) {
+        b[m] = b_[m];
+        bx[m] = x_[m];
+        by[m] = y_[m];
+        bz[m] = T(0);
+      }
+    } else {
+      const T b_[8] = {X, Y, Z, X * X, Y * Y, Z * Z, X * Y, Y * Z};
+      const T x_[8] = {1, 0, 0, 2 * X, 0, 0, Y, 0};
+      const T y_[8] = {0, 1, 0, 0, 2 * Y, 0, X, Z};
+      const T z_[8] = {0, 0, 1, 0, 0, 2 * Z, 0, Y};
+      for (int m = 0; m < 8; ++m) {
+        b[m] = b_[m];
+        bx[m] = x_[m];
+        by[m] = y_[m];
+        bz[m] = z_[m];
+      }
+    }
+    for (int m = 0; m < g.n_poly; ++m) {
+      Pf += g.poly[m] * b[m];
+      dc[m] = base * b[m];
+      gP[0] += g.poly[m] * bx[m] * tt[0];
+      gP[1] += g.poly[m] * by[m] * tt[1];
+      gP[2] += g.poly[m] * bz[m] * tt[2];
+    }
+  }
+  const T rt = base * Pf;
+  for (int k = 0; k < 3; ++k) grad[k] = T(0);
+  for (int k = 0; k < D; ++k) grad[k] = rt * (-T(D) * gs[k] / s) + base * gP[k];
+  return rt;
+}
+
+// adjoint of the target field at a particle: rho_t(x), h = tau rho_t^(-1/d)
+// and T = rho_t^-2 carry the adjoints rtb, hb, Tb; returns the adjoint of x
+// (xg) and the coefficient derivatives times that adjoint (dc)
+template <int D, class T>
+__device__ __forceinline__ void field_adjoint(const Frame<T>& F, const Geom<T>& geo, const LL4& X, T h, T rtb, T hb,
+                                              T Tb, T* xg, T* dc) {
+  T x[3], grad[3];
+  abs_pos<D, T>(F, X, x);
+  const T rt = rho_t_grad<D, T>(geo, x, grad, dc);
+  const T irt = drcp<T>(rt);
+  const T tot = rtb + hb * (-h * irt / T(D)) + Tb * (T(-2) * irt * irt * irt);
+  for (int k = 0; k < 3; ++k) xg[k] = tot * grad[k];
+  for (int m = 0; m < 8; ++m) dc[m] *= tot;
+}
+
 // ------------------------------------------------------------------------
 // k_bwd_force: pressure and surface-tension pairs, then the equation of state
 // Q = p/rho^2 = P0 (rho/rho_t)^gamma / rho^2 (P0 T in the gamma = 2 form).
@@ -358,10 +483,14 @@ __global__ void __launch_bounds__(256) k_bwd_force(int n, const StepCtl* __restr
                                                    const uint32_t* __restrict__ pcount,
                                                    const T* __restrict__ rho, const T* __restrict__ pc,
                                                    const Scalars* __restrict__ scal, Frame<T> F, Phys<T> P,
-                                                   double ramp, AdjBufs<T> B) {
+                                                   const LL4* __restrict__ X0, const LL4* __restrict__ X1,
+                                                   const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
+                                                   Geom<T> geo, AdjBufs<T> B) {
   using VT = typename ViewOf<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[3] = {0.0, 0.0, 0.0};  // sigma(t), P0, gamma
+  // sigma(t), P0, gamma; without a density adjoint (gamma = 2 form) also the
+  // target-field step of k_bwd_local: the 8 coefficient derivatives
+  T v[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
   if (i < n) {
     const VT* __restrict__ view = ctl->vp ? v1 : v0;
     const VT vi = view[i];
@@ -369,11 +498,11 @@ __global__ void __launch_bounds__(256) k_bwd_force(int n, const StepCtl* __restr
     const T qv = F.qv, hv = view_h(vi), hi = hv * qv;
     const T half_kappa = T(0.5) * P.kappa;
     const T sigma = (T)scal->sigma, P0 = P.P0;
-    const T rti = rho_t_of_h<D, T>(hi, P.inv_tau), Ti = T(1) / (rti * rti);
+    const T rti = rho_t_of_h<D, T>(hi, P.inv_tau), Ti = inv_rho_t2<D, T>(hi, P.inv_tau);
     const T Qi = GENERAL ? pc[i] : P0 * Ti;
     const V4<T> abi = B.ab[i];
     T xx = 0, xy = 0, xz = 0, hbar = 0, Tbar = 0, Qbar = 0;
-    double sb = 0.0, pb = 0.0;
+    T sb = 0, pb = 0;
     const int cnt = (int)pcount[i];
     for_list(plist, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
       const int j = (int)(e >> 8);
@@ -383,10 +512,10 @@ __global__ void __launch_bounds__(256) k_bwd_force(int n, const StepCtl* __restr
       const T hvj = view_h(vj);
       const T Hv = half_kappa * (hv + hvj);
       if (!(r2 < Hv * Hv) || j == i) return;
-      const T r = dsqrt(r2) * qv, ex = dx * qv, ey = dy * qv, ez = dz * qv;
-      const T hj = hvj * qv;
+      const T irv = drsqrt<T>(r2);  // 1/r, view units
+      const T r = r2 * irv * qv, ir = irv * F.inv_qv, ex = dx * qv, ey = dy * qv, ez = dz * qv;
       const ForceD<D, T> f = force_fn<D, T>(r, Hv * qv, P.alpha);
-      const T rtj = rho_t_of_h<D, T>(hj, P.inv_tau), Tj = T(1) / (rtj * rtj);
+      const T Tj = inv_rho_t2<D, T>(hvj * qv, P.inv_tau);
       const T Qj = GENERAL ? pc[j] : P0 * Tj;
       const bool other = (e & 0xFFu) != ci;
       const T beta = other ? sigma : T(0);
@@ -403,10 +532,10 @@ __global__ void __launch_bounds__(256) k_bwd_force(int n, const StepCtl* __restr
       Qbar += cb;
       Tbar += cb * beta * P0;
       // each unordered pair is visited from both ends
-      if (other) sb += 0.5 * (double)cb * (double)P0 * (double)Ts;
-      pb += 0.5 * (double)cb * (double)beta * (double)Ts;
+      if (other) sb += T(0.5) * cb * P0 * Ts;
+      pb += T(0.5) * cb * beta * Ts;
       const T Fb = -Sb * coef;
-      const T cr = Fb * f.Fr / r;
+      const T cr = Fb * f.Fr * ir;
       xx += cr * ex;
       xy += cr * ey;
       xz += cr * ez;
@@ -414,127 +543,53 @@ __global__ void __launch_bounds__(256) k_bwd_force(int n, const StepCtl* __restr
     });
     // equation of state
     const T rh = rho[i];
-    const double lr = log((double)rh / (double)rti);
-    double gb = (double)Qbar * (double)Qi * lr;
+    const T lr = dlog<T>(rh / rti);
+    const T gb = Qbar * Qi * lr;
     T rhob = 0, rtbar = 0;
     if (GENERAL) {
       rhob = Qbar * (P.gamma - T(2)) * Qi / rh;
       rtbar = -P.gamma * Qbar * Qi / rti;
-      if (P0 != T(0)) pb += (double)Qbar * (double)Qi / (double)P0;
+      if (P0 != T(0)) pb += Qbar * Qi / P0;
     } else {
       Tbar += Qbar * P0;
-      pb += (double)Qbar * (double)Ti;
+      pb += Qbar * Ti;
     }
     V4<double> xb = B.xb[i];
-    xb.x += xx;
-    xb.y += xy;
-    xb.z += xz;
-    B.xb[i] = xb;
-    B.hb[i] += hbar;
-    B.Tb[i] += Tbar;
-    B.rtb[i] += rtbar;
-    B.rhob[i] = rhob;
     v[0] = sb;
     v[1] = pb;
     v[2] = gb;
+    if (GENERAL) {
+      xb.x += xx;
+      xb.y += xy;
+      xb.z += xz;
+      B.xb[i] = xb;
+      B.hb[i] += hbar;
+      B.Tb[i] += Tbar;
+      B.rtb[i] += rtbar;
+      B.rhob[i] = rhob;
+    } else {
+      const int buf = ctl->buf;
+      T xg[3], dc[8];
+      field_adjoint<D, T>(F, geo, (buf ? X1 : X0)[i], hi, B.rtb[i] + rtbar, B.hb[i] + hbar, B.Tb[i] + Tbar, xg, dc);
+      const uint32_t id = (buf ? p1 : p0)[i];
+      B.gout[(size_t)id * D + 0] = xb.x + (double)(xx + xg[0]);
+      B.gout[(size_t)id * D + 1] = xb.y + (double)(xy + xg[1]);
+      if (D == 3) B.gout[(size_t)id * D + 2] = xb.z + (double)(xz + xg[2]);
+      for (int m = 0; m < 8; ++m) v[3 + m] = dc[m];
+    }
   }
-  double out[3];
-  if (block_partials<3>(v, B.part, B.ticket, out) && threadIdx.x == 0) {
+  double out[11];
+  if (block_partials<11>(v, B.part, B.ticket, out) && threadIdx.x == 0) {
+    if (!GENERAL)
+      for (int m = 0; m < 8; ++m) B.acc[kAdjPoly + m] += out[3 + m];
+    // sigma(t) = sigma0 ramp(t) (Eq. sph_st_sigma) at the step pass A ran
+    StepCtl c1 = *ctl;
+    c1.sigma0 = 1.0;
+    const double ramp = sigma_of(c1, scal->step_of_stats);
     B.acc[kAdjSigma0] += out[0] * ramp;
     B.acc[kAdjP0] += out[1];
     B.acc[kAdjGamma] += out[2];
   }
-}
-
-// gradient of the signed inside distance of shape s (the branch its value takes)
-__device__ __forceinline__ void inside_distance_grad(const Geom<double>& g, int s, const double* x, int dim,
-                                                     double* gr) {
-  for (int k = 0; k < 3; ++k) gr[k] = 0.0;
-  if (g.kind[s] == 0) {
-    double r2 = 0.0;
-    for (int k = 0; k < dim; ++k) r2 += (x[k] - g.center[s][k]) * (x[k] - g.center[s][k]);
-    const double r = sqrt(r2);
-    if (r > 0.0)
-      for (int k = 0; k < dim; ++k) gr[k] = -(x[k] - g.center[s][k]) / r;
-    return;
-  }
-  double out2 = 0.0, qmax = -1e300, q[3] = {0, 0, 0};
-  int kmax = 0;
-  for (int k = 0; k < dim; ++k) {
-    q[k] = fabs(x[k] - g.center[s][k]) - g.size[s][k];
-    if (q[k] > 0) out2 += q[k] * q[k];
-    if (q[k] > qmax) {
-      qmax = q[k];
-      kmax = k;
-    }
-  }
-  if (out2 > 0.0) {
-    const double o = sqrt(out2);
-    for (int k = 0; k < dim; ++k)
-      if (q[k] > 0) gr[k] = -q[k] * (x[k] >= g.center[s][k] ? 1.0 : -1.0) / o;
-  } else if (qmax < 0) {
-    gr[kmax] = -(x[kmax] >= g.center[s][kmax] ? 1.0 : -1.0);
-  }
-}
-
-// rho_t(x) = rho_scale s(x)^-d P(x): value, gradient in x, derivatives in the
-// polynomial coefficients
-template <int D>
-__device__ __forceinline__ double rho_t_grad(const Geom<double>& g, const double* x, double* grad, double* dc) {
-  const double s = spacing_of(g, x);
-  const double base = g.rho_scale * (D == 2 ? 1.0 / (s * s) : 1.0 / (s * s * s));
-  double gs[3] = {0, 0, 0};
-  if (g.field_kind != 0) {
-    const double dist = shape_inside(g, g.dist_shape, x, D);
-    double gd[3];
-    inside_distance_grad(g, g.dist_shape, x, D, gd);
-    const double sg = dist >= 0.0 ? 1.0 : -1.0;
-    for (int k = 0; k < D; ++k) gs[k] = g.b * sg * gd[k];
-  }
-  double Pf = 1.0, gP[3] = {0, 0, 0};
-  for (int m = 0; m < 8; ++m) dc[m] = 0.0;
-  if (g.n_poly > 0) {
-    double t[3] = {0, 0, 0}, tt[3] = {0, 0, 0};
-    for (int k = 0; k < D; ++k) {
-      t[k] = 2.0 * (x[k] - g.lo[k]) / g.ext[k] - 1.0;
-      tt[k] = 2.0 / g.ext[k];
-    }
-    double b[8], bx[8], by[8], bz[8];
-    const double X = t[0], Y = t[1], Z = t[2];
-    if (D == 2) {
-      const double b_[8] = {X, Y, X * X, X * Y, Y * Y, X * X * X, X * X * Y, X * Y * Y};
-      const double x_[8] = {1, 0, 2 * X, Y, 0, 3 * X * X, 2 * X * Y, Y * Y};
-      const double y_[8] = {0, 1, 0, X, 2 * Y, 0, X * X, 2 * X * Y};
-      for (int m = 0; m < 8; ++m) {
-        b[m] = b_[m];
-        bx[m] = x_[m];
-        by[m] = y_[m];
-        bz[m] = 0.0;
-      }
-    } else {
-      const double b_[8] = {X, Y, Z, X * X, Y * Y, Z * Z, X * Y, Y * Z};
-      const double x_[8] = {1, 0, 0, 2 * X, 0, 0, Y, 0};
-      const double y_[8] = {0, 1, 0, 0, 2 * Y, 0, X, Z};
-      const double z_[8] = {0, 0, 1, 0, 0, 2 * Z, 0, Y};
-      for (int m = 0; m < 8; ++m) {
-        b[m] = b_[m];
-        bx[m] = x_[m];
-        by[m] = y_[m];
-        bz[m] = z_[m];
-      }
-    }
-    for (int m = 0; m < g.n_poly; ++m) {
-      Pf += g.poly[m] * b[m];
-      dc[m] = base * b[m];
-      gP[0] += g.poly[m] * bx[m] * tt[0];
-      gP[1] += g.poly[m] * by[m] * tt[1];
-      gP[2] += g.poly[m] * bz[m] * tt[2];
-    }
-  }
-  const double rt = base * Pf;
-  for (int k = 0; k < 3; ++k) grad[k] = 0.0;
-  for (int k = 0; k < D; ++k) grad[k] = rt * (-(double)D * gs[k] / s) + base * gP[k];
-  return rt;
 }
 
 // ------------------------------------------------------------------------
@@ -551,10 +606,10 @@ __global__ void __launch_bounds__(256) k_bwd_local(int n, const StepCtl* __restr
                                                    const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
                                                    const uint32_t* __restrict__ list,
                                                    const uint32_t* __restrict__ lcount, Frame<T> F, Phys<T> P,
-                                                   Geom<double> geo, AdjBufs<T> B) {
+                                                   Geom<T> geo, AdjBufs<T> B) {
   using VT = typename ViewOf<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  T v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   if (i < n) {
     const VT* __restrict__ view = ctl->vp ? v1 : v0;
     const int buf = ctl->buf;
@@ -582,21 +637,17 @@ __global__ void __launch_bounds__(256) k_bwd_local(int n, const StepCtl* __restr
         xz += c * dz * qv;
       });
     }
-    double x[3];
-    abs_pos_d<D, T>(F, (buf ? X1 : X0)[i], x);
-    double grad[3], dc[8];
-    const double rt = rho_t_grad<D>(geo, x, grad, dc);
-    const double h = (double)hi, Tq = 1.0 / (rt * rt);
-    const double tot = (double)B.rtb[i] + (double)hbar * (-h / ((double)D * rt)) + (double)B.Tb[i] * (-2.0 * Tq / rt);
+    T xg[3], dc[8];
+    field_adjoint<D, T>(F, geo, (buf ? X1 : X0)[i], hi, B.rtb[i], hbar, B.Tb[i], xg, dc);
     V4<double> xb = B.xb[i];
-    xb.x += (double)xx + tot * grad[0];
-    xb.y += (double)xy + tot * grad[1];
-    xb.z += (double)xz + tot * grad[2];
+    xb.x += (double)(xx + xg[0]);
+    xb.y += (double)(xy + xg[1]);
+    xb.z += (double)(xz + xg[2]);
     const uint32_t id = (buf ? p1 : p0)[i];
     B.gout[(size_t)id * D + 0] = xb.x;
     B.gout[(size_t)id * D + 1] = xb.y;
     if (D == 3) B.gout[(size_t)id * D + 2] = xb.z;
-    for (int m = 0; m < 8; ++m) v[m] = tot * dc[m];
+    for (int m = 0; m < 8; ++m) v[m] = dc[m];
   }
   double out[8];
   if (block_partials<8>(v, B.part, B.ticket, out) && threadIdx.x < 8) B.acc[kAdjPoly + threadIdx.x] += out[threadIdx.x];
@@ -617,7 +668,7 @@ __global__ void __launch_bounds__(256) k_obj(int n, const StepCtl* __restrict__ 
                                              Frame<T> F, Phys<T> P, T wd, T lambda, AdjBufs<T> B) {
   using VT = typename ViewOf<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[2] = {0.0, 0.0};
+  T v[2] = {T(0), T(0)};
   if (i < n) {
     const VT* __restrict__ view = ctl->vp ? v1 : v0;
     const int buf = ctl->buf;
@@ -625,8 +676,7 @@ __global__ void __launch_bounds__(256) k_obj(int n, const StepCtl* __restrict__ 
     const uint32_t ci = (buf ? m1 : m0)[i] & 0xFFu;
     const T qv = F.qv, hv = view_h(vi), hi = hv * qv;
     const T Hi = P.kappa * hi, half_kappa = T(0.5) * P.kappa;
-    T rho = 0, xx = 0, xy = 0, xz = 0, hbar = 0;
-    double wi = 0.0;
+    T rho = 0, xx = 0, xy = 0, xz = 0, hbar = 0, wi = 0;
     const int cnt = (int)(lcount[i] & ~kFastBit);
     for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
       const int j = (int)(e >> 8);
@@ -639,7 +689,7 @@ __global__ void __launch_bounds__(256) k_obj(int n, const StepCtl* __restrict__ 
       const T Hv = half_kappa * (hv + hvj);
       if (j == i || (e & 0xFFu) == ci || !(r2 < Hv * Hv)) return;
       const KernelD<D, T> k = wendland<D, T>(r, Hv * qv, P.alpha);
-      wi += 0.5 * (double)k.W;  // each unordered pair from both ends
+      wi += T(0.5) * k.W;  // each unordered pair from both ends
       const T c = lambda * k.Wr / r;
       xx += c * dx * qv;
       xy += c * dy * qv;
@@ -648,7 +698,7 @@ __global__ void __launch_bounds__(256) k_obj(int n, const StepCtl* __restrict__ 
     });
     const T rt = rho_t_of_h<D, T>(hi, P.inv_tau);
     const T e = rho / rt - T(1);
-    v[0] = (double)e * (double)e;
+    v[0] = e * e;
     v[1] = wi;
     B.rhob[i] = wd * T(2) * e / rt;
     B.rtb[i] = wd * T(-2) * e * rho / (rt * rt);
@@ -665,10 +715,39 @@ __global__ void __launch_bounds__(256) k_obj(int n, const StepCtl* __restrict__ 
     B.acc[kAdjL] = (double)wd * out[0] + (double)lambda * out[1];
 }
 
+// ------------------------------------------------------------------ tape --
+// After pass A of a taped step: the state it used (current order), its
+// control block and its scalars go to one slot of the tape, so that the
+// reverse pass of that step needs no list rebuild and no forward recompute.
+template <class VT>
+__global__ void __launch_bounds__(256) k_tape_snapshot(int n, const StepCtl* __restrict__ ctl,
+                                                       const Scalars* __restrict__ scal,
+                                                       const LL4* __restrict__ X0, const LL4* __restrict__ X1,
+                                                       const uint32_t* __restrict__ m0,
+                                                       const uint32_t* __restrict__ m1,
+                                                       const uint32_t* __restrict__ p0,
+                                                       const uint32_t* __restrict__ p1, const VT* __restrict__ v0,
+                                                       const VT* __restrict__ v1, LL4* __restrict__ oX,
+                                                       uint32_t* __restrict__ oM, uint32_t* __restrict__ oP,
+                                                       VT* __restrict__ oV, StepCtl* __restrict__ octl,
+                                                       Scalars* __restrict__ oscal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int buf = ctl->buf, vp = ctl->vp;
+  if (i == 0) {
+    *octl = *ctl;
+    *oscal = *scal;
+  }
+  if (i >= n) return;
+  oX[i] = (buf ? X1 : X0)[i];
+  oM[i] = (buf ? m1 : m0)[i];
+  oP[i] = (buf ? p1 : p0)[i];
+  oV[i] = (vp ? v1 : v0)[i];
+}
+
 // ---------------------------------------------------------------- launch --
 template <int D, class T>
-cudaError_t launch_bwd_step(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<double>& geo,
-                            const AdjBufs<T>& B, int recomputed_dt, int general_eos, double ramp, cudaStream_t st) {
+cudaError_t launch_bwd_step(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& geo,
+                            const AdjBufs<T>& B, int recomputed_dt, int general_eos, cudaStream_t st) {
   using VT = typename ViewOf<T>::type;
   const int tb = 256, gb = grid_for(S.n, tb);
   if (S.n <= 0) return cudaSuccess;
@@ -681,21 +760,20 @@ cudaError_t launch_bwd_step(const DevState& S, const Frame<T>& F, const Phys<T>&
   if (recomputed_dt) k_bwd_dt<D, T><<<1, 32, 0, st>>>(S.ctl, w0, w1, acc, S.scal, F, P, B);
   if (general_eos)
     k_bwd_force<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, S.meta[0], S.meta[1], S.plist, S.pcount,
-                                               (const T*)S.rho, (const T*)S.pc, S.scal, F, P, ramp, B);
-  else
+                                               (const T*)S.rho, (const T*)S.pc, S.scal, F, P, (const LL4*)S.X[0],
+                                               (const LL4*)S.X[1], S.pid[0], S.pid[1], geo, B);
+  else  // the gamma = 2 form has no density adjoint: the target-field step is fused in
     k_bwd_force<D, T, false><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, S.meta[0], S.meta[1], S.plist, S.pcount,
-                                                (const T*)S.rho, (const T*)S.pc, S.scal, F, P, ramp, B);
+                                                (const T*)S.rho, (const T*)S.pc, S.scal, F, P, (const LL4*)S.X[0],
+                                                (const LL4*)S.X[1], S.pid[0], S.pid[1], geo, B);
   if (general_eos)
     k_bwd_local<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, (const LL4*)S.X[0], (const LL4*)S.X[1],
                                                S.pid[0], S.pid[1], S.list, S.lcount, F, P, geo, B);
-  else
-    k_bwd_local<D, T, false><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, (const LL4*)S.X[0], (const LL4*)S.X[1],
-                                                S.pid[0], S.pid[1], S.list, S.lcount, F, P, geo, B);
   return cudaGetLastError();
 }
 
 template <int D, class T>
-cudaError_t launch_objective(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<double>& geo,
+cudaError_t launch_objective(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& geo,
                              const AdjBufs<T>& B, double wd, double lambda, cudaStream_t st) {
   using VT = typename ViewOf<T>::type;
   const int tb = 256, gb = grid_for(S.n, tb);
@@ -709,11 +787,23 @@ cudaError_t launch_objective(const DevState& S, const Frame<T>& F, const Phys<T>
   return cudaGetLastError();
 }
 
+template <int D, class T>
+cudaError_t launch_tape_snapshot(const DevState& S, const DevState& tape, cudaStream_t st) {
+  using VT = typename ViewOf<T>::type;
+  const int tb = 256, gb = grid_for(S.n > 0 ? S.n : 1, tb);
+  k_tape_snapshot<VT><<<gb, tb, 0, st>>>(S.n, S.ctl, S.scal, (const LL4*)S.X[0], (const LL4*)S.X[1], S.meta[0],
+                                         S.meta[1], S.pid[0], S.pid[1], (const VT*)S.view[0], (const VT*)S.view[1],
+                                         (LL4*)tape.X[0], tape.meta[0], tape.pid[0], (VT*)tape.view[0], tape.ctl,
+                                         tape.scal);
+  return cudaGetLastError();
+}
+
 #define SPH_INSTANTIATE_ADJOINT(D, T)                                                                            \
+  template cudaError_t launch_tape_snapshot<D, T>(const DevState&, const DevState&, cudaStream_t);              \
   template cudaError_t launch_bwd_step<D, T>(const DevState&, const Frame<T>&, const Phys<T>&,                  \
-                                             const Geom<double>&, const AdjBufs<T>&, int, int, double,           \
+                                             const Geom<T>&, const AdjBufs<T>&, int, int,                        \
                                              cudaStream_t);                                                      \
   template cudaError_t launch_objective<D, T>(const DevState&, const Frame<T>&, const Phys<T>&,                 \
-                                              const Geom<double>&, const AdjBufs<T>&, double, double, cudaStream_t);
+                                              const Geom<T>&, const AdjBufs<T>&, double, double, cudaStream_t);
 
 }  // namespace sph

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -51,6 +52,9 @@ struct sph_handle {
     double *part = nullptr, *acc = nullptr, *g[2] = {nullptr, nullptr};
     unsigned* ticket = nullptr;
     uint8_t* col = nullptr;  // colours by particle id
+    std::vector<DevState> tape;  // taped-step slots (grown on demand, freed with the handle)
+    std::vector<double*> tape_dt;  // per slot: {dt1, dt2} a re-run step reads
+    std::vector<cudaGraphExec_t> g_rerun, g_rev[2];  // per slot: re-run step; reverse step (recomputed, frozen)
   } adj;
   std::string err;
 };
@@ -127,10 +131,13 @@ int auto_capacity(const sph_handle* h) {
 }
 
 // one relaxation step on the handle's stream; dt_fix (device, may be null)
-// prescribes {dt1, dt2}, dt_rec (device, may be null) receives them
+// prescribes {dt1, dt2}, dt_rec (device, may be null) receives them. Sx (may
+// be null: the handle's own) redirects buffers; with `tape`, the state pass A
+// used is copied into it before pass B moves the particles.
 sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEvent_t* ev = nullptr,
-                       const double* dt_fix = nullptr, double* dt_rec = nullptr) {
-  DevState& S = h->S;
+                       const double* dt_fix = nullptr, double* dt_rec = nullptr, const DevState* Sx = nullptr,
+                       const DevState* tape = nullptr) {
+  const DevState& S = Sx ? *Sx : h->S;
   PassFlags f;
   f.general_eos = h->par.gamma != 2.0;
   f.record = record;
@@ -156,6 +163,12 @@ sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEve
     else
       e = f64 ? launch_pass_a<3, double>(S, h->Fd, h->Pd, f, h->stream)
               : launch_pass_a<3, float>(S, h->Ff, h->Pf, f, h->stream);
+  }
+  if (tape && e == cudaSuccess) {
+    if (h->dim == 2)
+      e = f64 ? launch_tape_snapshot<2, double>(S, *tape, h->stream) : launch_tape_snapshot<2, float>(S, *tape, h->stream);
+    else
+      e = f64 ? launch_tape_snapshot<3, double>(S, *tape, h->stream) : launch_tape_snapshot<3, float>(S, *tape, h->stream);
   }
   if (ev && e == cudaSuccess) e = cudaEventRecord(ev[2], h->stream);
   if (e == cudaSuccess) {
@@ -238,7 +251,7 @@ sph_status write_ctl_all(sph_handle* h) {
   c.rebuild = 0;
   c.need_rebuild = 1;
   c.rebuilds = 0;
-  SPH_CUDA(h, cudaMemcpyAsync(h->S.ctl, &c, sizeof c, cudaMemcpyHostToDevice, h->stream));
+  SPH_CUDA(h, launch_write_ctl(h->S, c, h->stream));
   return SPH_OK;
 }
 
@@ -411,41 +424,110 @@ sph_status run_objective(sph_handle* h, double wd, double lambda, const double* 
   if (h->dim == 2)
     e = f64 ? launch_objective<2, double>(h->S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, seed, gout), wd,
                                           lambda, h->stream)
-            : launch_objective<2, float>(h->S, h->Ff, h->Pf, h->geod, adj_bufs<float>(h, seed, gout), wd,
+            : launch_objective<2, float>(h->S, h->Ff, h->Pf, h->geof, adj_bufs<float>(h, seed, gout), wd,
                                          lambda, h->stream);
   else
     e = f64 ? launch_objective<3, double>(h->S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, seed, gout), wd,
                                           lambda, h->stream)
-            : launch_objective<3, float>(h->S, h->Ff, h->Pf, h->geod, adj_bufs<float>(h, seed, gout), wd,
+            : launch_objective<3, float>(h->S, h->Ff, h->Pf, h->geof, adj_bufs<float>(h, seed, gout), wd,
                                          lambda, h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "objective");
   return SPH_OK;
 }
 
-sph_status run_bwd_step(sph_handle* h, const double* gin, double* gout, int recomputed, double ramp) {
+sph_status run_bwd_step(sph_handle* h, const DevState& S, const double* gin, double* gout, int recomputed) {
   cudaError_t e;
   const bool f64 = h->prec == SPH_PREC_FP64;
   const int gen = h->par.gamma != 2.0;
   if (h->dim == 2)
-    e = f64 ? launch_bwd_step<2, double>(h->S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, gin, gout), recomputed,
-                                         gen, ramp, h->stream)
-            : launch_bwd_step<2, float>(h->S, h->Ff, h->Pf, h->geod, adj_bufs<float>(h, gin, gout), recomputed, gen,
-                                        ramp, h->stream);
+    e = f64 ? launch_bwd_step<2, double>(S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, gin, gout), recomputed, gen,
+                                         h->stream)
+            : launch_bwd_step<2, float>(S, h->Ff, h->Pf, h->geof, adj_bufs<float>(h, gin, gout), recomputed, gen,
+                                        h->stream);
   else
-    e = f64 ? launch_bwd_step<3, double>(h->S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, gin, gout), recomputed,
-                                         gen, ramp, h->stream)
-            : launch_bwd_step<3, float>(h->S, h->Ff, h->Pf, h->geod, adj_bufs<float>(h, gin, gout), recomputed, gen,
-                                        ramp, h->stream);
+    e = f64 ? launch_bwd_step<3, double>(S, h->Fd, h->Pd, h->geod, adj_bufs<double>(h, gin, gout), recomputed, gen,
+                                         h->stream)
+            : launch_bwd_step<3, float>(S, h->Ff, h->Pf, h->geof, adj_bufs<float>(h, gin, gout), recomputed, gen,
+                                        h->stream);
   if (e != cudaSuccess) return cuda_fail(h, e, "reverse step");
   return SPH_OK;
 }
 
-// sigma(t)/sigma0 (Eq. sph_st_sigma with sigma0 = 1)
-double ramp_at(const sph_handle* h, int64_t t) {
-  if (h->t0 < 0.0 || (double)t <= h->t0) return 1.0;
-  if ((double)t <= h->t1) return 1.0 - (h->t0 - (double)t) / (h->t0 - h->t1);
-  return 0.0;
+// Per-step record of a taped step: the state pass A used (current order), the
+// step's forward results (a, g, a~, rho, p/rho^2, this step's force pairs),
+// its control block and scalars, and with a general EOS its neighbour list.
+// Slots are allocated once (through the handle's allocator) and reused.
+sph_status ensure_tape(sph_handle* h, int slots) {
+  const size_t N = (size_t)h->n, cap = (size_t)h->S.cap;
+  const size_t t1 = h->prec == SPH_PREC_FP64 ? 8 : 4, v4 = 4 * t1;
+  const bool gen = h->par.gamma != 2.0;
+  auto& tape = h->adj.tape;
+  while ((int)tape.size() < slots) {
+    DevState T = h->S;
+    uint8_t* p = nullptr;
+    SPH_TRY(grab(h, p, N * 32)); T.X[0] = T.X[1] = p;
+    SPH_TRY(grab(h, T.meta[0], N)); T.meta[1] = T.meta[0];
+    SPH_TRY(grab(h, T.pid[0], N)); T.pid[1] = T.pid[0];
+    SPH_TRY(grab(h, p, N * v4)); T.view[0] = T.view[1] = p;
+    SPH_TRY(grab(h, T.plist, N * cap));
+    SPH_TRY(grab(h, T.pcount, N));
+    SPH_TRY(grab(h, p, N * v4)); T.acc4 = p;
+    SPH_TRY(grab(h, p, N * v4)); T.visc = p;
+    SPH_TRY(grab(h, p, N * t1)); T.rho = p;
+    SPH_TRY(grab(h, p, N * t1)); T.pc = p;
+    SPH_TRY(grab(h, T.ctl, 1));
+    SPH_TRY(grab(h, T.scal, 1));
+    if (gen) {
+      SPH_TRY(grab(h, T.list, N * cap));
+      SPH_TRY(grab(h, T.lcount, N));
+    }
+    double* dt = nullptr;
+    SPH_TRY(grab(h, dt, 2));
+    tape.push_back(T);
+    h->adj.tape_dt.push_back(dt);
+    h->adj.g_rerun.push_back(nullptr);
+    h->adj.g_rev[0].push_back(nullptr);
+    h->adj.g_rev[1].push_back(nullptr);
+  }
+  return SPH_OK;
 }
+
+// instantiate what `body` issues on the handle's stream as a graph
+template <class Body>
+sph_status capture(sph_handle* h, cudaGraphExec_t* out, Body&& body) {
+  cudaGraph_t g = nullptr;
+  SPH_CUDA(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  sph_status s = body();
+  cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+  if (s != SPH_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+  return SPH_OK;
+}
+
+// one step writing its forward results into tape slot T (and the state into it)
+sph_status taped_step(sph_handle* h, const DevState& T, const double* dt_fix, double* dt_rec) {
+  DevState S2 = h->S;
+  S2.plist = T.plist;
+  S2.pcount = T.pcount;
+  S2.acc4 = T.acc4;
+  S2.visc = T.visc;
+  S2.rho = T.rho;
+  S2.pc = T.pc;
+  SPH_TRY(launch_step(h, 1, 0, nullptr, dt_fix, dt_rec, &S2, &T));
+  if (T.list != h->S.list) {
+    SPH_CUDA(h, cudaMemcpyAsync(T.list, h->S.list, (size_t)h->n * (size_t)h->S.cap * 4, cudaMemcpyDeviceToDevice,
+                                h->stream));
+    SPH_CUDA(h, cudaMemcpyAsync(T.lcount, h->S.lcount, (size_t)h->n * 4, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return SPH_OK;
+}
+
 
 }  // namespace
 
@@ -888,14 +970,11 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   const int c = obj->ckpt_every;
   const int nck = K > 0 ? (K + c - 1) / c : 0;
   const size_t nseg = (size_t)std::min(c, std::max(K, 1));
-  // device scratch: checkpoints, the segment being reversed, x_K, step sizes, host-side inputs
-  Temp tck(h, sizeof(double) * nd * (size_t)std::max(nck, 1)), tseg(h, sizeof(double) * nd * nseg),
-      txk(h, sizeof(double) * nd), tdt(h, sizeof(double) * 2 * (size_t)std::max(K, 1)),
-      tseed(h, (seed && !on_device) ? sizeof(double) * nd : 0);
-  if (!tck.p || !tseg.p || !txk.p || !tdt.p || !tseed.p)
-    return fail(h, SPH_ERR_OOM, "reverse-pass scratch allocation failed");
+  // device scratch: checkpoints, x_K, step sizes, host-side inputs
+  Temp tck(h, sizeof(double) * nd * (size_t)std::max(nck, 1)), txk(h, sizeof(double) * nd),
+      tdt(h, sizeof(double) * 2 * (size_t)std::max(K, 1)), tseed(h, (seed && !on_device) ? sizeof(double) * nd : 0);
+  if (!tck.p || !txk.p || !tdt.p || !tseed.p) return fail(h, SPH_ERR_OOM, "reverse-pass scratch allocation failed");
   double* ck = (double*)tck.p;
-  double* sg = (double*)tseg.p;
   double* xk = (double*)txk.p;
   double* dts = (double*)tdt.p;
   const double* seed_d = seed;
@@ -910,34 +989,56 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   SPH_CUDA(h, cudaMemsetAsync(h->S.err, 0, sizeof(int), h->stream));
   SPH_CUDA(h, cudaMemsetAsync(a.acc, 0, sizeof(double) * kAdjSlots, h->stream));
   if (launch_get_colors(h->S, a.col, h->stream) != cudaSuccess) return fail(h, SPH_ERR_CUDA, "colours");
-  // forward run with checkpoints; the step sizes are recorded (or prescribed)
+  // Forward run with a position checkpoint at the start of every segment; the
+  // step sizes are recorded (or prescribed). The last segment is taped on the
+  // way; every other segment is re-run from its checkpoint (with the recorded
+  // sizes) into the tape just before its reverse sweep.
+  SPH_TRY(ensure_tape(h, (int)nseg));
+  const std::vector<DevState>& tape = h->adj.tape;
+  const int last0 = nck > 0 ? (nck - 1) * c : 0;
   for (int s = 0; s < K; ++s) {
     if (s % c == 0) SPH_TRY(positions_to(h, ck + nd * (size_t)(s / c)));
-    SPH_TRY(launch_step(h, 0, 0, nullptr, dt_in ? dts + 2 * s : nullptr, dt_in ? nullptr : dts + 2 * s));
+    const double* fix = dt_in ? dts + 2 * s : nullptr;
+    double* rec = dt_in ? nullptr : dts + 2 * s;
+    if (s >= last0) {
+      SPH_TRY(taped_step(h, tape[s - last0], fix, rec));
+    } else if (!fix) {
+      // the handle's graph of one step, then its step sizes copied out
+      SPH_TRY(ensure_graph(h, 0));
+      SPH_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
+      SPH_CUDA(h, cudaMemcpyAsync(rec, &h->S.scal->dt1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      SPH_TRY(launch_step(h, 0, 0, nullptr, fix, rec));
+    }
     h->steps += 1;
   }
   SPH_TRY(positions_to(h, xk));
   // objective at x_K: the gradient seed
-  int cur = 0;
+  const int cur = 0;
   SPH_TRY(reverse_setup(h, false, nullptr));
   SPH_TRY(run_objective(h, obj->density_weight, obj->lambda, seed_d, a.g[cur]));
-  // reverse sweep, segment by segment
+  // reverse sweep, segment by segment; every re-run step and every reverse
+  // step is one replay of a graph cached per tape slot (the buffers are fixed)
+  const int fz = obj->frozen_dt ? 1 : 0;
   for (int seg = nck - 1; seg >= 0; --seg) {
     const int s0 = seg * c, s1 = std::min(K, s0 + c);
-    SPH_CUDA(h, cudaMemcpyAsync(sg, ck + nd * (size_t)seg, sizeof(double) * nd, cudaMemcpyDeviceToDevice,
-                                h->stream));
-    if (s1 - s0 > 1) {
-      SPH_TRY(set_state_at(h, sg, a.col, t0 + s0));
-      for (int s = s0; s < s1 - 1; ++s) {
-        SPH_TRY(launch_step(h, 0, 0, nullptr, dts + 2 * s, nullptr));
-        SPH_TRY(positions_to(h, sg + nd * (size_t)(s - s0 + 1)));
+    if (seg != nck - 1) {
+      SPH_TRY(set_state_at(h, ck + nd * (size_t)seg, a.col, t0 + s0));
+      for (int s = s0; s < s1; ++s) {
+        const int k = s - s0;
+        if (!a.g_rerun[k])
+          SPH_TRY(capture(h, &a.g_rerun[k], [&] { return taped_step(h, tape[k], a.tape_dt[k], nullptr); }));
+        SPH_CUDA(h, cudaMemcpyAsync(a.tape_dt[k], dts + 2 * s, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    h->stream));
+        SPH_CUDA(h, cudaGraphLaunch(a.g_rerun[k], h->stream));
       }
     }
     for (int s = s1 - 1; s >= s0; --s) {
-      SPH_TRY(set_state_at(h, sg + nd * (size_t)(s - s0), a.col, t0 + s));
-      SPH_TRY(reverse_setup(h, true, obj->frozen_dt ? dts + 2 * s : nullptr));
-      SPH_TRY(run_bwd_step(h, a.g[cur], a.g[1 - cur], !obj->frozen_dt, ramp_at(h, t0 + s)));
-      cur = 1 - cur;
+      const int k = s - s0;
+      if (!a.g_rev[fz][k])
+        SPH_TRY(capture(h, &a.g_rev[fz][k], [&] { return run_bwd_step(h, tape[k], a.g[0], a.g[1], !fz); }));
+      SPH_CUDA(h, cudaGraphLaunch(a.g_rev[fz][k], h->stream));
+      SPH_CUDA(h, cudaMemcpyAsync(a.g[0], a.g[1], sizeof(double) * nd, cudaMemcpyDeviceToDevice, h->stream));
     }
   }
   // results
@@ -965,6 +1066,297 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   return status_from_flags(h, flags);
 }
 
+// ================================================================ batch ==
+// Many independent instances stepped by one CUDA graph per step. Instance k's
+// step (its 12 kernels, predicated on its own list-rebuild flag) sits on
+// branch b(k) of the graph; the branches fork from and join to the batch's
+// stream, so instances on different branches run concurrently and fill the
+// SMs that one small instance leaves idle. Instances are dealt to branches
+// longest first onto the least-loaded branch (load = particles x dimension
+// cost); the branch count is the autotuned parameter.
+}  // extern "C"
+
+struct sph_batch {
+  std::vector<sph_handle*> inst;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> ev;  // [0]: fork, [1 + b]: join of branch b
+  cudaGraphExec_t gexec = nullptr;
+  int n_branches = 0;
+  std::vector<float> tuned_ms;  // per candidate branch count (autotuner)
+  std::vector<int> tuned_b;
+  std::string err;
+};
+
+namespace {
+
+double inst_cost(const sph_handle* h) { return (double)h->n * (h->dim == 3 ? 2.5 : 1.0); }
+
+sph_status batch_fail(sph_batch* b, sph_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+
+void batch_drop_graph(sph_batch* b) {
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  b->gexec = nullptr;
+}
+
+// capture one step of every instance into a graph with nb branches
+sph_status batch_capture(sph_batch* b, int nb) {
+  batch_drop_graph(b);
+  while ((int)b->branch.size() < nb) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess)
+      return batch_fail(b, SPH_ERR_CUDA, "stream creation failed");
+    b->branch.push_back(s);
+  }
+  while ((int)b->ev.size() < nb + 1) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return batch_fail(b, SPH_ERR_CUDA, "event creation failed");
+    b->ev.push_back(e);
+  }
+  // longest-first onto the least-loaded branch
+  std::vector<int> order(b->inst.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = (int)k;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return inst_cost(b->inst[x]) > inst_cost(b->inst[y]); });
+  std::vector<double> load(nb, 0.0);
+  std::vector<int> where(b->inst.size(), 0);
+  for (int k : order) {
+    int best = 0;
+    for (int q = 1; q < nb; ++q)
+      if (load[q] < load[best]) best = q;
+    where[k] = best;
+    load[best] += inst_cost(b->inst[k]);
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return batch_fail(b, SPH_ERR_CUDA, "begin capture");
+  sph_status st = SPH_OK;
+  if (cudaEventRecord(b->ev[0], b->stream) != cudaSuccess) st = SPH_ERR_CUDA;
+  for (int q = 0; q < nb && st == SPH_OK; ++q)
+    if (cudaStreamWaitEvent(b->branch[q], b->ev[0], 0) != cudaSuccess) st = SPH_ERR_CUDA;
+  // each branch issues its instances in submission order
+  for (size_t k = 0; k < order.size() && st == SPH_OK; ++k) {
+    sph_handle* h = b->inst[order[k]];
+    cudaStream_t keep = h->stream;
+    h->stream = b->branch[where[order[k]]];
+    st = launch_step(h, h->par.record_fields ? 1 : 0);
+    h->stream = keep;
+  }
+  for (int q = 0; q < nb && st == SPH_OK; ++q) {
+    if (cudaEventRecord(b->ev[1 + q], b->branch[q]) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ev[1 + q], 0) != cudaSuccess)
+      st = SPH_ERR_CUDA;
+  }
+  e = cudaStreamEndCapture(b->stream, &g);
+  if (st != SPH_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return batch_fail(b, SPH_ERR_CUDA, "capture of the batched step failed");
+  }
+  e = cudaGraphInstantiate(&b->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return batch_fail(b, SPH_ERR_CUDA, "graph instantiation failed");
+  b->n_branches = nb;
+  return SPH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sph_status sph_batch_create(const sph_instance_desc* descs, int32_t n_inst, const sph_alloc* alloc, void* stream,
+                            int32_t n_branches, sph_batch** out) {
+  if (!out || !descs || n_inst <= 0 || n_branches < 0) return SPH_ERR_INVALID_ARG;
+  *out = nullptr;
+  sph_batch* b = new sph_batch();
+  b->stream = (cudaStream_t)stream;
+  if (!b->stream) {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return SPH_ERR_CUDA;
+    }
+    b->own_stream = true;
+  }
+  for (int k = 0; k < n_inst; ++k) {
+    sph_handle* h = nullptr;
+    sph_params par = descs[k].params;
+    par.use_graph = 0;
+    sph_status s = sph_create(&descs[k].dom, &descs[k].field, descs[k].n_particles, descs[k].n_colors, &par, alloc,
+                              b->stream, &h);
+    if (s != SPH_OK) {
+      fprintf(stderr, "sph_batch_create: instance %d failed\n", k);
+      sph_batch_destroy(b);
+      return s;
+    }
+    b->inst.push_back(h);
+  }
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    sph_batch_destroy(b);
+    return SPH_ERR_CUDA;
+  }
+  if (n_branches > 0) {
+    sph_status s = batch_capture(b, std::min<int>(n_branches, n_inst));
+    if (s != SPH_OK) {
+      fprintf(stderr, "sph_batch_create: %s\n", b->err.c_str());
+      sph_batch_destroy(b);
+      return s;
+    }
+  }
+  *out = b;
+  return SPH_OK;
+}
+
+sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_candidates, int32_t steps_each) {
+  if (!b || !candidates || n_candidates <= 0 || steps_each <= 0) return SPH_ERR_INVALID_ARG;
+  // Every trial starts from the same state (so each sees the same steps and
+  // list rebuilds) and the state is put back afterwards.
+  std::vector<std::unique_ptr<Temp>> saved, cols;
+  std::vector<int64_t> steps0;
+  for (sph_handle* h : b->inst) {
+    saved.emplace_back(new Temp(h, sizeof(double) * (size_t)h->n * (size_t)h->dim));
+    cols.emplace_back(new Temp(h, (size_t)h->n));
+    steps0.push_back(h->steps);
+    if (h->n > 0) {
+      if (!saved.back()->p || !cols.back()->p) return batch_fail(b, SPH_ERR_OOM, "tuning snapshot allocation failed");
+      sph_status s = positions_to(h, (double*)saved.back()->p);
+      if (s != SPH_OK) return s;
+      if (launch_get_colors(h->S, (uint8_t*)cols.back()->p, h->stream) != cudaSuccess)
+        return batch_fail(b, SPH_ERR_CUDA, "tuning snapshot");
+    }
+  }
+  auto restore = [&]() -> sph_status {
+    for (size_t k = 0; k < b->inst.size(); ++k) {
+      sph_handle* h = b->inst[k];
+      if (h->n == 0) continue;
+      sph_status s = set_state_at(h, (const double*)saved[k]->p, (const uint8_t*)cols[k]->p, steps0[k]);
+      if (s != SPH_OK) return s;
+    }
+    return SPH_OK;
+  };
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  b->tuned_b.clear();
+  b->tuned_ms.clear();
+  int best = 0;
+  float best_ms = 0.0f;
+  sph_status st = SPH_OK;
+  for (int c = 0; c < n_candidates && st == SPH_OK; ++c) {
+    const int nb = std::max(1, std::min<int>(candidates[c], (int)b->inst.size()));
+    st = batch_capture(b, nb);
+    if (st != SPH_OK) break;
+    st = restore();
+    if (st != SPH_OK) break;
+    cudaGraphLaunch(b->gexec, b->stream);  // warm-up (rebuilds every list)
+    cudaEventRecord(e0, b->stream);
+    for (int s = 0; s < steps_each; ++s) cudaGraphLaunch(b->gexec, b->stream);
+    cudaEventRecord(e1, b->stream);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = batch_fail(b, SPH_ERR_CUDA, "tuning run failed");
+      break;
+    }
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    ms /= (float)steps_each;
+    b->tuned_b.push_back(nb);
+    b->tuned_ms.push_back(ms);
+    if (best == 0 || ms < best_ms) {
+      best = nb;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st == SPH_OK) st = restore();
+  saved.clear();
+  cols.clear();
+  if (st != SPH_OK) return st;
+  st = batch_capture(b, best);
+  if (st != SPH_OK) return st;
+  return cudaStreamSynchronize(b->stream) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+sph_status sph_batch_step(sph_batch* b, int32_t n_steps) {
+  if (!b || n_steps < 0) return SPH_ERR_INVALID_ARG;
+  if (!b->gexec) {
+    sph_status s = batch_capture(b, std::min<int>(16, (int)b->inst.size()));
+    if (s != SPH_OK) return s;
+  }
+  for (int s = 0; s < n_steps; ++s)
+    if (cudaGraphLaunch(b->gexec, b->stream) != cudaSuccess) return batch_fail(b, SPH_ERR_CUDA, "graph launch");
+  for (sph_handle* h : b->inst) {
+    h->steps += n_steps;
+    h->recorded = h->par.record_fields != 0;
+  }
+  return SPH_OK;
+}
+
+sph_status sph_batch_step_each(sph_batch* b, int32_t n_steps) {
+  if (!b || n_steps < 0) return SPH_ERR_INVALID_ARG;
+  for (sph_handle* h : b->inst) {
+    sph_status s = ensure_graph(h, h->par.record_fields ? 1 : 0);
+    if (s != SPH_OK) return s;
+  }
+  for (int s = 0; s < n_steps; ++s)
+    for (sph_handle* h : b->inst)
+      if (h->n > 0 && cudaGraphLaunch(h->gexec, h->stream) != cudaSuccess)
+        return batch_fail(b, SPH_ERR_CUDA, "graph launch");
+  for (sph_handle* h : b->inst) {
+    h->steps += n_steps;
+    h->recorded = h->par.record_fields != 0;
+  }
+  return SPH_OK;
+}
+
+sph_status sph_batch_get(sph_batch* b, int32_t k, sph_handle** h) {
+  if (!b || !h || k < 0 || k >= (int)b->inst.size()) return SPH_ERR_INVALID_ARG;
+  *h = b->inst[k];
+  return SPH_OK;
+}
+
+sph_status sph_batch_info(const sph_batch* b, int32_t* n_inst, int32_t* n_branches, int32_t* n_tuned,
+                          int32_t* tuned_branches, float* tuned_ms) {
+  if (!b) return SPH_ERR_INVALID_ARG;
+  if (n_inst) *n_inst = (int32_t)b->inst.size();
+  if (n_branches) *n_branches = b->n_branches;
+  if (n_tuned) *n_tuned = (int32_t)b->tuned_b.size();
+  for (size_t q = 0; q < b->tuned_b.size(); ++q) {
+    if (tuned_branches) tuned_branches[q] = b->tuned_b[q];
+    if (tuned_ms) tuned_ms[q] = b->tuned_ms[q];
+  }
+  return SPH_OK;
+}
+
+sph_status sph_batch_sync(sph_batch* b) {
+  if (!b) return SPH_ERR_INVALID_ARG;
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return batch_fail(b, SPH_ERR_CUDA, "sync");
+  for (sph_handle* h : b->inst) {
+    int flags = 0;
+    sph_status s = read_flags(h, &flags);
+    if (s != SPH_OK) return s;
+    s = status_from_flags(h, flags);
+    if (s != SPH_OK) return s;
+  }
+  return SPH_OK;
+}
+
+const char* sph_batch_last_error(const sph_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void sph_batch_destroy(sph_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  batch_drop_graph(b);
+  for (sph_handle* h : b->inst) sph_destroy(h);
+  for (cudaStream_t s : b->branch) cudaStreamDestroy(s);
+  for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
 const char* sph_last_error(const sph_handle* h) { return h ? h->err.c_str() : "null handle"; }
 
 sph_status sph_get_info(const sph_handle* h, int64_t* n, int32_t* dim, double* rho_scale) {
@@ -979,6 +1371,9 @@ void sph_destroy(sph_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  for (auto* v : {&h->adj.g_rerun, &h->adj.g_rev[0], &h->adj.g_rev[1]})
+    for (cudaGraphExec_t g : *v)
+      if (g) cudaGraphExecDestroy(g);
   for (auto& b : h->blocks) h->alloc.free(b.first, b.second, h->alloc.ctx);
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_stream) cudaStreamDestroy(h->stream);

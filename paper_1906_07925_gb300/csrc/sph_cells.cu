@@ -33,6 +33,7 @@ __global__ void k_gate(StepCtl* __restrict__ ctl, int force) {
 }
 
 __global__ void k_request_rebuild(StepCtl* __restrict__ ctl) { ctl->need_rebuild = 1; }
+__global__ void k_write_ctl(StepCtl* __restrict__ ctl, StepCtl v) { *ctl = v; }
 
 __global__ void __launch_bounds__(256) k_count(int n, const StepCtl* __restrict__ ctl, const uint32_t* __restrict__ key,
                                                uint32_t* __restrict__ cnt) {
@@ -206,6 +207,11 @@ __global__ void __launch_bounds__(256) k_get_colors(int n, const StepCtl* __rest
 
 cudaError_t launch_gate(const DevState& S, int force, cudaStream_t st) {
   k_gate<<<1, 1, 0, st>>>(S.ctl, force);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_write_ctl(const DevState& S, const StepCtl& v, cudaStream_t st) {
+  k_write_ctl<<<1, 1, 0, st>>>(S.ctl, v);
   return cudaGetLastError();
 }
 

@@ -49,6 +49,8 @@ struct DevState {
 cudaError_t launch_gate(const DevState& S, int force, cudaStream_t st);
 // the next step rebuilds the list (after set-up or a diagnostic evaluation)
 cudaError_t launch_request_rebuild(const DevState& S, cudaStream_t st);
+// overwrite the control block (a kernel: no host synchronisation)
+cudaError_t launch_write_ctl(const DevState& S, const StepCtl& v, cudaStream_t st);
 // cell list of the old order -> gather into the new order (predicated on ctl->rebuild)
 cudaError_t build_cells(const DevState& S, cudaStream_t st);
 // colours by particle id
@@ -110,17 +112,21 @@ struct AdjBufs {
   unsigned* ticket = nullptr;
 };
 
-// reverse pass of one step: the step's state, list and forward quantities
-// (pass A with advance = 0, pass B with move = 0 and record = 1) in place;
-// B.gin -> B.gout. ramp = sigma(t)/sigma0 of the step.
+// reverse pass of one step whose state, lists and forward quantities (a tape
+// slot) are in S; B.gin -> B.gout
 template <int D, class T>
-cudaError_t launch_bwd_step(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<double>& geo,
-                            const AdjBufs<T>& B, int recomputed_dt, int general_eos, double ramp, cudaStream_t st);
+cudaError_t launch_bwd_step(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& geo,
+                            const AdjBufs<T>& B, int recomputed_dt, int general_eos, cudaStream_t st);
 // objective at the current state (list in place) and its gradient -> B.gout;
 // B.gin (may be null) is an extra seed added to dL/dx
 template <int D, class T>
-cudaError_t launch_objective(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<double>& geo,
+cudaError_t launch_objective(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& geo,
                              const AdjBufs<T>& B, double wd, double lambda, cudaStream_t st);
+
+// copy the state pass A used (current order: X, meta, pid, view), ctl and
+// scal into tape.X[0], meta[0], pid[0], view[0], ctl, scal
+template <int D, class T>
+cudaError_t launch_tape_snapshot(const DevState& S, const DevState& tape, cudaStream_t st);
 
 // initial sampling (create)
 struct FieldBounds {
