@@ -45,6 +45,9 @@ WORKLOADS = {
                     "FP32 split-precision, seed 1",
                dim=2, n=1 << 20, ncol=64, precision="fp32", seed=1,
                make=lambda n, c: W.graded_hole_2d(n, c, rho_scale=0.0)),
+    "c4": dict(desc="adjoint: 2D graded hole + 8-coefficient polynomial density (seed 3), 262,144 particles, "
+                    "32 colours, FP32, K = 20 steps, checkpoint every 5",
+               dim=2, n=1 << 18, ncol=32, precision="fp32", seed=3, make=None),
     "c5": dict(desc="512 independent instances (256 2D + 256 3D), particle counts log-uniform in [2k, 200k] "
                     "(seed 4), 2-64 colours, random sphere/box region, linear graded spacing, FP32",
                dim=0, n=0, ncol=0, precision="fp32", seed=4, make=None),
@@ -189,7 +192,7 @@ def run_gpu(args, wl, rank, world):
     n = wl["n"]
     t_setup = time.perf_counter()
     r = Relaxation(p, n, wl["ncol"], precision=wl["precision"], seed=wl["seed"] + 1000 * rank, use_graph=True,
-                   skin=args.skin)
+                   skin=args.skin, cell_factor=args.cell_factor)
     torch.cuda.synchronize()
     log(f"[rank {rank}] create {time.perf_counter() - t_setup:.2f}s, grid {r.grid()['n_levels']} levels")
     stream = r.stream
@@ -419,6 +422,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skin", type=float, default=0.0, help="neighbour-list skin / (kappa h); 0: library default")
+    ap.add_argument("--cell-factor", type=float, default=0.0, help="finest cell edge / smallest support; 0: default")
     ap.add_argument("--particles", type=int, default=0,
                     help="override the particle count (small cases for profiler captures)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -426,6 +430,8 @@ def main():
     args = ap.parse_args()
     if args.workload == "c5":
         return main_batch(args)
+    if args.workload == "c4":
+        return main_adjoint(args)
     wl = dict(WORKLOADS[args.workload])
     if args.particles > 0:
         wl["n"] = args.particles
@@ -504,6 +510,31 @@ def main():
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def main_adjoint(args):
+    """Adjoint cost: backward (sph_backward: its forward run, the objective,
+    the checkpointed reverse sweep) over K forward steps, one GPU."""
+    rank = int(os.environ.get("RANK", "0"))
+    wl = WORKLOADS["c4"]
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        print(json.dumps({"impl": "reference", "unavailable": "the adjoint cost ratio is a GPU-only measurement; "
+                          "the oracle's reverse pass is a correctness reference (tests/test_oracle_adjoint.py)"}))
+        return
+    import torch
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    adj = run_adjoint(rank)
+    ck = clocks.stop()
+    if rank == 0:
+        print(json.dumps({"metric": "adjoint/forward cost ratio", "value": adj["ratio"], "unit": "x",
+                          "n_gpus": 1, "steps": adj["K"], "warmup": 1, "ms_per_step": adj["backward_ms"] / adj["K"],
+                          "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                          "data": "synthetic", "config": {"workload": wl["desc"]}, "clocks": ck, "adjoint": adj}),
+              flush=True)
 
 
 def main_batch(args):
