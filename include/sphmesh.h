@@ -131,6 +131,8 @@ typedef struct {
   int32_t n_levels;        /* cell levels of the multi-resolution grid */
   int64_t list_entries;    /* neighbour-list entries scanned by the last step (sum over i) */
   int64_t list_rebuilds;   /* neighbour-list builds so far */
+  int32_t list_max;        /* longest list of the last build (> list_capacity: overflow) */
+  int32_t list_capacity;   /* entries per particle the lists hold */
 } sph_stats;
 
 typedef struct {

@@ -56,7 +56,8 @@ class sph_stats(C.Structure):
                 ("err_l2", C.c_double), ("err_max", C.c_double), ("interface_pairs", C.c_int64),
                 ("force_pairs", C.c_int64), ("wall_moved", C.c_int64), ("rho_scale", C.c_double),
                 ("error_flags", C.c_int32), ("n_levels", C.c_int32),
-                ("list_entries", C.c_int64), ("list_rebuilds", C.c_int64)]
+                ("list_entries", C.c_int64), ("list_rebuilds", C.c_int64), ("list_max", C.c_int32),
+                ("list_capacity", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -127,11 +127,21 @@ void setup_frames(sph_handle* h) {
 
 // expected list length for a support kappa h and a skin: the ball of radius
 // kappa h (1 + skin) holds about V_d (kappa tau (1 + skin))^d particles
+// Expected list length: the list radius R = kappa max(h_i, h_j)(1 + skin) is at
+// most g h_i with g = kappa (1 + skin) / (1 - kappa L (1 + skin)) (h_j <= h_i + L r,
+// L the field's Lipschitz bound of h), and inside that ball the number density
+// (tau/h)^d is at most (tau/h_i)^d / (1 - L g)^d. The capacity is the larger of
+// twice that and that plus ten standard deviations of a Poisson count (random
+// initial states cluster), plus 16.
 int auto_capacity(const sph_handle* h) {
   const double skin = h->par.skin > 0 ? h->par.skin : kDefaultSkin;
-  const double r = h->par.kappa * h->par.tau * (1.0 + skin) * 1.05;
-  const double e = h->dim == 2 ? M_PI * r * r : 4.0 / 3.0 * M_PI * r * r * r;
-  int cap = (int)std::ceil(2.0 * e + 16.0);
+  const double k1 = h->par.kappa * (1.0 + skin);
+  const double L = std::min(h->lip_h, 0.5 / k1);
+  const double g = k1 / (1.0 - L * k1);
+  const double dens = std::pow(1.0 / std::max(1.0 - L * g, 0.25), (double)h->dim);
+  const double r = h->par.tau * g * 1.05;
+  const double e = (h->dim == 2 ? M_PI * r * r : 4.0 / 3.0 * M_PI * r * r * r) * dens;
+  int cap = (int)std::ceil(std::max(2.0 * e, e + 10.0 * std::sqrt(e)) + 16.0);
   return (cap + 7) & ~7;
 }
 
@@ -821,6 +831,8 @@ sph_status sph_get_stats(sph_handle* h, sph_stats* out) {
   out->n_levels = h->hg.n_levels;
   out->list_entries = sc.lentries;
   out->list_rebuilds = ctl.rebuilds;
+  out->list_max = ctl.lmax;
+  out->list_capacity = h->S.cap;
   return status_from_flags(h, flags);
 }
 

@@ -26,6 +26,7 @@ __global__ void k_gate(StepCtl* __restrict__ ctl, int force) {
     c.buf ^= 1;
     c.need_rebuild = 0;
     c.rebuilds += 1;
+    c.lmax = 0;
   } else {
     c.rebuild = 0;
   }

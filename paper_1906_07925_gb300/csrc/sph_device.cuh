@@ -107,6 +107,7 @@ struct StepCtl {
   long long step;
   double t0, t1, sigma0;
   int buf, vp, rebuild, need_rebuild;
+  int lmax, pad_;  // longest neighbour list of the last build
   long long rebuilds;
 };
 

@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cfloat>
+#include <climits>
 #include <type_traits>
 
 #include "sph_internal.h"
@@ -243,7 +244,7 @@ __global__ void __launch_bounds__(256) k_make_view(int n, const StepCtl* __restr
 // criteria is still listed. Candidates come from rows of cells of every level
 // that can hold such a j.
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_list_build(int n, const StepCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(256) k_list_build(int n, StepCtl* __restrict__ ctl,
                                                     const LL4* __restrict__ X0, const LL4* __restrict__ X1,
                                                     const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
                                                     const typename ViewOf<T>::type* __restrict__ v0,
@@ -349,6 +350,10 @@ __global__ void __launch_bounds__(256) k_list_build(int n, const StepCtl* __rest
   const bool fast = reach < T(0.999) * T(1 << (22 - kCoarseBits));
   lcount[i] = (uint32_t)(cnt < cap ? cnt : cap) | (fast ? kFastBit : 0u);
   if (over) atomicOr(err, kErrListOverflow);
+  // longest list of this build (one atomic per warp)
+  const unsigned mask = __activemask();
+  const int wmax = __reduce_max_sync(mask, cnt);
+  if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicMax(&ctl->lmax, wmax);
 }
 
 // --------------------------------------------------------------------------
