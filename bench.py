@@ -102,10 +102,15 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "25"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once the sampler is producing samples
+            t0 = time.time()
+            while not self.lines and time.time() - t0 < 5.0:
+                time.sleep(0.01)
+            self.lines.clear()
         except Exception:
             self.proc = None
 
@@ -198,6 +203,13 @@ def run_gpu(args, wl, rank, world):
     stream = r.stream
     r.step(args.warmup)
     r.sync()
+    # the state the timed steps start from, kept in pinned host memory: the
+    # end-to-end run below replays exactly these steps from the host
+    d = wl["dim"]
+    xh = torch.empty((n, d), dtype=torch.float64, pin_memory=True)
+    ch = torch.empty((n,), dtype=torch.uint8, pin_memory=True)
+    xh.numpy()[:] = r.positions()
+    ch.numpy()[:] = r.colors()
 
     def barrier():
         if world > 1:
@@ -231,13 +243,9 @@ def run_gpu(args, wl, rank, world):
     ph = r.step_profiled(kprof)
     phase_ms = {"cells": ph[0] / kprof, "pass_a": ph[1] / kprof, "pass_b": ph[2] / kprof}
 
-    # end to end through the public API with host buffers: upload the state
-    # from pinned memory, K steps, read positions and stats back
-    d = wl["dim"]
-    xh = torch.empty((n, d), dtype=torch.float64, pin_memory=True)
-    ch = torch.empty((n,), dtype=torch.uint8, pin_memory=True)
-    xh.numpy()[:] = r.positions()
-    ch.numpy()[:] = r.colors()
+    # end to end through the public API with host buffers: upload the state the
+    # timed steps started from (pinned memory), the same K steps, positions and
+    # statistics back
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -416,7 +424,7 @@ def batch_oracle_sample(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])

@@ -133,6 +133,7 @@ typedef struct {
   int64_t list_rebuilds;   /* neighbour-list builds so far */
   int32_t list_max;        /* longest list of the last build (> list_capacity: overflow) */
   int32_t list_capacity;   /* entries per particle the lists hold */
+  double ramp_t0, ramp_t1; /* surface-tension ramp window in steps (-1: none yet) */
 } sph_stats;
 
 typedef struct {
@@ -181,6 +182,16 @@ sph_status sph_step_profiled(sph_handle* h, int32_t n_steps, float* ms_out);
  * linear to 0 on (t0, t1], 0 after; step counted from sph_set_state/create.
  * t0 < 0 removes the ramp. Errors: INVALID_ARG (t1 <= t0 with t0 >= 0). */
 sph_status sph_ramp_surface_tension(sph_handle* h, int64_t t0_step, int64_t t1_step);
+
+/* Start the ramp automatically when the partition has converged (Sec. 3.3,
+ * "topology static for e.g. 50 iterations"): after a step whose interface-pair
+ * count closes a run of `window` steps that all stayed within `tol` (relative)
+ * of the count that opened the run, t0 = that step and t1 = (1 + theta) t0
+ * (theta in [0.1, 0.2] in the paper). The test runs on the device inside the
+ * step (no host synchronisation); sph_get_stats reports the window it chose.
+ * window = 0 turns it off; sph_ramp_surface_tension also turns it off.
+ * Errors: INVALID_ARG (window < 0, tol < 0, theta <= 0). Synchronises. */
+sph_status sph_auto_ramp(sph_handle* h, int32_t window, double tol, double theta);
 
 /* Current positions (n x dim doubles, particle-id order). Synchronises. */
 sph_status sph_get_positions(sph_handle* h, double* out, int32_t on_device);

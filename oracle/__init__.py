@@ -277,3 +277,42 @@ def backward(p, pos0, col, n_steps, lam, dt=None, seed=None, start_step=0):
     if rc != 0:
         raise RuntimeError("oracle backward failed")
     return dict(L=L.value, dpos0=dpos, grads=dict(zip(GRAD_NAMES, g)), dt=dt_out.reshape(-1, 2))
+
+
+def convergence_step(counts, window, tol):
+    """Index of the step at which the partition is taken as converged (Sec. 3.3:
+    the interface topology stays static for a number of iterations, e.g. 50),
+    read as: the interface-pair count of every step stays within tol (relative)
+    of the count that opened the current run for `window` further steps.
+    counts[s] is step s's count; returns the first s that closes such a run,
+    or None."""
+    ref, stable = None, 0
+    for s, c in enumerate(counts):
+        if ref is not None and abs(c - ref) <= tol * ref:
+            stable += 1
+        else:
+            ref, stable = c, 0
+        if stable >= window:
+            return s
+    return None
+
+
+def run_auto_ramp(p, pos, col, n_steps, window, tol, theta, start_step=0, mode=1):
+    """n_steps steps with the surface-tension ramp started automatically: once
+    convergence_step fires at step s, t0 = s and t1 = (1 + theta) t0 (the ramp
+    of Eq. sph_st_sigma over the fraction theta of the steps taken, Sec. 3.3).
+    Returns (pos, infos, t0)."""
+    import copy
+    q = copy.deepcopy(p)
+    q.t0, q.t1 = -1.0, -1.0
+    infos, counts, t0 = [], [], None
+    for s in range(n_steps):
+        step_index = start_step + s
+        pos, info, _ = step(q, pos, col, step_index, mode, want=False)
+        infos.append(info)
+        if t0 is None:
+            counts.append(info["interface_pairs"])
+            if convergence_step(counts, window, tol) == len(counts) - 1:
+                t0 = step_index
+                q.t0, q.t1 = float(t0), (1.0 + theta) * t0
+    return pos, infos, t0

@@ -166,6 +166,10 @@ class Relaxation:
     def ramp_surface_tension(self, t0, t1):
         self._check(self.lib.sph_ramp_surface_tension(self.h, int(t0), int(t1)))
 
+    def auto_ramp(self, window=50, tol=1e-3, theta=0.15):
+        """Start the ramp when the partition has converged (sph_auto_ramp)."""
+        self._check(self.lib.sph_auto_ramp(self.h, int(window), float(tol), float(theta)))
+
     def positions(self, out=None):
         """(n, dim) float64 in particle-id order: numpy, or into a CUDA tensor `out`."""
         if out is not None:

@@ -57,7 +57,7 @@ class sph_stats(C.Structure):
                 ("force_pairs", C.c_int64), ("wall_moved", C.c_int64), ("rho_scale", C.c_double),
                 ("error_flags", C.c_int32), ("n_levels", C.c_int32),
                 ("list_entries", C.c_int64), ("list_rebuilds", C.c_int64), ("list_max", C.c_int32),
-                ("list_capacity", C.c_int32)]
+                ("list_capacity", C.c_int32), ("ramp_t0", C.c_double), ("ramp_t1", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -115,6 +115,7 @@ def load():
             "sph_step": [H, C.c_int32],
             "sph_step_profiled": [H, C.c_int32, P(C.c_float)],
             "sph_ramp_surface_tension": [H, C.c_int64, C.c_int64],
+            "sph_auto_ramp": [H, C.c_int32, C.c_double, C.c_double],
             "sph_get_positions": [H, C.c_void_p, C.c_int32],
             "sph_get_colors": [H, C.c_void_p, C.c_int32],
             "sph_get_stats": [H, P(sph_stats)],

@@ -41,6 +41,8 @@ struct sph_handle {
   std::vector<std::pair<void*, size_t>> blocks;
   int64_t steps = 0;
   double t0 = -1.0, t1 = -1.0;
+  int auto_window = 0;  // > 0: automatic ramp start (sph_auto_ramp)
+  double auto_tol = 0.0, auto_theta = 0.0;
   bool recorded = false;
   cudaGraphExec_t gexec = nullptr;
   int graph_record = -1;
@@ -266,18 +268,25 @@ sph_status write_ctl_all(sph_handle* h) {
   c.rebuild = 0;
   c.need_rebuild = 1;
   c.rebuilds = 0;
+  c.auto_on = h->auto_window > 0;
+  c.auto_window = h->auto_window;
+  c.auto_tol = h->auto_tol;
+  c.auto_theta = h->auto_theta;
+  c.auto_ref = -1;
   SPH_CUDA(h, launch_write_ctl(h->S, c, h->stream));
   return SPH_OK;
 }
 
-// only the schedule and the counter (the list bookkeeping stays on the device)
+// only the schedule and the counter (the list bookkeeping stays on the device);
+// with the automatic ramp on, the device owns the schedule
 sph_status write_ctl_sched(sph_handle* h) {
   const double sched[2] = {h->t0, h->t1};
   const long long step = h->steps;
   SPH_CUDA(h, cudaMemcpyAsync((char*)h->S.ctl + offsetof(StepCtl, step), &step, sizeof step,
                               cudaMemcpyHostToDevice, h->stream));
-  SPH_CUDA(h, cudaMemcpyAsync((char*)h->S.ctl + offsetof(StepCtl, t0), sched, sizeof sched,
-                              cudaMemcpyHostToDevice, h->stream));
+  if (h->auto_window <= 0)
+    SPH_CUDA(h, cudaMemcpyAsync((char*)h->S.ctl + offsetof(StepCtl, t0), sched, sizeof sched,
+                                cudaMemcpyHostToDevice, h->stream));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   return SPH_OK;
 }
@@ -767,7 +776,37 @@ sph_status sph_ramp_surface_tension(sph_handle* h, int64_t t0, int64_t t1) {
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   h->t0 = t0 < 0 ? -1.0 : (double)t0;
   h->t1 = t0 < 0 ? -1.0 : (double)t1;
+  if (h->auto_window > 0) {  // an explicit schedule replaces the automatic one
+    h->auto_window = 0;
+    const int off = 0;
+    SPH_CUDA(h, cudaMemcpyAsync((char*)h->S.ctl + offsetof(StepCtl, auto_on), &off, sizeof off,
+                                cudaMemcpyHostToDevice, h->stream));
+  }
   return write_ctl_sched(h);
+}
+
+sph_status sph_auto_ramp(sph_handle* h, int32_t window, double tol, double theta) {
+  if (!h || window < 0 || !(tol >= 0.0) || !(theta > 0.0)) return fail(h, SPH_ERR_INVALID_ARG, "bad arguments");
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  StepCtl c{};
+  SPH_CUDA(h, cudaMemcpy(&c, h->S.ctl, sizeof c, cudaMemcpyDeviceToHost));
+  h->auto_window = window;
+  h->auto_tol = tol;
+  h->auto_theta = theta;
+  if (window > 0) {
+    h->t0 = h->t1 = -1.0;
+    c.t0 = c.t1 = -1.0;
+  }
+  c.auto_on = window > 0;
+  c.auto_window = window;
+  c.auto_tol = tol;
+  c.auto_theta = theta;
+  c.auto_stable = 0;
+  c.auto_done = 0;
+  c.auto_ref = -1;
+  SPH_CUDA(h, launch_write_ctl(h->S, c, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SPH_OK;
 }
 
 sph_status sph_get_positions(sph_handle* h, double* out, int32_t on_device) {
@@ -833,6 +872,12 @@ sph_status sph_get_stats(sph_handle* h, sph_stats* out) {
   out->list_rebuilds = ctl.rebuilds;
   out->list_max = ctl.lmax;
   out->list_capacity = h->S.cap;
+  out->ramp_t0 = ctl.t0;
+  out->ramp_t1 = ctl.t1;
+  if (h->auto_window > 0 && ctl.auto_done) {  // the device fixed the schedule
+    h->t0 = ctl.t0;
+    h->t1 = ctl.t1;
+  }
   return status_from_flags(h, flags);
 }
 

@@ -109,6 +109,12 @@ struct StepCtl {
   int buf, vp, rebuild, need_rebuild;
   int lmax, pad_;  // longest neighbour list of the last build
   long long rebuilds;
+  // automatic start of the ramp (Sec. 3.3 convergence test): on, run length in
+  // steps, relative tolerance, ramp fraction; state: current run, its opening
+  // count (-1: none yet), fired
+  int auto_on, auto_window, auto_stable, auto_done;
+  double auto_tol, auto_theta;
+  long long auto_ref;
 };
 
 __device__ __forceinline__ double sigma_of(const StepCtl& c, long long t) {

@@ -23,9 +23,13 @@
 
 #include "sph_internal.h"
 
-// resident 256-thread blocks per SM asked of the pair passes (caps registers)
+// resident 256-thread blocks per SM asked of the pair passes and of the list
+// build (caps registers)
 #ifndef SPH_PASS_MIN_BLOCKS
 #define SPH_PASS_MIN_BLOCKS 5
+#endif
+#ifndef SPH_LIST_MIN_BLOCKS
+#define SPH_LIST_MIN_BLOCKS 4
 #endif
 
 namespace sph {
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(256) k_make_view(int n, const StepCtl* __restr
 // criteria is still listed. Candidates come from rows of cells of every level
 // that can hold such a j.
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_list_build(int n, StepCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, StepCtl* __restrict__ ctl,
                                                     const LL4* __restrict__ X0, const LL4* __restrict__ X1,
                                                     const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
                                                     const typename ViewOf<T>::type* __restrict__ v0,
@@ -616,6 +620,27 @@ __global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, Step
     scal->lentries = acc.lentries;
     scal->wall_moved = 0;
     scal->step_of_stats = step;
+    if (advance && cc.auto_on && !cc.auto_done) {
+      // convergence of the partition (Sec. 3.3): the interface-pair count stays
+      // within auto_tol of the count that opened the run for auto_window steps;
+      // then the ramp of Eq. sph_st_sigma starts: t0 = this step, t1 = (1 + theta) t0
+      const long long ip = acc.ipairs / 2;
+      long long ref = cc.auto_ref;
+      int stable = cc.auto_stable;
+      if (ref >= 0 && fabs((double)(ip - ref)) <= cc.auto_tol * (double)ref) {
+        ++stable;
+      } else {
+        ref = ip;
+        stable = 0;
+      }
+      ctl->auto_ref = ref;
+      ctl->auto_stable = stable;
+      if (stable >= cc.auto_window) {
+        ctl->t0 = (double)step;
+        ctl->t1 = (1.0 + cc.auto_theta) * (double)step;
+        ctl->auto_done = 1;
+      }
+    }
     if (advance) ctl->step = step + 1;
     *ticket = 0u;
   }

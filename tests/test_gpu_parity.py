@@ -257,3 +257,27 @@ def test_create_samples_inside_region_with_target_density():
     want = np.mean(np.abs(np.linalg.norm(q - 0.5, axis=1) - 0.2) < 0.05)
     assert near == pytest.approx(want, rel=0.03)
     r.close()
+
+
+def test_auto_ramp_fires_at_the_oracles_step():
+    """Automatic start of the ramp (the convergence test of Sec. 3.3, read as
+    in oracle.convergence_step): on the 4,096-particle square in FP64 the GPU
+    fires at the same step as the oracle, takes the same ramp window, and the
+    trajectories through the ramp stay as close as plain FP64 ones."""
+    p, pos, col = c1_state()
+    window, tol, theta, n = 10, 0.02, 0.15, 45
+    xo, infos, t0 = oracle.run_auto_ramp(p, pos, col, n, window, tol, theta)
+    assert t0 is not None and t0 < n - 5
+    r = make_gpu(p, pos, col, "fp64")
+    r.auto_ramp(window, tol, theta)
+    r.step(n)
+    st = r.stats()
+    assert st["ramp_t0"] == t0
+    assert st["ramp_t1"] == pytest.approx((1 + theta) * t0, rel=1e-15)
+    assert st["sigma"] == pytest.approx(infos[-1]["sigma"], abs=1e-12)
+    assert np.abs(r.positions() - xo).max() < 1e-6 * (1 / 64)
+    # an explicit schedule turns the automatic one off
+    r.ramp_surface_tension(100, 120)
+    r.step(1)
+    assert r.stats()["ramp_t0"] == 100
+    r.close()

@@ -374,3 +374,19 @@ def test_viscous_kick_slows_separation(orc):
         assert np.linalg.norm(d[i]) < np.linalg.norm(inviscid[i])
         assert abs(d[i, 0] * e[1] - d[i, 1] * e[0]) < 1e-15
     assert np.dot(d[0], e) > 0 > np.dot(d[1], e)
+
+
+# ------------------------------------------------- convergence detection ----
+
+def test_convergence_step_rule(orc):
+    """The reading of Sec. 3.3's convergence test on hand-made count sequences:
+    a run opens at a count, each later count within tol of it extends the run,
+    a count outside restarts it; the run closes after `window` extensions."""
+    f = orc.convergence_step
+    assert f([100] * 6, 5, 1e-3) == 5
+    assert f([100] * 5, 5, 1e-3) is None
+    # 100.05 is within 0.1 % of 100; 101 is not and restarts the run at 101
+    assert f([100, 100, 100.05, 101, 101, 101, 101, 101, 101], 5, 1e-3) == 8
+    assert f([100, 90, 80, 70, 60, 50], 2, 1e-3) is None
+    assert f([1000, 1001, 999, 1000], 3, 1e-3) == 3
+    assert f([1000, 1002, 1000, 1000], 3, 1e-3) is None
