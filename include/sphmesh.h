@@ -248,10 +248,13 @@ sph_status sph_load(sph_handle* h, const void* buf, size_t nbytes);
  * argmin particle); with frozen_dt = 1 they are constants: those of dt_in when
  * given, else those this run chose.
  *
- * Memory: the run keeps a checkpoint of the positions every ckpt_every steps
- * and recomputes the steps in between during the reverse sweep (FP64, by
- * particle id: ceil(K / ckpt_every) + ckpt_every + 3 arrays of n x dim
- * doubles, through the handle's allocator, released before returning).
+ * Memory: the run keeps the positions (FP64, by particle id) at the start of
+ * every segment of ckpt_every steps and re-runs each segment from there into a
+ * tape of ckpt_every steps (each step's state, a, a~, rho and force pairs:
+ * roughly 100 + 4 * list_capacity bytes per particle) just before reversing it.
+ * Checkpoints, tape and five n-sized reverse-pass arrays are allocated once
+ * through the handle's allocator (grown when K or ckpt_every grows) and kept
+ * until sph_destroy.
  * --------------------------------------------------------------------------- */
 typedef struct {
   double density_weight; /* w: weight of the density-error term */

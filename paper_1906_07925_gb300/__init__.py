@@ -196,7 +196,10 @@ class Relaxation:
         g = B.sph_grad()
         if out is not None:
             torch = self._torch
-            dt_dev = torch.zeros((max(int(n_steps), 0), 2), dtype=torch.float64, device=out.device)
+            dt_dev = getattr(self, "_dt_dev", None)
+            if dt_dev is None or dt_dev.shape[0] != max(int(n_steps), 0) or dt_dev.device != out.device:
+                dt_dev = torch.zeros((max(int(n_steps), 0), 2), dtype=torch.float64, device=out.device)
+                self._dt_dev = dt_dev
             self._check(self.lib.sph_backward(self.h, int(n_steps), C.byref(obj),
                                               None if seed is None else seed.data_ptr(),
                                               None if dt is None else dt.data_ptr(),

@@ -56,7 +56,10 @@ struct sph_handle {
     uint8_t* col = nullptr;  // colours by particle id
     std::vector<DevState> tape;  // taped-step slots (grown on demand, freed with the handle)
     std::vector<double*> tape_dt;  // per slot: {dt1, dt2} a re-run step reads
-    std::vector<cudaGraphExec_t> g_rerun, g_rev[2];  // per slot: re-run step; reverse step (recomputed, frozen)
+    std::vector<cudaGraphExec_t> g_rerun;     // per slot: re-run step
+    std::vector<cudaGraphExec_t> g_rev[2][2];  // per step-size mode, direction (g0 -> g1, g1 -> g0) and slot
+    double *ck = nullptr, *xk = nullptr, *dts = nullptr, *seed = nullptr;  // checkpoints, x_K, step sizes, seed
+    size_t ck_n = 0, dts_n = 0;                                           // their capacities (grown on demand)
   } adj;
   std::string err;
 };
@@ -369,7 +372,9 @@ sph_status reverse_setup(sph_handle* h, bool forward, const double* dt_fix) {
   f.move = 0;
   f.dt_fix = dt_fix;
   const bool f64 = h->prec == SPH_PREC_FP64;
-  cudaError_t e = launch_gate(S, 1, h->stream);
+  // without `forward` (the objective at x_K) the list is rebuilt only if the
+  // last step asked for it: otherwise it still holds every pair of x_K
+  cudaError_t e = launch_gate(S, forward ? 1 : 0, h->stream);
   if (e == cudaSuccess) {
     if (h->dim == 2)
       e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
@@ -510,8 +515,8 @@ sph_status ensure_tape(sph_handle* h, int slots) {
     tape.push_back(T);
     h->adj.tape_dt.push_back(dt);
     h->adj.g_rerun.push_back(nullptr);
-    h->adj.g_rev[0].push_back(nullptr);
-    h->adj.g_rev[1].push_back(nullptr);
+    for (auto& m : h->adj.g_rev)
+      for (auto& v : m) v.push_back(nullptr);
   }
   return SPH_OK;
 }
@@ -1032,17 +1037,27 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   const int c = obj->ckpt_every;
   const int nck = K > 0 ? (K + c - 1) / c : 0;
   const size_t nseg = (size_t)std::min(c, std::max(K, 1));
-  // device scratch: checkpoints, x_K, step sizes, host-side inputs
-  Temp tck(h, sizeof(double) * nd * (size_t)std::max(nck, 1)), txk(h, sizeof(double) * nd),
-      tdt(h, sizeof(double) * 2 * (size_t)std::max(K, 1)), tseed(h, (seed && !on_device) ? sizeof(double) * nd : 0);
-  if (!tck.p || !txk.p || !tdt.p || !tseed.p) return fail(h, SPH_ERR_OOM, "reverse-pass scratch allocation failed");
-  double* ck = (double*)tck.p;
-  double* xk = (double*)txk.p;
-  double* dts = (double*)tdt.p;
+  // device scratch (kept by the handle, grown on demand): checkpoints, x_K,
+  // step sizes, a host-side seed
+  if ((size_t)std::max(nck, 1) > a.ck_n) {
+    SPH_TRY(grab(h, a.ck, nd * (size_t)std::max(nck, 1)));
+    a.ck_n = (size_t)std::max(nck, 1);
+  }
+  if (!a.xk) {
+    SPH_TRY(grab(h, a.xk, nd));
+    SPH_TRY(grab(h, a.seed, nd));
+  }
+  if ((size_t)std::max(K, 1) > a.dts_n) {
+    SPH_TRY(grab(h, a.dts, 2 * (size_t)std::max(K, 1)));
+    a.dts_n = (size_t)std::max(K, 1);
+  }
+  double* ck = a.ck;
+  double* xk = a.xk;
+  double* dts = a.dts;
   const double* seed_d = seed;
   if (seed && !on_device) {
-    SPH_CUDA(h, cudaMemcpyAsync(tseed.p, seed, sizeof(double) * nd, cudaMemcpyHostToDevice, h->stream));
-    seed_d = (const double*)tseed.p;
+    SPH_CUDA(h, cudaMemcpyAsync(a.seed, seed, sizeof(double) * nd, cudaMemcpyHostToDevice, h->stream));
+    seed_d = a.seed;
   }
   if (dt_in) {
     SPH_CUDA(h, cudaMemcpyAsync(dts, dt_in, sizeof(double) * 2 * (size_t)K,
@@ -1075,8 +1090,8 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
     h->steps += 1;
   }
   SPH_TRY(positions_to(h, xk));
-  // objective at x_K: the gradient seed
-  const int cur = 0;
+  // objective at x_K: the gradient seed (g[cur])
+  int cur = 0;
   SPH_TRY(reverse_setup(h, false, nullptr));
   SPH_TRY(run_objective(h, obj->density_weight, obj->lambda, seed_d, a.g[cur]));
   // reverse sweep, segment by segment; every re-run step and every reverse
@@ -1097,10 +1112,10 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
     }
     for (int s = s1 - 1; s >= s0; --s) {
       const int k = s - s0;
-      if (!a.g_rev[fz][k])
-        SPH_TRY(capture(h, &a.g_rev[fz][k], [&] { return run_bwd_step(h, tape[k], a.g[0], a.g[1], !fz); }));
-      SPH_CUDA(h, cudaGraphLaunch(a.g_rev[fz][k], h->stream));
-      SPH_CUDA(h, cudaMemcpyAsync(a.g[0], a.g[1], sizeof(double) * nd, cudaMemcpyDeviceToDevice, h->stream));
+      cudaGraphExec_t& g = a.g_rev[fz][cur][k];
+      if (!g) SPH_TRY(capture(h, &g, [&] { return run_bwd_step(h, tape[k], a.g[cur], a.g[1 - cur], !fz); }));
+      SPH_CUDA(h, cudaGraphLaunch(g, h->stream));
+      cur = 1 - cur;
     }
   }
   // results
@@ -1433,7 +1448,8 @@ void sph_destroy(sph_handle* h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
-  for (auto* v : {&h->adj.g_rerun, &h->adj.g_rev[0], &h->adj.g_rev[1]})
+  for (auto* v : {&h->adj.g_rerun, &h->adj.g_rev[0][0], &h->adj.g_rev[0][1], &h->adj.g_rev[1][0],
+                  &h->adj.g_rev[1][1]})
     for (cudaGraphExec_t g : *v)
       if (g) cudaGraphExecDestroy(g);
   for (auto& b : h->blocks) h->alloc.free(b.first, b.second, h->alloc.ctx);
