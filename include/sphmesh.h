@@ -165,7 +165,7 @@ sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_p
  * Resets the step counter. Errors: INVALID_ARG, CUDA. */
 sph_status sph_set_state(sph_handle* h, const double* xyz, const uint8_t* col, int32_t on_device);
 
-/* Advance n_steps relaxation steps (Algorithm 1, lines 6-16): cell list,
+/* Advance n_steps relaxation steps (Algorithm 1): cell list,
  * density + pressure + surface-tension forces, time step, viscous force,
  * two-stage integration, level-set projection. Asynchronous on the handle's
  * stream. Errors: INVALID_ARG, CUDA, STATE. */
@@ -211,7 +211,7 @@ sph_status sph_get_stats(sph_handle* h, sph_stats* out);
 enum { SPH_OUT_RHO = 0, SPH_OUT_ACC = 1, SPH_OUT_VISC = 2 };
 sph_status sph_get_field(sph_handle* h, int32_t which, double* out, int32_t on_device);
 
-/* Neighbour sets of the current state (Algorithm 1, line 8), per particle id:
+/* Neighbour sets of the current state (Algorithm 1's neighbour search), per particle id:
  * density set (r_ij < kappa h_i, self included) and force set (j != i,
  * r_ij < kappa (h_i + h_j)/2): sizes and the sum of member ids. Any output may
  * be NULL. Host arrays. Synchronises. */
@@ -237,7 +237,7 @@ sph_status sph_load(sph_handle* h, const void* buf, size_t nbytes);
 
 /* ---------------------------------------------------------------------------
  * Sensitivities of a relaxation run (reverse mode). The paper tunes nothing by
- * gradient; this differentiates K steps of Algorithm 1 (lines 6-16) as the
+ * gradient; this differentiates K steps of Algorithm 1 as the
  * library computes them, for the objective
  *   L = w sum_i (rho_i/rho_t,i - 1)^2 + lambda sum_{i<j, C_i != C_j} W(r_ij, kappa h_ij)
  * at the end state (rho from Eq. density_sum, W the kernel), plus seed . x_K

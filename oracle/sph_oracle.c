@@ -210,7 +210,7 @@ double orc_total_mass(const orc_problem* p, int res) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Neighbour search (Algorithm 1, line 8).                                   */
+/* Neighbour search (the neighbour sets of Algorithm 1).                     */
 /* Density set of i: all j (self included) with r_ij < kappa h_i            */
 /*   (Eq. density_sum gathers with h_i).                                     */
 /* Force set of i: all j != i with r_ij < kappa h_ij, h_ij = (h_i + h_j)/2   */
@@ -407,7 +407,7 @@ int orc_neighbor_sets(const orc_problem* p, int64_t n, const double* pos, int mo
 }
 
 /* ------------------------------------------------------------------------ */
-/* One relaxation step (Algorithm 1, lines 6-16).                            */
+/* One relaxation step (Algorithm 1).                                        */
 /* ------------------------------------------------------------------------ */
 static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,
                      int mode, const double* dt_fixed, orc_step_info* info, double* rho_out,
@@ -430,12 +430,12 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
   double* eta = (double*)malloc(sizeof(double) * (size_t)n);
   if (!h || !rt || !rho || !Pc || !a || !vt || !at || !eta) return -1;
 
-  /* line 6: target density and scale at r_i^n */
+  /* target density and scale at r_i^n */
   for (int64_t i = 0; i < n; ++i) {
     rt[i] = orc_rho_t(p, pos + i * d);
     h[i] = p->tau * pow(1.0 / rt[i], 1.0 / d);
   }
-  /* lines 7-8: neighbour sets */
+  /* neighbour sets */
   nbr_sets S; memset(&S, 0, sizeof S);
   if (build_sets(p, n, pos, h, mode, &S) != 0) return -1;
 
@@ -457,8 +457,8 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
     else Pc[i] = P0 * pow(rho[i] / rt[i], gamma) / (rho[i] * rho[i]);
   }
 
-  /* line 9: velocity reset (v_n = 0, infinite friction, Sec. 3.3);
-   * lines 10-11: a_n = -F_p + F_s (Eq. momentum_equation without F_v), with
+  /* velocity reset (v_n = 0, infinite friction, Sec. 3.3);
+   * a_n = -F_p + F_s (Eq. momentum_equation without F_v), with
    *   F_p,i = sum_j (P_i + P_j) dW(r_ij, h_ij)/dr e_ij          (pressure)
    *   F_s,i = -sum_j beta_ij (P0/rho_t,i^2 + P0/rho_t,j^2) dW e_ij (surface tension)
    * beta_ij = sigma(t) for distinct colours, 0 otherwise (Eq. sph_st_beta).
@@ -486,7 +486,7 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
   I.interface_pairs = ipairs / 2;
   I.force_pairs = fpairs / 2;
 
-  /* line 13: Eq. time_step_size with v_n = 0 leaves only the body-force term:
+  /* first time step: Eq. time_step_size with v_n = 0 leaves only the body-force term:
    * dt1 = min_i 0.25 sqrt(r_c,i / |a_i|), r_c,i = kappa h_i (global minimum).
    * Reading: if every a_i = 0 nothing moves (dt = 0). */
   double dt1 = INFINITY, mra = INFINITY, amax = 0.0;
@@ -507,9 +507,9 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
   /* Eq. time_int_01: v~ = v_n + a_n dt1 / 2 with v_n = 0 */
   for (size_t q = 0; q < nd; ++q) vt[q] = 0.5 * a[q] * dt1;
 
-  /* line 15: Eq. time_step_size again with v~: the CFL term r_c/(40|v~|) and the
+  /* second time step: Eq. time_step_size again with v~: the CFL term r_c/(40|v~|) and the
    * viscous term 0.125 r_c^2 / nu with nu = 0.1 r_c |v~| (Eq. viscosity_coefficient),
-   * together with the body-force term of line 13 (reading: dt2 <= dt1). */
+   * together with the body-force term of the first (reading: dt2 <= dt1). */
   double dt2 = dt1;
   for (int64_t i = 0; i < n; ++i) {
     double vn = 0.0;
@@ -527,7 +527,7 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
   }
   if (dt_fixed) dt2 = dt_fixed[1];
 
-  /* line 14: Eq. sph_viscous_force with rho := rho_t (Eq. sph_viscous_force_2):
+  /* viscous force: Eq. sph_viscous_force with rho := rho_t (Eq. sph_viscous_force_2):
    * a~_i = sum_j 2 eta_i eta_j/(eta_i + eta_j) (1/rho_t,i^2 + 1/rho_t,j^2)
    *        dW(r_ij, h_ij)/dr (v~_i - v~_j) / r_ij ;
    * reading: the harmonic mean is 0 when eta_i + eta_j = 0. */
@@ -556,7 +556,7 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
     if (pair_abs_b) pair_abs_b[i] = sabs;
   }
 
-  /* Eq. time_int_02 and time_int_03 with dt2, then line 16 (Eq. displacement_surface). */
+  /* Eq. time_int_02 and time_int_03 with dt2, then the projection (Eq. displacement_surface). */
   int64_t moved = 0;
   for (int64_t i = 0; i < n; ++i) {
     for (int k = 0; k < d; ++k) {
@@ -601,7 +601,7 @@ int orc_step_fixed_dt(const orc_problem* p, int64_t n, double* pos, const uint8_
 /* Sensitivities of a relaxation run (reverse mode, written by hand).        */
 /*                                                                          */
 /* The paper tunes nothing by gradient; this part differentiates the step of */
-/* Algorithm 1 (lines 6-16) as the forward code above computes it, for the   */
+/* Algorithm 1 as the forward code above computes it, for the                */
 /* objective                                                                 */
 /*   L = sum_i (rho_i/rho_t,i - 1)^2 + lambda sum_{i<j, C_i != C_j} W(r_ij, kappa h_ij) */
 /* after K steps, with respect to the initial positions, sigma0, gamma, P0    */
@@ -888,7 +888,7 @@ static int step_vjp(const orc_problem* p, int64_t n, const double* pos, const ui
     }
   for (size_t q = 0; q < nd; ++q) y[q] = pos[q] + dt2 * (vt[q] + 0.5 * dt2 * at[q]);
 
-  /* reverse: projection (line 16), drift and kicks (Eqs. time_int_01..03) */
+  /* reverse: projection, drift and kicks (Eqs. time_int_01..03) */
   double dt1b = 0.0, dt2b = 0.0;
   for (int64_t i = 0; i < n; ++i) {
     double gi[3] = {0, 0, 0};

@@ -92,7 +92,7 @@ int orc_neighbor_sets(const orc_problem* p, int64_t n, const double* pos, int mo
                       int64_t* dens_idsum, int64_t* force_idsum,
                       int64_t* dens_idxor, int64_t* force_idxor);
 
-/* One relaxation step (Algorithm 1, lines 6-16) advancing pos in place.
+/* One relaxation step (Algorithm 1) advancing pos in place.
  * Any of the per-particle outputs may be NULL:
  *   rho (n), acc (n*dim) = a_n, visc (n*dim) = a~, pair_abs_a (n) = sum_j of
  *   |pair term| of a_i, pair_abs_b (n) = sum_j |coefficient of a~ pair term| *

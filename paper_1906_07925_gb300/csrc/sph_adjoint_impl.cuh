@@ -2,7 +2,7 @@
 // dimension D and the working precision T; instantiated in sph_adjoint_2d.cu /
 // sph_adjoint_3d.cu.
 //
-// The step (Algorithm 1, lines 6-16) maps the state x to x' through
+// The step of Algorithm 1 maps the state x to x' through
 //   a_i  = sum_j S_ij (x_i - x_j),      S_ij = -coef_ij F(r_ij, H_ij)
 //   v~_i = dt1 a_i / 2,                  eta_i = rho_t,i 0.1 r_c,i |v~_i|
 //   a~_i = sum_j K_ij (v~_i - v~_j),    K_ij = hm(eta_i, eta_j) (T_i + T_j) F(r_ij, H_ij)

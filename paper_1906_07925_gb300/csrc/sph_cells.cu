@@ -1,4 +1,4 @@
-// Cell-linked list of the multi-resolution grid (Algorithm 1, lines 7-8).
+// Cell-linked list of the multi-resolution grid (the neighbour search of Algorithm 1).
 //
 // At a neighbour-list rebuild, particles are ordered by cell key with a
 // counting sort over the dense key range: warp-aggregated atomic counts per

@@ -1,4 +1,4 @@
-// Relaxation-step kernels (Algorithm 1, lines 6-16), templated on the
+// Relaxation-step kernels (the step of Algorithm 1), templated on the
 // dimension D and the working precision T. Instantiated per dimension in
 // sph_step_2d.cu / sph_step_3d.cu.
 //
@@ -8,7 +8,7 @@
 // conversion unit; FP64 keeps physical coordinates. Either way the rounding of
 // a pair vector is relative to the pair distance, not to the domain size.
 //
-// Neighbour list (Algorithm 1, line 8). The list of particle i holds every j
+// Neighbour list (the neighbour search of Algorithm 1). The list of particle i holds every j
 // (itself included) that can come within kappa max(h_i, h_j) before some
 // particle has moved half its skin; it is rebuilt, on the device, only then.
 // The criterion is symmetric, so i also finds every j whose own support
@@ -415,7 +415,8 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
 }
 
 // --------------------------------------------------------------------------
-// Pass A (Algorithm 1, lines 9-13): per target i, over its listed j
+// Pass A (Algorithm 1: velocity reset, forces, first time step): per target i,
+// over its listed j
 //   rho_i = sum_j W(r_ij, h_i)                                 (Eq. density_sum)
 //   a_i   = -sum_j [(P_i + P_j) + beta_ij P0 (1/rho_t,i^2 + 1/rho_t,j^2)]
 //                  dW(r_ij, h_ij)/dr e_ij                      (Eqs. sph_pressure_force_2,
@@ -587,9 +588,10 @@ __global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, Step
   }
   acc = block_reduce(acc, sm);
   if (threadIdx.x == 0) {
-    // Eq. time_step_size with v_n = 0 (velocity reset, line 9): line 13 keeps
-    // only the body-force term, dt1 = min_i 0.25 sqrt(r_c,i/|a_i|). With
-    // v~_i = a_i dt1/2 and nu_i = 0.1 r_c,i |v~_i|, line 15's terms are
+    // Eq. time_step_size with v_n = 0 (the velocity reset of Algorithm 1): the
+    // first time step keeps only the body-force term, dt1 = min_i 0.25
+    // sqrt(r_c,i/|a_i|). With v~_i = a_i dt1/2 and nu_i = 0.1 r_c,i |v~_i|, the
+    // second time step's terms are
     // r_c/(40|v~|) = m/(20 dt1) and 0.125 r_c^2/nu = 2.5 m/dt1, m = min r_c/|a|
     // (all three are monotone in r_c,i/|a_i|, so their minima share the argmin).
     const double m = acc.min_rc_a;
@@ -647,7 +649,7 @@ __global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, Step
 }
 
 // --------------------------------------------------------------------------
-// Pass B (Algorithm 1, lines 14-16): viscous force (Eq. sph_viscous_force with
+// Pass B (Algorithm 1: viscous force, kicks, drift, projection): viscous force (Eq. sph_viscous_force with
 // rho := rho_t, Eq. sph_viscous_force_2), the kicks and the drift
 // (Eqs. time_int_01..03) and the level-set projection (Eq. displacement_surface).
 // With v~ = a dt1/2 and eta = dt1 g:
@@ -752,7 +754,7 @@ __global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_b(int n, Step
         abs_pos<D, T>(F, X, xa);
       }
       Xs[i] = X;
-      // smoothing length at the new position (Algorithm 1, line 6 of the next step)
+      // smoothing length at the new position (the target field of the next step)
       const T hn = h_of<D, T>(geo, xa);
       const VT vn = make_view<D>(F, X, hn);
       (vp ? w0 : w1)[i] = vn;
