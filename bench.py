@@ -71,6 +71,10 @@ KERNELS_PER_STEP = 12
 # density 8, pressure + surface tension 30 (pass A), viscous 28 (pass B)
 FLOP_PER_PAIR = {"density": 8, "force": 30, "visc": 28}
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
+# DRAM bytes per particle of one k_pass_a launch (ncu dram__bytes_read + write on
+# the 1,048,576-particle 3D case, FP32, default skin; profiles/k_pass_a_traffic_c3_1m.md);
+# per-particle traffic does not depend on the particle count. None once the kernel changes.
+PASS_A_DRAM_BYTES_PER_PARTICLE_3D_FP32 = 647.0
 
 
 def log(*a):
@@ -485,8 +489,14 @@ def main():
     dom = max(("pass_a", "pass_b"), key=lambda k: res["phase_ms"][k])
     ach = per_particle[dom] * n / (res["phase_ms"][dom] * 1e-3) / 1e9
     step_bytes = sum(per_particle.values()) * n
+    traffic = None
+    if (dom == "pass_a" and wl["dim"] == 3 and wl["precision"] == "fp32" and args.skin == 0.0
+            and args.cell_factor == 0.0):
+        traffic = PASS_A_DRAM_BYTES_PER_PARTICLE_3D_FP32 * n
     roof = {"kernel": "k_pass_a" if dom == "pass_a" else "k_pass_b", "bound": "hbm", "achieved": ach,
-            "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None,
+            "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
+            "traffic_source": "ncu dram bytes per particle at 1,048,576 particles, scaled by the particle count"
+                              if traffic else None,
             "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
             "alg_bytes_per_particle": per_particle[dom],
             "step_alg_bytes_per_particle": sum(per_particle.values()),
