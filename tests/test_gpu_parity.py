@@ -158,6 +158,32 @@ def test_relaxation_end_state_statistics_fp32():
     r.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_end_state_triangle_quality_matches_oracle(precision):
+    """A random start in the square (4,096 particles) relaxed for 100 steps on
+    the GPU and in the oracle: the Delaunay triangulations of the two end
+    states have the same quality (Sec. 4's G and angle measures). The
+    trajectories separate through rounding, so the measures are compared as
+    statistics of the point sets, not triangle by triangle."""
+    import mesh_quality as MQ
+    p = W.uniform_square_2d(64, 4)
+    pos, col, _ = W.sample_density(p, 4096, 1)
+    r = make_gpu(p, pos, col, precision, use_graph=True)
+    r.step(100)
+    qg = MQ.quality(r.positions(), r.colors())
+    xo, _ = oracle.run(p, pos, col, 100)
+    qo = MQ.quality(xo, col)
+    r.close()
+    assert qg["G_avg"] == pytest.approx(qo["G_avg"], abs=0.01)
+    assert qg["theta_min_mean"] == pytest.approx(qo["theta_min_mean"], abs=0.75)
+    assert qg["share_55_65"] == pytest.approx(qo["share_55_65"], abs=0.02)
+    assert qg["theta_min"] > 15.0 and qg["theta_max"] < 140.0
+    assert abs(qg["n_lt30"] - qo["n_lt30"]) <= 0.5 * qo["n_lt30"] + 10
+    assert abs(qg["n_tri"] - qo["n_tri"]) <= 0.01 * qo["n_tri"]
+    # communication volume of the colour partition, N_eg / N_et
+    assert qg["n_eg"] / qg["n_et"] == pytest.approx(qo["n_eg"] / qo["n_et"], rel=0.05)
+
+
 # ------------------------------------------------------------- edge cases ----
 
 def test_empty_and_single_particle():

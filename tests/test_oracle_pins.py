@@ -390,3 +390,45 @@ def test_convergence_step_rule(orc):
     assert f([100, 90, 80, 70, 60, 50], 2, 1e-3) is None
     assert f([1000, 1001, 999, 1000], 3, 1e-3) == 3
     assert f([1000, 1002, 1000, 1000], 3, 1e-3) is None
+
+
+# ------------------------------------------------------------ mesh quality ----
+
+def test_triangle_quality_measure():
+    """The paper's G = 2 sqrt(3) S / (P H) is 1 for an equilateral triangle and
+    sqrt(3)/(1 + sqrt(2)) for a right isosceles one; a perfect triangular lattice
+    gives G = 1 and 60-degree angles throughout."""
+    import mesh_quality as MQ
+    a = np.array([[0.0, 0.0]]); b = np.array([[1.0, 0.0]]); c = np.array([[0.5, math.sqrt(3) / 2]])
+    G, A = MQ.triangle_metrics(a, b, c)
+    assert G[0] == pytest.approx(1.0, abs=1e-12) and np.allclose(A, 60.0)
+    G, A = MQ.triangle_metrics(a, b, np.array([[0.0, 1.0]]))
+    assert G[0] == pytest.approx(math.sqrt(3) / (1 + math.sqrt(2)), abs=1e-12)
+    assert sorted(A[0]) == pytest.approx([45.0, 45.0, 90.0])
+    ii, jj = np.meshgrid(np.arange(12), np.arange(12))
+    pts = np.stack([ii + 0.5 * (jj % 2), jj * math.sqrt(3) / 2], axis=-1).reshape(-1, 2).astype(float)
+    q = MQ.quality(pts)
+    assert q["G_avg"] == pytest.approx(1.0, abs=1e-9) and q["share_55_65"] == pytest.approx(1.0)
+    # a rhombus of two equilateral triangles: 5 edges, 3 of them join the
+    # bottom pair (colour 0) to the top pair (colour 1)
+    rh = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, math.sqrt(3) / 2], [1.5, math.sqrt(3) / 2]])
+    q = MQ.quality(rh, np.array([0, 0, 1, 1]), drop_hull=False)
+    assert (q["n_tri"], q["n_et"], q["n_eg"]) == (2, 5, 3) and q["G_avg"] == pytest.approx(1.0)
+
+
+def test_oracle_relaxation_raises_triangle_quality():
+    """Relaxing a random start in the unit square (4,096 particles, 100 steps)
+    turns a Poisson point set (G_avg ~0.60, thousands of triangles with an angle
+    below 30 degrees) into a near-regular one, the outcome the method exists
+    for (Sec. 4's quality measures)."""
+    import mesh_quality as MQ
+    import oracle
+    p = W.uniform_square_2d(64, 4)
+    pos, col, _ = W.sample_density(p, 4096, 1)
+    q0 = MQ.quality(pos)
+    xo, _ = oracle.run(p, pos, col, 100)
+    q1 = MQ.quality(xo)
+    assert q0["G_avg"] < 0.65 and q1["G_avg"] > 0.78
+    assert q1["theta_min"] > 15.0 and q1["theta_max"] < 140.0
+    assert q1["n_lt30"] < 0.05 * q0["n_lt30"]
+    assert q1["theta_min_mean"] > q0["theta_min_mean"] + 10.0
