@@ -655,7 +655,7 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   SPH_TRY(grab(h, S.cnt, (size_t)S.total_cells));
   SPH_TRY(grab(h, S.cstart, (size_t)S.total_cells + 1));
   SPH_TRY(grab(h, S.scan_part, (size_t)S.total_cells / 4096 + 2));
-  SPH_TRY(grab(h, S.partials, N / 256 + 2));
+  SPH_TRY(grab(h, S.partials, N / 128 + 2));
   SPH_TRY(grab(h, S.scal, 2));
   SPH_TRY(grab(h, S.ctl, 1));
   SPH_TRY(grab(h, S.tickets, 4));

@@ -44,7 +44,7 @@ constexpr size_t kCnt = kPc + al(4 * kN);
 constexpr size_t kCstart = kCnt + al(4 * kC);
 constexpr size_t kScanPart = kCstart + al(4 * (kC + 1));
 constexpr size_t kPartials = kScanPart + al(4 * (kC / 4096 + 2));
-constexpr size_t kScal = kPartials + al(sizeof(Partial) * (kN / 256 + 2));
+constexpr size_t kScal = kPartials + al(sizeof(Partial) * (kN / 128 + 2));
 constexpr size_t kCtl = kScal + al(2 * sizeof(Scalars));
 constexpr size_t kTickets = kCtl + al(sizeof(StepCtl));
 constexpr size_t kErr = kTickets + al(16);

@@ -28,6 +28,19 @@
 #ifndef SPH_PASS_MIN_BLOCKS
 #define SPH_PASS_MIN_BLOCKS 5
 #endif
+// store of a force-pair list word (streaming: read once, by pass B)
+#ifndef SPH_PLIST_STREAM
+#define SPH_PLIST_STREAM 1
+#endif
+#if SPH_PLIST_STREAM
+#define SPH_PLIST_STORE(p, v) __stcs((p), (v))
+#else
+#define SPH_PLIST_STORE(p, v) (*(p) = (v))
+#endif
+// threads per block of the pair passes
+#ifndef SPH_PASS_THREADS
+#define SPH_PASS_THREADS 256
+#endif
 #ifndef SPH_LIST_MIN_BLOCKS
 #define SPH_LIST_MIN_BLOCKS 4
 #endif
@@ -102,22 +115,26 @@ __device__ __forceinline__ int4 with_w(int4 v, float w) { return make_int4(v.x, 
 __device__ __forceinline__ V4<double> with_w(V4<double> v, double w) { return V4<double>{v.x, v.y, v.z, w}; }
 
 // Visit the cnt listed entries of particle i (column i of the list) in
-// batches of four: the four list words, then the four neighbour views, are
+// batches of SPH_LIST_BATCH: the list words, then the neighbour views, are
 // loaded before any is used, so each warp keeps several independent gathers in
 // flight. List words are streamed (read once per pass).
+#ifndef SPH_LIST_BATCH
+#define SPH_LIST_BATCH 4
+#endif
 template <class VT, class Fn>
 __device__ __forceinline__ void for_list(const uint32_t* __restrict__ list, const VT* __restrict__ view, int n, int i,
                                          int cnt, Fn&& pair) {
+  constexpr int B = SPH_LIST_BATCH;
   int k = 0;
-  for (; k + 4 <= cnt; k += 4) {
-    uint32_t e[4];
-    VT v[4];
+  for (; k + B <= cnt; k += B) {
+    uint32_t e[B];
+    VT v[B];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) e[q] = __ldcs(list + (size_t)(k + q) * n + i);
+    for (int q = 0; q < B; ++q) e[q] = __ldcs(list + (size_t)(k + q) * n + i);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = view[e[q] >> 8];
+    for (int q = 0; q < B; ++q) v[q] = view[e[q] >> 8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) pair(e[q], v[q]);
+    for (int q = 0; q < B; ++q) pair(e[q], v[q]);
   }
   for (; k < cnt; ++k) {
     const uint32_t e = __ldcs(list + (size_t)k * n + i);
@@ -431,7 +448,7 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
 // (Eq. time_step_size, see below).
 // --------------------------------------------------------------------------
 template <int D, class T, bool GENERAL, bool DBG>
-__global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, StepCtl* ctl,
+__global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, StepCtl* ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
@@ -519,7 +536,7 @@ __global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, Step
           ax += s * dx;
           ay += s * dy;
           az += s * dz;
-          plist[(size_t)nf * n + i] = e;  // this step's force pairs, for pass B
+          SPH_PLIST_STORE(plist + (size_t)nf * n + i, e);  // this step's force pairs, for pass B
           ++nf;
           ni += other;
           if (DBG) sf += pid[j];
@@ -660,7 +677,7 @@ __global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, Step
 // skin since the list was built raises need_rebuild.
 // --------------------------------------------------------------------------
 template <int D, class T, bool RECORD>
-__global__ void __launch_bounds__(256, SPH_PASS_MIN_BLOCKS) k_pass_b(int n, StepCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_b(int n, StepCtl* __restrict__ ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 typename ViewOf<T>::type* __restrict__ w0,
@@ -870,7 +887,7 @@ cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& 
 template <int D, class T>
 cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P, PassFlags f, cudaStream_t st) {
   using VT = typename ViewOf<T>::type;
-  const int tb = 256, gb = grid_for(S.n, tb);
+  const int tb = SPH_PASS_THREADS, gb = grid_for(S.n, tb);
   T* rho = (T*)S.rho;
   T* pc = (T*)S.pc;
   if (f.general_eos)
@@ -897,7 +914,7 @@ template <int D, class T>
 cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& g, PassFlags f,
                           cudaStream_t st) {
   using VT = typename ViewOf<T>::type;
-  const int tb = 256, gb = grid_for(S.n, tb);
+  const int tb = SPH_PASS_THREADS, gb = grid_for(S.n, tb);
   unsigned long long* wm = (unsigned long long*)&S.scal->wall_moved;
   if (f.record)
     k_pass_b<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
