@@ -676,7 +676,7 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
 // The new view goes to the other view buffer; a particle that moved half its
 // skin since the list was built raises need_rebuild.
 // --------------------------------------------------------------------------
-template <int D, class T, bool RECORD>
+template <int D, class T>
 __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_b(int n, StepCtl* __restrict__ ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
@@ -737,7 +737,9 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
     bz *= km;
     const T dt1 = (T)scal->dt1, dt2 = (T)scal->dt2;
     const T kv = T(0.5) * dt1 * dt1;  // a~ = kv B
-    if (RECORD) visc_out[i] = V4<T>{kv * bx, kv * by, kv * bz, T(0)};
+    // a~ for the caller when asked (a run-time test: one compiled kernel, so
+    // recording cannot change the arithmetic of the step)
+    if (visc_out) visc_out[i] = V4<T>{kv * bx, kv * by, kv * bz, T(0)};
     if (move) {
     T d[3];
     d[0] = (T(0.5) * dt1 * ai.x + T(0.5) * dt2 * kv * bx) * dt2;
@@ -916,16 +918,10 @@ cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P
   using VT = typename ViewOf<T>::type;
   const int tb = SPH_PASS_THREADS, gb = grid_for(S.n, tb);
   unsigned long long* wm = (unsigned long long*)&S.scal->wall_moved;
-  if (f.record)
-    k_pass_b<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
-                                            (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0],
-                                            (LL4*)S.X[1], S.plist, S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
-                                            (V4<T>*)S.visc, S.err, wm, f.move);
-  else
-    k_pass_b<D, T, false><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
-                                             (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0],
-                                             (LL4*)S.X[1], S.plist, S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
-                                             (V4<T>*)S.visc, S.err, wm, f.move);
+  k_pass_b<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1], (VT*)S.view[0],
+                                    (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0], (LL4*)S.X[1], S.plist,
+                                    S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
+                                    f.record ? (V4<T>*)S.visc : nullptr, S.err, wm, f.move);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,140 @@
+"""Parity at the benchmarked sizes, in the launch configuration the benchmark
+times (CUDA graph replay, default skin, particles drawn on the device by
+sph_create): the 8,388,608-particle 3D graded inclusion (FP32 split precision
+and FP64) and the 1,048,576-particle 2D graded hole (FP32).
+
+The first step of the GPU run is compared with one oracle step from the same
+positions and colours. Density and force are compared for every particle
+(the oracle step is O(N) with its own cell grid, about a minute at 8M on 16
+cores); the quantities whose bound needs a neighbourhood maximum (a~,
+displacement) are compared on a sample: 2,000 random particles plus the 100
+that moved most. Tolerances are those of the small-size parity tests
+(tol = 1e-5 FP32, 1e-12 FP64; forces relative to the sum of pair magnitudes),
+with the FP32 force bound widened where a pair near the support edge dominates
+a particle's sum (see the force check).
+A second handle records the fields of the same step: recording must not change
+the positions the step produces."""
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import oracle
+import workloads as W
+from parity_util import TOL
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "3d_8m": dict(make=lambda: W.graded_inclusion_3d(1 << 23, 256, rho_scale=0.0), n=1 << 23, ncol=256, seed=2),
+    "2d_1m": dict(make=lambda: W.graded_hole_2d(1 << 20, 64, rho_scale=0.0), n=1 << 20, ncol=64, seed=1),
+}
+
+
+def _h_local(p, pos, idx):
+    return np.array([oracle.h_of(p, pos[i]) for i in idx])
+
+
+def _kappa_h_all(p, x):
+    """kappa h at every particle, from the workloads' vectorised spacing shape
+    (s^-d), to which the oracle's h is proportional on these fields; the ratio
+    is checked against the oracle's h at a few particles."""
+    s = W.spacing_shape(p, x) ** (-1.0 / p.dim)
+    idx = np.linspace(0, len(x) - 1, 7).astype(int)
+    ratio = _h_local(p, x, idx) / s[idx]
+    assert np.allclose(ratio, ratio[0], rtol=1e-9)
+    return p.kappa * ratio[0] * s
+
+
+def _edge_amplification(p, x, idx):
+    """max over the force pairs of each particle in idx of 3 q / (1 - q),
+    q = r / (kappa (h_i + h_j) / 2), from the oracle's h."""
+    tree = cKDTree(x)
+    out = np.zeros(len(idx))
+    for t, i in enumerate(idx):
+        hi = oracle.h_of(p, x[i])
+        nb = np.array([j for j in tree.query_ball_point(x[i], 2.0 * p.kappa * hi) if j != i], dtype=np.int64)
+        if len(nb) == 0:
+            continue
+        hf = 0.5 * p.kappa * (hi + _h_local(p, x, nb))
+        q = np.linalg.norm(x[nb] - x[i], axis=1) / hf
+        q = q[q < 1.0]
+        if len(q):
+            out[t] = (3 * q / (1 - q)).max()
+    return out
+
+
+@pytest.mark.parametrize("case,precision", [("2d_1m", "fp32"), ("3d_8m", "fp32"), ("3d_8m", "fp64")])
+def test_first_step_at_benchmark_size_matches_oracle(case, precision):
+    from paper_1906_07925_gb300 import Relaxation
+    cfg = CASES[case]
+    p = cfg["make"]()
+    n = cfg["n"]
+    tol = TOL[precision]
+    # the benchmark's configuration: graph replay, no field recording
+    r = Relaxation(p, n, cfg["ncol"], precision=precision, seed=cfg["seed"], use_graph=True)
+    x0, c0 = r.positions(), r.colors()
+    p = p.copy(rho_scale=r.info()["rho_scale"])
+    r.step(1)
+    x1 = r.positions()
+    st = r.stats()
+    r.close()
+    # the same step with the fields recorded: identical positions
+    rf = Relaxation(p, n, cfg["ncol"], precision=precision, seed=cfg["seed"], use_graph=True, record_fields=True)
+    assert np.array_equal(rf.positions(), x0)
+    rf.step(1)
+    assert np.array_equal(rf.positions(), x1)
+    rho, acc, visc = rf.field("rho"), rf.field("acc"), rf.field("visc")
+    rf.close()
+
+    xo, info, f = oracle.step(p, x0, c0, 0)
+    assert np.all(np.isfinite(rho)) and np.all(np.isfinite(x1))
+    # density, every particle
+    rel = np.abs(rho - f["rho"]) / f["rho"]
+    assert rel.max() <= tol, ("rho", rel.max(), int(rel.argmax()))
+    # force, every particle, relative to the sum of pair magnitudes. In FP32
+    # a pair near the support edge carries its kernel factor (1 - q)^3 with a
+    # relative error of about 3 q / (1 - q) ulp of q (the rounding of r and of
+    # the FP32 h enters 1 - q unreduced); a particle whose sum that pair
+    # dominates gets the bound tol S + 8 ulp S max_j 3 q_j / (1 - q_j). Such
+    # particles are rare.
+    Sa = f["pair_abs_a"]
+    ea = np.abs(acc - f["acc"]).max(axis=1)
+    over = np.nonzero(ea > tol * Sa + 1e-300)[0]
+    rel_a = np.full(n, tol)  # relative error bound of each a_i, for a~ and the drift below
+    if precision == "fp64":
+        assert len(over) == 0, ("acc", (ea[over] / Sa[over]).max())
+    else:
+        assert len(over) <= 1e-4 * n, len(over)
+        amp = _edge_amplification(p, x0, over)
+        bound = tol * Sa[over] + 8 * 2.0 ** -23 * Sa[over] * amp
+        assert (ea[over] <= bound).all(), ("acc", (ea[over] / bound).max())
+        rel_a[over] += 8 * 2.0 ** -23 * amp
+    # step sizes: relative error of a at the particle that sets them
+    an = np.linalg.norm(f["acc"], axis=1)
+    cond = np.where(an > 0, Sa / np.maximum(an, 1e-300), 1.0)
+    k = int(np.argmin(np.where(an > 0, _kappa_h_all(p, x0) / np.maximum(an, 1e-300), np.inf)))
+    dt_tol = 2 * rel_a[k] * (1 + cond[k])
+    assert abs(st["dt1"] - info["dt1"]) <= dt_tol * info["dt1"], (st["dt1"], info["dt1"])
+    assert abs(st["dt2"] - info["dt2"]) <= dt_tol * info["dt2"], (st["dt2"], info["dt2"])
+    # pair counts: FP32 may differ only by pairs at a support edge
+    slack = 0 if precision == "fp64" else max(2, int(1e-5 * info["force_pairs"]))
+    assert abs(st["force_pairs"] - info["force_pairs"]) <= slack
+    assert abs(st["interface_pairs"] - info["interface_pairs"]) <= slack
+
+    # a~ and displacement on a sample, bounds as in the small-size tests
+    rng = np.random.default_rng(0)
+    do = xo - x0
+    dn = np.linalg.norm(do, axis=1)
+    sample = np.unique(np.concatenate([rng.choice(n, 2000, replace=False), np.argsort(dn)[-100:]]))
+    tree = cKDTree(x0)
+    R = p.kappa * _h_local(p, x0, sample).max() * 1.5
+    eps = np.array([(rel_a[nb] * (1 + cond[nb])).max()
+                    for nb in map(np.asarray, tree.query_ball_point(x0[sample], R))])
+    ev = np.abs(visc[sample] - f["visc"][sample]).max(axis=1)
+    bound_v = 4 * (eps + dt_tol) * f["pair_abs_b"][sample] + 1e-300
+    assert (ev <= bound_v).all(), ("visc", (ev / bound_v).max())
+    ed = np.abs((x1 - x0)[sample] - do[sample]).max(axis=1)
+    scale = np.abs(x0).max() + 1.0
+    rep = (6e-8 if precision == "fp32" else 1e-15) * scale
+    bound_d = 4 * (eps + 2 * dt_tol) * (dn[sample] + 0.5 * info["dt1"] * info["dt2"] * Sa[sample]) + 4 * rep
+    assert (ed <= bound_d).all(), ("disp", (ed / bound_d).max())
