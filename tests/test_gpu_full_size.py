@@ -3,6 +3,11 @@ times (CUDA graph replay, default skin, particles drawn on the device by
 sph_create): the 8,388,608-particle 3D graded inclusion (FP32 split precision
 and FP64) and the 1,048,576-particle 2D graded hole (FP32).
 
+The 512-instance batch (256 2D + 256 3D, 2k-200k particles each) is created
+and stepped as the benchmark does; sampled instances must match the same
+instances stepped alone bit for bit, and the smallest 2D and 3D instances the
+oracle.
+
 The first step of the GPU run is compared with one oracle step from the same
 positions and colours. Density and force are compared for every particle
 (the oracle step is O(N) with its own cell grid, about a minute at 8M on 16
@@ -138,3 +143,54 @@ def test_first_step_at_benchmark_size_matches_oracle(case, precision):
     rep = (6e-8 if precision == "fp32" else 1e-15) * scale
     bound_d = 4 * (eps + 2 * dt_tol) * (dn[sample] + 0.5 * info["dt1"] * info["dt2"] * Sa[sample]) + 4 * rep
     assert (ed <= bound_d).all(), ("disp", (ed / bound_d).max())
+
+
+def _check_rho_acc(p, x0, c0, rho, acc, tol):
+    """Density and force of one step from (x0, c0) against the oracle, with the
+    force bound of the full-size test."""
+    _, _, f = oracle.step(p, x0, c0, 0)
+    rel = np.abs(rho - f["rho"]) / f["rho"]
+    assert rel.max() <= tol, ("rho", rel.max())
+    Sa = f["pair_abs_a"]
+    ea = np.abs(acc - f["acc"]).max(axis=1)
+    over = np.nonzero(ea > tol * Sa + 1e-300)[0]
+    assert len(over) <= max(2, 1e-4 * len(x0)), len(over)
+    if len(over):
+        bound = tol * Sa[over] + 8 * 2.0 ** -23 * Sa[over] * _edge_amplification(p, x0, over)
+        assert (ea[over] <= bound).all(), ("acc", (ea[over] / bound).max())
+
+
+def test_batch_of_512_instances_matches_standalone_and_oracle():
+    from paper_1906_07925_gb300 import Batch, Relaxation
+    inst = W.batch_instances(512, seed=4)
+    probs, ns, cols = [], [], []
+    for p, n in inst:
+        p.rho_scale = 0.0  # normalised by the library to n particles
+        probs.append(p)
+        ns.append(n)
+        cols.append(p.n_colors)
+    seeds = list(range(len(probs)))
+    b = Batch(probs, ns, cols, precision="fp32", seeds=seeds)
+    assert sum(ns) > 10_000_000
+    x0 = {}
+    dims = np.array([p.dim for p in probs])
+    order = np.argsort(ns)
+    small2 = int(next(k for k in order if dims[k] == 2))
+    small3 = int(next(k for k in order if dims[k] == 3))
+    picks = sorted({small2, small3, int(order[-1]), int(np.argmax(np.where(dims == 3, ns, -1))), 137, 400})
+    for k in picks:
+        x0[k] = (b.positions(k), b.colors(k))
+    b.step(1)
+    b.sync()
+    for k in picks:
+        r = Relaxation(probs[k], ns[k], cols[k], precision="fp32", seed=seeds[k], use_graph=True,
+                       record_fields=k in (small2, small3))
+        assert np.array_equal(r.positions(), x0[k][0]), k
+        r.step(1)
+        assert np.array_equal(r.positions(), b.positions(k)), k
+        assert np.array_equal(r.colors(), b.colors(k)), k
+        if k in (small2, small3):
+            p = probs[k].copy(rho_scale=r.info()["rho_scale"])
+            _check_rho_acc(p, x0[k][0], x0[k][1], r.field("rho"), r.field("acc"), TOL["fp32"])
+        r.close()
+    b.close()
