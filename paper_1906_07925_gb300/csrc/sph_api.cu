@@ -169,10 +169,10 @@ sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEve
   if (e == cudaSuccess) e = launch_gate(S, force_rebuild, h->stream);
   if (e == cudaSuccess) {
     if (h->dim == 2)
-      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream, &h->Gf, &h->Ff)
               : launch_rebuild<2, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
     else
-      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream, &h->Gf, &h->Ff)
               : launch_rebuild<3, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
   }
   if (ev && e == cudaSuccess) e = cudaEventRecord(ev[1], h->stream);
@@ -217,10 +217,10 @@ sph_status launch_evaluate(sph_handle* h, int nbr_debug) {
   cudaError_t e = launch_gate(S, 1, h->stream);
   if (e == cudaSuccess) {
     if (h->dim == 2)
-      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream, &h->Gf, &h->Ff)
               : launch_rebuild<2, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
     else
-      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream, &h->Gf, &h->Ff)
               : launch_rebuild<3, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
   }
   if (e == cudaSuccess) {
@@ -377,10 +377,10 @@ sph_status reverse_setup(sph_handle* h, bool forward, const double* dt_fix) {
   cudaError_t e = launch_gate(S, forward ? 1 : 0, h->stream);
   if (e == cudaSuccess) {
     if (h->dim == 2)
-      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+      e = f64 ? launch_rebuild<2, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream, &h->Gf, &h->Ff)
               : launch_rebuild<2, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
     else
-      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream)
+      e = f64 ? launch_rebuild<3, double>(S, h->Gdw, h->Fd, h->geod, h->par.kappa, h->stream, &h->Gf, &h->Ff)
               : launch_rebuild<3, float>(S, h->Gf, h->Ff, h->geof, (float)h->par.kappa, h->stream);
   }
   if (forward && e == cudaSuccess) {
@@ -642,6 +642,9 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
     SPH_TRY(grab(h, tmpb, N * v4)); S.view[b] = tmpb;
   }
   SPH_TRY(grab(h, tmpb, N * v4)); S.vbuild = tmpb;
+  if (h->prec == SPH_PREC_FP64) {
+    SPH_TRY(grab(h, tmpb, N * 16)); S.view32 = tmpb;
+  }
   SPH_TRY(grab(h, tmpb, N * v4)); S.acc4 = tmpb;
   SPH_TRY(grab(h, tmpb, N * v4)); S.visc = tmpb;
   SPH_TRY(grab(h, tmpb, N * t1)); S.rho = tmpb;

@@ -21,6 +21,7 @@ struct DevState {
   uint32_t* pid[2] = {nullptr, nullptr};   // particle id
   void* view[2] = {nullptr, nullptr};    // int4 (FP32) or double4 (FP64)
   void* vbuild = nullptr;                // view at the list build, w = half skin
+  void* view32 = nullptr;                // FP64 path: FP32 view for the list build (rebuild only)
   uint32_t* key = nullptr;               // cell key (old order, rebuild only)
   uint32_t* tmp = nullptr;               // scatter slots
   uint32_t* cnt = nullptr;               // per-cell counters (all zero between rebuilds)
@@ -68,7 +69,7 @@ struct PassFlags {
 
 template <int D, class T>
 cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& F, const Geom<T>& g, T kappa,
-                           cudaStream_t st);
+                           cudaStream_t st, const Grid<float>* G32 = nullptr, const Frame<float>* F32 = nullptr);
 template <int D, class T>
 cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P, PassFlags f, cudaStream_t st);
 template <int D, class T>

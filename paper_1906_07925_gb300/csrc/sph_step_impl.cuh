@@ -258,6 +258,26 @@ __global__ void __launch_bounds__(256) k_make_view(int n, const StepCtl* __restr
   vbuild[i] = with_w(v, T(0.5) * F.skin * view_h(v));  // half the skin, view units (kappa folded in by the host)
 }
 
+// FP32 view of the FP64 path's particles, made at a list rebuild for its list
+// build: the list only has to hold every pair the exact FP64 tests can accept
+// before the next rebuild, and an FP32 candidate test errs by ~1e-7 of the
+// distance, far inside the list's margins (the skin and the 1e-5 factor),
+// while FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU.
+template <int D>
+__global__ void __launch_bounds__(256) k_view32(int n, const StepCtl* __restrict__ ctl,
+                                                const LL4* __restrict__ X0, const LL4* __restrict__ X1,
+                                                Frame<float> F, const V4<double>* __restrict__ vd0,
+                                                const V4<double>* __restrict__ vd1, int4* __restrict__ out) {
+  if (!ctl->rebuild) return;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const LL4 X = (ctl->buf ? X1 : X0)[i];
+  const double hv = (ctl->vp ? vd1 : vd0)[i].w;  // h in view units (c0, both precisions)
+  const long long half = 1LL << (F.sv - 1);
+  out[i] = make_int4((int)((X.x + half) >> F.sv), (int)((X.y + half) >> F.sv),
+                     D == 3 ? (int)((X.z + half) >> F.sv) : 0, __float_as_int((float)hv));
+}
+
 // Neighbour list of each particle: every j (itself included) with
 //   r < kappa max(h_i, h_j) (1 + 1e-5) + kappa lip_h s_max / 2 + s_max,
 // s = skin (kappa folded) of i and j: after both moved at most half their skin
@@ -270,7 +290,6 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
                                                     const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
                                                     const typename ViewOf<T>::type* __restrict__ v0,
                                                     const typename ViewOf<T>::type* __restrict__ v1,
-                                                    const typename ViewOf<T>::type* __restrict__ vbuild,
                                                     const uint32_t* __restrict__ cstart, Frame<T> F, Grid<T> G,
                                                     T kappa, int cap, uint32_t* __restrict__ list,
                                                     uint32_t* __restrict__ lcount, int* __restrict__ err) {
@@ -284,7 +303,8 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   const uint32_t* __restrict__ meta = buf ? m1 : m0;
   const VT vi = view[i];
   const T hv = view_h(vi);                 // view units
-  const T sk = view_h(vbuild[i]) * T(2);   // skin of i, view units
+  const T sk = F.skin * hv;                // skin of i, view units (kappa folded in by the host)
+  const T sk_hv = F.skin;                  // skin per unit h
   const T lip = G.lip_h;
   // search radius: bound h_j by Lipschitz continuity, iterate twice
   T hhi = hv, Rs = kappa * hv * G.rfac + sk * (T(1) + T(0.5) * kappa * lip);
@@ -349,7 +369,7 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
           const T r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
           if (r2 >= R2) continue;
           const T hj = view_h(vj);
-          const T skj = sk * hj / hv;
+          const T skj = sk_hv * hj;
           const T smax = sk > skj ? sk : skj;
           const T hm = hv > hj ? hv : hj;  // symmetric: j lists i whenever i lists j
           // h_j is known here: only rounding and the h change over the skin need a margin
@@ -870,7 +890,7 @@ inline int grid_for(int n, int tb) { return (n + tb - 1) / tb; }
 
 template <int D, class T>
 cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& F, const Geom<T>& g, T kappa,
-                           cudaStream_t st) {
+                           cudaStream_t st, const Grid<float>* G32, const Frame<float>* F32) {
   using VT = typename ViewOf<T>::type;
   const int tb = 256, gb = grid_for(S.n, tb);
   const LL4* X0 = (const LL4*)S.X[0];
@@ -880,9 +900,20 @@ cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& 
   if (e != cudaSuccess) return e;
   k_make_view<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, 0, X0, X1, F, g, (VT*)S.view[0], (VT*)S.view[1],
                                        (VT*)S.vbuild);
-  k_list_build<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const VT*)S.view[0],
-                                        (const VT*)S.view[1], (const VT*)S.vbuild, S.cstart, F, G, kappa, S.cap,
-                                        S.list, S.lcount, S.err);
+  if constexpr (std::is_same<T, double>::value) {
+    // the FP64 path lists its pairs through an FP32 view (same frame origin,
+    // same cells, same list format)
+    if (!S.view32 || !F32 || !G32) return cudaErrorInvalidValue;
+    k_view32<D><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, *F32, (const V4<double>*)S.view[0],
+                                   (const V4<double>*)S.view[1], (int4*)S.view32);
+    k_list_build<D, float><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const int4*)S.view32,
+                                              (const int4*)S.view32, S.cstart, *F32, *G32, (float)kappa, S.cap,
+                                              S.list, S.lcount, S.err);
+  } else {
+    k_list_build<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const VT*)S.view[0],
+                                          (const VT*)S.view[1], S.cstart, F, G, kappa, S.cap, S.list, S.lcount,
+                                          S.err);
+  }
   return cudaGetLastError();
 }
 
@@ -954,7 +985,7 @@ cudaError_t launch_get_fields(const DevState& S, int which, double* out, cudaStr
 
 #define SPH_INSTANTIATE_STEP(D, T)                                                                             \
   template cudaError_t launch_rebuild<D, T>(const DevState&, const Grid<T>&, const Frame<T>&, const Geom<T>&, \
-                                            T, cudaStream_t);                                                 \
+                                            T, cudaStream_t, const Grid<float>*, const Frame<float>*);        \
   template cudaError_t launch_pass_a<D, T>(const DevState&, const Frame<T>&, const Phys<T>&, PassFlags,       \
                                            cudaStream_t);                                                     \
   template cudaError_t launch_pass_b<D, T>(const DevState&, const Frame<T>&, const Phys<T>&, const Geom<T>&,  \
