@@ -167,10 +167,24 @@ static double poly_factor(const orc_problem* p, const double* x) {
   return f;
 }
 
+/* Target spacing s(x). The circle case of Sec. 4.1 prescribes the target
+ * size h_min + tanh(2.5 phi / 43) / tanh(2.5) (h_max - h_min), phi the
+ * distance to the circle: kind ORC_FIELD_TANH_DISTANCE with a = h_min,
+ * b = (h_max - h_min) / tanh(2.5) and s0 = 2.5 / 43. */
 static double spacing(const orc_problem* p, const double* x) {
   if (p->field_kind == ORC_FIELD_UNIFORM) return p->s0;
   double dist = fabs(shape_inside_distance(&p->shapes[p->dist_shape], x, p->dim));
+  if (p->field_kind == ORC_FIELD_TANH_DISTANCE) return p->a + p->b * tanh(p->s0 * dist);
   return p->a + p->b * dist;
+}
+
+/* ds/d|dist| of the distance fields */
+static double spacing_slope(const orc_problem* p, double dist) {
+  if (p->field_kind == ORC_FIELD_TANH_DISTANCE) {
+    double t = tanh(p->s0 * fabs(dist));
+    return p->b * p->s0 * (1.0 - t * t);
+  }
+  return p->b;
 }
 
 double orc_rho_t(const orc_problem* p, const double* x) {
@@ -702,7 +716,8 @@ static double rho_t_grad(const orc_problem* p, const double* x, double* grad, do
     double dist = shape_inside_distance(sh, x, d), gd[3];
     inside_distance_grad(sh, x, d, gd);
     double sg = dist >= 0.0 ? 1.0 : -1.0;
-    for (int k = 0; k < d; ++k) gs[k] = p->b * sg * gd[k];
+    double slope = spacing_slope(p, dist);
+    for (int k = 0; k < d; ++k) gs[k] = slope * sg * gd[k];
   }
   double b[8], db[8][3], gP[3] = {0, 0, 0};
   for (int m = 0; m < 8; ++m) dcoef[m] = 0.0;

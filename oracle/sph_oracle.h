@@ -26,6 +26,7 @@ extern "C" {
 #define ORC_BOX 1
 #define ORC_FIELD_UNIFORM 0
 #define ORC_FIELD_LINEAR_DISTANCE 1
+#define ORC_FIELD_TANH_DISTANCE 2  /* s = a + b tanh(s0 |dist|): the circle case of Sec. 4.1 */
 
 typedef struct {
   int32_t kind;        /* ORC_SPHERE or ORC_BOX */

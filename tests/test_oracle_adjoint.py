@@ -47,6 +47,19 @@ def _general_3d(n=300, seed=7):
     return p, pos, col
 
 
+def _tanh_2d(n=260, seed=5):
+    """The circle case's tanh-graded field (Sec. 4.1) on the unit square (the
+    circle of radius 0.43 at the centre), with a polynomial factor: the field's
+    spatial gradient, largest at the circle, enters the reverse pass."""
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0], shapes=[W.Shape(W.SPHERE, True, [0.5, 0.5, 0.0], [0.43, 0, 0])],
+                  field_kind=W.FIELD_TANH_DISTANCE, a=0.0391, b=(0.3125 - 0.0391) / np.tanh(2.5), s0=2.5 / 0.43,
+                  dist_shape=0, n_colors=5)
+    p.poly = [0.05, -0.04, 0.03, 0.02, -0.03, 0.01, 0.02, -0.01]
+    p.rho_scale = W.rho_scale_for(p, n)
+    pos, col, _ = W.sample_density(p, n, seed=seed)
+    return p, pos, col
+
+
 def _loss(orc, p, x, col, K, lam, dt, seed):
     xe = orc.run(p, x, col, K)[0] if dt is None else orc.run_fixed_dt(p, x, col, dt)
     L = orc.objective(p, xe, col, lam)
@@ -143,3 +156,9 @@ def test_adjoint_zero_steps_is_objective_gradient(orc):
         x2[i, k] -= h
         fd = (orc.objective(p, x1, col, 1.0) - orc.objective(p, x2, col, 1.0)) / (2 * h)
         assert abs(r["dpos0"][i, k] - fd) <= FD_REL * max(abs(fd), 1e-3 * np.abs(r["dpos0"]).max())
+
+
+@pytest.mark.parametrize("frozen", [True, False])
+def test_adjoint_matches_fd_tanh_field(orc, frozen):
+    p, pos, col = _tanh_2d()
+    _check(orc, p, pos, col, K=3, lam=1.0, frozen=frozen)

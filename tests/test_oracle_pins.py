@@ -432,3 +432,31 @@ def test_oracle_relaxation_raises_triangle_quality():
     assert q1["theta_min"] > 15.0 and q1["theta_max"] < 140.0
     assert q1["n_lt30"] < 0.05 * q0["n_lt30"]
     assert q1["theta_min_mean"] > q0["theta_min_mean"] + 10.0
+
+
+# ------------------------------------------------------- circle case (Sec. 4.1) ----
+
+def test_circle_field_is_the_papers_target_size():
+    """The circle workload's spacing is the target size printed for the circle
+    case: h_min + tanh(2.5 phi / 43) / tanh(2.5) (h_max - h_min), phi the
+    distance to the circle of radius 43 at (50, 50), for both printed
+    resolutions; h = hfac s with hfac = tau rho_scale^(-1/2)."""
+    import oracle
+    gold = json.load(open(GOLD))["circle"]
+    c, R, g = np.array(gold["center"]), gold["radius"], gold["tanh_gain"]
+    for case in ("circle_6mpi", "circle_12mpi"):
+        k = gold[case]
+        p = W.circle_2d(k["N_p"], k["mpi_tasks"], h_min=k["h_min"], h_max=k["h_max"])
+        hfac = p.tau * p.rho_scale ** -0.5
+        rng = np.random.default_rng(1)
+        for _ in range(40):
+            phi = rng.uniform(0, R)
+            ang = rng.uniform(0, 2 * math.pi)
+            x = c + (R - phi) * np.array([math.cos(ang), math.sin(ang)])
+            want = k["h_min"] + math.tanh(g * phi / R) / math.tanh(g) * (k["h_max"] - k["h_min"])
+            assert oracle.h_of(p, x) / hfac == pytest.approx(want, rel=1e-12)
+        # the extremes of the printed formula: h_min on the circle, h_max at the centre
+        assert oracle.h_of(p, c) / hfac == pytest.approx(k["h_max"], rel=1e-12)
+        assert oracle.h_of(p, c + [R, 0.0]) / hfac == pytest.approx(k["h_min"], rel=1e-12)
+        # unit mass: the target density integrates to the particle count (Eq. total_mass_2)
+        assert oracle.total_mass(p, 2048) == pytest.approx(k["N_p"], rel=3e-3)

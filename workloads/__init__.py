@@ -27,6 +27,7 @@ BOX = 1
 
 FIELD_UNIFORM = 0
 FIELD_LINEAR_DISTANCE = 1
+FIELD_TANH_DISTANCE = 2  # s = a + b tanh(s0 |dist|), s0 a reciprocal length
 
 
 @dataclasses.dataclass
@@ -111,7 +112,7 @@ def spacing_shape(p: Problem, x: np.ndarray) -> np.ndarray:
         s = np.full(x.shape[0], p.s0)
     else:
         dist = np.abs(_shape_signed(p.shapes[p.dist_shape], x))
-        s = p.a + p.b * dist
+        s = p.a + p.b * (np.tanh(p.s0 * dist) if p.field_kind == FIELD_TANH_DISTANCE else dist)
     w = s ** (-d)
     if p.poly:
         w = w * (1.0 + poly_value(p, x))
@@ -202,7 +203,7 @@ def sample_density(p: Problem, n: int, seed: int, gens: Optional[np.ndarray] = N
     probe = uniform_in_domain(p, 20000, rng)
     wmax = float(np.max(spacing_shape(p, probe))) * 1.5
     for s in p.shapes:  # the densest region may be a thin shell at a shape surface
-        if p.field_kind == FIELD_LINEAR_DISTANCE:
+        if p.field_kind in (FIELD_LINEAR_DISTANCE, FIELD_TANH_DISTANCE):
             wmax = max(wmax, (p.a ** (-d)) * (1.0 + sum(abs(c) for c in p.poly)) * 1.01)
     chunks = []
     have = 0
@@ -280,6 +281,20 @@ def graded_inclusion_3d(n: int = 1 << 23, n_colors: int = 256, rho_scale: Option
                 shapes=[Shape(SPHERE, False, [0.5, 0.5, 0.5], [0.25, 0, 0])],
                 field_kind=FIELD_LINEAR_DISTANCE, a=0.004, b=0.03, dist_shape=0,
                 n_colors=n_colors)
+    p.rho_scale = rho_scale if rho_scale is not None else rho_scale_for(p, n)
+    return p
+
+
+def circle_2d(n: int = 4289, n_colors: int = 6, h_min: float = 0.391, h_max: float = 3.125,
+              rho_scale: Optional[float] = None) -> Problem:
+    """The circle of Sec. 4.1: the disk of radius 43 at (50, 50) in
+    [0, 100]^2, target size h_min + tanh(2.5 phi / 43) / tanh(2.5) (h_max - h_min)
+    with phi the distance to the circle (defaults: the circle_6mpi case, 4,289
+    particles, one colour per MPI task of the paper's run)."""
+    p = Problem(dim=2, lo=[0, 0, 0], hi=[100, 100, 0],
+                shapes=[Shape(SPHERE, True, [50.0, 50.0, 0.0], [43.0, 0, 0])],
+                field_kind=FIELD_TANH_DISTANCE, a=h_min, b=(h_max - h_min) / math.tanh(2.5), s0=2.5 / 43.0,
+                dist_shape=0, n_colors=n_colors)
     p.rho_scale = rho_scale if rho_scale is not None else rho_scale_for(p, n)
     return p
 
