@@ -407,7 +407,8 @@ __device__ __forceinline__ T rho_t_grad(const Geom<T>& g, const T* x, T* grad, T
     T gd[3];
     inside_distance_grad(g, g.dist_shape, x, D, gd);
     const T sg = dist >= T(0) ? T(1) : T(-1);
-    for (int k = 0; k < D; ++k) gs[k] = g.b * sg * gd[k];
+    const T slope = spacing_slope(g, dist);
+    for (int k = 0; k < D; ++k) gs[k] = slope * sg * gd[k];
   }
   T Pf = 1, gP[3] = {0, 0, 0};
   for (int m = 0; m < 8; ++m) dc[m] = T(0);

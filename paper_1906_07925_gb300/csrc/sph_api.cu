@@ -611,7 +611,7 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   double diag = 0.0;
   for (int k = 0; k < d; ++k) diag += pow((h->dom.hi[k] - h->dom.lo[k]) / res, 2);
   diag = sqrt(diag);
-  h->lip_h = lipschitz_h(h->dom, h->field, hfac, fb.max_seff * (1.0 + 1e-6) + fabs(h->field.b) * diag);
+  h->lip_h = lipschitz_h(h->dom, h->field, hfac, fb.max_seff * (1.0 + 1e-6) + field_slope(h->field) * diag);
   h->hmin = std::max(0.5 * hfac * fb.min_seff, hfac * fb.min_seff - h->lip_h * diag);
   h->hmax = hfac * fb.max_seff + h->lip_h * diag;
   fill_geom<double>(h->dom, h->field, hfac, h->rho_scale, h->geod);

@@ -265,10 +265,28 @@ __device__ __forceinline__ T poly_factor(const Geom<T>& g, const T* x) {
   return f;
 }
 
+template <class T> __device__ __forceinline__ T dtanh(T x);
+template <> __device__ __forceinline__ float dtanh<float>(float x) { return tanhf(x); }
+template <> __device__ __forceinline__ double dtanh<double>(double x) { return tanh(x); }
+
+// target spacing s(x): uniform, linear or tanh in the distance to a shape
+// (field kinds 0, 1, 2)
 template <class T>
 __device__ __forceinline__ T spacing_of(const Geom<T>& g, const T* x) {
   if (g.field_kind == 0) return g.s0;
-  return g.a + g.b * fabs(shape_inside(g, g.dist_shape, x, g.dim));
+  const T dist = fabs(shape_inside(g, g.dist_shape, x, g.dim));
+  if (g.field_kind == 2) return g.a + g.b * dtanh(g.s0 * dist);
+  return g.a + g.b * dist;
+}
+
+// ds/d|dist| of the distance fields
+template <class T>
+__device__ __forceinline__ T spacing_slope(const Geom<T>& g, T dist) {
+  if (g.field_kind == 2) {
+    const T t = dtanh(g.s0 * fabs(dist));
+    return g.b * g.s0 * (T(1) - t * t);
+  }
+  return g.b;
 }
 
 // smoothing length h = tau rho_t^(-1/d) with rho_t = rho_scale s^-d (1+P)

@@ -53,8 +53,15 @@ inline void fill_phys(int dim, const sph_params& par, Phys<T>& P) {
   P.alpha = (T)(dim == 2 ? 7.0 / M_PI : 21.0 / (2.0 * M_PI));
 }
 
+// Upper bound of |grad s|: distance functions are 1-Lipschitz and tanh' <= 1.
+inline double field_slope(const sph_field& f) {
+  if (f.kind == SPH_FIELD_LINEAR_DISTANCE) return fabs(f.b);
+  if (f.kind == SPH_FIELD_TANH_DISTANCE) return fabs(f.b) * f.s0;
+  return 0.0;
+}
+
 // Upper bound of |grad h| over the box for h = hfac s (1+P)^(-1/d):
-// |grad s| <= b (distance functions are 1-Lipschitz); |P| <= sum|c_k| = S on
+// |grad s| <= field_slope; |P| <= sum|c_k| = S on
 // x~ in [-1,1]^d; |dP/dx| <= 3 sqrt(d) S * 2/min(ext) (each monomial has
 // |d/dx~| <= 3 there).
 inline double lipschitz_h(const sph_domain& dom, const sph_field& f, double hfac, double smax) {
@@ -63,7 +70,7 @@ inline double lipschitz_h(const sph_domain& dom, const sph_field& f, double hfac
   for (int k = 0; k < f.n_poly; ++k) S += fabs(f.poly[k]);
   double ext_min = DBL_MAX;
   for (int k = 0; k < d; ++k) ext_min = std::min(ext_min, dom.hi[k] - dom.lo[k]);
-  const double gb = f.kind == SPH_FIELD_UNIFORM ? 0.0 : fabs(f.b);
+  const double gb = field_slope(f);
   const double fmin = 1.0 - S;
   const double gradP = 3.0 * sqrt((double)d) * S * 2.0 / ext_min;
   const double L = hfac * (gb * pow(fmin, -1.0 / d) + smax / d * pow(fmin, -1.0 / d - 1.0) * gradP);
@@ -214,9 +221,13 @@ inline sph_status validate(const sph_domain* dom, const sph_field* f, int64_t n,
   if (ncol < 1 || ncol > 256) { why = "n_colors must be in 1..256"; return SPH_ERR_INVALID_ARG; }
   if (f->kind == SPH_FIELD_UNIFORM) {
     if (!(f->s0 > 0)) { why = "s0 must be > 0"; return SPH_ERR_INVALID_ARG; }
-  } else if (f->kind == SPH_FIELD_LINEAR_DISTANCE) {
+  } else if (f->kind == SPH_FIELD_LINEAR_DISTANCE || f->kind == SPH_FIELD_TANH_DISTANCE) {
     if (!(f->a > 0) || !(f->b >= 0) || f->dist_shape < 0 || f->dist_shape >= dom->n_shapes) {
-      why = "bad linear-distance field";
+      why = "bad distance field";
+      return SPH_ERR_INVALID_ARG;
+    }
+    if (f->kind == SPH_FIELD_TANH_DISTANCE && !(f->s0 > 0)) {
+      why = "tanh field needs s0 > 0 (reciprocal length)";
       return SPH_ERR_INVALID_ARG;
     }
   } else { why = "bad field kind"; return SPH_ERR_INVALID_ARG; }

@@ -124,6 +124,9 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
   if (field->kind == SPH_FIELD_LINEAR_DISTANCE) {
     smin = field->a;
     smax = field->a + std::fabs(field->b) * max_surface_distance(*dom, field->dist_shape);
+  } else if (field->kind == SPH_FIELD_TANH_DISTANCE) {
+    smin = field->a;
+    smax = field->a + std::fabs(field->b) * std::tanh(field->s0 * max_surface_distance(*dom, field->dist_shape));
   }
   const double hmin = hfac * smin * std::pow(1.0 + S, -1.0 / d);
   const double hmax = hfac * smax * std::pow(1.0 - S, -1.0 / d);

@@ -28,8 +28,10 @@ def quality(pos, col=None, max_edge_factor=2.5, drop_hull=True):
     """G_avg, G_min, theta_min, theta_max, mean of each triangle's smallest
     angle, count of triangles with an angle < 30 degrees, share of angles in
     [55, 65] degrees, triangle count; with colours, also the communication
-    volume of the partition (Sec. 4): N_eg / N_et, the share of the kept
-    triangles' edges whose end points have different colours."""
+    volume of the partition (Sec. 4): N_eg / N_et, N_eg the kept elements
+    (triangles) with vertices of different colours and N_et all kept elements.
+    max_edge_factor None keeps triangles of any size (convex regions whose
+    resolution varies strongly, where a long edge is no sign of a bridge)."""
     pos = np.asarray(pos, dtype=np.float64)
     dl = Delaunay(pos)
     tri = dl.simplices
@@ -41,17 +43,15 @@ def quality(pos, col=None, max_edge_factor=2.5, drop_hull=True):
     med = np.median(edges)
     longest = np.maximum(np.maximum(np.linalg.norm(a - b, axis=1), np.linalg.norm(b - c, axis=1)),
                          np.linalg.norm(c - a, axis=1))
-    keep = longest < max_edge_factor * med
+    keep = longest < max_edge_factor * med if max_edge_factor else np.ones(len(tri), dtype=bool)
     if drop_hull:
         keep &= ~on_hull[tri].any(axis=1)
     G, A = triangle_metrics(a[keep], b[keep], c[keep])
     extra = {}
     if col is not None:
-        t = tri[keep]
-        e = np.sort(np.concatenate([t[:, [0, 1]], t[:, [1, 2]], t[:, [2, 0]]]), axis=1)
-        e = np.unique(e, axis=0)
-        col = np.asarray(col)
-        extra = dict(n_et=int(len(e)), n_eg=int((col[e[:, 0]] != col[e[:, 1]]).sum()))
+        c = np.asarray(col)[tri[keep]]
+        mixed = (c[:, 0] != c[:, 1]) | (c[:, 1] != c[:, 2])
+        extra = dict(n_et=int(len(c)), n_eg=int(mixed.sum()))
     return dict(**extra, G_avg=float(G.mean()), G_min=float(G.min()), theta_min=float(A.min()), theta_max=float(A.max()),
                 theta_min_mean=float(A.min(axis=1).mean()), n_lt30=int((A.min(axis=1) < 30.0).sum()),
                 share_55_65=float(((A >= 55.0) & (A <= 65.0)).mean()), n_tri=int(keep.sum()))

@@ -25,7 +25,7 @@ from scipy.spatial import cKDTree
 
 import oracle
 import workloads as W
-from parity_util import TOL
+from parity_util import TOL, check_force
 
 pytestmark = pytest.mark.gpu
 
@@ -48,24 +48,6 @@ def _kappa_h_all(p, x):
     ratio = _h_local(p, x, idx) / s[idx]
     assert np.allclose(ratio, ratio[0], rtol=1e-9)
     return p.kappa * ratio[0] * s
-
-
-def _edge_amplification(p, x, idx):
-    """max over the force pairs of each particle in idx of 3 q / (1 - q),
-    q = r / (kappa (h_i + h_j) / 2), from the oracle's h."""
-    tree = cKDTree(x)
-    out = np.zeros(len(idx))
-    for t, i in enumerate(idx):
-        hi = oracle.h_of(p, x[i])
-        nb = np.array([j for j in tree.query_ball_point(x[i], 2.0 * p.kappa * hi) if j != i], dtype=np.int64)
-        if len(nb) == 0:
-            continue
-        hf = 0.5 * p.kappa * (hi + _h_local(p, x, nb))
-        q = np.linalg.norm(x[nb] - x[i], axis=1) / hf
-        q = q[q < 1.0]
-        if len(q):
-            out[t] = (3 * q / (1 - q)).max()
-    return out
 
 
 @pytest.mark.parametrize("case,precision", [("2d_1m", "fp32"), ("3d_8m", "fp32"), ("3d_8m", "fp64")])
@@ -96,24 +78,11 @@ def test_first_step_at_benchmark_size_matches_oracle(case, precision):
     # density, every particle
     rel = np.abs(rho - f["rho"]) / f["rho"]
     assert rel.max() <= tol, ("rho", rel.max(), int(rel.argmax()))
-    # force, every particle, relative to the sum of pair magnitudes. In FP32
-    # a pair near the support edge carries its kernel factor (1 - q)^3 with a
-    # relative error of about 3 q / (1 - q) ulp of q (the rounding of r and of
-    # the FP32 h enters 1 - q unreduced); a particle whose sum that pair
-    # dominates gets the bound tol S + 8 ulp S max_j 3 q_j / (1 - q_j). Such
-    # particles are rare.
+    # force, every particle, relative to the sum of pair magnitudes (with the
+    # FP32 widening for pairs near the support edge, see parity_util)
     Sa = f["pair_abs_a"]
-    ea = np.abs(acc - f["acc"]).max(axis=1)
-    over = np.nonzero(ea > tol * Sa + 1e-300)[0]
-    rel_a = np.full(n, tol)  # relative error bound of each a_i, for a~ and the drift below
-    if precision == "fp64":
-        assert len(over) == 0, ("acc", (ea[over] / Sa[over]).max())
-    else:
-        assert len(over) <= 1e-4 * n, len(over)
-        amp = _edge_amplification(p, x0, over)
-        bound = tol * Sa[over] + 8 * 2.0 ** -23 * Sa[over] * amp
-        assert (ea[over] <= bound).all(), ("acc", (ea[over] / bound).max())
-        rel_a[over] += 8 * 2.0 ** -23 * amp
+    tree = cKDTree(x0)
+    rel_a = check_force(p, x0, acc, f, precision, tree)
     # step sizes: relative error of a at the particle that sets them
     an = np.linalg.norm(f["acc"], axis=1)
     cond = np.where(an > 0, Sa / np.maximum(an, 1e-300), 1.0)
@@ -131,7 +100,6 @@ def test_first_step_at_benchmark_size_matches_oracle(case, precision):
     do = xo - x0
     dn = np.linalg.norm(do, axis=1)
     sample = np.unique(np.concatenate([rng.choice(n, 2000, replace=False), np.argsort(dn)[-100:]]))
-    tree = cKDTree(x0)
     R = p.kappa * _h_local(p, x0, sample).max() * 1.5
     eps = np.array([(rel_a[nb] * (1 + cond[nb])).max()
                     for nb in map(np.asarray, tree.query_ball_point(x0[sample], R))])
@@ -151,13 +119,7 @@ def _check_rho_acc(p, x0, c0, rho, acc, tol):
     _, _, f = oracle.step(p, x0, c0, 0)
     rel = np.abs(rho - f["rho"]) / f["rho"]
     assert rel.max() <= tol, ("rho", rel.max())
-    Sa = f["pair_abs_a"]
-    ea = np.abs(acc - f["acc"]).max(axis=1)
-    over = np.nonzero(ea > tol * Sa + 1e-300)[0]
-    assert len(over) <= max(2, 1e-4 * len(x0)), len(over)
-    if len(over):
-        bound = tol * Sa[over] + 8 * 2.0 ** -23 * Sa[over] * _edge_amplification(p, x0, over)
-        assert (ea[over] <= bound).all(), ("acc", (ea[over] / bound).max())
+    check_force(p, x0, acc, f, "fp32" if tol == TOL["fp32"] else "fp64")
 
 
 def test_batch_of_512_instances_matches_standalone_and_oracle():

@@ -409,11 +409,15 @@ def test_triangle_quality_measure():
     pts = np.stack([ii + 0.5 * (jj % 2), jj * math.sqrt(3) / 2], axis=-1).reshape(-1, 2).astype(float)
     q = MQ.quality(pts)
     assert q["G_avg"] == pytest.approx(1.0, abs=1e-9) and q["share_55_65"] == pytest.approx(1.0)
-    # a rhombus of two equilateral triangles: 5 edges, 3 of them join the
-    # bottom pair (colour 0) to the top pair (colour 1)
+    # communication volume (Sec. 4: elements with vertices of different colours
+    # over all elements): a rhombus of two equilateral triangles whose bottom
+    # pair has colour 0 and top pair colour 1 has both elements mixed; with the
+    # right vertex recoloured, only the left triangle (vertices 0, 1, 2) is
     rh = np.array([[0.0, 0.0], [1.0, 0.0], [0.5, math.sqrt(3) / 2], [1.5, math.sqrt(3) / 2]])
     q = MQ.quality(rh, np.array([0, 0, 1, 1]), drop_hull=False)
-    assert (q["n_tri"], q["n_et"], q["n_eg"]) == (2, 5, 3) and q["G_avg"] == pytest.approx(1.0)
+    assert (q["n_tri"], q["n_et"], q["n_eg"]) == (2, 2, 2) and q["G_avg"] == pytest.approx(1.0)
+    q = MQ.quality(rh, np.array([0, 1, 1, 1]), drop_hull=False)
+    assert (q["n_et"], q["n_eg"]) == (2, 1)
 
 
 def test_oracle_relaxation_raises_triangle_quality():
