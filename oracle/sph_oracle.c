@@ -55,8 +55,50 @@ double orc_dW(double r, double H, int dim) {
 /* each shape constraint; phi is the minimum of the constraint distances.    */
 /* ------------------------------------------------------------------------ */
 
+/* Interpolation on the Cartesian background mesh (Sec. 3.1: the level set is
+ * discretised on it; Sec. 3.2: the target density is interpolated from it at
+ * the particle positions). Reading: multilinear interpolation of the node
+ * values (bilinear in 2D, trilinear in 3D) in the cell that holds x, x clamped
+ * into the mesh box; grad receives the gradient of the interpolant there. */
+static double bg_interp(const orc_problem* p, const double* v, const double* x, double* grad) {
+  int d = p->dim, i0[3] = {0, 0, 0};
+  double f[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+  for (int k = 0; k < d; ++k) {
+    int n = p->bg_dims[k];
+    h[k] = (p->bg_hi[k] - p->bg_lo[k]) / (n - 1);
+    double t = (x[k] - p->bg_lo[k]) / h[k];
+    if (t < 0.0) t = 0.0;
+    if (t > n - 1) t = n - 1;
+    int i = (int)floor(t);
+    if (i > n - 2) i = n - 2;
+    i0[k] = i;
+    f[k] = t - i;
+  }
+  double val = 0.0, g[3] = {0, 0, 0};
+  int corners = 1 << d;
+  for (int c = 0; c < corners; ++c) {
+    int idx[3] = {0, 0, 0};
+    double w = 1.0, dw[3] = {1, 1, 1};
+    for (int k = 0; k < d; ++k) {
+      int b = (c >> k) & 1;
+      idx[k] = i0[k] + b;
+      double wk = b ? f[k] : 1.0 - f[k];
+      double dk = (b ? 1.0 : -1.0) / h[k];
+      for (int m = 0; m < d; ++m) dw[m] *= (m == k) ? dk : wk;
+      w *= wk;
+    }
+    double node = v[idx[0] + (int64_t)p->bg_dims[0] * (idx[1] + (int64_t)p->bg_dims[1] * idx[2])];
+    val += w * node;
+    for (int m = 0; m < d; ++m) g[m] += dw[m] * node;
+  }
+  if (grad)
+    for (int k = 0; k < 3; ++k) grad[k] = k < d ? g[k] : 0.0;
+  return val;
+}
+
 /* signed distance, positive inside the shape */
-static double shape_inside_distance(const orc_shape* s, const double* x, int dim) {
+static double shape_inside_distance(const orc_problem* p, const orc_shape* s, const double* x, int dim) {
+  if (s->kind == ORC_GRID) return bg_interp(p, p->bg_phi, x, NULL);
   if (s->kind == ORC_SPHERE) {
     double r2 = 0.0;
     for (int k = 0; k < dim; ++k) r2 += (x[k] - s->center[k]) * (x[k] - s->center[k]);
@@ -72,8 +114,8 @@ static double shape_inside_distance(const orc_shape* s, const double* x, int dim
   return -(sqrt(outside2) + inside);
 }
 
-static double constraint_phi(const orc_shape* s, const double* x, int dim) {
-  double v = shape_inside_distance(s, x, dim);
+static double constraint_phi(const orc_problem* p, const orc_shape* s, const double* x, int dim) {
+  double v = shape_inside_distance(p, s, x, dim);
   return s->keep_inside ? v : -v;
 }
 
@@ -90,9 +132,9 @@ static orc_shape box_shape(const orc_problem* p) {
 
 double orc_phi(const orc_problem* p, const double* x) {
   orc_shape b = box_shape(p);
-  double phi = constraint_phi(&b, x, p->dim);
+  double phi = constraint_phi(p, &b, x, p->dim);
   for (int s = 0; s < p->n_shapes; ++s) {
-    double v = constraint_phi(&p->shapes[s], x, p->dim);
+    double v = constraint_phi(p, &p->shapes[s], x, p->dim);
     if (v < phi) phi = v;
   }
   return phi;
@@ -104,10 +146,25 @@ double orc_phi(const orc_problem* p, const double* x) {
  *  - box kept inside: clamp to the box;
  *  - box kept outside: push out through the nearest face;
  *  - sphere (either side): c + R (x - c)/|x - c|.
+ *  - background-mesh level set: N = grad(phi) / |grad(phi)|^2 of the
+ *    interpolant (Newton's step towards phi = 0, the printed step when |grad
+ *    phi| = 1), taken three times from the point that violated it.
  * Reading: constraints are applied in order, the bounding box first. */
-static int project_one(const orc_shape* s, double* x, int dim) {
-  double phi = constraint_phi(s, x, dim);
+static int project_one(const orc_problem* p, const orc_shape* s, double* x, int dim) {
+  double phi = constraint_phi(p, s, x, dim);
   if (!(phi < 0.0)) return 0;
+  if (s->kind == ORC_GRID) {
+    double sg = s->keep_inside ? 1.0 : -1.0;
+    for (int it = 0; it < 3; ++it) {
+      double g[3];
+      double v = sg * bg_interp(p, p->bg_phi, x, g);
+      double g2 = 0.0;
+      for (int k = 0; k < dim; ++k) g2 += g[k] * g[k];
+      if (!(g2 > 0.0)) break;
+      for (int k = 0; k < dim; ++k) x[k] -= v * sg * g[k] / g2;
+    }
+    return 1;
+  }
   if (s->kind == ORC_SPHERE) {
     double d[3] = {0, 0, 0}, r2 = 0.0;
     for (int k = 0; k < dim; ++k) { d[k] = x[k] - s->center[k]; r2 += d[k] * d[k]; }
@@ -138,8 +195,8 @@ static int project_one(const orc_shape* s, double* x, int dim) {
 
 int orc_project(const orc_problem* p, double* x) {
   orc_shape b = box_shape(p);
-  int moved = project_one(&b, x, p->dim);
-  for (int s = 0; s < p->n_shapes; ++s) moved |= project_one(&p->shapes[s], x, p->dim);
+  int moved = project_one(p, &b, x, p->dim);
+  for (int s = 0; s < p->n_shapes; ++s) moved |= project_one(p, &p->shapes[s], x, p->dim);
   return moved;
 }
 
@@ -173,7 +230,8 @@ static double poly_factor(const orc_problem* p, const double* x) {
  * b = (h_max - h_min) / tanh(2.5) and s0 = 2.5 / 43. */
 static double spacing(const orc_problem* p, const double* x) {
   if (p->field_kind == ORC_FIELD_UNIFORM) return p->s0;
-  double dist = fabs(shape_inside_distance(&p->shapes[p->dist_shape], x, p->dim));
+  if (p->field_kind == ORC_FIELD_BACKGROUND) return bg_interp(p, p->bg_s, x, NULL);
+  double dist = fabs(shape_inside_distance(p, &p->shapes[p->dist_shape], x, p->dim));
   if (p->field_kind == ORC_FIELD_TANH_DISTANCE) return p->a + p->b * tanh(p->s0 * dist);
   return p->a + p->b * dist;
 }
@@ -651,8 +709,12 @@ static void force_kernel(double r, double H, int dim, double* F, double* F_r, do
 }
 
 /* gradient of the signed inside distance of a shape (the branch the value takes) */
-static void inside_distance_grad(const orc_shape* s, const double* x, int dim, double* g) {
+static void inside_distance_grad(const orc_problem* p, const orc_shape* s, const double* x, int dim, double* g) {
   for (int k = 0; k < 3; ++k) g[k] = 0.0;
+  if (s->kind == ORC_GRID) {
+    bg_interp(p, p->bg_phi, x, g);
+    return;
+  }
   if (s->kind == ORC_SPHERE) {
     double r2 = 0.0;
     for (int k = 0; k < dim; ++k) r2 += (x[k] - s->center[k]) * (x[k] - s->center[k]);
@@ -711,10 +773,12 @@ static double rho_t_grad(const orc_problem* p, const double* x, double* grad, do
   double base = p->rho_scale * pow(s, -(double)d);
   double rt = base * Pf;
   double gs[3] = {0, 0, 0};
-  if (p->field_kind != ORC_FIELD_UNIFORM) {
+  if (p->field_kind == ORC_FIELD_BACKGROUND) {
+    bg_interp(p, p->bg_s, x, gs);
+  } else if (p->field_kind != ORC_FIELD_UNIFORM) {
     const orc_shape* sh = &p->shapes[p->dist_shape];
-    double dist = shape_inside_distance(sh, x, d), gd[3];
-    inside_distance_grad(sh, x, d, gd);
+    double dist = shape_inside_distance(p, sh, x, d), gd[3];
+    inside_distance_grad(p, sh, x, d, gd);
     double sg = dist >= 0.0 ? 1.0 : -1.0;
     double slope = spacing_slope(p, dist);
     for (int k = 0; k < d; ++k) gs[k] = slope * sg * gd[k];
@@ -747,12 +811,12 @@ static void project_vjp(const orc_problem* p, const double* y, double* g) {
   for (int k = 0; k < 3; ++k) z[0][k] = k < d ? y[k] : 0.0;
   for (int c = 0; c < nc; ++c) {
     memcpy(z[c + 1], z[c], sizeof z[c]);
-    project_one(&cons[c], z[c + 1], d);
+    project_one(p, &cons[c], z[c + 1], d);
   }
   for (int c = nc - 1; c >= 0; --c) {
     const orc_shape* s = &cons[c];
     const double* x = z[c];
-    if (!(constraint_phi(s, x, d) < 0.0)) continue;
+    if (!(constraint_phi(p, s, x, d) < 0.0)) continue;
     if (s->kind == ORC_SPHERE) {
       double dv[3] = {0, 0, 0}, r2 = 0.0;
       for (int k = 0; k < d; ++k) { dv[k] = x[k] - s->center[k]; r2 += dv[k] * dv[k]; }
@@ -1090,6 +1154,9 @@ int orc_backward(const orc_problem* p, int64_t n, const double* pos0, const uint
                  int32_t K, const double* dt_in, double* dt_out, double lambda, const double* seed,
                  double* L, double* dpos0, double* grads) {
   const int d = p->dim;
+  /* the reverse pass covers analytic shapes only (no background-mesh level set) */
+  for (int s = 0; s < p->n_shapes; ++s)
+    if (p->shapes[s].kind == ORC_GRID) return -1;
   size_t nd = (size_t)n * (size_t)d;
   double* traj = (double*)malloc(sizeof(double) * nd * (size_t)(K + 1));
   if (!traj) return -1;

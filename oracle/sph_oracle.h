@@ -24,9 +24,11 @@ extern "C" {
 
 #define ORC_SPHERE 0
 #define ORC_BOX 1
+#define ORC_GRID 2  /* the level set sampled on the background mesh (bg_phi) */
 #define ORC_FIELD_UNIFORM 0
 #define ORC_FIELD_LINEAR_DISTANCE 1
 #define ORC_FIELD_TANH_DISTANCE 2  /* s = a + b tanh(s0 |dist|): the circle case of Sec. 4.1 */
+#define ORC_FIELD_BACKGROUND 3     /* s sampled on the background mesh (bg_s) */
 
 typedef struct {
   int32_t kind;        /* ORC_SPHERE or ORC_BOX */
@@ -49,6 +51,15 @@ typedef struct {
   double rho_scale;
   double P0, gamma, sigma0, tau, kappa;
   double t0, t1;       /* surface-tension ramp window in steps; t0 < 0: none */
+  /* Cartesian background mesh (Sec. 3.1, 3.2): node values at
+   * bg_lo + i (bg_hi - bg_lo) / (bg_dims - 1), x fastest; bg_dims[2] = 1 in 2D.
+   * bg_phi: level set (positive in the region) for ORC_GRID shapes; bg_s:
+   * target spacing for ORC_FIELD_BACKGROUND. NULL when unused. */
+  int32_t bg_dims[3];
+  int32_t bg_pad;
+  double bg_lo[3], bg_hi[3];
+  const double* bg_phi;
+  const double* bg_s;
 } orc_problem;
 
 typedef struct {

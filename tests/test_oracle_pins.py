@@ -464,3 +464,82 @@ def test_circle_field_is_the_papers_target_size():
         assert oracle.h_of(p, c + [R, 0.0]) / hfac == pytest.approx(k["h_min"], rel=1e-12)
         # unit mass: the target density integrates to the particle count (Eq. total_mass_2)
         assert oracle.total_mass(p, 2048) == pytest.approx(k["N_p"], rel=3e-3)
+
+
+# ------------------------------------------- background mesh (Sec. 3.1, 3.2) ----
+
+def _bg_problem(phi_fn, s_fn, nodes=(21, 17), hi=(10.0, 8.0)):
+    """A 2D problem whose level set and spacing are node samples of phi_fn and
+    s_fn on a background mesh over [0, hi]."""
+    tx, ty = np.linspace(0, hi[0], nodes[0]), np.linspace(0, hi[1], nodes[1])
+    X, Y = np.meshgrid(tx, ty, indexing="ij")
+    bg = W.Background(dims=[nodes[0], nodes[1], 1], lo=[0, 0, 0], hi=[hi[0], hi[1], 0],
+                      phi=phi_fn(X, Y)[:, :, None], spacing=s_fn(X, Y)[:, :, None])
+    return W.Problem(dim=2, lo=[0, 0, 0], hi=[hi[0], hi[1], 0], shapes=[W.Shape(W.GRID, True, [0, 0, 0], [1, 0, 0])],
+                     field_kind=W.FIELD_BACKGROUND, rho_scale=1.0, bg=bg)
+
+
+def test_background_mesh_reproduces_bilinear_fields():
+    """Multilinear interpolation is exact for functions that are bilinear in
+    (x, y): a planar level set and a bilinear spacing field come back exactly at
+    any point, and h = tau s (rho_scale 1, no polynomial)."""
+    import oracle
+    phi_fn = lambda x, y: 6.0 - 0.8 * x + 0.3 * y  # noqa: E731
+    s_fn = lambda x, y: 0.2 + 0.03 * x + 0.02 * y + 0.004 * x * y  # noqa: E731
+    p = _bg_problem(phi_fn, s_fn)
+    rng = np.random.default_rng(3)
+    for _ in range(50):
+        x = rng.uniform([0.2, 0.2], [9.8, 7.8])
+        box = min(x[0], 10 - x[0], x[1], 8 - x[1])
+        assert oracle.phi(p, x) == pytest.approx(min(phi_fn(*x), box), abs=1e-12)
+        assert oracle.h_of(p, x) == pytest.approx(p.tau * s_fn(*x), rel=1e-12)
+
+
+def test_background_mesh_projection_onto_a_planar_level_set():
+    """For a planar level set the projection (Newton steps along the
+    interpolant's gradient) lands on the closest point of the plane, the
+    printed displacement r - phi N with N the unit normal."""
+    import oracle
+    a, b, c = 6.0, -0.8, 0.3
+    p = _bg_problem(lambda x, y: a + b * x + c * y, lambda x, y: 0.3 + 0 * x)
+    g = np.array([b, c])
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        x = rng.uniform([8.5, 0.5], [9.5, 2.0])  # phi < 0 there
+        ph = a + g @ x
+        assert ph < 0
+        want = x - ph * g / (g @ g)
+        got = oracle.project(p, x)
+        assert np.allclose(got, want, atol=1e-12)
+        assert abs(a + g @ got) < 1e-12
+
+
+def test_background_circle_matches_the_analytic_circle():
+    """The circle case sampled on a 101 x 101 background mesh: the
+    interpolated level set is the circle's distance function up to the
+    bilinear interpolation error of a unit mesh, h^2 / 8 times the cone's
+    Laplacian 1/r over the cell (r - 1.5 at least), the target size is the
+    printed formula within 1 %, and the target density integrates to the
+    particle count."""
+    import oracle
+    pb = W.circle_2d_background(4289, 6)
+    pa = W.circle_2d(4289, 6)
+    rng = np.random.default_rng(5)
+    for _ in range(100):
+        r, t = rng.uniform(2.0, 42.0), rng.uniform(0, 2 * math.pi)
+        x = np.array([50 + r * math.cos(t), 50 + r * math.sin(t)])
+        assert oracle.phi(pb, x) == pytest.approx(43.0 - r, abs=1.0 / (8.0 * (r - 1.5)))
+        sa = oracle.h_of(pa, x) / (pa.tau * pa.rho_scale ** -0.5)
+        sb = oracle.h_of(pb, x) / (pb.tau * pb.rho_scale ** -0.5)
+        assert sb == pytest.approx(sa, rel=0.01)
+    assert oracle.total_mass(pb, 2048) == pytest.approx(4289, rel=3e-3)
+
+
+def test_background_level_set_is_not_differentiated():
+    """The reverse pass covers analytic shapes only: the oracle refuses a
+    background-mesh level set."""
+    import oracle
+    p = W.circle_2d_background(300, 3)
+    pos, col, _ = W.sample_density(p, 300, 1)
+    with pytest.raises(RuntimeError):
+        oracle.backward(p, pos, col, 1, 1.0)

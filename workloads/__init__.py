@@ -24,10 +24,51 @@ import numpy as np
 
 SPHERE = 0
 BOX = 1
+GRID = 2  # the level set sampled on the problem's background mesh (Problem.bg.phi)
 
 FIELD_UNIFORM = 0
 FIELD_LINEAR_DISTANCE = 1
 FIELD_TANH_DISTANCE = 2  # s = a + b tanh(s0 |dist|), s0 a reciprocal length
+FIELD_BACKGROUND = 3  # s sampled on the problem's background mesh (Problem.bg.spacing)
+
+
+@dataclasses.dataclass
+class Background:
+    """Cartesian background mesh: node (i, j, k) at lo + (i, j, k) (hi - lo) /
+    (dims - 1); phi (level set, positive in the region) and spacing are arrays
+    of shape dims indexed [i, j, k] (dims[2] = 1 in 2D), either may be None."""
+
+    dims: Sequence[int]
+    lo: Sequence[float]
+    hi: Sequence[float]
+    phi: Optional[np.ndarray] = None
+    spacing: Optional[np.ndarray] = None
+
+
+def bg_interp(bg: Background, v: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """Multilinear interpolation of node values v at points x (n, d), x clamped
+    into the mesh box (input shaping only: the sampler's density envelope)."""
+    n, d = x.shape
+    vv = np.asarray(v, dtype=np.float64).reshape(tuple(bg.dims[:d]) if d == 3 else (bg.dims[0], bg.dims[1]))
+    i0 = np.zeros((n, d), dtype=np.int64)
+    f = np.zeros((n, d))
+    for k in range(d):
+        m = int(bg.dims[k])
+        h = (bg.hi[k] - bg.lo[k]) / (m - 1)
+        t = np.clip((x[:, k] - bg.lo[k]) / h, 0.0, m - 1)
+        i = np.minimum(np.floor(t).astype(np.int64), m - 2)
+        i0[:, k] = i
+        f[:, k] = t - i
+    out = np.zeros(n)
+    for c in range(1 << d):
+        w = np.ones(n)
+        idx = []
+        for k in range(d):
+            b = (c >> k) & 1
+            idx.append(i0[:, k] + b)
+            w *= f[:, k] if b else 1.0 - f[:, k]
+        out += w * vv[tuple(idx)]
+    return out
 
 
 @dataclasses.dataclass
@@ -70,6 +111,7 @@ class Problem:
     t0: float = -1.0  # surface-tension ramp start (steps); < 0: no ramp
     t1: float = -1.0
     eos_general: bool = False  # use p/rho^2 even at gamma = 2 (identity checks)
+    bg: Optional[Background] = None  # background mesh for GRID shapes / FIELD_BACKGROUND
 
     def copy(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
@@ -79,9 +121,11 @@ class Problem:
 # geometry helpers used only to shape the inputs
 # ----------------------------------------------------------------------------
 
-def _shape_signed(shape: Shape, x: np.ndarray) -> np.ndarray:
+def _shape_signed(shape: Shape, x: np.ndarray, bg: Optional[Background] = None) -> np.ndarray:
     """Signed distance, positive inside the shape (x: (n, d))."""
     d = x.shape[1]
+    if shape.kind == GRID:
+        return bg_interp(bg, bg.phi, x)
     c = np.asarray(shape.center[:d], dtype=np.float64)
     if shape.kind == SPHERE:
         return shape.size[0] - np.linalg.norm(x - c, axis=1)
@@ -99,7 +143,7 @@ def inside_mask(p: Problem, x: np.ndarray) -> np.ndarray:
     lo = np.asarray(p.lo[:d]); hi = np.asarray(p.hi[:d])
     m = np.all((x >= lo) & (x <= hi), axis=1)
     for s in p.shapes:
-        v = _shape_signed(s, x)
+        v = _shape_signed(s, x, p.bg)
         m &= (v > 0) if s.keep_inside else (v < 0)
     return m
 
@@ -110,8 +154,10 @@ def spacing_shape(p: Problem, x: np.ndarray) -> np.ndarray:
     d = p.dim
     if p.field_kind == FIELD_UNIFORM:
         s = np.full(x.shape[0], p.s0)
+    elif p.field_kind == FIELD_BACKGROUND:
+        s = bg_interp(p.bg, p.bg.spacing, x)
     else:
-        dist = np.abs(_shape_signed(p.shapes[p.dist_shape], x))
+        dist = np.abs(_shape_signed(p.shapes[p.dist_shape], x, p.bg))
         s = p.a + p.b * (np.tanh(p.s0 * dist) if p.field_kind == FIELD_TANH_DISTANCE else dist)
     w = s ** (-d)
     if p.poly:
@@ -205,6 +251,8 @@ def sample_density(p: Problem, n: int, seed: int, gens: Optional[np.ndarray] = N
     for s in p.shapes:  # the densest region may be a thin shell at a shape surface
         if p.field_kind in (FIELD_LINEAR_DISTANCE, FIELD_TANH_DISTANCE):
             wmax = max(wmax, (p.a ** (-d)) * (1.0 + sum(abs(c) for c in p.poly)) * 1.01)
+    if p.field_kind == FIELD_BACKGROUND:  # multilinear interpolation stays within the node values
+        wmax = max(wmax, float(np.min(p.bg.spacing)) ** (-d) * (1.0 + sum(abs(c) for c in p.poly)) * 1.01)
     chunks = []
     have = 0
     while have < n:
@@ -295,6 +343,24 @@ def circle_2d(n: int = 4289, n_colors: int = 6, h_min: float = 0.391, h_max: flo
                 shapes=[Shape(SPHERE, True, [50.0, 50.0, 0.0], [43.0, 0, 0])],
                 field_kind=FIELD_TANH_DISTANCE, a=h_min, b=(h_max - h_min) / math.tanh(2.5), s0=2.5 / 43.0,
                 dist_shape=0, n_colors=n_colors)
+    p.rho_scale = rho_scale if rho_scale is not None else rho_scale_for(p, n)
+    return p
+
+
+def circle_2d_background(n: int = 4289, n_colors: int = 6, h_min: float = 0.391, h_max: float = 3.125,
+                         nodes: int = 101, rho_scale: Optional[float] = None) -> Problem:
+    """The circle case of Sec. 4.1 given as the paper's method takes geometry in
+    (Sec. 3.1, 3.2): the level set 43 - |x - (50, 50)| and the target size
+    sampled on a Cartesian background mesh of nodes x nodes points over
+    [0, 100]^2, interpolated at the particle positions."""
+    t = np.linspace(0.0, 100.0, nodes)
+    X, Y = np.meshgrid(t, t, indexing="ij")
+    phi = 43.0 - np.hypot(X - 50.0, Y - 50.0)
+    size = h_min + np.tanh(2.5 * np.abs(phi) / 43.0) / math.tanh(2.5) * (h_max - h_min)
+    bg = Background(dims=[nodes, nodes, 1], lo=[0.0, 0.0, 0.0], hi=[100.0, 100.0, 0.0],
+                    phi=phi[:, :, None], spacing=size[:, :, None])
+    p = Problem(dim=2, lo=[0, 0, 0], hi=[100, 100, 0], shapes=[Shape(GRID, True, [0.0, 0.0, 0.0], [1.0, 0, 0])],
+                field_kind=FIELD_BACKGROUND, n_colors=n_colors, bg=bg)
     p.rho_scale = rho_scale if rho_scale is not None else rho_scale_for(p, n)
     return p
 
