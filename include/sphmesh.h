@@ -50,10 +50,12 @@ typedef enum {
 
 /* Level-set constraints (Sec. 3.1, Eq. level_set_function). The mesh region
  * (phi > 0) is the box [lo, hi] intersected with every shape constraint. */
-enum { SPH_SHAPE_SPHERE = 0, SPH_SHAPE_BOX = 1 };
+enum { SPH_SHAPE_SPHERE = 0, SPH_SHAPE_BOX = 1, SPH_SHAPE_GRID = 2 };
 
 typedef struct {
-  int32_t kind;        /* SPH_SHAPE_SPHERE or SPH_SHAPE_BOX */
+  int32_t kind;        /* SPH_SHAPE_SPHERE, SPH_SHAPE_BOX, or SPH_SHAPE_GRID (the level set of
+                          the background mesh, sph_create_background; center and size
+                          unused, size[0] > 0) */
   int32_t keep_inside; /* 1: region inside the shape; 0: outside (a hole) */
   double center[3];
   double size[3];      /* sphere: size[0] = radius; box: half extents */
@@ -78,7 +80,8 @@ typedef struct {
  * rho_scale = 0 asks sph_create to choose it so that the total mass
  * M_v = integral of rho_t over the region (Eq. total_mass_2) equals the
  * particle count (unit mass, Eq. mass_SPH_particle). sum_k |poly[k]| < 1. */
-enum { SPH_FIELD_UNIFORM = 0, SPH_FIELD_LINEAR_DISTANCE = 1, SPH_FIELD_TANH_DISTANCE = 2 };
+enum { SPH_FIELD_UNIFORM = 0, SPH_FIELD_LINEAR_DISTANCE = 1, SPH_FIELD_TANH_DISTANCE = 2,
+       SPH_FIELD_BACKGROUND = 3 /* s interpolated from the background mesh (sph_create_background) */ };
 
 typedef struct {
   int32_t kind;
@@ -162,6 +165,34 @@ typedef struct sph_handle sph_handle;
 sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_particles,
                       int32_t n_colors, const sph_params* params, const sph_alloc* alloc,
                       void* stream, sph_handle** out);
+
+/* Cartesian background mesh (Sec. 3.1: the level set is discretised on a
+ * Cartesian background mesh; Sec. 3.2: the target information is computed on
+ * it and interpolated at the particle positions). Node (i, j, k) sits at
+ * lo + (i, j, k) (hi - lo) / (dims - 1); values are stored x fastest. Values
+ * are interpolated multilinearly (bilinear in 2D, trilinear in 3D) in the cell
+ * that holds the point, points clamped into the mesh box. A level-set
+ * constraint (SPH_SHAPE_GRID) violated by a particle is corrected by three
+ * Newton steps x <- x - phi grad(phi) / |grad(phi)|^2 of the interpolant (the
+ * printed Eq. displacement_surface when phi is a distance function). */
+typedef struct {
+  int32_t dims[3];       /* nodes per axis, >= 2 (dims[2] = 1 in 2D); product <= 2^28 */
+  int32_t reserved;
+  double lo[3], hi[3];   /* mesh box; must contain the domain box */
+  const double* phi;     /* host: level set at the nodes, positive in the region (NULL: none) */
+  const double* spacing; /* host: target spacing s > 0 at the nodes (NULL: none) */
+} sph_background;
+
+/* sph_create with a background mesh: shapes of kind SPH_SHAPE_GRID use bg->phi
+ * and a field of kind SPH_FIELD_BACKGROUND uses bg->spacing (the distance
+ * fields may also name a SPH_SHAPE_GRID shape). The node arrays are copied to
+ * the device; the caller may free them when the call returns. sph_backward
+ * refuses a handle with a SPH_SHAPE_GRID constraint (INVALID_ARG); the batch
+ * API takes no background mesh. Errors as sph_create, and INVALID_ARG for an
+ * inconsistent mesh. */
+sph_status sph_create_background(const sph_domain* dom, const sph_field* field, const sph_background* bg,
+                                 int64_t n_particles, int32_t n_colors, const sph_params* params,
+                                 const sph_alloc* alloc, void* stream, sph_handle** out);
 
 /* Replace the particle state (Algorithm 1 state = positions + colours; velocity
  * is zeroed every step, Sec. 3.3). xyz: n x dim doubles, col: n uint8 (colour <

@@ -73,6 +73,28 @@ def problem_structs(p, precision="fp32", seed=0, cell_factor=0.0, use_graph=True
     return d, f, q
 
 
+def background_struct(bg):
+    """Marshal a background mesh (attributes dims, lo, hi, phi, spacing; the
+    arrays shaped dims and indexed [i, j, k]) into sph_background. Returns
+    (struct, arrays kept alive for the call) or None."""
+    if bg is None:
+        return None
+    import numpy as np
+    s = B.sph_background()
+    keep = []
+    for k in range(3):
+        s.dims[k] = int(bg.dims[k])
+        s.lo[k] = float(bg.lo[k])
+        s.hi[k] = float(bg.hi[k])
+    for name in ("phi", "spacing"):
+        v = getattr(bg, name, None)
+        if v is not None:
+            a = np.ascontiguousarray(np.asarray(v, dtype=np.float64).ravel(order="F"))
+            keep.append(a)
+            setattr(s, name, a.ctypes.data)
+    return s, keep
+
+
 class Relaxation:
     """One relaxation instance on the current CUDA device.
 
@@ -109,9 +131,15 @@ class Relaxation:
         self._cb = (B.ALLOC_FN(_alloc), B.FREE_FN(_free))
         al = B.sph_alloc(self._cb[0], self._cb[1], None)
         h = B.H()
+        bg = background_struct(getattr(problem, "bg", None))
         with torch.cuda.device(self.device):
-            st = self.lib.sph_create(C.byref(dom), C.byref(fld), self.n, ncol, C.byref(par), C.byref(al),
-                                     C.c_void_p(stream.cuda_stream), C.byref(h))
+            if bg is None:
+                st = self.lib.sph_create(C.byref(dom), C.byref(fld), self.n, ncol, C.byref(par), C.byref(al),
+                                         C.c_void_p(stream.cuda_stream), C.byref(h))
+            else:
+                st = self.lib.sph_create_background(C.byref(dom), C.byref(fld), C.byref(bg[0]), self.n, ncol,
+                                                    C.byref(par), C.byref(al), C.c_void_p(stream.cuda_stream),
+                                                    C.byref(h))
         if st != B.SPH_OK:
             raise SphError(st, "sph_create failed (details on stderr)")
         self.h = h

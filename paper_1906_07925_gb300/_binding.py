@@ -63,6 +63,11 @@ class sph_stats(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sph_background(C.Structure):
+    _fields_ = [("dims", C.c_int32 * 3), ("reserved", C.c_int32), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("phi", C.c_void_p), ("spacing", C.c_void_p)]
+
+
 class sph_grid_info(C.Structure):
     _fields_ = [("n_levels", C.c_int32), ("dim", C.c_int32), ("lo", C.c_double * 3), ("h0", C.c_double),
                 ("lip_h", C.c_double), ("cell", C.c_double * 8), ("dims", (C.c_int32 * 3) * 8),
@@ -111,6 +116,8 @@ def load():
         sig = {
             "sph_create": [P(sph_domain), P(sph_field), C.c_int64, C.c_int32, P(sph_params), P(sph_alloc),
                            C.c_void_p, P(H)],
+            "sph_create_background": [P(sph_domain), P(sph_field), P(sph_background), C.c_int64, C.c_int32,
+                                      P(sph_params), P(sph_alloc), C.c_void_p, P(H)],
             "sph_set_state": [H, C.c_void_p, C.c_void_p, C.c_int32],
             "sph_step": [H, C.c_int32],
             "sph_step_profiled": [H, C.c_int32, P(C.c_float)],

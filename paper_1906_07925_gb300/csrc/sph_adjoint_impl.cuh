@@ -368,6 +368,10 @@ __global__ void k_bwd_dt(const StepCtl* __restrict__ ctl, const typename ViewOf<
 template <class T>
 __device__ __forceinline__ void inside_distance_grad(const Geom<T>& g, int s, const T* x, int dim, T* gr) {
   for (int k = 0; k < 3; ++k) gr[k] = T(0);
+  if (g.kind[s] == 2) {  // not reached: the reverse pass refuses background-mesh geometry
+    bg_interp(g, g.bg_phi, x, dim, gr);
+    return;
+  }
   if (g.kind[s] == 0) {
     T r2 = 0;
     for (int k = 0; k < dim; ++k) r2 += (x[k] - g.center[s][k]) * (x[k] - g.center[s][k]);
@@ -402,7 +406,9 @@ __device__ __forceinline__ T rho_t_grad(const Geom<T>& g, const T* x, T* grad, T
   const T s = spacing_of(g, x);
   const T base = g.rho_scale * (D == 2 ? T(1) / (s * s) : T(1) / (s * s * s));
   T gs[3] = {0, 0, 0};
-  if (g.field_kind != 0) {
+  if (g.field_kind == 3) {
+    bg_interp(g, g.bg_s, x, D, gs);
+  } else if (g.field_kind != 0) {
     const T dist = shape_inside(g, g.dist_shape, x, D);
     T gd[3];
     inside_distance_grad(g, g.dist_shape, x, D, gd);

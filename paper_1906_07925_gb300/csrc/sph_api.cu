@@ -28,6 +28,14 @@ struct sph_handle {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   double rho_scale = 1.0, lip_h = 0.0, hmin = 0.0, hmax = 0.0;
+  // background mesh (sph_create_background): device node arrays, the mesh box
+  // and the interpolants' gradient bounds
+  bool has_bg = false, bg_grid_shape = false;
+  const double* bg_phi = nullptr;
+  const double* bg_s = nullptr;
+  int bg_n[3] = {1, 1, 1};
+  double bg_lo[3] = {0, 0, 0}, bg_hi[3] = {0, 0, 0};
+  double bg_lip_phi = 1.0, bg_lip_s = 0.0;
   HostGrid hg{};
   Grid<float> Gf{};
   Grid<double> Gdw{};
@@ -560,13 +568,45 @@ sph_status taped_step(sph_handle* h, const DevState& T, const double* dt_fix, do
 
 }  // namespace
 
+// gradient bound of the multilinear interpolant of node values v: in a cell,
+// d/dx_k is a convex combination of the cell's k-edge differences / h_k
+static double bg_slope(const sph_background& b, int d, const double* v) {
+  double s2 = 0.0;
+  const int64_t nx = b.dims[0], ny = b.dims[1], nz = b.dims[2];
+  for (int k = 0; k < d; ++k) {
+    const double hk = (b.hi[k] - b.lo[k]) / (b.dims[k] - 1);
+    const int64_t step = k == 0 ? 1 : (k == 1 ? nx : nx * ny);
+    double m = 0.0;
+    for (int64_t q = 0; q < nx * ny * nz; ++q) {
+      const int64_t ik = k == 0 ? q % nx : (k == 1 ? (q / nx) % ny : q / (nx * ny));
+      if (ik + 1 < b.dims[k]) m = std::max(m, fabs(v[q + step] - v[q]) / hk);
+    }
+    s2 += m * m;
+  }
+  return sqrt(s2);
+}
+
+template <class T>
+static void set_bg(const sph_handle* h, Geom<T>& g) {
+  g.bg_phi = h->bg_phi;
+  g.bg_s = h->bg_s;
+  for (int k = 0; k < 3; ++k) {
+    g.bg_n[k] = h->bg_n[k];
+    g.bg_lo[k] = (T)h->bg_lo[k];
+    const double hk = h->bg_n[k] > 1 ? (h->bg_hi[k] - h->bg_lo[k]) / (h->bg_n[k] - 1) : 1.0;
+    g.bg_h[k] = (T)hk;
+    g.bg_inv_h[k] = (T)(1.0 / hk);
+  }
+}
+
 // ================================================================== C ABI ==
 extern "C" {
 
 void sph_destroy(sph_handle* h);
 
 static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_field* field, int64_t n_particles,
-                              int32_t n_colors, const sph_params* params, const sph_alloc* alloc, void* stream) {
+                              int32_t n_colors, const sph_params* params, const sph_alloc* alloc, void* stream,
+                              const sph_background* bg) {
   h->dom = *dom;
   h->field = *field;
   h->par = *params;
@@ -589,9 +629,43 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   const int d = h->dim;
   const int nn = (int)n_particles;
 
+  // ---- background mesh: node arrays to the device ----
+  if (bg) {
+    h->has_bg = true;
+    const size_t nodes = (size_t)bg->dims[0] * bg->dims[1] * bg->dims[2];
+    for (int k = 0; k < 3; ++k) {
+      h->bg_n[k] = bg->dims[k];
+      h->bg_lo[k] = bg->lo[k];
+      h->bg_hi[k] = bg->hi[k];
+    }
+    for (int s = 0; s < dom->n_shapes; ++s) h->bg_grid_shape |= dom->shapes[s].kind == SPH_SHAPE_GRID;
+    if (bg->phi) {
+      double* dv;
+      SPH_TRY(grab(h, dv, nodes));
+      SPH_CUDA(h, cudaMemcpy(dv, bg->phi, nodes * sizeof(double), cudaMemcpyHostToDevice));
+      h->bg_phi = dv;
+      h->bg_lip_phi = bg_slope(*bg, d, bg->phi);
+    }
+    if (bg->spacing) {
+      double* dv;
+      SPH_TRY(grab(h, dv, nodes));
+      SPH_CUDA(h, cudaMemcpy(dv, bg->spacing, nodes * sizeof(double), cudaMemcpyHostToDevice));
+      h->bg_s = dv;
+      h->bg_lip_s = bg_slope(*bg, d, bg->spacing);
+    }
+  }
+  // |grad s| bound: the field's slope, times the background level set's
+  // gradient bound when the distance is measured to it
+  double gslope = field_slope(h->field);
+  if (h->field.kind == SPH_FIELD_BACKGROUND) gslope = h->bg_lip_s;
+  else if (h->field.kind != SPH_FIELD_UNIFORM && dom->n_shapes > 0 &&
+           dom->shapes[h->field.dist_shape].kind == SPH_SHAPE_GRID)
+    gslope *= h->bg_lip_phi;
+
   // ---- target field: total mass (Eq. total_mass_2) and the range of h ----
   Geom<double> g1;
   fill_geom<double>(h->dom, h->field, 1.0, 1.0, g1);
+  set_bg(h, g1);
   const int res = d == 2 ? 2048 : 192;
   FieldBounds fb{};
   {
@@ -611,11 +685,13 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   double diag = 0.0;
   for (int k = 0; k < d; ++k) diag += pow((h->dom.hi[k] - h->dom.lo[k]) / res, 2);
   diag = sqrt(diag);
-  h->lip_h = lipschitz_h(h->dom, h->field, hfac, fb.max_seff * (1.0 + 1e-6) + field_slope(h->field) * diag);
+  h->lip_h = lipschitz_h(h->dom, h->field, hfac, fb.max_seff * (1.0 + 1e-6) + gslope * diag, gslope);
   h->hmin = std::max(0.5 * hfac * fb.min_seff, hfac * fb.min_seff - h->lip_h * diag);
   h->hmax = hfac * fb.max_seff + h->lip_h * diag;
   fill_geom<double>(h->dom, h->field, hfac, h->rho_scale, h->geod);
   fill_geom<float>(h->dom, h->field, hfac, h->rho_scale, h->geof);
+  set_bg(h, h->geod);
+  set_bg(h, h->geof);
   fill_phys(d, h->par, h->Pf);
   fill_phys(d, h->par, h->Pd);
   {
@@ -687,12 +763,13 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   return status_from_flags(h, flags);
 }
 
-sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_particles, int32_t n_colors,
-                      const sph_params* params, const sph_alloc* alloc, void* stream, sph_handle** out) {
+static sph_status create_common(const sph_domain* dom, const sph_field* field, const sph_background* bg,
+                                int64_t n_particles, int32_t n_colors, const sph_params* params,
+                                const sph_alloc* alloc, void* stream, sph_handle** out, const char* who) {
   if (!out) return SPH_ERR_INVALID_ARG;
   *out = nullptr;
   std::string why;
-  sph_status vs = validate(dom, field, n_particles, n_colors, params, why);
+  sph_status vs = validate(dom, field, n_particles, n_colors, params, why, bg);
   if (vs == SPH_OK && n_particles > (int64_t)(1 << 24)) {
     why = "at most 2^24 particles per instance";
     vs = SPH_ERR_INVALID_ARG;
@@ -702,18 +779,30 @@ sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_p
     vs = SPH_ERR_INVALID_ARG;
   }
   if (vs != SPH_OK) {
-    fprintf(stderr, "sph_create: %s\n", why.c_str());
+    fprintf(stderr, "%s: %s\n", who, why.c_str());
     return vs;
   }
   sph_handle* h = new sph_handle();
-  sph_status s = create_impl(h, dom, field, n_particles, n_colors, params, alloc, stream);
+  sph_status s = create_impl(h, dom, field, n_particles, n_colors, params, alloc, stream, bg);
   if (s != SPH_OK) {
-    fprintf(stderr, "sph_create: %s\n", h->err.c_str());
+    fprintf(stderr, "%s: %s\n", who, h->err.c_str());
     sph_destroy(h);
     return s;
   }
   *out = h;
   return SPH_OK;
+}
+
+sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_particles, int32_t n_colors,
+                      const sph_params* params, const sph_alloc* alloc, void* stream, sph_handle** out) {
+  return create_common(dom, field, nullptr, n_particles, n_colors, params, alloc, stream, out, "sph_create");
+}
+
+sph_status sph_create_background(const sph_domain* dom, const sph_field* field, const sph_background* bg,
+                                 int64_t n_particles, int32_t n_colors, const sph_params* params,
+                                 const sph_alloc* alloc, void* stream, sph_handle** out) {
+  if (!bg) return SPH_ERR_INVALID_ARG;
+  return create_common(dom, field, bg, n_particles, n_colors, params, alloc, stream, out, "sph_create_background");
 }
 
 sph_status sph_set_state(sph_handle* h, const double* xyz, const uint8_t* col, int32_t on_device) {
@@ -1028,6 +1117,8 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   if (!h || !obj || !grad || (h->n > 0 && !dpos0)) return fail(h, SPH_ERR_INVALID_ARG, "null argument");
   if (K < 0 || obj->ckpt_every < 1) return fail(h, SPH_ERR_INVALID_ARG, "K < 0 or ckpt_every < 1");
   if (dt_in && !obj->frozen_dt) return fail(h, SPH_ERR_INVALID_ARG, "dt_in needs frozen_dt = 1");
+  if (h->bg_grid_shape)
+    return fail(h, SPH_ERR_INVALID_ARG, "the reverse pass covers analytic shapes only (no background level set)");
   memset(grad, 0, sizeof *grad);
   const size_t N = (size_t)h->n, d = (size_t)h->dim, nd = N * d;
   const int64_t t0 = h->steps;

@@ -34,6 +34,13 @@ struct Geom {
   T poly[8];
   T hfac;      // tau * rho_scale^(-1/d): h = hfac * s * (1 + P)^(-1/d)
   T rho_scale;
+  // Cartesian background mesh (Sec. 3.1, 3.2): node values (x fastest) of the
+  // level set (shapes of kind 2) and of the target spacing (field kind 3);
+  // device pointers, null when unused
+  const double* bg_phi;
+  const double* bg_s;
+  int bg_n[3];
+  T bg_lo[3], bg_h[3], bg_inv_h[3];
 };
 
 // Multi-resolution cell grid. Level l has cells of edge c0 2^l; a particle is
@@ -167,9 +174,49 @@ __device__ __forceinline__ T inv_rho_t2(T h, T inv_tau) {
 
 // ------------------------------------------------------------ geometry ----
 
-// signed distance, positive inside shape s
+// Node values v of the background mesh interpolated at x: multilinear
+// (bilinear in 2D, trilinear in 3D) in the mesh cell that holds x, x clamped
+// into the mesh box; grad (may be null) receives the interpolant's gradient.
+template <class T>
+__device__ __forceinline__ T bg_interp(const Geom<T>& g, const double* __restrict__ v, const T* x, int dim,
+                                       T* grad) {
+  int i0[3] = {0, 0, 0};
+  T f[3] = {0, 0, 0};
+  for (int k = 0; k < dim; ++k) {
+    const int n = g.bg_n[k];
+    T t = (x[k] - g.bg_lo[k]) * g.bg_inv_h[k];
+    t = t < T(0) ? T(0) : (t > T(n - 1) ? T(n - 1) : t);
+    int i = (int)dfloor(t);
+    i = i > n - 2 ? n - 2 : i;
+    i0[k] = i;
+    f[k] = t - (T)i;
+  }
+  T val = 0, gr[3] = {0, 0, 0};
+  for (int c = 0; c < (1 << dim); ++c) {
+    long long idx = 0, stride = 1;
+    T w = 1, dw[3] = {1, 1, 1};
+    for (int k = 0; k < dim; ++k) {
+      const int b = (c >> k) & 1;
+      idx += (long long)(i0[k] + b) * stride;
+      stride *= g.bg_n[k];
+      const T wk = b ? f[k] : T(1) - f[k];
+      const T dk = (b ? T(1) : T(-1)) * g.bg_inv_h[k];
+      for (int m = 0; m < dim; ++m) dw[m] *= (m == k) ? dk : wk;
+      w *= wk;
+    }
+    const T node = (T)v[idx];
+    val += w * node;
+    for (int m = 0; m < dim; ++m) gr[m] += dw[m] * node;
+  }
+  if (grad)
+    for (int k = 0; k < 3; ++k) grad[k] = k < dim ? gr[k] : T(0);
+  return val;
+}
+
+// signed distance, positive inside shape s (kind 2: the background level set)
 template <class T>
 __device__ __forceinline__ T shape_inside(const Geom<T>& g, int s, const T* x, int dim) {
+  if (g.kind[s] == 2) return bg_interp(g, g.bg_phi, x, dim, (T*)nullptr);
   if (g.kind[s] == 0) {
     T r2 = 0;
     for (int k = 0; k < dim; ++k) {
@@ -199,6 +246,20 @@ __device__ __forceinline__ T constraint_phi(const Geom<T>& g, int s, const T* x,
 template <class T>
 __device__ __forceinline__ int project_shape(const Geom<T>& g, int s, T* x, int dim) {
   if (!(constraint_phi(g, s, x, dim) < 0)) return 0;
+  if (g.kind[s] == 2) {
+    // interpolated level set: three Newton steps x <- x - phi grad / |grad|^2
+    // (the printed step when |grad phi| = 1)
+    const T sg = g.keep_inside[s] ? T(1) : T(-1);
+    for (int it = 0; it < 3; ++it) {
+      T gr[3];
+      const T v = sg * bg_interp(g, g.bg_phi, x, dim, gr);
+      T g2 = 0;
+      for (int k = 0; k < dim; ++k) g2 += gr[k] * gr[k];
+      if (!(g2 > T(0))) break;
+      for (int k = 0; k < dim; ++k) x[k] -= v * sg * gr[k] / g2;
+    }
+    return 1;
+  }
   if (g.kind[s] == 0) {
     T d[3] = {0, 0, 0}, r2 = 0;
     for (int k = 0; k < dim; ++k) {
@@ -270,10 +331,11 @@ template <> __device__ __forceinline__ float dtanh<float>(float x) { return tanh
 template <> __device__ __forceinline__ double dtanh<double>(double x) { return tanh(x); }
 
 // target spacing s(x): uniform, linear or tanh in the distance to a shape
-// (field kinds 0, 1, 2)
+// (field kinds 0, 1, 2) or sampled on the background mesh (kind 3)
 template <class T>
 __device__ __forceinline__ T spacing_of(const Geom<T>& g, const T* x) {
   if (g.field_kind == 0) return g.s0;
+  if (g.field_kind == 3) return bg_interp(g, g.bg_s, x, g.dim, (T*)nullptr);
   const T dist = fabs(shape_inside(g, g.dist_shape, x, g.dim));
   if (g.field_kind == 2) return g.a + g.b * dtanh(g.s0 * dist);
   return g.a + g.b * dist;

@@ -61,16 +61,16 @@ inline double field_slope(const sph_field& f) {
 }
 
 // Upper bound of |grad h| over the box for h = hfac s (1+P)^(-1/d):
-// |grad s| <= field_slope; |P| <= sum|c_k| = S on
+// |grad s| <= gslope (field_slope, with the background mesh's bounds); |P| <= sum|c_k| = S on
 // x~ in [-1,1]^d; |dP/dx| <= 3 sqrt(d) S * 2/min(ext) (each monomial has
 // |d/dx~| <= 3 there).
-inline double lipschitz_h(const sph_domain& dom, const sph_field& f, double hfac, double smax) {
+inline double lipschitz_h(const sph_domain& dom, const sph_field& f, double hfac, double smax, double gslope) {
   const int d = dom.dim;
   double S = 0.0;
   for (int k = 0; k < f.n_poly; ++k) S += fabs(f.poly[k]);
   double ext_min = DBL_MAX;
   for (int k = 0; k < d; ++k) ext_min = std::min(ext_min, dom.hi[k] - dom.lo[k]);
-  const double gb = field_slope(f);
+  const double gb = gslope;
   const double fmin = 1.0 - S;
   const double gradP = 3.0 * sqrt((double)d) * S * 2.0 / ext_min;
   const double L = hfac * (gb * pow(fmin, -1.0 / d) + smax / d * pow(fmin, -1.0 / d - 1.0) * gradP);
@@ -206,7 +206,7 @@ inline void make_frames(const sph_domain& dom, double kappa, double skin, const 
 }
 
 inline sph_status validate(const sph_domain* dom, const sph_field* f, int64_t n, int32_t ncol, const sph_params* p,
-                    std::string& why) {
+                    std::string& why, const sph_background* bg = nullptr) {
   if (!dom || !f || !p) { why = "null argument"; return SPH_ERR_INVALID_ARG; }
   if (dom->dim != 2 && dom->dim != 3) { why = "dim must be 2 or 3"; return SPH_ERR_INVALID_ARG; }
   if (dom->n_shapes < 0 || dom->n_shapes > kMaxShapes) { why = "n_shapes out of range"; return SPH_ERR_INVALID_ARG; }
@@ -214,7 +214,8 @@ inline sph_status validate(const sph_domain* dom, const sph_field* f, int64_t n,
     if (!(dom->hi[k] > dom->lo[k])) { why = "empty box"; return SPH_ERR_INVALID_ARG; }
   for (int s = 0; s < dom->n_shapes; ++s) {
     const sph_shape& sh = dom->shapes[s];
-    if (sh.kind != SPH_SHAPE_SPHERE && sh.kind != SPH_SHAPE_BOX) { why = "bad shape kind"; return SPH_ERR_INVALID_ARG; }
+    if (sh.kind == SPH_SHAPE_GRID && !(bg && bg->phi)) { why = "grid shape without a background level set"; return SPH_ERR_INVALID_ARG; }
+    if (sh.kind != SPH_SHAPE_SPHERE && sh.kind != SPH_SHAPE_BOX && sh.kind != SPH_SHAPE_GRID) { why = "bad shape kind"; return SPH_ERR_INVALID_ARG; }
     if (!(sh.size[0] > 0)) { why = "bad shape size"; return SPH_ERR_INVALID_ARG; }
   }
   if (n < 0 || n > (int64_t)(1u << 30)) { why = "particle count out of range"; return SPH_ERR_INVALID_ARG; }
@@ -230,7 +231,28 @@ inline sph_status validate(const sph_domain* dom, const sph_field* f, int64_t n,
       why = "tanh field needs s0 > 0 (reciprocal length)";
       return SPH_ERR_INVALID_ARG;
     }
+  } else if (f->kind == SPH_FIELD_BACKGROUND) {
+    if (!(bg && bg->spacing)) { why = "background field without background spacing"; return SPH_ERR_INVALID_ARG; }
   } else { why = "bad field kind"; return SPH_ERR_INVALID_ARG; }
+  if (bg) {
+    int64_t nodes = 1;
+    for (int k = 0; k < 3; ++k) {
+      const int need = k < dom->dim ? 2 : 1;
+      if (bg->dims[k] < need || (k >= dom->dim && bg->dims[k] != 1)) { why = "background mesh dims"; return SPH_ERR_INVALID_ARG; }
+      nodes *= bg->dims[k];
+      if (k < dom->dim && !(bg->lo[k] <= dom->lo[k] && bg->hi[k] >= dom->hi[k] && bg->hi[k] > bg->lo[k])) {
+        why = "background mesh must contain the domain box";
+        return SPH_ERR_INVALID_ARG;
+      }
+    }
+    if (nodes > (int64_t)1 << 28) { why = "background mesh too large"; return SPH_ERR_INVALID_ARG; }
+    if (bg->spacing)
+      for (int64_t q = 0; q < nodes; ++q)
+        if (!(bg->spacing[q] > 0) || !std::isfinite(bg->spacing[q])) { why = "background spacing must be > 0"; return SPH_ERR_INVALID_ARG; }
+    if (bg->phi)
+      for (int64_t q = 0; q < nodes; ++q)
+        if (!std::isfinite(bg->phi[q])) { why = "background level set must be finite"; return SPH_ERR_INVALID_ARG; }
+  }
   if (f->n_poly < 0 || f->n_poly > 8) { why = "n_poly out of range"; return SPH_ERR_INVALID_ARG; }
   double S = 0;
   for (int k = 0; k < f->n_poly; ++k) S += fabs(f->poly[k]);

@@ -130,7 +130,7 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
   }
   const double hmin = hfac * smin * std::pow(1.0 + S, -1.0 / d);
   const double hmax = hfac * smax * std::pow(1.0 - S, -1.0 / d);
-  const double lip = lipschitz_h(*dom, *field, hfac, smax);
+  const double lip = lipschitz_h(*dom, *field, hfac, smax, field_slope(*field));
   HostGrid hg;
   why = grid_setup(*dom, params->kappa, params->cell_factor, hmin, hmax, lip, hg);
   if (!why.empty()) {

@@ -32,16 +32,18 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sphmesh.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(sph_shape),sizeof(sph_domain),sizeof(sph_field),sizeof(sph_params),"
         "sizeof(sph_alloc),sizeof(sph_stats),sizeof(sph_grid_info),"
-        "offsetof(sph_params,seed),offsetof(sph_stats,rho_scale));return 0;}\n")
+        "offsetof(sph_params,seed),offsetof(sph_stats,rho_scale),"
+        "sizeof(sph_background),offsetof(sph_background,spacing));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
     want = [C.sizeof(B.sph_shape), C.sizeof(B.sph_domain), C.sizeof(B.sph_field), C.sizeof(B.sph_params),
             C.sizeof(B.sph_alloc), C.sizeof(B.sph_stats), C.sizeof(B.sph_grid_info),
-            B.sph_params.seed.offset, B.sph_stats.rho_scale.offset]
+            B.sph_params.seed.offset, B.sph_stats.rho_scale.offset,
+            C.sizeof(B.sph_background), B.sph_background.spacing.offset]
     assert got == want
 
 
@@ -78,3 +80,41 @@ def test_null_handle_calls(lib):
     assert lib.sph_sync(None) == 1
     assert lib.sph_last_error(None) == b"null handle"
     lib.sph_destroy(None)
+
+
+def _create_bg(lib, p, n=100, ncol=4):
+    from paper_1906_07925_gb300 import background_struct
+    d, f, q = problem_structs(p)
+    bg = background_struct(p.bg)
+    h = B.H()
+    st = lib.sph_create_background(C.byref(d), C.byref(f), C.byref(bg[0]), n, ncol, C.byref(q), None, None,
+                                   C.byref(h))
+    return st, h
+
+
+@pytest.mark.parametrize("mutate", [
+    lambda p: setattr(p.bg, "dims", [1, 101, 1]),                 # an axis with one node
+    lambda p: setattr(p.bg, "dims", [101, 101, 2]),               # 2D mesh with a z extent
+    lambda p: setattr(p.bg, "hi", [90.0, 100.0, 0.0]),            # mesh does not cover the box
+    lambda p: p.bg.spacing.__setitem__((3, 4, 0), 0.0),            # spacing must be > 0
+    lambda p: p.bg.phi.__setitem__((3, 4, 0), float("nan")),       # level set must be finite
+    lambda p: setattr(p.bg, "spacing", None),                     # background field without spacing
+    lambda p: setattr(p.bg, "phi", None),                         # grid shape without level set
+])
+def test_invalid_background_rejected_before_any_device_work(lib, mutate):
+    p = W.circle_2d_background(100, 4)
+    p.bg.phi = p.bg.phi.copy()
+    p.bg.spacing = p.bg.spacing.copy()
+    mutate(p)
+    if p.bg.phi is not None and p.bg.spacing is not None and p.bg.dims[0] == 1:
+        p.bg.phi = p.bg.phi[:1]
+        p.bg.spacing = p.bg.spacing[:1]
+    st, h = _create_bg(lib, p)
+    assert st == 1 and not h.value
+
+
+def test_grid_shape_needs_a_background_mesh(lib):
+    p = W.circle_2d_background(100, 4)
+    p.field_kind, p.s0 = W.FIELD_UNIFORM, 1.0
+    st, h = _create(lib, p)
+    assert st == 1 and not h.value

@@ -26,6 +26,13 @@ def circle_state(n=4289, seed=1, ncol=6):
     return p, pos, col
 
 
+def circle_bg_state(n=4289, seed=1, ncol=6):
+    """The circle case given on a 101 x 101 background mesh (Sec. 3.1, 3.2)."""
+    p = W.circle_2d_background(n, ncol)
+    pos, col, _ = W.sample_density(p, n, seed)
+    return p, pos, col
+
+
 def graded2d_state(n=20000, seed=1, ncol=16):
     p = W.graded_hole_2d(n, ncol)
     pos, col, _ = W.sample_density(p, n, seed)
@@ -40,10 +47,11 @@ def graded3d_state(n=30000, seed=2, ncol=32):
 
 # ------------------------------------------------------------ neighbours ----
 
-@pytest.mark.parametrize("case", ["c1", "g2", "g3", "circle"])
+@pytest.mark.parametrize("case", ["c1", "g2", "g3", "circle", "circle_bg"])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_neighbor_sets_match_oracle(case, precision):
-    p, pos, col = {"c1": c1_state, "g2": graded2d_state, "g3": graded3d_state, "circle": circle_state}[case]()
+    p, pos, col = {"c1": c1_state, "g2": graded2d_state, "g3": graded3d_state, "circle": circle_state,
+                   "circle_bg": circle_bg_state}[case]()
     r = make_gpu(p, pos, col, precision)
     got = r.neighbor_sets()
     want = oracle.neighbor_sets(p, pos, 1)
@@ -219,6 +227,47 @@ def test_circle_relaxed_quality_matches_oracle():
     assert abs(qg["n_tri"] - qo["n_tri"]) <= 0.01 * qo["n_tri"]
     assert qg["n_eg"] / qg["n_et"] == pytest.approx(qo["n_eg"] / qo["n_et"], rel=0.25)
     assert abs(qg["n_lt30"] - qo["n_lt30"]) <= 0.5 * qo["n_lt30"] + 10
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_step_parity_background_mesh(precision):
+    """Level set and target spacing interpolated from a background mesh, a
+    few particles projected back onto the interpolated level set."""
+    p, pos, col = circle_bg_state()
+    pos = pos.copy()
+    pos[:5] = [[50.0, 93.4], [93.5, 50.0], [50.0, 6.8], [19.4, 19.4], [80.6, 80.6]]  # just outside the circle
+    compare_step(p, pos, col, precision)
+
+
+def test_background_mesh_relaxed_quality_matches_oracle():
+    """The background-mesh circle relaxed for 1,500 steps (ramp over steps
+    800-1,000) on the GPU and in the oracle: the same mesh statistics, and
+    every particle inside the interpolated level set."""
+    import mesh_quality as MQ
+    p, pos, col = circle_bg_state()
+    p.t0, p.t1 = 800, 1000
+    r = make_gpu(p, pos, col, "fp32", use_graph=True)
+    r.ramp_surface_tension(800, 1000)
+    r.step(1500)
+    xg = r.positions()
+    qg = MQ.quality(xg, r.colors(), max_edge_factor=None, drop_hull=False)
+    r.close()
+    xo, _ = oracle.run(p, pos, col, 1500)
+    qo = MQ.quality(xo, col, max_edge_factor=None, drop_hull=False)
+    assert qg["G_avg"] == pytest.approx(qo["G_avg"], abs=0.01)
+    assert qg["theta_min_mean"] == pytest.approx(qo["theta_min_mean"], abs=1.0)
+    assert abs(qg["n_tri"] - qo["n_tri"]) <= 0.01 * qo["n_tri"]
+    assert qg["n_eg"] / qg["n_et"] == pytest.approx(qo["n_eg"] / qo["n_et"], rel=0.25)
+    assert min(oracle.phi(p, x) for x in xg) > -1e-4
+
+
+def test_backward_refuses_background_level_set():
+    from paper_1906_07925_gb300 import SphError
+    p, pos, col = circle_bg_state()
+    r = make_gpu(p, pos, col, "fp32")
+    with pytest.raises(SphError):
+        r.backward(2, lam=1.0)
+    r.close()
 
 
 def test_circle_paper_schedule():
