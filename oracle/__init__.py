@@ -54,7 +54,8 @@ class Problem(C.Structure):
                 ("tau", C.c_double), ("kappa", C.c_double),
                 ("t0", C.c_double), ("t1", C.c_double),
                 ("bg_dims", C.c_int32 * 3), ("bg_pad", C.c_int32), ("bg_lo", C.c_double * 3),
-                ("bg_hi", C.c_double * 3), ("bg_phi", C.c_void_p), ("bg_s", C.c_void_p)]
+                ("bg_hi", C.c_double * 3), ("bg_phi", C.c_void_p), ("bg_s", C.c_void_p),
+                ("surface", C.c_void_p)]
 
 
 class StepInfo(C.Structure):
@@ -142,9 +143,14 @@ def to_c(p) -> Problem:
     c.rho_scale = p.rho_scale
     c.P0, c.gamma, c.sigma0, c.tau, c.kappa = p.P0, p.gamma, p.sigma0, p.tau, p.kappa
     c.t0, c.t1 = p.t0, p.t1
+    keep = []
+    surf = getattr(p, "surface", None)
+    if surf is not None:
+        a = np.ascontiguousarray(np.asarray(surf, dtype=bool).astype(np.uint8))
+        keep.append(a)
+        c.surface = a.ctypes.data
     bg = getattr(p, "bg", None)
     if bg is not None:
-        keep = []
         for k in range(3):
             c.bg_dims[k] = int(bg.dims[k])
             c.bg_lo[k] = float(bg.lo[k])
@@ -155,7 +161,7 @@ def to_c(p) -> Problem:
                 a = np.ascontiguousarray(v, dtype=np.float64).ravel(order="F")
                 keep.append(a)
                 setattr(c, "bg_phi" if name == "phi" else "bg_s", a.ctypes.data)
-        c._keep = keep  # the node arrays live as long as the struct
+    c._keep = keep  # the arrays live as long as the struct
     return c
 
 

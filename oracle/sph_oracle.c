@@ -193,6 +193,77 @@ static int project_one(const orc_problem* p, const orc_shape* s, double* x, int 
   return 1;
 }
 
+/* Feature-surface particles (Sec. 3.5). Reading: a surface particle belongs to
+ * the constraint surface nearest to it (the constraint value of smallest
+ * magnitude, the bounding box first on ties); N is that constraint's unit
+ * normal (the gradient of its signed distance, pointing into the region). */
+static const orc_shape* nearest_constraint(const orc_problem* p, const double* x, orc_shape* box, double* phi) {
+  *box = box_shape(p);
+  const orc_shape* best = box;
+  double bv = constraint_phi(p, box, x, p->dim);
+  for (int s = 0; s < p->n_shapes; ++s) {
+    double v = constraint_phi(p, &p->shapes[s], x, p->dim);
+    if (fabs(v) < fabs(bv)) { bv = v; best = &p->shapes[s]; }
+  }
+  *phi = bv;
+  return best;
+}
+
+static void inside_distance_grad(const orc_problem* p, const orc_shape* s, const double* x, int dim, double* g);
+
+/* gradient of a constraint's value (the signed distance with the region positive) */
+static void constraint_grad(const orc_problem* p, const orc_shape* s, const double* x, int dim, double* g) {
+  inside_distance_grad(p, s, x, dim, g);
+  if (!s->keep_inside)
+    for (int k = 0; k < 3; ++k) g[k] = -g[k];
+}
+
+/* unit normal N(r_i) of the surface a feature-surface particle belongs to;
+ * zero where the gradient vanishes */
+static void surface_normal(const orc_problem* p, const double* x, double* N) {
+  orc_shape box;
+  double phi;
+  const orc_shape* s = nearest_constraint(p, x, &box, &phi);
+  constraint_grad(p, s, x, p->dim, N);
+  double n2 = 0.0;
+  for (int k = 0; k < p->dim; ++k) n2 += N[k] * N[k];
+  double inv = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+  for (int k = 0; k < 3; ++k) N[k] *= inv;
+}
+
+/* Eq. force_surface: drop the normal component, F <- F - (N . F) N */
+static void tangential(const double* N, double* F, int dim) {
+  double dn = 0.0;
+  for (int k = 0; k < dim; ++k) dn += N[k] * F[k];
+  for (int k = 0; k < dim; ++k) F[k] -= dn * N[k];
+}
+
+/* Eq. displacement_surface for a feature-surface particle, applied after every
+ * drift whatever the sign of phi: r <- r - phi N onto the nearest constraint
+ * surface (the closest point for the exact distance functions of the sphere
+ * and the box; three Newton steps for the background level set). */
+static void project_to_surface(const orc_problem* p, double* x) {
+  orc_shape box;
+  double phi;
+  const orc_shape* s = nearest_constraint(p, x, &box, &phi);
+  int d = p->dim;
+  if (s->kind == ORC_GRID) {
+    double sg = s->keep_inside ? 1.0 : -1.0;
+    for (int it = 0; it < 3; ++it) {
+      double g[3];
+      double v = sg * bg_interp(p, p->bg_phi, x, g);
+      double g2 = 0.0;
+      for (int k = 0; k < d; ++k) g2 += g[k] * g[k];
+      if (!(g2 > 0.0)) break;
+      for (int k = 0; k < d; ++k) x[k] -= v * sg * g[k] / g2;
+    }
+    return;
+  }
+  double g[3];
+  constraint_grad(p, s, x, d, g);
+  for (int k = 0; k < d; ++k) x[k] -= phi * g[k];
+}
+
 int orc_project(const orc_problem* p, double* x) {
   orc_shape b = box_shape(p);
   int moved = project_one(p, &b, x, p->dim);
@@ -540,8 +611,10 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
 #pragma omp parallel for schedule(static) reduction(+ : ipairs, fpairs)
   for (int64_t i = 0; i < n; ++i) {
     double ai[3] = {0, 0, 0}, sabs = 0.0;
+    const int surf_i = p->surface && p->surface[i];
     for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
       int64_t j = S.flist[t];
+      if (surf_i && !p->surface[j]) continue; /* Sec. 3.5: normal particles do not act on surface ones */
       double r = sqrt(dist2(pos + i * d, pos + j * d, d));
       double hij = 0.5 * (h[i] + h[j]);
       double dw = orc_dW(r, kappa * hij, d);
@@ -551,6 +624,11 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
       sabs += fabs(coef * dw);
       fpairs += 1;
       ipairs += (col[i] != col[j]);
+    }
+    if (surf_i) {
+      double N[3];
+      surface_normal(p, pos + i * d, N);
+      tangential(N, ai, d);
     }
     for (int k = 0; k < d; ++k) a[i * d + k] = ai[k];
     if (pair_abs_a) pair_abs_a[i] = sabs;
@@ -606,8 +684,10 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double s[3] = {0, 0, 0}, sabs = 0.0;
+    const int surf_i = p->surface && p->surface[i];
     for (int64_t t = S.fstart[i]; t < S.fstart[i + 1]; ++t) {
       int64_t j = S.flist[t];
+      if (surf_i && !p->surface[j]) continue;
       double r = sqrt(dist2(pos + i * d, pos + j * d, d));
       double hij = 0.5 * (h[i] + h[j]);
       double dw = orc_dW(r, kappa * hij, d);
@@ -624,6 +704,11 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
       /* normaliser: magnitudes of the two velocity terms of the pair */
       sabs += fabs(coef) * (sqrt(vi2) + sqrt(vj2));
     }
+    if (surf_i) {
+      double N[3];
+      surface_normal(p, pos + i * d, N);
+      tangential(N, s, d);
+    }
     for (int k = 0; k < d; ++k) at[i * d + k] = s[k];
     if (pair_abs_b) pair_abs_b[i] = sabs;
   }
@@ -635,7 +720,8 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
       double v = vt[i * d + k] + 0.5 * at[i * d + k] * dt2;
       pos[i * d + k] += v * dt2;
     }
-    moved += orc_project(p, pos + i * d);
+    if (p->surface && p->surface[i]) project_to_surface(p, pos + i * d);
+    else moved += orc_project(p, pos + i * d);
   }
 
   /* diagnostics */
@@ -1157,6 +1243,7 @@ int orc_backward(const orc_problem* p, int64_t n, const double* pos0, const uint
   /* the reverse pass covers analytic shapes only (no background-mesh level set) */
   for (int s = 0; s < p->n_shapes; ++s)
     if (p->shapes[s].kind == ORC_GRID) return -1;
+  if (p->surface) return -1; /* nor feature-surface particles */
   size_t nd = (size_t)n * (size_t)d;
   double* traj = (double*)malloc(sizeof(double) * nd * (size_t)(K + 1));
   if (!traj) return -1;

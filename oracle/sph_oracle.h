@@ -60,6 +60,9 @@ typedef struct {
   double bg_lo[3], bg_hi[3];
   const double* bg_phi;
   const double* bg_s;
+  /* feature-surface particles (Sec. 3.5): surface[i] != 0 marks particle i
+   * (index order of the positions passed to a step); NULL: none */
+  const uint8_t* surface;
 } orc_problem;
 
 typedef struct {

@@ -543,3 +543,46 @@ def test_background_level_set_is_not_differentiated():
     pos, col, _ = W.sample_density(p, 300, 1)
     with pytest.raises(RuntimeError):
         oracle.backward(p, pos, col, 1, 1.0)
+
+
+# -------------------------------------------- feature-surface particles (Sec. 3.5) ----
+
+def test_surface_particles_move_along_the_surface():
+    """Feature-surface particles on the circle: their forces have no normal
+    component (Eq. force_surface: N the radial unit vector), they are
+    projected back onto the circle after every drift (Eq.
+    displacement_surface) and so stay on it over many steps."""
+    import oracle
+    p, pos, col = W.circle_with_surface(1500, 4)
+    s = p.surface
+    _, _, f = oracle.step(p, pos, col, 0)
+    N = (pos[s] - 50.0) / np.linalg.norm(pos[s] - 50.0, axis=1)[:, None]
+    for key in ("acc", "visc"):
+        normal = np.abs((f[key][s] * N).sum(axis=1))
+        assert normal.max() <= 1e-12 * np.abs(f[key][s]).max(), key
+    assert np.abs(f["acc"][s]).max() > 0
+    x, _ = oracle.run(p, pos, col, 30)
+    assert np.abs(np.linalg.norm(x[s] - 50.0, axis=1) - 43.0).max() < 1e-10
+    moved = np.linalg.norm(x[s] - pos[s], axis=1)
+    assert moved.max() > 1e-3  # they do move, along the circle
+
+
+def test_normal_particles_do_not_act_on_surface_particles():
+    """Removing every normal particle leaves the forces on the surface
+    particles bit for bit unchanged (their sums only see surface particles),
+    while normal particles next to the wall do feel the surface particles."""
+    import oracle
+    p, pos, col = W.circle_with_surface(1500, 4)
+    s = p.surface
+    ns = int(s.sum())
+    _, _, f = oracle.step(p, pos, col, 0)
+    q = p.copy(surface=s[:ns])
+    _, _, fs = oracle.step(q, pos[:ns], col[:ns], 0)
+    assert np.array_equal(f["acc"][:ns], fs["acc"])
+    # without the surface particles, near-wall normal particles feel a different force
+    q2 = p.copy(surface=None)
+    _, _, fn = oracle.step(q2, pos[ns:], col[ns:], 0)
+    r = np.linalg.norm(pos[ns:] - 50.0, axis=1)
+    near = r > 43.0 - 1.0
+    assert near.any()
+    assert np.abs(fn["acc"][near] - f["acc"][ns:][near]).max() > 1e-3 * np.abs(f["acc"][ns:][near]).max()

@@ -112,6 +112,7 @@ class Problem:
     t1: float = -1.0
     eos_general: bool = False  # use p/rho^2 even at gamma = 2 (identity checks)
     bg: Optional[Background] = None  # background mesh for GRID shapes / FIELD_BACKGROUND
+    surface: Optional[np.ndarray] = None  # per particle: feature-surface particle (Sec. 3.5)
 
     def copy(self, **kw) -> "Problem":
         return dataclasses.replace(self, **kw)
@@ -345,6 +346,27 @@ def circle_2d(n: int = 4289, n_colors: int = 6, h_min: float = 0.391, h_max: flo
                 dist_shape=0, n_colors=n_colors)
     p.rho_scale = rho_scale if rho_scale is not None else rho_scale_for(p, n)
     return p
+
+
+def circle_with_surface(n_volume: int = 4289, n_colors: int = 6, seed: int = 1, h_min: float = 0.391,
+                        h_max: float = 3.125):
+    """The circle case with feature-surface particles (Sec. 3.5): n_surface
+    particles evenly spaced (with a small jitter) on the circle at the target
+    spacing there, then n_volume density-proportional particles inside.
+    Returns (problem with .surface set, positions, colours); surface particles
+    come first and take the colour of the nearest volume generator."""
+    p = circle_2d(n_volume, n_colors, h_min=h_min, h_max=h_max)
+    vol, col, gens = sample_density(p, n_volume, seed)
+    spacing = h_min * p.rho_scale ** -0.5  # target spacing on the circle (s = h_min there)
+    n_surface = int(round(2 * math.pi * 43.0 / spacing))
+    rng = np.random.default_rng(seed + 7)
+    ang = (np.arange(n_surface) + rng.uniform(-0.2, 0.2, n_surface)) * (2 * math.pi / n_surface)
+    ring = np.stack([50.0 + 43.0 * np.cos(ang), 50.0 + 43.0 * np.sin(ang)], axis=1)
+    pos = np.concatenate([ring, vol])
+    colors = np.concatenate([nearest_color(ring, gens), col]).astype(np.uint8)
+    surface = np.zeros(len(pos), dtype=bool)
+    surface[:n_surface] = True
+    return p.copy(surface=surface), pos, colors
 
 
 def circle_2d_background(n: int = 4289, n_colors: int = 6, h_min: float = 0.391, h_max: float = 3.125,
