@@ -166,6 +166,22 @@ sph_status sph_create(const sph_domain* dom, const sph_field* field, int64_t n_p
                       int32_t n_colors, const sph_params* params, const sph_alloc* alloc,
                       void* stream, sph_handle** out);
 
+/* Feature-surface particles (Sec. 3.5): flags[id] != 0 (host, n bytes, by
+ * particle id; NULL clears every flag) marks particle id as a surface
+ * particle. A surface particle takes forces (pressure, surface tension,
+ * viscous) from other surface particles only, drops their component along the
+ * surface normal N (Eq. force_surface), and after every drift is moved onto the
+ * surface it belongs to, r <- r - phi N (Eq. displacement_surface). Reading:
+ * it belongs to the nearest constraint surface (the constraint value of
+ * smallest magnitude, the bounding box first on ties) and N is that
+ * constraint's unit normal into the region; the position is kept in the
+ * bounding box first. Normal particles treat surface particles as ordinary
+ * neighbours. sph_set_state and sph_load clear the flags; sph_backward refuses
+ * a handle with flagged particles (INVALID_ARG). With rho_scale = 0 the field
+ * is normalised to all n particles: pass rho_scale for the volume particles
+ * alone (the paper's M_v) when using surface particles. Synchronises. */
+sph_status sph_set_surface(sph_handle* h, const uint8_t* flags);
+
 /* Cartesian background mesh (Sec. 3.1: the level set is discretised on a
  * Cartesian background mesh; Sec. 3.2: the target information is computed on
  * it and interpolated at the particle positions). Node (i, j, k) sits at

@@ -191,6 +191,16 @@ class Relaxation:
         self._check(self.lib.sph_step_profiled(self.h, int(n), ms))
         return tuple(float(v) for v in ms)
 
+    def set_surface(self, flags):
+        """Mark feature-surface particles (bool per particle id; None clears)."""
+        import numpy as np
+        if flags is None:
+            self._check(self.lib.sph_set_surface(self.h, None))
+            return
+        f = np.ascontiguousarray(np.asarray(flags, dtype=bool).astype(np.uint8))
+        assert f.shape == (self.n,)
+        self._check(self.lib.sph_set_surface(self.h, f.ctypes.data))
+
     def ramp_surface_tension(self, t0, t1):
         self._check(self.lib.sph_ramp_surface_tension(self.h, int(t0), int(t1)))
 

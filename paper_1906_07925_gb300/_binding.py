@@ -116,6 +116,7 @@ def load():
         sig = {
             "sph_create": [P(sph_domain), P(sph_field), C.c_int64, C.c_int32, P(sph_params), P(sph_alloc),
                            C.c_void_p, P(H)],
+            "sph_set_surface": [H, C.c_void_p],
             "sph_create_background": [P(sph_domain), P(sph_field), P(sph_background), C.c_int64, C.c_int32,
                                       P(sph_params), P(sph_alloc), C.c_void_p, P(H)],
             "sph_set_state": [H, C.c_void_p, C.c_void_p, C.c_int32],

@@ -31,6 +31,7 @@ struct sph_handle {
   // background mesh (sph_create_background): device node arrays, the mesh box
   // and the interpolants' gradient bounds
   bool has_bg = false, bg_grid_shape = false;
+  bool has_surface = false;  // feature-surface particles flagged (sph_set_surface)
   const double* bg_phi = nullptr;
   const double* bg_s = nullptr;
   int bg_n[3] = {1, 1, 1};
@@ -172,6 +173,7 @@ sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEve
   f.dt_fix = dt_fix;
   f.dt_rec = dt_rec;
   const bool f64 = h->prec == SPH_PREC_FP64;
+  f.geo = f64 ? (const void*)&h->geod : (const void*)&h->geof;
   cudaError_t e = cudaSuccess;
   if (ev) e = cudaEventRecord(ev[0], h->stream);
   if (e == cudaSuccess) e = launch_gate(S, force_rebuild, h->stream);
@@ -222,6 +224,7 @@ sph_status launch_evaluate(sph_handle* h, int nbr_debug) {
   f.nbr_debug = nbr_debug;
   f.advance = 0;
   const bool f64 = h->prec == SPH_PREC_FP64;
+  f.geo = f64 ? (const void*)&h->geod : (const void*)&h->geof;
   cudaError_t e = launch_gate(S, 1, h->stream);
   if (e == cudaSuccess) {
     if (h->dim == 2)
@@ -310,6 +313,7 @@ sph_status read_flags(sph_handle* h, int* flags) {
 
 sph_status do_set_state(sph_handle* h, const double* xyz_dev, const uint8_t* col_dev) {
   DevState& S = h->S;
+  h->has_surface = false;  // the meta words are rewritten from the colours
   cudaError_t e;
   const bool f64 = h->prec == SPH_PREC_FP64;
   if (h->dim == 2)
@@ -824,6 +828,23 @@ sph_status sph_set_state(sph_handle* h, const double* xyz, const uint8_t* col, i
   return status_from_flags(h, flags);
 }
 
+sph_status sph_set_surface(sph_handle* h, const uint8_t* flags) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  const size_t N = (size_t)h->n;
+  bool any = false;
+  if (flags)
+    for (size_t q = 0; q < N && !any; ++q) any = flags[q] != 0;
+  if (N > 0) {
+    Temp tf(h, any ? N : 1);
+    if (!tf.p) return fail(h, SPH_ERR_OOM, "scratch allocation failed");
+    if (any) SPH_CUDA(h, cudaMemcpyAsync(tf.p, flags, N, cudaMemcpyHostToDevice, h->stream));
+    SPH_CUDA(h, launch_set_surface(h->S, any ? (const uint8_t*)tf.p : nullptr, h->stream));
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  h->has_surface = any;
+  return SPH_OK;
+}
+
 sph_status sph_step(sph_handle* h, int32_t n_steps) {
   if (!h || n_steps < 0) return fail(h, SPH_ERR_INVALID_ARG, "bad step count");
   if (h->n == 0 || n_steps == 0) {
@@ -1119,6 +1140,8 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   if (dt_in && !obj->frozen_dt) return fail(h, SPH_ERR_INVALID_ARG, "dt_in needs frozen_dt = 1");
   if (h->bg_grid_shape)
     return fail(h, SPH_ERR_INVALID_ARG, "the reverse pass covers analytic shapes only (no background level set)");
+  if (h->has_surface)
+    return fail(h, SPH_ERR_INVALID_ARG, "the reverse pass covers normal particles only (no feature-surface particles)");
   memset(grad, 0, sizeof *grad);
   const size_t N = (size_t)h->n, d = (size_t)h->dim, nd = N * d;
   const int64_t t0 = h->steps;

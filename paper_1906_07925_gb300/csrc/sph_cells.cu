@@ -195,6 +195,20 @@ __global__ void __launch_bounds__(256) k_stable_gather(
   (nb ? p1 : p0)[d] = (nb ? p0 : p1)[i];
 }
 
+// feature-surface flags by particle id into the current meta words (colours kept)
+__global__ void __launch_bounds__(256) k_set_surface(int n, const StepCtl* __restrict__ ctl,
+                                                     const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
+                                                     uint32_t* __restrict__ m0, uint32_t* __restrict__ m1,
+                                                     const uint8_t* __restrict__ flags) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int buf = ctl->buf;
+  uint32_t* __restrict__ m = buf ? m1 : m0;
+  const uint32_t id = (buf ? p1 : p0)[i];
+  const uint32_t v = m[i] & ~kSurfaceBit;
+  m[i] = (flags && flags[id]) ? (v | kSurfaceBit) : v;
+}
+
 __global__ void __launch_bounds__(256) k_get_colors(int n, const StepCtl* __restrict__ ctl,
                                                     const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
                                                     const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
@@ -218,6 +232,12 @@ cudaError_t launch_write_ctl(const DevState& S, const StepCtl& v, cudaStream_t s
 
 cudaError_t launch_request_rebuild(const DevState& S, cudaStream_t st) {
   k_request_rebuild<<<1, 1, 0, st>>>(S.ctl);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_surface(const DevState& S, const uint8_t* flags, cudaStream_t st) {
+  if (S.n > 0)
+    k_set_surface<<<(S.n + 255) / 256, 256, 0, st>>>(S.n, S.ctl, S.pid[0], S.pid[1], S.meta[0], S.meta[1], flags);
   return cudaGetLastError();
 }
 

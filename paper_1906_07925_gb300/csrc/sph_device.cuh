@@ -293,6 +293,122 @@ __device__ __forceinline__ int project_shape(const Geom<T>& g, int s, T* x, int 
   return 1;
 }
 
+// ------------------------------------------- feature-surface particles ----
+// Sec. 3.5: a feature-surface particle belongs to the constraint surface
+// nearest to it (constraint value of smallest magnitude, the bounding box
+// first on ties); N is that constraint's unit normal, the gradient of its
+// signed distance (pointing into the region).
+constexpr uint32_t kSurfaceBit = 0x100u;  // in the particle's meta word, above its colour
+
+// signed distance inside the bounding box and its gradient
+template <class T>
+__device__ __forceinline__ T box_inside(const Geom<T>& g, const T* x, int dim, T* gr) {
+  T q[3] = {0, 0, 0}, out2 = 0, qmax = T(-1e30);
+  int kmax = 0;
+  for (int k = 0; k < dim; ++k) {
+    const T c = T(0.5) * (g.lo[k] + g.hi[k]);
+    q[k] = fabs(x[k] - c) - T(0.5) * (g.hi[k] - g.lo[k]);
+    if (q[k] > 0) out2 += q[k] * q[k];
+    if (q[k] > qmax) { qmax = q[k]; kmax = k; }
+  }
+  for (int k = 0; k < 3; ++k) gr[k] = T(0);
+  const T o = dsqrt(out2);
+  if (out2 > 0) {
+    for (int k = 0; k < dim; ++k)
+      if (q[k] > 0) gr[k] = -q[k] * (x[k] >= T(0.5) * (g.lo[k] + g.hi[k]) ? T(1) : T(-1)) / o;
+  } else if (qmax < 0) {
+    gr[kmax] = -(x[kmax] >= T(0.5) * (g.lo[kmax] + g.hi[kmax]) ? T(1) : T(-1));
+  }
+  return -(o + (qmax < 0 ? qmax : T(0)));
+}
+
+// gradient of shape s's signed inside distance (the branch the value takes)
+template <class T>
+__device__ __forceinline__ void shape_grad(const Geom<T>& g, int s, const T* x, int dim, T* gr) {
+  for (int k = 0; k < 3; ++k) gr[k] = T(0);
+  if (g.kind[s] == 2) {
+    bg_interp(g, g.bg_phi, x, dim, gr);
+    return;
+  }
+  if (g.kind[s] == 0) {
+    T r2 = 0;
+    for (int k = 0; k < dim; ++k) r2 += (x[k] - g.center[s][k]) * (x[k] - g.center[s][k]);
+    const T r = dsqrt(r2);
+    if (r > 0)
+      for (int k = 0; k < dim; ++k) gr[k] = -(x[k] - g.center[s][k]) / r;
+    return;
+  }
+  T q[3] = {0, 0, 0}, out2 = 0, qmax = T(-1e30);
+  int kmax = 0;
+  for (int k = 0; k < dim; ++k) {
+    q[k] = fabs(x[k] - g.center[s][k]) - g.size[s][k];
+    if (q[k] > 0) out2 += q[k] * q[k];
+    if (q[k] > qmax) { qmax = q[k]; kmax = k; }
+  }
+  if (out2 > 0) {
+    const T o = dsqrt(out2);
+    for (int k = 0; k < dim; ++k)
+      if (q[k] > 0) gr[k] = -q[k] * (x[k] >= g.center[s][k] ? T(1) : T(-1)) / o;
+  } else if (qmax < 0) {
+    gr[kmax] = -(x[kmax] >= g.center[s][kmax] ? T(1) : T(-1));
+  }
+}
+
+// the nearest constraint at x: its value phi and gradient (region positive);
+// returns -1 for the bounding box, else the shape index
+template <class T>
+__device__ __forceinline__ int nearest_constraint(const Geom<T>& g, const T* x, int dim, T& phi, T* gr) {
+  phi = box_inside(g, x, dim, gr);
+  int best = -1;
+  for (int s = 0; s < g.n_shapes; ++s) {
+    const T v = constraint_phi(g, s, x, dim);
+    if (fabs(v) < fabs(phi)) {
+      phi = v;
+      best = s;
+    }
+  }
+  if (best >= 0) {
+    shape_grad(g, best, x, dim, gr);
+    if (!g.keep_inside[best])
+      for (int k = 0; k < 3; ++k) gr[k] = -gr[k];
+  }
+  return best;
+}
+
+// unit normal N(x) of the surface a feature-surface particle belongs to
+template <class T>
+__device__ __forceinline__ void surface_normal(const Geom<T>& g, const T* x, int dim, T* N) {
+  T phi;
+  nearest_constraint(g, x, dim, phi, N);
+  T n2 = 0;
+  for (int k = 0; k < dim; ++k) n2 += N[k] * N[k];
+  const T inv = n2 > T(0) ? T(1) / dsqrt(n2) : T(0);
+  for (int k = 0; k < 3; ++k) N[k] *= inv;
+}
+
+// Eq. displacement_surface for a feature-surface particle, after every drift:
+// r <- r - phi N onto the nearest constraint surface (the closest point for
+// the sphere's and the box's exact distances; three Newton steps for the
+// background level set)
+template <class T>
+__device__ __forceinline__ void project_to_surface(const Geom<T>& g, T* x, int dim) {
+  T phi, gr[3];
+  const int s = nearest_constraint(g, x, dim, phi, gr);
+  if (s >= 0 && g.kind[s] == 2) {
+    const T sg = g.keep_inside[s] ? T(1) : T(-1);
+    for (int it = 0; it < 3; ++it) {
+      T gg[3];
+      const T v = sg * bg_interp(g, g.bg_phi, x, dim, gg);
+      T g2 = 0;
+      for (int k = 0; k < dim; ++k) g2 += gg[k] * gg[k];
+      if (!(g2 > T(0))) break;
+      for (int k = 0; k < dim; ++k) x[k] -= v * sg * gg[k] / g2;
+    }
+    return;
+  }
+  for (int k = 0; k < dim; ++k) x[k] -= phi * gr[k];
+}
+
 // inside the region (box and every shape constraint)?
 template <class T>
 __device__ __forceinline__ bool in_region(const Geom<T>& g, const T* x) {

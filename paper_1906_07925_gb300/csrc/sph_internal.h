@@ -55,6 +55,7 @@ cudaError_t launch_write_ctl(const DevState& S, const StepCtl& v, cudaStream_t s
 // cell list of the old order -> gather into the new order (predicated on ctl->rebuild)
 cudaError_t build_cells(const DevState& S, cudaStream_t st);
 // colours by particle id
+cudaError_t launch_set_surface(const DevState& S, const uint8_t* flags, cudaStream_t st);
 cudaError_t launch_get_colors(const DevState& S, uint8_t* out, cudaStream_t st);
 
 struct PassFlags {
@@ -65,6 +66,7 @@ struct PassFlags {
   int move = 1;         // pass B: integrate (0: only a~, for the reverse pass)
   const double* dt_fix = nullptr;  // pass A: prescribed {dt1, dt2} (device)
   double* dt_rec = nullptr;        // pass A: record {dt1, dt2} (device)
+  const void* geo = nullptr;       // pass A: the Geom<T> of the handle (feature-surface normals)
 };
 
 template <int D, class T>

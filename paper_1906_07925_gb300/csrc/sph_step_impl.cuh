@@ -481,7 +481,8 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
                                                 int* __restrict__ err, int advance, int* __restrict__ dbg_count,
                                                 long long* __restrict__ dbg_sum, uint32_t* __restrict__ plist,
                                                 uint32_t* __restrict__ pcount, const double* __restrict__ dt_fix,
-                                                double* __restrict__ dt_rec) {
+                                                double* __restrict__ dt_rec, const LL4* __restrict__ X0,
+                                                const LL4* __restrict__ X1, Geom<T> geo) {
   using VT = typename ViewOf<T>::type;
   __shared__ Partial sm[8];
   __shared__ bool last;
@@ -495,7 +496,11 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
   if (i < n) {
     const uint32_t* __restrict__ pid = buf ? p1 : p0;
     const VT vi = view[i];
-    const uint32_t ci = (buf ? m1 : m0)[i] & 0xFFu;
+    const uint32_t* __restrict__ meta = buf ? m1 : m0;
+    const uint32_t mi = meta[i];
+    const uint32_t ci = mi & 0xFFu;
+    // a feature-surface particle (Sec. 3.5) takes forces from surface particles only
+    const bool surf = (mi & kSurfaceBit) != 0;
     const T hv = view_h(vi);
     const T qv = F.qv;
     const T Hd = P.kappa * hv, Hd2 = Hd * Hd, invHd = T(1) / Hd;
@@ -530,7 +535,7 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
           r2 = dx * dx + dy * dy + dz * dz;
         }
         const bool inD = !GENERAL && r2 < Hd2;
-        const bool inF = r2 < Hf * Hf && j != i;
+        const bool inF = r2 < Hf * Hf && j != i && (!surf || (meta[j] & kSurfaceBit));
         if (!(inD || inF)) return;
         const T r = r2 > T(0) ? pair_r<T>(r2) : T(0);
         if (inD) {
@@ -574,6 +579,15 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
     ax *= k20;
     ay *= k20;
     az *= k20;
+    if (surf) {  // Eq. force_surface: the normal component is dropped
+      T xa[3], N[3];
+      abs_pos<D, T>(F, (buf ? X1 : X0)[i], xa);
+      surface_normal(geo, xa, D, N);
+      const T dn = ax * N[0] + ay * N[1] + az * N[2];
+      ax -= dn * N[0];
+      ay -= dn * N[1];
+      az -= dn * N[2];
+    }
     const T an = dsqrt(ax * ax + ay * ay + az * az);
     const T rt = T(1) / dsqrt(qi);
     const T rc = Hphys;
@@ -709,7 +723,8 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
                                                 const V4<T>* __restrict__ acc, Frame<T> F, Phys<T> P, Geom<T> geo,
                                                 const Scalars* __restrict__ scal, V4<T>* __restrict__ visc_out,
                                                 int* __restrict__ err, unsigned long long* __restrict__ wall_moved,
-                                                int move) {
+                                                int move, const uint32_t* __restrict__ m0,
+                                                const uint32_t* __restrict__ m1) {
   using VT = typename ViewOf<T>::type;
   __shared__ int moved_sm[8];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -755,6 +770,16 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
     bx *= km;
     by *= km;
     bz *= km;
+    const bool surf = ((buf ? m1 : m0)[i] & kSurfaceBit) != 0;
+    if (surf) {  // Eq. force_surface for the viscous force too
+      T xs[3], N[3];
+      abs_pos<D, T>(F, (buf ? X1 : X0)[i], xs);
+      surface_normal(geo, xs, D, N);
+      const T dn = bx * N[0] + by * N[1] + bz * N[2];
+      bx -= dn * N[0];
+      by -= dn * N[1];
+      bz -= dn * N[2];
+    }
     const T dt1 = (T)scal->dt1, dt2 = (T)scal->dt2;
     const T kv = T(0.5) * dt1 * dt1;  // a~ = kv B
     // a~ for the caller when asked (a run-time test: one compiled kernel, so
@@ -774,17 +799,23 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
       for (int k = 0; k < D; ++k) {
         long long v = *Xc[k] + (long long)llrint((double)(d[k] * F.inv_q64t));
         // bounding box (first constraint): clamp, the closest point
-        if (v < 0) { v = 0; moved = 1; }
-        if (v > F.xmax[k]) { v = F.xmax[k]; moved = 1; }
+        if (v < 0) { v = 0; moved |= !surf; }
+        if (v > F.xmax[k]) { v = F.xmax[k]; moved |= !surf; }
         *Xc[k] = v;
       }
-      // shape constraints, in order, at the absolute position
+      // shape constraints, in order, at the absolute position; a feature-surface
+      // particle goes onto the surface it belongs to instead (Eq. displacement_surface)
       T xa[3];
       abs_pos<D, T>(F, X, xa);
       int mv = 0;
-      for (int s = 0; s < geo.n_shapes; ++s) mv |= project_shape(geo, s, xa, D);
+      if (surf) {
+        project_to_surface(geo, xa, D);
+        mv = 1;
+      } else {
+        for (int s = 0; s < geo.n_shapes; ++s) mv |= project_shape(geo, s, xa, D);
+        moved |= mv;
+      }
       if (mv) {
-        moved = 1;
         for (int k = 0; k < D; ++k) {
           long long v = (long long)llrint((double)((xa[k] - F.lo[k]) * F.inv_q64t));
           v = v < 0 ? 0 : (v > F.xmax[k] ? F.xmax[k] : v);
@@ -920,6 +951,8 @@ cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& 
 template <int D, class T>
 cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P, PassFlags f, cudaStream_t st) {
   using VT = typename ViewOf<T>::type;
+  Geom<T> geo{};
+  if (f.geo) geo = *(const Geom<T>*)f.geo;
   const int tb = SPH_PASS_THREADS, gb = grid_for(S.n, tb);
   T* rho = (T*)S.rho;
   T* pc = (T*)S.pc;
@@ -931,7 +964,7 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
                                               S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount, F, P, \
                                               pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
                                               f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix,     \
-                                              f.dt_rec)
+                                              f.dt_rec, (const LL4*)S.X[0], (const LL4*)S.X[1], geo)
   if (f.general_eos) {
     if (f.nbr_debug) SPH_PASS_A(true, true);
     else SPH_PASS_A(true, false);
@@ -952,7 +985,7 @@ cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P
   k_pass_b<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1], (VT*)S.view[0],
                                     (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0], (LL4*)S.X[1], S.plist,
                                     S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
-                                    f.record ? (V4<T>*)S.visc : nullptr, S.err, wm, f.move);
+                                    f.record ? (V4<T>*)S.visc : nullptr, S.err, wm, f.move, S.meta[0], S.meta[1]);
   return cudaGetLastError();
 }
 

@@ -270,6 +270,51 @@ def test_backward_refuses_background_level_set():
     r.close()
 
 
+# ---------------------------------------- feature-surface particles (Sec. 3.5) ----
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_step_parity_surface_particles(precision):
+    """The circle with feature-surface particles on its boundary: one step on
+    both sides (surface particles see surface particles only, lose the normal
+    force component and are projected back onto the circle)."""
+    p, pos, col = W.circle_with_surface(1500, 4)
+    r = make_gpu(p, pos, col, precision)
+    r.set_surface(p.surface)
+    compare_step(p, pos, col, precision, gpu=r)
+    x = r.positions()
+    s = p.surface
+    assert np.abs(np.linalg.norm(x[s] - 50.0, axis=1) - 43.0).max() < (1e-5 if precision == "fp32" else 1e-12)
+    r.close()
+
+
+def test_surface_particles_relaxation_matches_oracle():
+    """600 steps with surface particles (ramp over 300-400) on the GPU and in
+    the oracle: surface particles stay on the circle and the meshes have the
+    same statistics; the backward pass refuses the flagged handle."""
+    import mesh_quality as MQ
+    from paper_1906_07925_gb300 import SphError
+    p, pos, col = W.circle_with_surface(1500, 4)
+    p.t0, p.t1 = 300, 400
+    r = make_gpu(p, pos, col, "fp32", use_graph=True)
+    r.set_surface(p.surface)
+    r.ramp_surface_tension(300, 400)
+    r.step(600)
+    xg = r.positions()
+    with pytest.raises(SphError):
+        r.backward(1, lam=1.0)
+    r.close()
+    xo, _ = oracle.run(p, pos, col, 600)
+    s = p.surface
+    for x in (xg, xo):
+        assert np.abs(np.linalg.norm(x[s] - 50.0, axis=1) - 43.0).max() < 1e-5
+        assert np.linalg.norm(x[~s] - 50.0, axis=1).max() <= 43.0 + 1e-5
+    qg = MQ.quality(xg, col, max_edge_factor=None, drop_hull=False)
+    qo = MQ.quality(xo, col, max_edge_factor=None, drop_hull=False)
+    assert qg["G_avg"] == pytest.approx(qo["G_avg"], abs=0.015)
+    assert qg["theta_min_mean"] == pytest.approx(qo["theta_min_mean"], abs=1.5)
+    assert abs(qg["n_tri"] - qo["n_tri"]) <= 0.01 * qo["n_tri"]
+
+
 def test_circle_paper_schedule():
     """circle_6mpi run as the paper runs it (Sec. 4.1): 20,000 iterations, the
     surface tension ramped down once the partition has converged (automatic
