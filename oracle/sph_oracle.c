@@ -720,8 +720,15 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
       double v = vt[i * d + k] + 0.5 * at[i * d + k] * dt2;
       pos[i * d + k] += v * dt2;
     }
-    if (p->surface && p->surface[i]) project_to_surface(p, pos + i * d);
-    else moved += orc_project(p, pos + i * d);
+    if (p->surface && p->surface[i]) {
+      /* the position stays in the bounding box (the state space), then goes
+       * onto its surface */
+      orc_shape box = box_shape(p);
+      project_one(p, &box, pos + i * d, d);
+      project_to_surface(p, pos + i * d);
+    } else {
+      moved += orc_project(p, pos + i * d);
+    }
   }
 
   /* diagnostics */
