@@ -349,7 +349,7 @@ def circle_2d(n: int = 4289, n_colors: int = 6, h_min: float = 0.391, h_max: flo
 
 
 def circle_with_surface(n_volume: int = 4289, n_colors: int = 6, seed: int = 1, h_min: float = 0.391,
-                        h_max: float = 3.125):
+                        h_max: float = 3.125, surface_spacing: float = 1.0):
     """The circle case with feature-surface particles (Sec. 3.5): n_surface
     particles evenly spaced (with a small jitter) on the circle at the target
     spacing there, then n_volume density-proportional particles inside.
@@ -357,7 +357,8 @@ def circle_with_surface(n_volume: int = 4289, n_colors: int = 6, seed: int = 1, 
     come first and take the colour of the nearest volume generator."""
     p = circle_2d(n_volume, n_colors, h_min=h_min, h_max=h_max)
     vol, col, gens = sample_density(p, n_volume, seed)
-    spacing = h_min * p.rho_scale ** -0.5  # target spacing on the circle (s = h_min there)
+    # target spacing on the circle (s = h_min there), times surface_spacing
+    spacing = surface_spacing * h_min * p.rho_scale ** -0.5
     n_surface = int(round(2 * math.pi * 43.0 / spacing))
     rng = np.random.default_rng(seed + 7)
     ang = (np.arange(n_surface) + rng.uniform(-0.2, 0.2, n_surface)) * (2 * math.pi / n_surface)
