@@ -174,6 +174,7 @@ sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEve
   f.dt_rec = dt_rec;
   const bool f64 = h->prec == SPH_PREC_FP64;
   f.geo = f64 ? (const void*)&h->geod : (const void*)&h->geof;
+  f.surface = h->has_surface ? 1 : 0;
   cudaError_t e = cudaSuccess;
   if (ev) e = cudaEventRecord(ev[0], h->stream);
   if (e == cudaSuccess) e = launch_gate(S, force_rebuild, h->stream);
@@ -225,6 +226,7 @@ sph_status launch_evaluate(sph_handle* h, int nbr_debug) {
   f.advance = 0;
   const bool f64 = h->prec == SPH_PREC_FP64;
   f.geo = f64 ? (const void*)&h->geod : (const void*)&h->geof;
+  f.surface = h->has_surface ? 1 : 0;
   cudaError_t e = launch_gate(S, 1, h->stream);
   if (e == cudaSuccess) {
     if (h->dim == 2)
@@ -249,7 +251,10 @@ sph_status launch_evaluate(sph_handle* h, int nbr_debug) {
 }
 
 sph_status ensure_graph(sph_handle* h, int record) {
-  if (h->gexec && h->graph_record == record) return SPH_OK;
+  // the captured step depends on field recording and on whether pass A takes
+  // its feature-surface variant
+  const int key = record | (h->has_surface ? 2 : 0);
+  if (h->gexec && h->graph_record == key) return SPH_OK;
   if (h->gexec) {
     cudaGraphExecDestroy(h->gexec);
     h->gexec = nullptr;
@@ -266,7 +271,7 @@ sph_status ensure_graph(sph_handle* h, int record) {
   e = cudaGraphInstantiate(&h->gexec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
-  h->graph_record = record;
+  h->graph_record = key;
   return SPH_OK;
 }
 

@@ -67,6 +67,7 @@ struct PassFlags {
   const double* dt_fix = nullptr;  // pass A: prescribed {dt1, dt2} (device)
   double* dt_rec = nullptr;        // pass A: record {dt1, dt2} (device)
   const void* geo = nullptr;       // pass A: the Geom<T> of the handle (feature-surface normals)
+  int surface = 0;                 // pass A: feature-surface particles may be flagged
 };
 
 template <int D, class T>

@@ -41,6 +41,9 @@
 #ifndef SPH_PASS_THREADS
 #define SPH_PASS_THREADS 256
 #endif
+#ifndef SPH_PASSB_MIN_BLOCKS
+#define SPH_PASSB_MIN_BLOCKS SPH_PASS_MIN_BLOCKS
+#endif
 #ifndef SPH_LIST_MIN_BLOCKS
 #define SPH_LIST_MIN_BLOCKS 4
 #endif
@@ -467,7 +470,7 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
 // pair counts; the last block reduces them in fixed order and sets dt1, dt2
 // (Eq. time_step_size, see below).
 // --------------------------------------------------------------------------
-template <int D, class T, bool GENERAL, bool DBG>
+template <int D, class T, bool GENERAL, bool DBG, bool SURF>
 __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, StepCtl* ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
@@ -499,8 +502,9 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
     const uint32_t* __restrict__ meta = buf ? m1 : m0;
     const uint32_t mi = meta[i];
     const uint32_t ci = mi & 0xFFu;
-    // a feature-surface particle (Sec. 3.5) takes forces from surface particles only
-    const bool surf = (mi & kSurfaceBit) != 0;
+    // a feature-surface particle (Sec. 3.5) takes forces from surface particles
+    // only (SURF: the variant launched when the handle has any)
+    const bool surf = SURF && (mi & kSurfaceBit) != 0;
     const T hv = view_h(vi);
     const T qv = F.qv;
     const T Hd = P.kappa * hv, Hd2 = Hd * Hd, invHd = T(1) / Hd;
@@ -711,7 +715,7 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
 // skin since the list was built raises need_rebuild.
 // --------------------------------------------------------------------------
 template <int D, class T>
-__global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_b(int n, StepCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASSB_MIN_BLOCKS) k_pass_b(int n, StepCtl* __restrict__ ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 typename ViewOf<T>::type* __restrict__ w0,
@@ -960,7 +964,8 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
     k_density<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1], S.list, S.lcount,
                                        F, P, rho, pc);
 #define SPH_PASS_A(GEN, DBG)                                                                                    \
-  k_pass_a<D, T, GEN, DBG><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],           \
+  (f.surface ? k_pass_a<D, T, GEN, DBG, true> : k_pass_a<D, T, GEN, DBG, false>)<<<gb, tb, 0, st>>>(            \
+                                              S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],           \
                                               S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount, F, P, \
                                               pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
                                               f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix,     \
