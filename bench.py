@@ -74,7 +74,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max
 # DRAM bytes per particle of one k_pass_a launch (ncu dram__bytes_read + write on
 # the 1,048,576-particle 3D case, FP32, default skin; profiles/k_pass_a_traffic_c3_1m.md);
 # per-particle traffic does not depend on the particle count. None once the kernel changes.
-PASS_A_DRAM_BYTES_PER_PARTICLE_3D_FP32 = 640.0
+PASS_A_DRAM_BYTES_PER_PARTICLE_3D_FP32 = 639.0
 
 
 def log(*a):
