@@ -190,6 +190,23 @@ def oracle_time(q, pos, col, steps):
 
 
 # ---------------------------------------------------------------- GPU arm --
+def max_over_ranks(x, world, device="cuda"):
+    """The largest value of x over the ranks: the job's time is its slowest
+    rank's (replicas run independently; this is the only collective)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, steps, seconds):
+    """Whole-job throughput: the units every rank advanced, over the job time."""
+    return world * units_per_rank * steps / seconds
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     import torch.distributed as dist
@@ -234,12 +251,9 @@ def run_gpu(args, wl, rank, world):
     ck = clocks.stop()
     ms = e0.elapsed_time(e1)
     st = r.stats()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     ms_step = ms / args.steps
-    value = world * n * args.steps / (ms / 1e3)
+    value = job_rate(n, world, args.steps, ms / 1e3)
 
     # per-kernel device time over a second timed run (direct launches, events
     # on the handle's stream around each phase)
@@ -260,11 +274,8 @@ def run_gpu(args, wl, rank, world):
     st2 = r.stats()
     e2e_s = time.perf_counter() - t0
     assert rc == 0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": world * n * args.steps / e2e_s, "unit": METRIC,
+    e2e_s = max_over_ranks(e2e_s, world)
+    e2e = {"value": job_rate(n, world, args.steps, e2e_s), "unit": METRIC,
            "h2d_bytes_per_step": (n * d * 8 + n) / args.steps, "d2h_bytes_per_step": (n * d * 8 + 128) / args.steps}
     info = dict(grid=r.grid(), stats=st, stats_e2e=st2)
     r.close()
@@ -392,13 +403,10 @@ def run_batch(args, rank, world):
         xs[k] = b.positions(k)
     e2e_s = time.perf_counter() - t0
     b.close()
-    if world > 1:
-        t = torch.tensor([ms, ms_each, e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms, ms_each, e2e_s = [float(v) for v in t.tolist()]
+    ms, ms_each, e2e_s = (max_over_ranks(v, world) for v in (ms, ms_each, e2e_s))
     hb = sum(n * p.dim * 8 + n for p, n in zip(probs, ns))
     return dict(ms=ms, ms_each=ms_each, total=total, clocks=ck, tune=tune,
-                e2e={"value": world * total * args.steps / e2e_s, "unit": METRIC,
+                e2e={"value": job_rate(total, world, args.steps, e2e_s), "unit": METRIC,
                      "h2d_bytes_per_step": hb / args.steps, "d2h_bytes_per_step": (hb - total) / args.steps})
 
 
@@ -584,12 +592,12 @@ def main_batch(args):
             v, cores, desc = batch_oracle_sample(args)
             cpu = {"value": v, "unit": METRIC, "cores": cores, "kind": "oracle", "sample": desc}
         ms_step = res["ms"] / args.steps
-        out = {"metric": METRIC, "value": world * res["total"] * args.steps / (res["ms"] * 1e-3), "unit": METRIC,
+        out = {"metric": METRIC, "value": job_rate(res["total"], world, args.steps, res["ms"] * 1e-3), "unit": METRIC,
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic", "config": config, "clocks": res["clocks"], "e2e": res["e2e"],
                "gpu_launches": KERNELS_PER_STEP * 512 * args.steps,
-               "per_instance_graphs": {"value": world * res["total"] * args.steps / (res["ms_each"] * 1e-3),
+               "per_instance_graphs": {"value": job_rate(res["total"], world, args.steps, res["ms_each"] * 1e-3),
                                        "ms_per_step": res["ms_each"] / args.steps,
                                        "speedup_of_batched": res["ms_each"] / res["ms"]},
                "autotuner": res["tune"], "cpu_baseline": cpu}
