@@ -49,6 +49,16 @@ double orc_dW(double r, double H, int dim) {
   return wendland_alpha(H, dim) / H * (-20.0 * q * u * u * u);
 }
 
+/* (dW/dr) / r, written out so that it is defined at r = 0 as its limit:
+ * dW/dr = -20 alpha q u^3 / H is linear in r there, so the ratio tends to
+ * -20 alpha / H^2 (coincident particles). */
+static double dW_over_r(double r, double H, int dim) {
+  double q = r / H;
+  if (q >= 1.0) return 0.0;
+  double u = 1.0 - q;
+  return wendland_alpha(H, dim) / (H * H) * (-20.0 * u * u * u);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Geometry: level set phi, positive in the mesh region (Sec. 3.1,           */
 /* Eq. level_set_function). The region is the box [lo,hi] intersected with  */
@@ -620,7 +630,9 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
       double dw = orc_dW(r, kappa * hij, d);
       double beta = (col[i] != col[j]) ? sigma : 0.0;
       double coef = (Pc[i] + Pc[j]) + beta * (P0 / (rt[i] * rt[i]) + P0 / (rt[j] * rt[j]));
-      for (int k = 0; k < d; ++k) ai[k] -= coef * dw * (pos[i * d + k] - pos[j * d + k]) / r;
+      /* dW e_ij: at r = 0 (coincident particles) dW = 0 and e_ij is bounded, so the term is 0 */
+      if (r > 0.0)
+        for (int k = 0; k < d; ++k) ai[k] -= coef * dw * (pos[i * d + k] - pos[j * d + k]) / r;
       sabs += fabs(coef * dw);
       fpairs += 1;
       ipairs += (col[i] != col[j]);
@@ -690,10 +702,9 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
       if (surf_i && !p->surface[j]) continue;
       double r = sqrt(dist2(pos + i * d, pos + j * d, d));
       double hij = 0.5 * (h[i] + h[j]);
-      double dw = orc_dW(r, kappa * hij, d);
       double es = eta[i] + eta[j];
       double hm = es > 0.0 ? 2.0 * eta[i] * eta[j] / es : 0.0;
-      double coef = hm * (1.0 / (rt[i] * rt[i]) + 1.0 / (rt[j] * rt[j])) * dw / r;
+      double coef = hm * (1.0 / (rt[i] * rt[i]) + 1.0 / (rt[j] * rt[j])) * dW_over_r(r, kappa * hij, d);
       double vi2 = 0.0, vj2 = 0.0;
       for (int k = 0; k < d; ++k) {
         double vij = vt[i * d + k] - vt[j * d + k];

@@ -586,3 +586,24 @@ def test_normal_particles_do_not_act_on_surface_particles():
     near = r > 43.0 - 1.0
     assert near.any()
     assert np.abs(fn["acc"][near] - f["acc"][ns:][near]).max() > 1e-3 * np.abs(f["acc"][ns:][near]).max()
+
+
+def test_coincident_particles_take_the_limit_of_the_pair_terms():
+    """Two particles at the same point (a degenerate input of the method):
+    dW/dr vanishes linearly at r = 0, so the pressure term dW e_ij is 0 and the
+    viscous term's dW/(r dr) takes its finite limit. The step is finite and
+    matches the same step with the pair a tiny distance apart."""
+    import oracle
+    p = W.uniform_square_2d(32, 2)
+    pos, col, _ = W.lattice_jitter_2d(p, 32, 0.3, 0)
+    pos = pos.copy()
+    pos[1] = pos[0]
+    x0, info0, f0 = oracle.step(p, pos, col, 0)
+    assert np.isfinite(x0).all() and np.isfinite(f0["acc"]).all() and np.isfinite(f0["visc"]).all()
+    near = pos.copy()
+    near[1, 0] += 1e-9 / 32
+    x1, info1, f1 = oracle.step(p, near, col, 0)
+    scale = np.abs(f0["visc"]).max()
+    assert np.abs(f0["visc"] - f1["visc"]).max() <= 1e-5 * scale
+    assert np.abs(f0["acc"] - f1["acc"]).max() <= 1e-5 * np.abs(f0["acc"]).max()
+    assert info0["force_pairs"] == info1["force_pairs"]
