@@ -357,6 +357,18 @@ def test_empty_and_single_particle():
     r1.close()
 
 
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_coincident_particles(precision):
+    """Two particles at the same point: the pair's pressure term is 0 and its
+    viscous term takes the limit of dW/(r dr), on both sides."""
+    p, pos, col = c1_state()
+    pos = pos.copy()
+    pos[1] = pos[0]
+    r, _ = compare_step(p, pos, col, precision)
+    assert np.isfinite(r.positions()).all()
+    r.close()
+
+
 def test_ragged_sizes_and_graph_matches_direct():
     for n in (257, 1000, 4097):
         p = W.graded_hole_2d(n, 3)
