@@ -75,7 +75,9 @@ typedef struct {
  * shapes[dist_shape]|) (SPH_FIELD_TANH_DISTANCE, s0 a reciprocal length: the
  * target size of the paper's circle case, Sec. 4.1, is
  * h_min + tanh(2.5 phi / 43) / tanh(2.5) (h_max - h_min), i.e. a = h_min,
- * b = (h_max - h_min) / tanh(2.5), s0 = 2.5 / 43); x~ = 2 (x - lo)/(hi - lo) - 1 and b_k are
+ * b = (h_max - h_min) / tanh(2.5), s0 = 2.5 / 43), or the node values of a
+ * background mesh interpolated at x (SPH_FIELD_BACKGROUND, sph_create_background);
+ * x~ = 2 (x - lo)/(hi - lo) - 1 and b_k are
  *   2D: x, y, x^2, xy, y^2, x^3, x^2 y, x y^2;  3D: x, y, z, x^2, y^2, z^2, xy, yz.
  * rho_scale = 0 asks sph_create to choose it so that the total mass
  * M_v = integral of rho_t over the region (Eq. total_mass_2) equals the
