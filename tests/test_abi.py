@@ -79,6 +79,11 @@ def test_null_handle_calls(lib):
     assert lib.sph_step(None, 1) == 1
     assert lib.sph_sync(None) == 1
     assert lib.sph_last_error(None) == b"null handle"
+    assert lib.sph_set_surface(None, None) == 1
+    d, f, q = problem_structs(W.uniform_square_2d(16))
+    h = B.H()
+    assert lib.sph_create_background(C.byref(d), C.byref(f), None, 10, 1, C.byref(q), None, None, C.byref(h)) == 1
+    assert not h.value
     lib.sph_destroy(None)
 
 
@@ -118,3 +123,21 @@ def test_grid_shape_needs_a_background_mesh(lib):
     p.field_kind, p.s0 = W.FIELD_UNIFORM, 1.0
     st, h = _create(lib, p)
     assert st == 1 and not h.value
+
+
+def test_background_nodes_are_passed_x_fastest():
+    """Node arrays given shaped dims and indexed [i, j, k] reach the library
+    (and the oracle) stored x fastest, as the header specifies."""
+    import numpy as np
+    import oracle
+    from paper_1906_07925_gb300 import background_struct
+    nx, ny = 4, 3
+    phi = np.add.outer(10.0 * np.arange(nx), np.arange(ny))[:, :, None]  # phi[i, j] = 10 i + j
+    bg = W.Background(dims=[nx, ny, 1], lo=[0, 0, 0], hi=[3, 2, 0], phi=phi, spacing=None)
+    s, keep = background_struct(bg)
+    flat = np.ctypeslib.as_array((C.c_double * (nx * ny)).from_address(s.phi))
+    assert list(flat[:5]) == [0.0, 10.0, 20.0, 30.0, 1.0]  # x fastest: (0,0), (1,0), (2,0), (3,0), (0,1)
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[3, 2, 0], shapes=[W.Shape(W.GRID, True, [0, 0, 0], [1, 0, 0])], bg=bg)
+    c = oracle.to_c(p)
+    oflat = np.ctypeslib.as_array((C.c_double * (nx * ny)).from_address(c.bg_phi))
+    assert np.array_equal(oflat, flat)
