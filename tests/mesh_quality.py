@@ -55,3 +55,63 @@ def quality(pos, col=None, max_edge_factor=2.5, drop_hull=True):
     return dict(**extra, G_avg=float(G.mean()), G_min=float(G.min()), theta_min=float(A.min()), theta_max=float(A.max()),
                 theta_min_mean=float(A.min(axis=1).mean()), n_lt30=int((A.min(axis=1) < 30.0).sum()),
                 share_55_65=float(((A >= 55.0) & (A <= 65.0)).mean()), n_tri=int(keep.sum()))
+
+
+def tet_metrics(a, b, c, d):
+    """Radius ratio gamma = 3 r_in / r_circ and the six dihedral angles
+    (degrees) of tetrahedra with vertices a, b, c, d (k x 3), the paper's
+    tetrahedral quality measures (Sec. 3.6)."""
+    V = np.abs(np.einsum("ij,ij->i", b - a, np.cross(c - a, d - a))) / 6.0
+    faces = [(b, c, d), (a, c, d), (a, b, d), (a, b, c)]  # face k is opposite vertex k
+    areas = [0.5 * np.linalg.norm(np.cross(q - p, r - p), axis=1) for p, q, r in faces]
+    r_in = 3.0 * V / np.sum(areas, axis=0)
+    # circumcentre: solve 2 (p_k - a) . x = |p_k|^2 - |a|^2 for k = b, c, d
+    M = 2.0 * np.stack([b - a, c - a, d - a], axis=1)
+    rhs = np.stack([(b * b).sum(1) - (a * a).sum(1), (c * c).sum(1) - (a * a).sum(1),
+                    (d * d).sum(1) - (a * a).sum(1)], axis=1)
+    cc = np.linalg.solve(M, rhs[:, :, None])[:, :, 0]
+    r_circ = np.linalg.norm(cc - a, axis=1)
+    verts = [a, b, c, d]
+    # unit normals of the faces, pointing away from the opposite vertex
+    normals = []
+    for k, (p, q, r) in enumerate(faces):
+        n = np.cross(q - p, r - p)
+        n /= np.linalg.norm(n, axis=1)[:, None]
+        s = np.sign(np.einsum("ij,ij->i", n, p - verts[k]))
+        normals.append(n * s[:, None])
+    dih = []
+    for i in range(4):
+        for j in range(i + 1, 4):  # the edge shared by faces i and j
+            cosang = -np.einsum("ij,ij->i", normals[i], normals[j])
+            dih.append(np.degrees(np.arccos(np.clip(cosang, -1.0, 1.0))))
+    return 3.0 * r_in / r_circ, np.stack(dih, axis=1)
+
+
+def quality3d(pos, col=None, max_edge_factor=2.5, drop_hull=True):
+    """Tetrahedral quality of a 3D point set's Delaunay mesh (Sec. 3.6): radius
+    ratio average and minimum, dihedral angle extremes, the mean of each
+    tetrahedron's smallest dihedral angle, the counts of tetrahedra whose
+    smallest dihedral angle is below 10, 20, 30 and 40 degrees, and with
+    colours the communication volume (mixed-colour elements / all elements).
+    The same filters as quality() drop hull and bridging elements."""
+    pos = np.asarray(pos, dtype=np.float64)
+    dl = Delaunay(pos)
+    tet = dl.simplices
+    a, b, c, d = (pos[tet[:, k]] for k in range(4))
+    edges = np.stack([np.linalg.norm(p - q, axis=1) for p, q in ((a, b), (a, c), (a, d), (b, c), (b, d), (c, d))],
+                     axis=1)
+    keep = edges.max(axis=1) < max_edge_factor * np.median(edges) if max_edge_factor else np.ones(len(tet), bool)
+    if drop_hull:
+        on_hull = np.zeros(len(pos), dtype=bool)
+        on_hull[np.unique(dl.convex_hull)] = True
+        keep &= ~on_hull[tet].any(axis=1)
+    g, dih = tet_metrics(a[keep], b[keep], c[keep], d[keep])
+    mins = dih.min(axis=1)
+    out = dict(gamma_avg=float(g.mean()), gamma_min=float(g.min()), theta_min=float(dih.min()),
+               theta_max=float(dih.max()), theta_min_mean=float(mins.mean()), n_tet=int(keep.sum()),
+               slivers={t: int((mins < t).sum()) for t in (10, 20, 30, 40)})
+    if col is not None:
+        cc = np.asarray(col)[tet[keep]]
+        mixed = np.any(cc != cc[:, :1], axis=1)
+        out.update(n_et=int(len(cc)), n_eg=int(mixed.sum()))
+    return out

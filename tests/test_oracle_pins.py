@@ -607,3 +607,38 @@ def test_coincident_particles_take_the_limit_of_the_pair_terms():
     assert np.abs(f0["visc"] - f1["visc"]).max() <= 1e-5 * scale
     assert np.abs(f0["acc"] - f1["acc"]).max() <= 1e-5 * np.abs(f0["acc"]).max()
     assert info0["force_pairs"] == info1["force_pairs"]
+
+
+def test_tetrahedron_quality_measures():
+    """Sec. 3.6's tetrahedral measures in closed form: the regular tetrahedron
+    has radius ratio 3 r_in / r_circ = 1 and every dihedral angle arccos(1/3);
+    the corner tetrahedron (0, e_x, e_y, e_z) has ratio sqrt(3) - 1, three right
+    dihedral angles and three of arccos(1/sqrt(3))."""
+    import mesh_quality as MQ
+    reg = np.array([[1, 1, 1], [1, -1, -1], [-1, 1, -1], [-1, -1, 1]], dtype=float)
+    g, d = MQ.tet_metrics(*[reg[k:k + 1] for k in range(4)])
+    assert g[0] == pytest.approx(1.0, abs=1e-12)
+    assert np.allclose(d, math.degrees(math.acos(1 / 3)), atol=1e-9)
+    cor = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=float)
+    g, d = MQ.tet_metrics(*[cor[k:k + 1] for k in range(4)])
+    assert g[0] == pytest.approx(math.sqrt(3) - 1, abs=1e-12)
+    assert sorted(d[0]) == pytest.approx([math.degrees(math.acos(1 / math.sqrt(3)))] * 3 + [90.0] * 3)
+
+
+def test_oracle_relaxation_raises_tetrahedral_quality():
+    """Relaxing a random start in the unit cube (2,000 particles, 150 steps)
+    turns a Poisson point set's Delaunay mesh (radius ratio ~0.54, hundreds of
+    slivers with a dihedral angle below 10 degrees) into a far more regular
+    one (Sec. 3.6 measures)."""
+    import mesh_quality as MQ
+    import oracle
+    n = 2000
+    p = W.Problem(dim=3, lo=[0, 0, 0], hi=[1, 1, 1], field_kind=W.FIELD_UNIFORM, s0=1.0, n_colors=4)
+    p.rho_scale = W.rho_scale_for(p, n)
+    pos, col, _ = W.sample_density(p, n, 3)
+    q0 = MQ.quality3d(pos, col)
+    x, _ = oracle.run(p, pos, col, 150)
+    q1 = MQ.quality3d(x, col)
+    assert q0["gamma_avg"] < 0.6 and q1["gamma_avg"] > 0.72
+    assert q1["slivers"][10] < 0.2 * q0["slivers"][10]
+    assert q1["theta_min_mean"] > q0["theta_min_mean"] + 8.0
