@@ -141,3 +141,12 @@ def test_background_nodes_are_passed_x_fastest():
     c = oracle.to_c(p)
     oflat = np.ctypeslib.as_array((C.c_double * (nx * ny)).from_address(c.bg_phi))
     assert np.array_equal(oflat, flat)
+
+
+def test_missing_library_raises_instead_of_falling_back(monkeypatch, tmp_path):
+    """Without libsphmesh.so the package refuses to run: there is no CPU
+    implementation to fall back on."""
+    monkeypatch.setattr(B, "_lib", None)
+    monkeypatch.setattr(B, "LIB_PATH", str(tmp_path / "libsphmesh.so"))
+    with pytest.raises(RuntimeError, match="missing"):
+        B.load()
