@@ -75,48 +75,60 @@ _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 _i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
 
 
+def bind(path):
+    """Load an oracle library from `path` and declare its function types
+    (lib() binds the one build() makes)."""
+    L = C.CDLL(path)
+    _declare(L)
+    return L
+
+
 def lib():
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
-            L.orc_W.restype = C.c_double
-            L.orc_W.argtypes = [C.c_double, C.c_double, C.c_int]
-            L.orc_dW.restype = C.c_double
-            L.orc_dW.argtypes = [C.c_double, C.c_double, C.c_int]
-            L.orc_phi.restype = C.c_double
-            L.orc_phi.argtypes = [C.POINTER(Problem), _dp]
-            L.orc_project.restype = C.c_int
-            L.orc_project.argtypes = [C.POINTER(Problem), _dp]
-            L.orc_rho_t.restype = C.c_double
-            L.orc_rho_t.argtypes = [C.POINTER(Problem), _dp]
-            L.orc_h.restype = C.c_double
-            L.orc_h.argtypes = [C.POINTER(Problem), _dp]
-            L.orc_sigma.restype = C.c_double
-            L.orc_sigma.argtypes = [C.POINTER(Problem), C.c_double]
-            L.orc_total_mass.restype = C.c_double
-            L.orc_total_mass.argtypes = [C.POINTER(Problem), C.c_int]
-            L.orc_neighbor_sets.restype = C.c_int
-            L.orc_neighbor_sets.argtypes = [C.POINTER(Problem), C.c_int64, _dp, C.c_int,
-                                            _i32p, _i32p, _i64p, _i64p, _i64p, _i64p]
-            L.orc_step.restype = C.c_int
-            L.orc_step.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int,
-                                   C.POINTER(StepInfo), C.c_void_p, C.c_void_p, C.c_void_p,
-                                   C.c_void_p, C.c_void_p]
-            L.orc_step_fixed_dt.restype = C.c_int
-            L.orc_step_fixed_dt.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int,
-                                            _dp, C.POINTER(StepInfo)]
-            L.orc_objective.restype = C.c_int
-            L.orc_objective.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_double,
-                                        C.POINTER(C.c_double)]
-            L.orc_backward.restype = C.c_int
-            L.orc_backward.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int32,
-                                       C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
-                                       C.POINTER(C.c_double), _dp, _dp]
-            L.orc_num_threads.restype = C.c_int
-            L.orc_num_threads.argtypes = []
-            _lib = L
+            _lib = bind(build())
     return _lib
+
+
+def _declare(L):
+    L.orc_W.restype = C.c_double
+    L.orc_W.argtypes = [C.c_double, C.c_double, C.c_int]
+    L.orc_dW.restype = C.c_double
+    L.orc_dW.argtypes = [C.c_double, C.c_double, C.c_int]
+    L.orc_dW_over_r.restype = C.c_double
+    L.orc_dW_over_r.argtypes = [C.c_double, C.c_double, C.c_int]
+    L.orc_phi.restype = C.c_double
+    L.orc_phi.argtypes = [C.POINTER(Problem), _dp]
+    L.orc_project.restype = C.c_int
+    L.orc_project.argtypes = [C.POINTER(Problem), _dp]
+    L.orc_rho_t.restype = C.c_double
+    L.orc_rho_t.argtypes = [C.POINTER(Problem), _dp]
+    L.orc_h.restype = C.c_double
+    L.orc_h.argtypes = [C.POINTER(Problem), _dp]
+    L.orc_sigma.restype = C.c_double
+    L.orc_sigma.argtypes = [C.POINTER(Problem), C.c_double]
+    L.orc_total_mass.restype = C.c_double
+    L.orc_total_mass.argtypes = [C.POINTER(Problem), C.c_int]
+    L.orc_neighbor_sets.restype = C.c_int
+    L.orc_neighbor_sets.argtypes = [C.POINTER(Problem), C.c_int64, _dp, C.c_int,
+                                    _i32p, _i32p, _i64p, _i64p, _i64p, _i64p]
+    L.orc_step.restype = C.c_int
+    L.orc_step.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int,
+                           C.POINTER(StepInfo), C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_void_p, C.c_void_p]
+    L.orc_step_fixed_dt.restype = C.c_int
+    L.orc_step_fixed_dt.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int,
+                                    _dp, C.POINTER(StepInfo)]
+    L.orc_objective.restype = C.c_int
+    L.orc_objective.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_double,
+                                C.POINTER(C.c_double)]
+    L.orc_backward.restype = C.c_int
+    L.orc_backward.argtypes = [C.POINTER(Problem), C.c_int64, _dp, _u8p, C.c_int64, C.c_int32,
+                               C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                               C.POINTER(C.c_double), _dp, _dp]
+    L.orc_num_threads.restype = C.c_int
+    L.orc_num_threads.argtypes = []
 
 
 def to_c(p) -> Problem:
@@ -171,6 +183,10 @@ def W(r, H, dim):
 
 def dW(r, H, dim):
     return lib().orc_dW(float(r), float(H), int(dim))
+
+
+def dW_over_r(r, H, dim):
+    return lib().orc_dW_over_r(float(r), float(H), int(dim))
 
 
 def _pt(p, x):

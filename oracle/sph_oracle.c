@@ -52,7 +52,7 @@ double orc_dW(double r, double H, int dim) {
 /* (dW/dr) / r, written out so that it is defined at r = 0 as its limit:
  * dW/dr = -20 alpha q u^3 / H is linear in r there, so the ratio tends to
  * -20 alpha / H^2 (coincident particles). */
-static double dW_over_r(double r, double H, int dim) {
+double orc_dW_over_r(double r, double H, int dim) {
   double q = r / H;
   if (q >= 1.0) return 0.0;
   double u = 1.0 - q;
@@ -704,7 +704,7 @@ static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t
       double hij = 0.5 * (h[i] + h[j]);
       double es = eta[i] + eta[j];
       double hm = es > 0.0 ? 2.0 * eta[i] * eta[j] / es : 0.0;
-      double coef = hm * (1.0 / (rt[i] * rt[i]) + 1.0 / (rt[j] * rt[j])) * dW_over_r(r, kappa * hij, d);
+      double coef = hm * (1.0 / (rt[i] * rt[i]) + 1.0 / (rt[j] * rt[j])) * orc_dW_over_r(r, kappa * hij, d);
       double vi2 = 0.0, vj2 = 0.0;
       for (int k = 0; k < d; ++k) {
         double vij = vt[i * d + k] - vt[j * d + k];

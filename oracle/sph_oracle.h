@@ -82,6 +82,9 @@ typedef struct {
  * unspecified "smooth isotropic kernel"). */
 double orc_W(double r, double H, int dim);
 double orc_dW(double r, double H, int dim);
+/* (dW/dr)/r, continued at r = 0 by its limit -20 alpha_d / H^2 (coincident
+ * particles); the factor of the viscous pair term (Eq. sph_viscous_force). */
+double orc_dW_over_r(double r, double H, int dim);
 
 /* Level set (positive in the mesh region, Sec. 3.1) and the projection of
  * Eq. displacement_surface, applied to each violated constraint in order. */
