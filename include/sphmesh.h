@@ -271,9 +271,12 @@ sph_status sph_get_field(sph_handle* h, int32_t which, double* out, int32_t on_d
 sph_status sph_neighbor_sets(sph_handle* h, int32_t* dens_count, int32_t* force_count,
                              int64_t* dens_idsum, int64_t* force_idsum);
 
-/* Cell list of the current state: cell key of each particle (particle-id
- * order) and the particle ids in sorted order (stable: equal keys keep the
- * order they had before the sort). Host arrays. Synchronises. */
+/* Cell list of the current state (the cell structure the neighbour search of
+ * Algorithm 1 runs on): cell key of each particle (particle-id order; the key
+ * of level l = floor(log2(h/h0)) clamped to the grid's levels, cell c =
+ * floor((x - lo)/cell_l) per axis, key = base_l + c_x + dims_x (c_y + dims_y
+ * c_z), see sph_get_grid) and the particle ids in sorted order (by key, equal
+ * keys by particle id). Host arrays. Synchronises. */
 sph_status sph_get_cell_list(sph_handle* h, uint32_t* key_by_id, uint32_t* sorted_ids);
 
 /* Grid description (levels, cell edges, dims, key bases). */
@@ -425,13 +428,16 @@ void sph_destroy(sph_handle* h);
  * (NULL: legacy default stream).
  *
  * The first call on a device looks up the scratch array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call reuses the same array and leaves its
- * contents behind (the counters it needs zeroed are cleared at the start of
- * each call); calls that overlap on the GPU (two streams, two threads) race on
- * it and must be serialised by the caller. The call synchronises `stream`
- * before returning and reports device-side errors (SPH_ERR_NONFINITE,
- * SPH_ERR_OUT_OF_DOMAIN) through its status. */
+ * (cudaGetSymbolAddress) with that device current. Every call synchronises
+ * `stream` and copies the device error word into host memory before it
+ * returns, so no call may be made while `stream` (or, with stream NULL, the
+ * legacy default stream) is being captured into a CUDA graph. Every call
+ * reuses the same array and leaves its contents behind (the counters it needs
+ * zeroed are cleared at the start of each call); calls that overlap on the GPU
+ * (two streams, two threads) race on it and must be serialised by the caller.
+ * Device-side errors come back through the status: SPH_ERR_NONFINITE,
+ * SPH_ERR_OUT_OF_DOMAIN, SPH_ERR_CELL_OVERFLOW (more than 95 neighbours),
+ * SPH_ERR_TIMEOUT, and SPH_ERR_CUDA for any other device error bit. */
 #define SPH_NOALLOC_MAX_PARTICLES 32768
 #define SPH_NOALLOC_MAX_CELLS (1 << 19)
 sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_field* field, const sph_params* params,

@@ -58,6 +58,11 @@ class Problem(C.Structure):
                 ("surface", C.c_void_p)]
 
 
+class Grid(C.Structure):
+    _fields_ = [("n_levels", C.c_int32), ("dim", C.c_int32), ("lo", C.c_double * 3), ("h0", C.c_double),
+                ("cell", C.c_double * 8), ("dims", (C.c_int32 * 3) * 8), ("base", C.c_uint32 * 9)]
+
+
 class StepInfo(C.Structure):
     _fields_ = [("sigma", C.c_double), ("dt1", C.c_double), ("dt2", C.c_double),
                 ("min_rc_over_a", C.c_double), ("max_a", C.c_double),
@@ -129,6 +134,9 @@ def _declare(L):
                                C.POINTER(C.c_double), _dp, _dp]
     L.orc_num_threads.restype = C.c_int
     L.orc_num_threads.argtypes = []
+    L.orc_cell_keys.restype = C.c_int
+    L.orc_cell_keys.argtypes = [C.POINTER(Problem), C.c_int64, _dp, C.POINTER(Grid),
+                                np.ctypeslib.ndpointer(dtype=np.uint32, flags="C_CONTIGUOUS"), _dp]
 
 
 def to_c(p) -> Problem:
@@ -232,6 +240,35 @@ def neighbor_sets(p, pos, mode=1):
         raise RuntimeError("oracle neighbour search failed")
     return dict(dens_count=dc, force_count=fc, dens_idsum=ds, force_idsum=fs,
                 dens_idxor=dx, force_idxor=fx)
+
+
+def cell_keys(p, pos, grid):
+    """Cell key of every particle in the multi-resolution grid `grid` (a dict
+    with n_levels, lo, h0, cell[l], dims[l], base[l]: the cell structure's
+    configuration) and the smoothing lengths h_i. See orc_cell_keys."""
+    pos = np.ascontiguousarray(pos, dtype=np.float64)
+    g = Grid()
+    g.n_levels = int(grid["n_levels"])
+    g.dim = p.dim
+    for k in range(3):
+        g.lo[k] = float(grid["lo"][k])
+    g.h0 = float(grid["h0"])
+    for l in range(g.n_levels):
+        g.cell[l] = float(grid["cell"][l])
+        for k in range(3):
+            g.dims[l][k] = int(grid["dims"][l][k])
+    for l in range(g.n_levels + 1):
+        g.base[l] = int(grid["base"][l])
+    keys = np.zeros(pos.shape[0], np.uint32)
+    h = np.zeros(pos.shape[0])
+    lib().orc_cell_keys(C.byref(to_c(p)), pos.shape[0], pos, C.byref(g), keys, h)
+    return keys, h
+
+
+def cell_order(keys):
+    """Particle ids ordered by (cell key, particle id): a stable sort of the
+    keys, which leaves equal keys in ascending id order."""
+    return np.argsort(np.asarray(keys, dtype=np.int64), kind="stable").astype(np.uint32)
 
 
 def _ptr(a):

@@ -560,6 +560,33 @@ int orc_neighbor_sets(const orc_problem* p, int64_t n, const double* pos, int mo
 }
 
 /* ------------------------------------------------------------------------ */
+/* Cell keys of the multi-resolution grid (the neighbour search of           */
+/* Algorithm 1): each particle is filed at the level of its smoothing length */
+/* and, within that level, in the cell that holds it.                        */
+/* ------------------------------------------------------------------------ */
+int orc_cell_keys(const orc_problem* p, int64_t n, const double* pos, const orc_grid* g, uint32_t* keys,
+                  double* h_out) {
+  const int d = p->dim;
+  for (int64_t i = 0; i < n; ++i) {
+    const double* x = pos + i * d;
+    double h = orc_h(p, x);
+    if (h_out) h_out[i] = h;
+    /* level: the largest l with 2^l h0 <= h, at least 0, at most n_levels - 1 */
+    int l = 0;
+    while (l + 1 < g->n_levels && h >= ldexp(g->h0, l + 1)) ++l;
+    int64_t c[3] = {0, 0, 0};
+    for (int k = 0; k < d; ++k) {
+      int64_t v = (int64_t)floor((x[k] - g->lo[k]) / g->cell[l]);
+      if (v < 0) v = 0;
+      if (v > g->dims[l][k] - 1) v = g->dims[l][k] - 1;
+      c[k] = v;
+    }
+    keys[i] = g->base[l] + (uint32_t)(c[0] + (int64_t)g->dims[l][0] * (c[1] + (int64_t)g->dims[l][1] * c[2]));
+  }
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* One relaxation step (Algorithm 1).                                        */
 /* ------------------------------------------------------------------------ */
 static int step_core(const orc_problem* p, int64_t n, double* pos, const uint8_t* col, int64_t step,

@@ -110,6 +110,27 @@ int orc_neighbor_sets(const orc_problem* p, int64_t n, const double* pos, int mo
                       int64_t* dens_idsum, int64_t* force_idsum,
                       int64_t* dens_idxor, int64_t* force_idxor);
 
+/* Multi-resolution cell grid of the neighbour search (Algorithm 1 builds a
+ * neighbour list every step; this is the cell structure it is built from):
+ * level l has cells of edge cell[l] = cell[0] 2^l and dims[l] cells per axis
+ * from lo; keys of level l start at base[l] (base[n_levels] = total cells). */
+typedef struct {
+  int32_t n_levels;
+  int32_t dim;
+  double lo[3];
+  double h0;          /* a particle with h < 2 h0 lives at level 0 */
+  double cell[8];
+  int32_t dims[8][3];
+  uint32_t base[9];
+} orc_grid;
+
+/* Cell key of every particle: level l = floor(log2(h_i/h0)) clamped to
+ * [0, n_levels - 1], cell coordinates c_k = floor((x_k - lo_k)/cell[l]) clamped
+ * to [0, dims[l][k] - 1], key = base[l] + c_x + dims_x (c_y + dims_y c_z).
+ * h_out (n, may be NULL) receives h_i. Returns 0. */
+int orc_cell_keys(const orc_problem* p, int64_t n, const double* pos, const orc_grid* g, uint32_t* keys,
+                  double* h_out);
+
 /* One relaxation step (Algorithm 1) advancing pos in place.
  * Any of the per-particle outputs may be NULL:
  *   rho (n), acc (n*dim) = a_n, visc (n*dim) = a~, pair_abs_a (n) = sum_j of

@@ -4,8 +4,9 @@
 // counting sort over the dense key range: warp-aggregated atomic counts per
 // cell, an exclusive scan of the counts (which is also the cell-start table the
 // list build reads), an atomic scatter that counts each cell back down to zero,
-// and a gather that makes the order inside each cell stable (ascending previous
-// position) while it moves the particle state into the other buffer. Every
+// and a gather that orders each cell by particle id (so the order is a function
+// of the keys alone: by key, then id) while it moves the particle state into
+// the other buffer. Every
 // kernel here returns at once on steps without a rebuild (ctl->rebuild == 0),
 // so one captured graph serves every step.
 #include "sph_internal.h"
@@ -175,7 +176,8 @@ struct alignas(32) State64 {
 };
 
 // slot s of the scatter holds old index i; its rank among the cell's members by
-// old index gives the stable destination, where the state is copied
+// particle id gives its destination (cells ordered by key, each cell by
+// particle id), where the state is copied
 __global__ void __launch_bounds__(256) k_stable_gather(
     int n, const StepCtl* __restrict__ ctl, const uint32_t* __restrict__ slots, const uint32_t* __restrict__ key,
     const uint32_t* __restrict__ cstart, State64* __restrict__ X0, State64* __restrict__ X1,
@@ -184,11 +186,13 @@ __global__ void __launch_bounds__(256) k_stable_gather(
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n) return;
   const int nb = ctl->buf;  // new buffer; the old order lives in the other one
+  const uint32_t* __restrict__ pold = nb ? p0 : p1;
   uint32_t i = slots[s];
   uint32_t k = key[i];
+  const uint32_t id = pold[i];
   uint32_t b = cstart[k], e = cstart[k + 1];
   uint32_t rank = 0;
-  for (uint32_t t = b; t < e; ++t) rank += slots[t] < i;
+  for (uint32_t t = b; t < e; ++t) rank += pold[slots[t]] < id;
   uint32_t d = b + rank;
   (nb ? X1 : X0)[d] = (nb ? X0 : X1)[i];
   (nb ? m1 : m0)[d] = (nb ? m0 : m1)[i];

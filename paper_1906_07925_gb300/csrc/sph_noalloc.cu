@@ -240,5 +240,7 @@ extern "C" sph_status sph_eval_forces_noalloc(const sph_domain* dom, const sph_f
   if (flags & kErrNonfinite) return SPH_ERR_NONFINITE;
   if (flags & kErrOutOfDomain) return SPH_ERR_OUT_OF_DOMAIN;
   if (flags & kErrListOverflow) return SPH_ERR_CELL_OVERFLOW;
+  if (flags & kErrTimeout) return SPH_ERR_TIMEOUT;
+  if (flags) return SPH_ERR_CUDA;  // a device error bit this call does not name
   return SPH_OK;
 }

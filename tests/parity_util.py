@@ -22,6 +22,14 @@ import oracle
 TOL = {"fp32": 1e-5, "fp64": 1e-12}
 
 
+def oracle_rho_scale(p, n, res=None):
+    """rho_scale that makes the problem's field integrate to n particles (Eq.
+    total_mass_2 with unit mass), by the oracle's quadrature: the value both
+    sides are given when the GPU would otherwise choose it itself."""
+    res = res or (2048 if p.dim == 2 else 192)
+    return n / oracle.total_mass(p.copy(rho_scale=1.0), res)
+
+
 def make_gpu(p, pos, col, precision, **kw):
     from paper_1906_07925_gb300 import Relaxation
     r = Relaxation(p, n_particles=len(pos), n_colors=int(col.max()) + 1, precision=precision,

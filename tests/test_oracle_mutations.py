@@ -86,6 +86,9 @@ FORWARD = [
     ("sphere projection to the diameter (Eq. displacement_surface)",
      "x[k] = s->center[k] + s->size[0] * d[k] / r;", "x[k] = s->center[k] + 2.0 * s->size[0] * d[k] / r;",
      [(P.test_projection_and_wall, ())]),
+    ("cell level one band too low (multi-resolution cell key)",
+     "h >= ldexp(g->h0, l + 1)) ++l;", "h >= ldexp(g->h0, l + 2)) ++l;",
+     [(P.test_cell_key_files_each_particle_at_its_level_and_cell, (2,))]),
 ]
 
 REVERSE = [

@@ -741,3 +741,54 @@ def test_oracle_relaxation_raises_tetrahedral_quality():
     assert q0["gamma_avg"] < 0.6 and q1["gamma_avg"] > 0.72
     assert q1["slivers"][10] < 0.2 * q0["slivers"][10]
     assert q1["theta_min_mean"] > q0["theta_min_mean"] + 8.0
+
+
+# ----------------------------------------------------------- cell keys ----
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_cell_key_files_each_particle_at_its_level_and_cell(orc, dim):
+    """The key of the multi-resolution grid (the neighbour search's cell
+    structure) decodes to a level whose smoothing-length band holds h_i and to
+    a cell of that level whose box holds x_i; distinct cells have distinct keys
+    inside their level's range; the order is by key, then particle id."""
+    if dim == 2:
+        p = W.graded_hole_2d(6000, 4)
+        x, col, _ = W.sample_density(p, 6000, seed=3)
+    else:
+        p = W.graded_inclusion_3d(6000, 4)
+        x, col, _ = W.sample_density(p, 6000, seed=3)
+    h_all = np.array([orc.h_of(p, xi) for xi in x])
+    h0 = 0.9 * h_all.min()
+    L = int(np.floor(np.log2(h_all.max() / h0))) + 1
+    assert L >= 2
+    cell = [2.0 * h0 * 2 ** l for l in range(L)]
+    dims = [[int(math.ceil(1.0 / c)) if k < dim else 1 for k in range(3)] for c in cell]
+    base = [0]
+    for l in range(L):
+        base.append(base[-1] + int(np.prod(dims[l])))
+    g = dict(n_levels=L, lo=[0.0, 0.0, 0.0], h0=h0, cell=cell, dims=dims, base=base)
+    keys, h = orc.cell_keys(p, x, g)
+    assert np.allclose(h, h_all, rtol=1e-15)
+    lev = np.searchsorted(np.array(base[1:]), keys, side="right")
+    assert np.all(keys < base[-1])
+    for l in range(L):
+        m = lev == l
+        lo_h = h0 * 2.0 ** l if l > 0 else 0.0
+        hi_h = h0 * 2.0 ** (l + 1) if l < L - 1 else np.inf
+        assert np.all((h[m] >= lo_h) & (h[m] < hi_h))
+        rel = keys[m].astype(np.int64) - base[l]
+        cx = rel % dims[l][0]
+        cy = (rel // dims[l][0]) % dims[l][1]
+        cz = rel // (dims[l][0] * dims[l][1])
+        c = np.stack([cx, cy, cz], 1)[:, :dim]
+        assert np.all(c * cell[l] <= x[m] + 1e-15) and np.all(x[m] < (c + 1) * cell[l])
+    # distinct (level, cell) pairs <-> distinct keys
+    lev_cell = {}
+    for i in range(len(x)):
+        lc = (int(lev[i]),) + tuple(np.floor(x[i] / cell[lev[i]]).astype(int))
+        assert lev_cell.setdefault(lc, keys[i]) == keys[i]
+    assert len(set(lev_cell.values())) == len(lev_cell)
+    order = orc.cell_order(keys)
+    ks = keys[order].astype(np.int64)
+    assert np.all(np.diff(ks) >= 0)
+    assert np.all(np.diff(order.astype(np.int64))[np.diff(ks) == 0] > 0)
