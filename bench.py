@@ -67,14 +67,46 @@ ALG_BYTES_FP64 = {"cells": 92, "pass_a": 56, "pass_b": 83}
 # make_view, list_build (predicated: they exit at once unless the list is
 # rebuilt); pass A; pass B
 KERNELS_PER_STEP = 12
-# pair arithmetic per force/density pair (FP32 flop, counted from the kernels):
-# density 8, pressure + surface tension 30 (pass A), viscous 28 (pass B)
-FLOP_PER_PAIR = {"density": 8, "force": 30, "visc": 28}
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x FP32 lanes x FMA x max SM clock
-# DRAM bytes per particle of one k_pass_a launch (ncu dram__bytes_read + write on
-# the 1,048,576-particle 3D case, FP32, default skin; profiles/k_pass_a_traffic_c3_1m.md);
-# per-particle traffic does not depend on the particle count. None once the kernel changes.
-PASS_A_DRAM_BYTES_PER_PARTICLE_3D_FP32 = 639.0
+# pair arithmetic (FP32 flop, counted from the equations as the kernels evaluate
+# them): distance of a pair 10 (differences, squared norm, root), density term 8
+# (Eq. density_sum), pressure + surface-tension term 30 (Eqs.
+# sph_pressure_force_2, sph_st_force), viscous term 28 (Eq. sph_viscous_force)
+FLOP_PER_PAIR = {"distance": 10, "density": 8, "force": 30, "visc": 28}
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz (maximum SM clock)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# ncu DRAM traffic of the pair-pass kernel: a summary under profiles/ records the
+# bytes per particle of one k_pass_a launch and the hash of the kernel sources
+# it was captured from; the figure is reported only while the sources still
+# have that hash (else the counters describe another kernel and traffic is null)
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_pass_a_traffic_c3_1m.md")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_1906_07925_gb300", "csrc", f)
+                  for f in ("sph_step_impl.cuh", "sph_device.cuh", "sph_internal.h")]
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_per_particle():
+    """(bytes per particle of one k_pass_a launch, source hash) from the ncu
+    summary, or (None, reason) when it is missing or was taken on other sources."""
+    import re
+    try:
+        txt = open(TRAFFIC_PROFILE).read()
+    except OSError:
+        return None, "no ncu summary"
+    m = re.search(r"sources sha256/16: `?([0-9a-f]{16})", txt)
+    b = re.search(r"dram bytes per particle: ([0-9.]+)", txt)
+    if not m or not b:
+        return None, "ncu summary without source hash or bytes per particle"
+    if m.group(1) != kernel_source_hash():
+        return None, f"ncu summary taken on sources {m.group(1)}, current {kernel_source_hash()}"
+    return float(b.group(1)), m.group(1)
 
 
 def log(*a):
@@ -284,7 +316,16 @@ def run_gpu(args, wl, rank, world):
         out["fp64"] = run_fp64(args, wl, p, rank)
         if wl["dim"] == 3 and wl["n"] == 1 << 23:
             out["adjoint"] = run_adjoint(rank)
+            out["batch"] = batch_summary(run_batch(args, rank, world), args)
     return out
+
+
+def batch_summary(res, args):
+    """The batched form (512 instances) in a few numbers for the default line."""
+    return {"workload": WORKLOADS["c5"]["desc"], "instances": 512, "particles": res["total"],
+            "ms_per_step": res["ms"] / args.steps, "value": res["total"] * args.steps / (res["ms"] * 1e-3),
+            "unit": METRIC, "per_instance_graphs_ms_per_step": res["ms_each"] / args.steps,
+            "speedup_of_batched": res["ms_each"] / res["ms"], "autotuner": res["tune"], "clocks": res["clocks"]}
 
 
 def run_fp64(args, wl, p, rank):
@@ -495,27 +536,43 @@ def main():
     cells = res["info"]["grid"]["base"][-1]
     per_particle = dict(ab)
     dom = max(("pass_a", "pass_b"), key=lambda k: res["phase_ms"][k])
-    ach = per_particle[dom] * n / (res["phase_ms"][dom] * 1e-3) / 1e9
+    t_dom = res["phase_ms"][dom] * 1e-3
+    st0 = res["info"]["stats"]
+    fpp = 2 * st0["force_pairs"] / n  # ordered force pairs per particle
+    dpp = fpp + 1.0                   # density pairs (the particle itself included)
+    if dom == "pass_a":
+        flop_pp = dpp * (FLOP_PER_PAIR["distance"] + FLOP_PER_PAIR["density"]) + fpp * FLOP_PER_PAIR["force"]
+    else:
+        flop_pp = fpp * (FLOP_PER_PAIR["distance"] + FLOP_PER_PAIR["visc"])
+    tflops = flop_pp * n / t_dom / 1e12
+    ach_gbs = per_particle[dom] * n / t_dom / 1e9
     step_bytes = sum(per_particle.values()) * n
-    traffic = None
+    traffic, tsrc = None, "not captured for this workload"
     if (dom == "pass_a" and wl["dim"] == 3 and wl["precision"] == "fp32" and args.skin == 0.0
             and args.cell_factor == 0.0):
-        traffic = PASS_A_DRAM_BYTES_PER_PARTICLE_3D_FP32 * n
-    roof = {"kernel": "k_pass_a" if dom == "pass_a" else "k_pass_b", "bound": "hbm", "achieved": ach,
-            "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": traffic,
-            "traffic_source": "ncu dram bytes per particle at 1,048,576 particles, scaled by the particle count"
-                              if traffic else None,
-            "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else "fallback",
-            "alg_bytes_per_particle": per_particle[dom],
-            "step_alg_bytes_per_particle": sum(per_particle.values()),
-            "step_achieved_gbs": step_bytes / (res["ms_step"] * 1e-3) / 1e9,
+        bpp, tsrc = profiled_traffic_per_particle()
+        if bpp is not None:
+            traffic = bpp * n
+            tsrc = f"ncu dram bytes per particle at 1,048,576 particles (sources {tsrc}), x particle count"
+    # the pair passes are bound by instruction issue (ncu: issue active ~74 %,
+    # half the lanes idle on screened list entries), not by DRAM: the bound is
+    # the FP32 pipe, the achieved figure the pair arithmetic the equations need
+    roof = {"kernel": "k_pass_a" if dom == "pass_a" else "k_pass_b", "bound": "alu",
+            "achieved": tflops, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": tflops / FP32_PEAK_TFLOPS,
+            "traffic": traffic, "traffic_source": tsrc,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz (FP32 CUDA-core peak)",
+            "alg_flop_per_particle": flop_pp,
+            "hbm": {"alg_bytes_per_particle": per_particle[dom], "achieved_gbs": ach_gbs, "peak_gbs": hbm,
+                    "frac": ach_gbs / hbm, "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "dram_gbs_from_traffic": traffic / t_dom / 1e9 if traffic else None,
+                    "step_alg_bytes_per_particle": sum(per_particle.values()),
+                    "step_achieved_gbs": step_bytes / (res["ms_step"] * 1e-3) / 1e9},
             "phase_ms": res["phase_ms"]}
-    st0 = res["info"]["stats"]
-    fpp = 2 * st0["force_pairs"] / n
-    flop = fpp * (FLOP_PER_PAIR["density"] + FLOP_PER_PAIR["force"] + FLOP_PER_PAIR["visc"])
-    roof["fp32_pair_flop_per_particle"] = flop
+    flop = fpp * (FLOP_PER_PAIR["force"] + FLOP_PER_PAIR["visc"]) + dpp * FLOP_PER_PAIR["density"] + \
+        (dpp + fpp) * FLOP_PER_PAIR["distance"]
+    roof["fp32_pair_flop_per_particle_step"] = flop
     roof["fp32_tflops_step"] = flop * n / (res["ms_step"] * 1e-3) / 1e12
-    roof["fp32_frac_of_nominal_peak"] = roof["fp32_tflops_step"] / FP32_PEAK_TFLOPS
+    roof["fp32_frac_of_nominal_peak_step"] = roof["fp32_tflops_step"] / FP32_PEAK_TFLOPS
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         q, pos, col, desc = oracle_workload_sample(wl)

@@ -107,7 +107,7 @@ typedef struct {
   int32_t kernel_id;   /* 0: Wendland C2 (the only one) */
   uint64_t seed;       /* seed of the initial sampling (Philox4x32-10) */
   double cell_factor;  /* finest cell edge / smallest support; 0 -> 1.0 */
-  int32_t block_size;  /* threads per block of the neighbour kernels; 0 -> auto */
+  int32_t block_size;  /* threads per block of the pair passes: 0 (256), 128 or 256 */
   int32_t use_graph;   /* 1: sph_step replays a captured CUDA graph of one step */
   int32_t record_fields; /* 1: keep rho, a_n and a~ of the last step for sph_get_field */
   int32_t list_capacity; /* neighbour-list entries per particle; 0 -> auto */
@@ -218,6 +218,20 @@ sph_status sph_create_background(const sph_domain* dom, const sph_field* field, 
  * Resets the step counter. Errors: INVALID_ARG, CUDA. */
 sph_status sph_set_state(sph_handle* h, const double* xyz, const uint8_t* col, int32_t on_device);
 
+/* Launch configuration (no counterpart in the paper: it changes how the work
+ * is spread over the GPU, not what is computed). pass_threads: threads per
+ * block of the two pair passes, 128 or 256 (0: keep); list_ppw: particles per
+ * warp of the neighbour-list build, 1 (a warp walks one target's candidates)
+ * or 32 (a thread per target) (0: keep); cell_factor: finest cell edge over
+ * the smallest support, > 0 (0: keep), which rebuilds the multi-resolution
+ * grid. The first two leave every result bit for bit unchanged; a new cell
+ * factor changes the cell order and so the order of each particle's sums
+ * (rounding only). The next step rebuilds the neighbour list; captured
+ * graphs are re-captured. Synchronises. Errors: INVALID_ARG, OOM,
+ * CELL_OVERFLOW. sph_get_tuning reads the configuration in use. */
+sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, int32_t list_ppw, double cell_factor);
+sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, int32_t* list_ppw, double* cell_factor);
+
 /* Advance n_steps relaxation steps (Algorithm 1): cell list,
  * density + pressure + surface-tension forces, time step, viscous force,
  * two-stage integration, level-set projection. Asynchronous on the handle's
@@ -255,6 +269,18 @@ sph_status sph_get_colors(sph_handle* h, uint8_t* out, int32_t on_device);
 /* Reductions of the last step (FP64 on the device). Synchronises and reports
  * latched device errors. */
 sph_status sph_get_stats(sph_handle* h, sph_stats* out);
+
+/* Per-colour size of the partition. The method partitions the domain into
+ * sub-domains (one per colour) that are to be of equal size (Sec. 2.1) and
+ * gives each its share of the total mass (Sec. 2.3, Eq. mass_for_partition).
+ * volume[c] (n_colors doubles) receives V_c = sum over the particles of
+ * colour c of m_i/rho_i (unit mass, rho_i the summation density of Eq.
+ * density_sum from the last step), reduced in FP64 on the device in a fixed
+ * order (repeated calls give identical bits); count[c] (n_colors int64, may
+ * be NULL) the number of particles of colour c, i.e. its mass. Host arrays.
+ * Errors: STATE when no step was taken since the state was set (create,
+ * sph_set_state, sph_load, sph_backward). Synchronises. */
+sph_status sph_get_color_volumes(sph_handle* h, double* volume, int64_t* count);
 
 /* Per-particle results of the last step, particle-id order, as doubles:
  * SPH_OUT_RHO (n): summation density (Eq. density_sum);
@@ -365,11 +391,33 @@ typedef struct sph_batch sph_batch;
 sph_status sph_batch_create(const sph_instance_desc* descs, int32_t n_inst, const sph_alloc* alloc, void* stream,
                             int32_t n_branches, sph_batch** out);
 
-/* Autotuner: time steps_each graph-launched steps for each candidate branch
- * count, keep the fastest; instances are dealt longest first (particles x
- * dimension cost) to the least-loaded branch. The trial steps are undone (the
+/* Autotuner: time steps_each graph-launched steps of the whole batch for each
+ * candidate branch count and keep the fastest (instances are dealt longest
+ * first, particles x dimension cost, to the least-loaded branch); then, one
+ * knob at a time from the best so far, the launch configuration of every
+ * instance (sph_set_tuning): 128 or 256 threads per block of the pair passes,
+ * 1 or 32 particles per warp of the list build, cell factor 0.75, 1 or 1.5.
+ * Each trial starts from the same state; the trial steps are undone (the
  * state and step counters are restored). Synchronises. */
 sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_candidates, int32_t steps_each);
+
+/* One configuration the autotuner timed (or chose): graph branches, threads
+ * per block of the pair passes, particles per warp of the list build, cell
+ * factor, and its device time per batched step. */
+typedef struct {
+  int32_t branches;
+  int32_t pass_threads;
+  int32_t list_ppw;
+  int32_t reserved;
+  double cell_factor;
+  float ms_per_step;
+  float reserved2;
+} sph_batch_trial;
+
+/* The autotuner's choice and its trials in order (trials may be NULL; at most
+ * cap are written; *n_trials receives their number). */
+sph_status sph_batch_tuning(const sph_batch* b, sph_batch_trial* chosen, sph_batch_trial* trials, int32_t cap,
+                            int32_t* n_trials);
 
 /* n_steps steps of every instance, one graph launch per step (async). */
 sph_status sph_batch_step(sph_batch* b, int32_t n_steps);
@@ -383,7 +431,9 @@ sph_status sph_batch_step_each(sph_batch* b, int32_t n_steps);
 sph_status sph_batch_get(sph_batch* b, int32_t k, sph_handle** h);
 
 /* Instance count, branch count in use, and the autotuner's trials (n_tuned
- * entries of candidate branch count and ms per step; arrays may be NULL). */
+ * entries of branch count and ms per step; arrays may be NULL, else they hold
+ * at least n_candidates + 4 entries after sph_batch_tune; sph_batch_tuning
+ * gives the trials' full configurations). */
 sph_status sph_batch_info(const sph_batch* b, int32_t* n_inst, int32_t* n_branches, int32_t* n_tuned,
                           int32_t* tuned_branches, float* tuned_ms);
 

@@ -265,6 +265,21 @@ def cell_keys(p, pos, grid):
     return keys, h
 
 
+def color_volumes(rho, col, n_colors):
+    """Per colour c: V_c = sum over its particles of m_i/rho_i (unit mass,
+    Eq. mass_SPH_particle; rho from Eq. density_sum) and the particle count,
+    the size and mass of each sub-domain of the partition (Sec. 2.1, 2.3).
+    FP64 sums in particle order."""
+    col = np.asarray(col)
+    v = np.zeros(n_colors)
+    k = np.zeros(n_colors, np.int64)
+    for c in range(n_colors):
+        m = col == c
+        v[c] = float(np.sum(1.0 / np.asarray(rho, dtype=np.float64)[m]))
+        k[c] = int(m.sum())
+    return v, k
+
+
 def cell_order(keys):
     """Particle ids ordered by (cell key, particle id): a stable sort of the
     keys, which leaves equal keys in ascending id order."""

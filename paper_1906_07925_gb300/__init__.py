@@ -115,6 +115,7 @@ class Relaxation:
         self.dim = int(problem.dim)
         self.n = int(n_particles)
         ncol = int(n_colors if n_colors is not None else getattr(problem, "n_colors", 1))
+        self.n_colors = ncol
         dom, fld, par = problem_structs(problem, precision, seed, cell_factor, use_graph, record_fields, skin,
                                         list_capacity)
         dev, stream = self.device, self.stream
@@ -279,6 +280,23 @@ class Relaxation:
                                                fs.ctypes.data))
         return dict(dens_count=dc, force_count=fc, dens_idsum=ds, force_idsum=fs)
 
+    def set_tuning(self, pass_threads=0, list_ppw=0, cell_factor=0.0):
+        """Launch configuration (sph_set_tuning); 0 keeps a value."""
+        self._check(self.lib.sph_set_tuning(self.h, int(pass_threads), int(list_ppw), float(cell_factor)))
+
+    def tuning(self):
+        t, p, c = C.c_int32(), C.c_int32(), C.c_double()
+        self._check(self.lib.sph_get_tuning(self.h, C.byref(t), C.byref(p), C.byref(c)))
+        return dict(pass_threads=t.value, list_ppw=p.value, cell_factor=c.value)
+
+    def color_volumes(self):
+        """Per colour: sum of m/rho over its particles (the sub-domain's
+        volume, FP64 on the device) and its particle count, from the last step."""
+        v = np.zeros(self.n_colors, np.float64)
+        k = np.zeros(self.n_colors, np.int64)
+        self._check(self.lib.sph_get_color_volumes(self.h, v.ctypes.data, k.ctypes.data))
+        return v, k
+
     def cell_list(self):
         k = np.zeros(self.n, np.uint32); s = np.zeros(self.n, np.uint32)
         self._check(self.lib.sph_get_cell_list(self.h, k.ctypes.data, s.ctypes.data))
@@ -312,35 +330,84 @@ class Relaxation:
         return dict(n=n.value, dim=d.value, rho_scale=rs.value)
 
 
-def relax_fn(relaxation, n_steps, frozen_dt=True, ckpt_every=5):
-    """A torch.autograd function x0 -> x_K (n_steps steps of `relaxation`):
-    forward runs the steps from x0 (a CUDA float64 (n, dim) tensor, colours
-    kept), backward returns dL/dx0 for the incoming dL/dx_K through
-    sph_backward with both objective weights 0 (the seed alone)."""
+def relax_fn(problem, colors, n_steps, precision="fp32", lam=1.0, density_weight=1.0, frozen_dt=False,
+             ckpt_every=5, **handle_kw):
+    """K relaxation steps and the objective as a differentiable function:
+
+        f(x0, sigma0, gamma, P0, poly) -> (x_K, L)
+
+    x0: CUDA float64 (n, dim) initial positions (colours `colors` fixed);
+    sigma0, gamma, P0: scalar tensors (Eqs. sph_st_sigma, EOS_current); poly:
+    (8,) tensor, the coefficients of the target density's polynomial factor
+    (Eq. rho_target_function; rho_scale is held at problem.rho_scale, which
+    must be > 0). x_K: the positions after n_steps steps; L = density_weight
+    * sum_i (rho_i/rho_t,i - 1)^2 + lam * sum_{i<j, C_i != C_j} W(r_ij,
+    kappa h_ij) at x_K. Backward is one sph_backward call: the incoming dL/dx_K
+    is its seed (kept on the device), the incoming dL/dL scales the objective
+    weights, and it returns the gradients of all five inputs. A library handle
+    is created for each distinct parameter value and reused while the values
+    stay the same."""
     import torch
+
+    col = torch.as_tensor(np.ascontiguousarray(colors, dtype=np.uint8))
+    state = {"key": None, "r": None}
+    if not (problem.rho_scale > 0):
+        raise ValueError("relax_fn needs problem.rho_scale > 0 (held fixed)")
+
+    def handle(values):
+        key = tuple(float(v) for v in values)
+        if state["key"] != key:
+            if state["r"] is not None:
+                state["r"].close()
+            q = problem.copy(sigma0=key[0], gamma=key[1], P0=key[2], poly=list(key[3:]))
+            state["r"] = Relaxation(q, len(col), int(col.max()) + 1, precision=precision, **handle_kw)
+            state["key"] = key
+        return state["r"]
+
+    def values(sigma0, gamma, P0, poly):
+        return [float(sigma0), float(gamma), float(P0)] + [float(v) for v in poly.detach().reshape(-1).tolist()]
 
     class _Relax(torch.autograd.Function):
         @staticmethod
-        def forward(ctx, x0):
-            col = torch.from_numpy(relaxation.colors()).to(x0.device)
-            ctx.save_for_backward(x0.detach().clone(), col)
-            relaxation.set_state(x0.detach().to(torch.float64).contiguous(), col)
-            relaxation.step(n_steps)
-            out = torch.empty_like(x0, dtype=torch.float64)
-            relaxation.positions(out=out)
-            torch.cuda.current_stream().wait_stream(relaxation.stream)
-            return out
+        def forward(ctx, x0, sigma0, gamma, P0, poly):
+            r = handle(values(sigma0, gamma, P0, poly))
+            c = col.to(x0.device)
+            xs = x0.detach().to(torch.float64).contiguous()
+            ctx.save_for_backward(xs, c, sigma0, gamma, P0, poly)
+            r.set_state(xs, c)
+            r.step(n_steps)
+            out = torch.empty_like(xs)
+            r.positions(out=out)
+            torch.cuda.current_stream().wait_stream(r.stream)
+            # L at x_K: a zero-step reverse pass evaluates the objective
+            g = r.backward(0, lam=lam, density_weight=density_weight, ckpt_every=1,
+                           out=torch.empty_like(xs))
+            L = torch.tensor(g["L"], dtype=torch.float64, device=x0.device)
+            return out, L
 
         @staticmethod
-        def backward(ctx, gout):
-            x0, col = ctx.saved_tensors
-            relaxation.set_state(x0.to(torch.float64).contiguous(), col)
-            seed = gout.detach().to(torch.float64).contiguous().cpu().numpy()
-            r = relaxation.backward(n_steps, lam=0.0, density_weight=0.0, frozen_dt=frozen_dt,
-                                    ckpt_every=ckpt_every, seed=seed)
-            return torch.from_numpy(r["dpos0"]).to(gout.device, gout.dtype)
+        def backward(ctx, g_x, g_L):
+            xs, c, sigma0, gamma, P0, poly = ctx.saved_tensors
+            r = handle(values(sigma0, gamma, P0, poly))
+            r.set_state(xs, c)
+            seed = None if g_x is None else g_x.detach().to(torch.float64).contiguous()
+            wL = 0.0 if g_L is None else float(g_L)
+            dpos = torch.empty_like(xs)
+            res = r.backward(n_steps, lam=lam * wL, density_weight=density_weight * wL, frozen_dt=frozen_dt,
+                             ckpt_every=ckpt_every, seed=seed, out=dpos)
+            torch.cuda.current_stream().wait_stream(r.stream)
+            gr = res["grads"]
 
-    return _Relax.apply
+            def like(t, v):
+                return torch.as_tensor(v, dtype=t.dtype, device=t.device).reshape(t.shape)
+
+            dpoly = like(poly, [gr[f"poly{m}"] for m in range(8)][:poly.numel()])
+            return dpos, like(sigma0, gr["sigma0"]), like(gamma, gr["gamma"]), like(P0, gr["P0"]), dpoly
+
+    def f(x0, sigma0, gamma, P0, poly):
+        return _Relax.apply(x0, sigma0, gamma, P0, poly)
+
+    return f
 
 
 class Batch:
@@ -392,17 +459,23 @@ class Batch:
             raise SphError(st, self.lib.sph_batch_last_error(self.b).decode())
 
     def tune(self, candidates=(1, 4, 8, 16, 32, 64, 128), steps_each=2):
+        """Autotune the branch count, then the launch configuration (threads
+        per block of the pair passes, particles per warp of the list build,
+        cell factor); returns dict(chosen, trials, n_inst, n_branches)."""
         arr = (C.c_int32 * len(candidates))(*candidates)
         self._check(self.lib.sph_batch_tune(self.b, arr, len(candidates), int(steps_each)))
         return self.info()
 
     def info(self):
         ni, nb, nt = C.c_int32(), C.c_int32(), C.c_int32()
-        tb = (C.c_int32 * 64)()
-        tm = (C.c_float * 64)()
-        self._check(self.lib.sph_batch_info(self.b, C.byref(ni), C.byref(nb), C.byref(nt), tb, tm))
-        return dict(n_inst=ni.value, n_branches=nb.value,
-                    trials=[(tb[i], tm[i]) for i in range(nt.value)])
+        self._check(self.lib.sph_batch_info(self.b, C.byref(ni), C.byref(nb), C.byref(nt), None, None))
+        chosen = B.sph_batch_trial()
+        cap = max(nt.value, 1)
+        trials = (B.sph_batch_trial * cap)()
+        n = C.c_int32()
+        self._check(self.lib.sph_batch_tuning(self.b, C.byref(chosen), trials, cap, C.byref(n)))
+        return dict(n_inst=ni.value, n_branches=nb.value, chosen=chosen.as_dict(),
+                    trials=[trials[i].as_dict() for i in range(min(n.value, cap))])
 
     def step(self, n=1):
         self._check(self.lib.sph_batch_step(self.b, int(n)))

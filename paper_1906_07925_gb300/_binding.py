@@ -84,6 +84,15 @@ class sph_grad(C.Structure):
                 ("d_poly", C.c_double * 8)]
 
 
+class sph_batch_trial(C.Structure):
+    _fields_ = [("branches", C.c_int32), ("pass_threads", C.c_int32), ("list_ppw", C.c_int32),
+                ("reserved", C.c_int32), ("cell_factor", C.c_double), ("ms_per_step", C.c_float),
+                ("reserved2", C.c_float)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
+
+
 class sph_instance_desc(C.Structure):
     _fields_ = [("dom", sph_domain), ("field", sph_field), ("n_particles", C.c_int64), ("n_colors", C.c_int32),
                 ("reserved", C.c_int32), ("params", sph_params)]
@@ -144,6 +153,10 @@ def load():
             "sph_batch_get": [H, C.c_int32, P(H)],
             "sph_batch_info": [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
             "sph_batch_sync": [H],
+            "sph_batch_tuning": [H, P(sph_batch_trial), C.c_void_p, C.c_int32, P(C.c_int32)],
+            "sph_set_tuning": [H, C.c_int32, C.c_int32, C.c_double],
+            "sph_get_tuning": [H, P(C.c_int32), P(C.c_int32), P(C.c_double)],
+            "sph_get_color_volumes": [H, C.c_void_p, C.c_void_p],
             "sph_eval_forces_noalloc": [P(sph_domain), P(sph_field), P(sph_params), C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
         }

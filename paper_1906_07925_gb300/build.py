@@ -16,8 +16,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libsphmesh.so")
-SOURCES = ["sph_api.cu", "sph_cells.cu", "sph_init.cu", "sph_noalloc.cu", "sph_step_2d.cu", "sph_step_3d.cu",
-           "sph_adjoint_2d.cu", "sph_adjoint_3d.cu"]
+SOURCES = ["sph_api.cu", "sph_cells.cu", "sph_colors.cu", "sph_init.cu", "sph_noalloc.cu", "sph_step_2d.cu",
+           "sph_step_3d.cu", "sph_adjoint_2d.cu", "sph_adjoint_3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -53,6 +53,12 @@ struct sph_handle {
   int auto_window = 0;  // > 0: automatic ramp start (sph_auto_ramp)
   double auto_tol = 0.0, auto_theta = 0.0;
   bool recorded = false;
+  bool rho_valid = false;
+  uint32_t cells_cap = 0;  // cells the cell arrays hold  // S.rho holds the summation density of the current positions' last pass A
+  // per-colour volume scratch (sph_get_color_volumes; allocated on first use)
+  double* cv_part = nullptr;
+  unsigned long long* cv_cpart = nullptr;
+  double* cv_out = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int graph_record = -1;
   // reverse-pass buffers (allocated by the first sph_backward)
@@ -275,6 +281,21 @@ sph_status ensure_graph(sph_handle* h, int record) {
   return SPH_OK;
 }
 
+// every captured graph of the handle (the step's and the reverse pass's): they
+// bake launch configurations, grids and frames into their nodes
+void drop_graphs(sph_handle* h) {
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  h->gexec = nullptr;
+  h->graph_record = -1;
+  for (auto* v : {&h->adj.g_rerun, &h->adj.g_rev[0][0], &h->adj.g_rev[0][1], &h->adj.g_rev[1][0],
+                  &h->adj.g_rev[1][1]})
+    for (cudaGraphExec_t& g : *v)
+      if (g) {
+        cudaGraphExecDestroy(g);
+        g = nullptr;
+      }
+}
+
 // whole control block (set-up / set_state: the next step rebuilds the list)
 sph_status write_ctl_all(sph_handle* h) {
   StepCtl c{};
@@ -330,6 +351,7 @@ sph_status do_set_state(sph_handle* h, const double* xyz_dev, const uint8_t* col
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
   h->steps = 0;
   h->recorded = false;
+  h->rho_valid = false;
   return write_ctl_all(h);
 }
 
@@ -362,6 +384,7 @@ sph_status set_state_at(sph_handle* h, const double* xyz_dev, const uint8_t* col
   if (e != cudaSuccess) return cuda_fail(h, e, "set_state");
   h->steps = step;
   h->recorded = false;
+  h->rho_valid = false;
   return write_ctl_all(h);
 }
 
@@ -717,6 +740,7 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   S.dim = d;
   S.fp64 = h->prec == SPH_PREC_FP64;
   S.cap = h->par.list_capacity > 0 ? h->par.list_capacity : auto_capacity(h);
+  S.pass_threads = h->par.block_size == 128 ? 128 : 256;
   const size_t v4 = S.fp64 ? 32 : 16, t1 = S.fp64 ? 8 : 4;
   const size_t N = (size_t)std::max<int64_t>(n_particles, 1);
   uint8_t* tmpb;
@@ -741,6 +765,7 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   SPH_TRY(grab(h, S.plist, N * (size_t)S.cap));
   SPH_TRY(grab(h, S.pcount, N));
   SPH_TRY(grab(h, S.cnt, (size_t)S.total_cells));
+  h->cells_cap = S.total_cells;
   SPH_TRY(grab(h, S.cstart, (size_t)S.total_cells + 1));
   SPH_TRY(grab(h, S.scan_part, (size_t)S.total_cells / 4096 + 2));
   SPH_TRY(grab(h, S.partials, N / 128 + 2));
@@ -785,6 +810,10 @@ static sph_status create_common(const sph_domain* dom, const sph_field* field, c
   }
   if (vs == SPH_OK && (params->skin < 0 || params->list_capacity < 0)) {
     why = "skin and list_capacity must be >= 0";
+    vs = SPH_ERR_INVALID_ARG;
+  }
+  if (vs == SPH_OK && params->block_size != 0 && params->block_size != 128 && params->block_size != 256) {
+    why = "block_size must be 0, 128 or 256";
     vs = SPH_ERR_INVALID_ARG;
   }
   if (vs != SPH_OK) {
@@ -850,6 +879,62 @@ sph_status sph_set_surface(sph_handle* h, const uint8_t* flags) {
   return SPH_OK;
 }
 
+sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, int32_t list_ppw, double cell_factor) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  if ((pass_threads != 0 && pass_threads != 128 && pass_threads != 256) ||
+      (list_ppw != 0 && list_ppw != 1 && list_ppw != 32) || !(cell_factor >= 0.0) || cell_factor > 16.0)
+    return fail(h, SPH_ERR_INVALID_ARG, "pass_threads in {0, 128, 256}, list_ppw in {0, 1, 32}, 0 <= cell_factor <= 16");
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  drop_graphs(h);
+  if (pass_threads) h->S.pass_threads = pass_threads;
+  if (list_ppw) h->S.list_ppw = list_ppw;
+  const double cf_now = h->par.cell_factor > 0 ? h->par.cell_factor : 1.0;
+  if (cell_factor > 0 && cell_factor != cf_now) {
+    HostGrid hg;
+    const std::string why = grid_setup(h->dom, h->par.kappa, cell_factor, h->hmin, h->hmax, h->lip_h, hg);
+    if (!why.empty())
+      return fail(h, why == "cell grid too large" ? SPH_ERR_CELL_OVERFLOW : SPH_ERR_INVALID_ARG, why);
+    const uint32_t cells = hg.base[hg.n_levels];
+    if (cells > h->cells_cap) {  // larger cell arrays (the old ones are released with the handle)
+      uint32_t *cnt, *cstart, *part;
+      SPH_TRY(grab(h, cnt, (size_t)cells));
+      SPH_TRY(grab(h, cstart, (size_t)cells + 1));
+      SPH_TRY(grab(h, part, (size_t)cells / 4096 + 2));
+      h->S.cnt = cnt;
+      h->S.cstart = cstart;
+      h->S.scan_part = part;
+      h->cells_cap = cells;
+    }
+    SPH_CUDA(h, cudaMemsetAsync(h->S.cnt, 0, sizeof(uint32_t) * cells, h->stream));
+    h->hg = hg;
+    h->S.total_cells = cells;
+    h->par.cell_factor = cell_factor;
+    setup_frames(h);
+    for (DevState& T : h->adj.tape) {
+      T.cnt = h->S.cnt;
+      T.cstart = h->S.cstart;
+      T.scan_part = h->S.scan_part;
+      T.total_cells = cells;
+    }
+  }
+  for (DevState& T : h->adj.tape) {
+    T.pass_threads = h->S.pass_threads;
+    T.list_ppw = h->S.list_ppw;
+  }
+  // the next step rebuilds the list (and, after a new grid, the views)
+  SPH_CUDA(h, launch_request_rebuild(h->S, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  return SPH_OK;
+}
+
+sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, int32_t* list_ppw, double* cell_factor) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  if (pass_threads) *pass_threads = h->S.pass_threads;
+  if (list_ppw) *list_ppw = h->S.list_ppw;
+  if (cell_factor) *cell_factor = h->par.cell_factor > 0 ? h->par.cell_factor : 1.0;
+  return SPH_OK;
+}
+
 sph_status sph_step(sph_handle* h, int32_t n_steps) {
   if (!h || n_steps < 0) return fail(h, SPH_ERR_INVALID_ARG, "bad step count");
   if (h->n == 0 || n_steps == 0) {
@@ -865,6 +950,7 @@ sph_status sph_step(sph_handle* h, int32_t n_steps) {
   }
   h->steps += n_steps;
   h->recorded = record;
+  h->rho_valid = true;
   return SPH_OK;
 }
 
@@ -890,6 +976,7 @@ sph_status sph_step_profiled(sph_handle* h, int32_t n_steps, float* ms_out) {
   }
   for (auto& e : ev) cudaEventDestroy(e);
   h->recorded = record && st == SPH_OK;
+  h->rho_valid = h->rho_valid || st == SPH_OK;
   return st;
 }
 
@@ -1001,6 +1088,42 @@ sph_status sph_get_stats(sph_handle* h, sph_stats* out) {
     h->t0 = ctl.t0;
     h->t1 = ctl.t1;
   }
+  return status_from_flags(h, flags);
+}
+
+sph_status sph_get_color_volumes(sph_handle* h, double* volume, int64_t* count) {
+  if (!h || !volume) return fail(h, SPH_ERR_INVALID_ARG, "null output");
+  if (!h->rho_valid) return fail(h, SPH_ERR_STATE, "no step since the state was set: no densities to sum");
+  const int nc = h->ncol;
+  if (h->n == 0) {
+    for (int c = 0; c < nc; ++c) {
+      volume[c] = 0.0;
+      if (count) count[c] = 0;
+    }
+    return SPH_OK;
+  }
+  if (!h->cv_out) {
+    const size_t nb = (size_t)color_volume_blocks((int)h->n);
+    SPH_TRY(grab(h, h->cv_part, nb * 256));
+    SPH_TRY(grab(h, h->cv_cpart, nb * 256));
+    SPH_TRY(grab(h, h->cv_out, 512));
+  }
+  long long* cnt_d = (long long*)(h->cv_out + 256);
+  cudaError_t e = h->prec == SPH_PREC_FP64
+                      ? launch_color_volumes<double>(h->S, h->cv_part, h->cv_cpart, h->cv_out, cnt_d, h->stream)
+                      : launch_color_volumes<float>(h->S, h->cv_part, h->cv_cpart, h->cv_out, cnt_d, h->stream);
+  if (e != cudaSuccess) return cuda_fail(h, e, "color volumes");
+  double v[256];
+  long long k[256];
+  SPH_CUDA(h, cudaMemcpyAsync(v, h->cv_out, sizeof v, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaMemcpyAsync(k, cnt_d, sizeof k, cudaMemcpyDeviceToHost, h->stream));
+  SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+  for (int c = 0; c < nc; ++c) {
+    volume[c] = v[c];
+    if (count) count[c] = (int64_t)k[c];
+  }
+  int flags = 0;
+  SPH_TRY(read_flags(h, &flags));
   return status_from_flags(h, flags);
 }
 
@@ -1283,8 +1406,10 @@ struct sph_batch {
   std::vector<cudaEvent_t> ev;  // [0]: fork, [1 + b]: join of branch b
   cudaGraphExec_t gexec = nullptr;
   int n_branches = 0;
-  std::vector<float> tuned_ms;  // per candidate branch count (autotuner)
+  std::vector<float> tuned_ms;  // per trial of the autotuner: its branch count and ms per step
   std::vector<int> tuned_b;
+  std::vector<sph_batch_trial> trials;  // every trial with its full configuration
+  sph_batch_trial chosen{};
   std::string err;
 };
 
@@ -1436,47 +1561,112 @@ sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_can
     }
     return SPH_OK;
   };
+  // the same launch configuration on every instance
+  auto configure = [&](const sph_batch_trial& c) -> sph_status {
+    for (sph_handle* h : b->inst) {
+      sph_status s = sph_set_tuning(h, c.pass_threads, c.list_ppw, c.cell_factor);
+      if (s != SPH_OK) return s;
+    }
+    return SPH_OK;
+  };
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   b->tuned_b.clear();
   b->tuned_ms.clear();
-  int best = 0;
-  float best_ms = 0.0f;
-  sph_status st = SPH_OK;
-  for (int c = 0; c < n_candidates && st == SPH_OK; ++c) {
-    const int nb = std::max(1, std::min<int>(candidates[c], (int)b->inst.size()));
-    st = batch_capture(b, nb);
-    if (st != SPH_OK) break;
-    st = restore();
-    if (st != SPH_OK) break;
-    cudaGraphLaunch(b->gexec, b->stream);  // warm-up (rebuilds every list)
+  b->trials.clear();
+  // one trial: configure, capture, restore, a warm-up step (it rebuilds
+  // every list), then steps_each timed graph launches
+  auto trial = [&](sph_batch_trial c, float* ms_out) -> sph_status {
+    sph_status st = configure(c);
+    if (st == SPH_OK) st = batch_capture(b, c.branches);
+    if (st == SPH_OK) st = restore();
+    if (st != SPH_OK) return st;
+    cudaGraphLaunch(b->gexec, b->stream);
     cudaEventRecord(e0, b->stream);
     for (int s = 0; s < steps_each; ++s) cudaGraphLaunch(b->gexec, b->stream);
     cudaEventRecord(e1, b->stream);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
-      st = batch_fail(b, SPH_ERR_CUDA, "tuning run failed");
-      break;
-    }
+    if (cudaEventSynchronize(e1) != cudaSuccess) return batch_fail(b, SPH_ERR_CUDA, "tuning run failed");
     float ms = 0.0f;
     cudaEventElapsedTime(&ms, e0, e1);
     ms /= (float)steps_each;
-    b->tuned_b.push_back(nb);
+    c.ms_per_step = ms;
+    b->trials.push_back(c);
+    b->tuned_b.push_back(c.branches);
     b->tuned_ms.push_back(ms);
-    if (best == 0 || ms < best_ms) {
-      best = nb;
+    *ms_out = ms;
+    return SPH_OK;
+  };
+  sph_handle* h0 = b->inst[0];
+  sph_batch_trial best{};
+  best.branches = 0;
+  best.pass_threads = h0->S.pass_threads;
+  best.list_ppw = h0->S.list_ppw;
+  best.cell_factor = h0->par.cell_factor > 0 ? h0->par.cell_factor : 1.0;
+  float best_ms = 0.0f;
+  sph_status st = SPH_OK;
+  // 1. branch count
+  for (int c = 0; c < n_candidates && st == SPH_OK; ++c) {
+    sph_batch_trial t = best;
+    t.branches = std::max(1, std::min<int>(candidates[c], (int)b->inst.size()));
+    float ms = 0.0f;
+    st = trial(t, &ms);
+    if (st == SPH_OK && (best.branches == 0 || ms < best_ms)) {
+      best = t;
       best_ms = ms;
     }
   }
+  // 2. then, one knob at a time from the best so far: threads per block of
+  // the pair passes, particles per warp of the list build, cell factor
+  const int threads_alt[] = {128, 256};
+  const int ppw_alt[] = {1, 32};
+  const double cf_alt[] = {0.75, 1.0, 1.5};
+  for (int v : threads_alt) {
+    if (st != SPH_OK || v == best.pass_threads) continue;
+    sph_batch_trial t = best;
+    t.pass_threads = v;
+    float ms = 0.0f;
+    st = trial(t, &ms);
+    if (st == SPH_OK && ms < best_ms) { best = t; best_ms = ms; }
+  }
+  for (int v : ppw_alt) {
+    if (st != SPH_OK || v == best.list_ppw) continue;
+    sph_batch_trial t = best;
+    t.list_ppw = v;
+    float ms = 0.0f;
+    st = trial(t, &ms);
+    if (st == SPH_OK && ms < best_ms) { best = t; best_ms = ms; }
+  }
+  for (double v : cf_alt) {
+    if (st != SPH_OK || v == best.cell_factor) continue;
+    sph_batch_trial t = best;
+    t.cell_factor = v;
+    float ms = 0.0f;
+    st = trial(t, &ms);
+    if (st == SPH_OK && ms < best_ms) { best = t; best_ms = ms; }
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  if (st == SPH_OK) st = configure(best);
   if (st == SPH_OK) st = restore();
   saved.clear();
   cols.clear();
   if (st != SPH_OK) return st;
-  st = batch_capture(b, best);
+  best.ms_per_step = best_ms;
+  b->chosen = best;
+  st = batch_capture(b, best.branches);
   if (st != SPH_OK) return st;
   return cudaStreamSynchronize(b->stream) == cudaSuccess ? SPH_OK : SPH_ERR_CUDA;
+}
+
+sph_status sph_batch_tuning(const sph_batch* b, sph_batch_trial* chosen, sph_batch_trial* trials, int32_t cap,
+                            int32_t* n_trials) {
+  if (!b) return SPH_ERR_INVALID_ARG;
+  if (chosen) *chosen = b->chosen;
+  const int nt = (int)b->trials.size();
+  if (n_trials) *n_trials = nt;
+  for (int q = 0; trials && q < nt && q < cap; ++q) trials[q] = b->trials[q];
+  return SPH_OK;
 }
 
 sph_status sph_batch_step(sph_batch* b, int32_t n_steps) {
@@ -1490,6 +1680,7 @@ sph_status sph_batch_step(sph_batch* b, int32_t n_steps) {
   for (sph_handle* h : b->inst) {
     h->steps += n_steps;
     h->recorded = h->par.record_fields != 0;
+    h->rho_valid = h->rho_valid || n_steps > 0;
   }
   return SPH_OK;
 }
@@ -1507,6 +1698,7 @@ sph_status sph_batch_step_each(sph_batch* b, int32_t n_steps) {
   for (sph_handle* h : b->inst) {
     h->steps += n_steps;
     h->recorded = h->par.record_fields != 0;
+    h->rho_valid = h->rho_valid || n_steps > 0;
   }
   return SPH_OK;
 }

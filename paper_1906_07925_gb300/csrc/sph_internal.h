@@ -16,6 +16,8 @@ namespace sph {
 // ctl->vp (pass B writes the next step's views while pass A/B read the current).
 struct DevState {
   int n = 0, dim = 2, fp64 = 0, cap = 0;
+  int pass_threads = 256;  // threads per block of the pair passes (128 or 256)
+  int list_ppw = 1;        // neighbour-list build: 1 target per warp, or 32 (one per thread)
   void* X[2] = {nullptr, nullptr};       // int64 x, y, z (+ pad) per particle
   uint32_t* meta[2] = {nullptr, nullptr};  // colour
   uint32_t* pid[2] = {nullptr, nullptr};   // particle id
@@ -131,6 +133,14 @@ cudaError_t launch_objective(const DevState& S, const Frame<T>& F, const Phys<T>
 // scal into tape.X[0], meta[0], pid[0], view[0], ctl, scal
 template <int D, class T>
 cudaError_t launch_tape_snapshot(const DevState& S, const DevState& tape, cudaStream_t st);
+
+// per-colour volume sum m/rho and particle count over the current order (rho
+// of the last pass A); vpart/cpart hold color_volume_blocks(n) x 256 partials,
+// vol/cnt 256 results (device)
+int color_volume_blocks(int n);
+template <class T>
+cudaError_t launch_color_volumes(const DevState& S, double* vpart, unsigned long long* cpart, double* vol,
+                                 long long* cnt, cudaStream_t st);
 
 // initial sampling (create)
 struct FieldBounds {

@@ -17,6 +17,7 @@
 // listed pair, so the list only saves the search, never changes a result.
 #pragma once
 
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 #include <type_traits>
@@ -37,10 +38,9 @@
 #else
 #define SPH_PLIST_STORE(p, v) (*(p) = (v))
 #endif
-// threads per block of the pair passes
-#ifndef SPH_PASS_THREADS
-#define SPH_PASS_THREADS 256
-#endif
+// the pair passes are compiled for 128 and 256 threads per block
+// (DevState::pass_threads picks one at launch); resident blocks per SM asked
+// of them scale so that the register budget per thread is the same
 #ifndef SPH_PASSB_MIN_BLOCKS
 #define SPH_PASSB_MIN_BLOCKS SPH_PASS_MIN_BLOCKS
 #endif
@@ -49,6 +49,20 @@
 #endif
 
 namespace sph {
+
+// streaming multiprocessors of the current device (queried once per process)
+inline int sm_count() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+      cached = nsm;
+    else
+      return 152;
+  }
+  return cached;
+}
 
 // ---------------------------------------------------------------- views ----
 template <class T> struct ViewOf;
@@ -400,6 +414,188 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicMax(&ctl->lmax, wmax);
 }
 
+// The same lists built by one warp per target: the warp's lanes enumerate the
+// target's candidate rows 32 at a time (lane q decodes row q of the levels,
+// z and y offsets the search visits, in the order the per-thread build walks
+// them, and looks up its row's range of sorted particles), a warp prefix sum
+// of the row lengths flattens the rows into one candidate sequence, and the
+// candidates are tested 32 at a time, each lane finding its row by a binary
+// search over the prefix sums. Accepted candidates are written in candidate
+// order (ballot ranks), so every list holds exactly the entries, in exactly
+// the order, of the per-thread build; the lanes stay busy whatever the row
+// lengths.
+template <int D, class T>
+__global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build_warp(int n, StepCtl* __restrict__ ctl,
+                                                    const LL4* __restrict__ X0, const LL4* __restrict__ X1,
+                                                    const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
+                                                    const typename ViewOf<T>::type* __restrict__ v0,
+                                                    const typename ViewOf<T>::type* __restrict__ v1,
+                                                    const uint32_t* __restrict__ cstart, Frame<T> F, Grid<T> G,
+                                                    T kappa, int cap, uint32_t* __restrict__ list,
+                                                    uint32_t* __restrict__ lcount, int* __restrict__ err) {
+  using VT = typename ViewOf<T>::type;
+  if (!ctl->rebuild) return;
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
+  const int buf = ctl->buf;
+  const VT* __restrict__ view = ctl->vp ? v1 : v0;
+  const uint32_t* __restrict__ meta = buf ? m1 : m0;
+  const int nwarps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
+  int wmax = 0;
+  bool any_over = false;
+  // targets are dealt to warps round-robin: neighbouring warps take
+  // neighbouring targets (and so the same cells) at the same time
+  for (int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); i < n; i += nwarps) {
+    const LL4 X = (buf ? X1 : X0)[i];
+    const VT vi = view[i];
+    const T hv = view_h(vi);
+    const T sk = F.skin * hv;
+    const T sk_hv = F.skin;
+    const T lip = G.lip_h;
+    T hhi = hv, Rs = kappa * hv * G.rfac + sk * (T(1) + T(0.5) * kappa * lip);
+    for (int it = 0; it < 2; ++it) {
+      hhi = hv * T(1.00001) + lip * Rs;
+      const T shi = sk * hhi / hv;
+      Rs = kappa * hhi * G.rfac + shi * (T(1) + T(0.5) * kappa * lip);
+      Rs = Rs > kappa * hv * G.rfac ? Rs : kappa * hv * G.rfac;
+    }
+    const T hlo = hv * T(0.99999) - lip * Rs;
+    const T qv = F.qv;
+    const int l0 = level_of_h(G, hlo * qv), l1 = level_of_h(G, hhi * qv);
+    const T R2 = Rs * Rs;
+    // rows of every searched level: (l, dz, dy) with dy fastest
+    int nrows = 0;
+    for (int l = l0; l <= l1; ++l) {
+      const int sh = G.cshift + l;
+      const T c = G.cellv[l], ic = T(1) / c;
+      const long long cyl = min((long long)G.ny[l] - 1, X.y >> sh);
+      const long long czl = D == 3 ? min((long long)G.nz[l] - 1, X.z >> sh) : 0;
+      const T fy = (T)((double)(X.y - (cyl << sh)) * F.s2v);
+      const T fz = D == 3 ? (T)((double)(X.z - (czl << sh)) * F.s2v) : T(0);
+      const int nyr = (int)dfloor((fy + Rs) * ic) - (int)dfloor((fy - Rs) * ic) + 1;
+      const int nzr = D == 3 ? (int)dfloor((fz + Rs) * ic) - (int)dfloor((fz - Rs) * ic) + 1 : 1;
+      nrows += nyr * nzr;
+    }
+    int cnt = 0;
+    bool over = false;
+    T reach = 0;
+    for (int r0 = 0; r0 < nrows; r0 += 32) {
+      // lane q: row r0 + q -> its range [jb, je) of candidates
+      int jb = 0, len = 0;
+      int q = r0 + lane;
+      if (q < nrows) {
+        for (int l = l0; l <= l1; ++l) {
+          const int sh = G.cshift + l;
+          const long long cxl = min((long long)G.nx[l] - 1, X.x >> sh);
+          const long long cyl = min((long long)G.ny[l] - 1, X.y >> sh);
+          const long long czl = D == 3 ? min((long long)G.nz[l] - 1, X.z >> sh) : 0;
+          const T c = G.cellv[l], ic = T(1) / c;
+          const T fx = (T)((double)(X.x - (cxl << sh)) * F.s2v);
+          const T fy = (T)((double)(X.y - (cyl << sh)) * F.s2v);
+          const T fz = D == 3 ? (T)((double)(X.z - (czl << sh)) * F.s2v) : T(0);
+          const int ylo = (int)dfloor((fy - Rs) * ic), nyr = (int)dfloor((fy + Rs) * ic) - ylo + 1;
+          const int zlo = D == 3 ? (int)dfloor((fz - Rs) * ic) : 0;
+          const int nzr = D == 3 ? (int)dfloor((fz + Rs) * ic) - zlo + 1 : 1;
+          if (q >= nyr * nzr) {
+            q -= nyr * nzr;
+            continue;
+          }
+          const int dz = zlo + q / nyr, dy = ylo + q % nyr;
+          const long long czz = czl + dz, cyy = cyl + dy;
+          if ((D == 3 && (czz < 0 || czz >= G.nz[l])) || cyy < 0 || cyy >= G.ny[l]) break;
+          T dzp = 0;
+          if (D == 3) {
+            const T zrel = fz - (T)dz * c;
+            dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
+          }
+          const T yrel = fy - (T)dy * c;
+          const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
+          const T dp2 = dyp * dyp + dzp * dzp;
+          if (dp2 >= R2) break;
+          const T half = dsqrt(R2 - dp2);
+          long long x0 = cxl + (long long)dfloor((fx - half) * ic);
+          long long x1 = cxl + (long long)dfloor((fx + half) * ic);
+          x0 = x0 < 0 ? 0 : x0;
+          x1 = x1 > G.nx[l] - 1 ? G.nx[l] - 1 : x1;
+          if (x0 > x1) break;
+          const uint32_t krow =
+              G.base[l] + (uint32_t)G.nx[l] * ((uint32_t)cyy + (uint32_t)G.ny[l] * (uint32_t)(D == 3 ? czz : 0));
+          jb = (int)cstart[krow + (uint32_t)x0];
+          len = (int)cstart[krow + (uint32_t)x1 + 1] - jb;
+          break;
+        }
+      }
+      // flatten the rows: inclusive prefix of the lengths
+      int incl = len;
+  #pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const int total = __shfl_sync(full, incl, 31);
+      const int first = incl - len;  // first flattened index of this lane's row
+      for (int b = 0; b < total; b += 32) {
+        const int cidx = b + lane;
+        // row holding cidx: the number of rows whose inclusive prefix is <= cidx
+        int r = 0;
+  #pragma unroll
+        for (int step = 16; step >= 1; step >>= 1) {
+          const int v = __shfl_sync(full, incl, r + step - 1);
+          if (v <= cidx) r += step;
+        }
+        const int rjb = __shfl_sync(full, jb, r);
+        const int rfirst = __shfl_sync(full, first, r);
+        bool acc = false;
+        int j = 0;
+        T dx = 0, dy2 = 0, dz2 = 0, smax = 0;
+        if (cidx < total) {
+          j = rjb + (cidx - rfirst);
+          const VT vj = view[j];
+          dx = vd<false>(F, vi.x, vj.x);
+          dy2 = vd<false>(F, vi.y, vj.y);
+          dz2 = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+          const T r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+          if (r2 < R2) {
+            const T hj = view_h(vj);
+            const T skj = sk_hv * hj;
+            smax = sk > skj ? sk : skj;
+            const T hm = hv > hj ? hv : hj;  // symmetric: j lists i whenever i lists j
+            const T Rl = kappa * hm * T(1.00001) + smax * (T(1) + T(0.5) * kappa * lip);
+            acc = r2 < Rl * Rl;
+          }
+        }
+        const unsigned ball = __ballot_sync(full, acc);
+        if (acc) {
+          const int pos = cnt + __popc(ball & ((1u << lane) - 1u));
+          if (pos < cap) list[(size_t)pos * n + i] = ((uint32_t)j << 8) | (meta[j] & 0xFFu);
+          else over = true;
+          const T ax = fabs(dx) > fabs(dy2) ? fabs(dx) : fabs(dy2);
+          const T am = (ax > fabs(dz2) ? ax : fabs(dz2)) + smax;
+          reach = reach > am ? reach : am;
+        }
+        cnt += __popc(ball);
+      }
+    }
+    // the coarse FP32 conversion is exact below 2^22 coarse integers = 2^(22 - kCoarseBits) c0
+  #pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T other = __shfl_xor_sync(full, reach, o);
+      reach = reach > other ? reach : other;
+    }
+    if (lane == 0) {
+      const bool fast = reach < T(0.999) * T(1 << (22 - kCoarseBits));
+      lcount[i] = (uint32_t)(cnt < cap ? cnt : cap) | (fast ? kFastBit : 0u);
+    }
+    any_over |= __any_sync(full, over);
+    wmax = wmax > cnt ? wmax : cnt;
+  }  // targets
+  // longest list and overflow: one atomic per warp
+  if (lane == 0) {
+    if (any_over) atomicOr(err, kErrListOverflow);
+    if (wmax > 0) atomicMax(&ctl->lmax, wmax);
+  }
+}
+
 // --------------------------------------------------------------------------
 // Density pass (general gamma): rho_i (Eq. density_sum) and p_i / rho_i^2 with
 // p = P0 (rho/rho_t)^gamma (Eq. EOS_current), needed by the neighbours' forces.
@@ -470,8 +666,8 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
 // pair counts; the last block reduces them in fixed order and sets dt1, dt2
 // (Eq. time_step_size, see below).
 // --------------------------------------------------------------------------
-template <int D, class T, bool GENERAL, bool DBG, bool SURF>
-__global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_a(int n, StepCtl* ctl,
+template <int D, class T, bool GENERAL, bool DBG, bool SURF, int NT>
+__global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(int n, StepCtl* ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
@@ -714,8 +910,8 @@ __global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASS_MIN_BLOCKS) k_pass_
 // The new view goes to the other view buffer; a particle that moved half its
 // skin since the list was built raises need_rebuild.
 // --------------------------------------------------------------------------
-template <int D, class T>
-__global__ void __launch_bounds__(SPH_PASS_THREADS, SPH_PASSB_MIN_BLOCKS) k_pass_b(int n, StepCtl* __restrict__ ctl,
+template <int D, class T, int NT>
+__global__ void __launch_bounds__(NT, SPH_PASSB_MIN_BLOCKS * 256 / NT) k_pass_b(int n, StepCtl* __restrict__ ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 typename ViewOf<T>::type* __restrict__ w0,
@@ -931,6 +1127,11 @@ cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& 
   const LL4* X0 = (const LL4*)S.X[0];
   const LL4* X1 = (const LL4*)S.X[1];
   k_rekey<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, F, G, g, S.key);
+  // one warp per target (list_ppw = 1), round-robin over a grid of 16 blocks
+  // of 8 warps per SM, or one thread per target (list_ppw = 32)
+  const bool per_warp = S.list_ppw != 32;
+  const int gbw = per_warp ? (int)std::min<size_t>(((size_t)S.n * 32 + tb - 1) / tb, (size_t)sm_count() * 16) : gb;
+#define SPH_LIST_BUILD(TT) (per_warp ? k_list_build_warp<D, TT> : k_list_build<D, TT>)<<<gbw, tb, 0, st>>>
   cudaError_t e = build_cells(S, st);
   if (e != cudaSuccess) return e;
   k_make_view<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, 0, X0, X1, F, g, (VT*)S.view[0], (VT*)S.view[1],
@@ -941,14 +1142,14 @@ cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& 
     if (!S.view32 || !F32 || !G32) return cudaErrorInvalidValue;
     k_view32<D><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, *F32, (const V4<double>*)S.view[0],
                                    (const V4<double>*)S.view[1], (int4*)S.view32);
-    k_list_build<D, float><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const int4*)S.view32,
-                                              (const int4*)S.view32, S.cstart, *F32, *G32, (float)kappa, S.cap,
-                                              S.list, S.lcount, S.err);
+    SPH_LIST_BUILD(float)(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const int4*)S.view32,
+                          (const int4*)S.view32, S.cstart, *F32, *G32, (float)kappa, S.cap, S.list, S.lcount,
+                          S.err);
   } else {
-    k_list_build<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const VT*)S.view[0],
-                                          (const VT*)S.view[1], S.cstart, F, G, kappa, S.cap, S.list, S.lcount,
-                                          S.err);
+    SPH_LIST_BUILD(T)(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const VT*)S.view[0], (const VT*)S.view[1],
+                      S.cstart, F, G, kappa, S.cap, S.list, S.lcount, S.err);
   }
+#undef SPH_LIST_BUILD
   return cudaGetLastError();
 }
 
@@ -957,19 +1158,26 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
   using VT = typename ViewOf<T>::type;
   Geom<T> geo{};
   if (f.geo) geo = *(const Geom<T>*)f.geo;
-  const int tb = SPH_PASS_THREADS, gb = grid_for(S.n, tb);
+  const int tb = S.pass_threads == 128 ? 128 : 256, gb = grid_for(S.n, tb);
   T* rho = (T*)S.rho;
   T* pc = (T*)S.pc;
   if (f.general_eos)
-    k_density<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1], S.list, S.lcount,
-                                       F, P, rho, pc);
-#define SPH_PASS_A(GEN, DBG)                                                                                    \
-  (f.surface ? k_pass_a<D, T, GEN, DBG, true> : k_pass_a<D, T, GEN, DBG, false>)<<<gb, tb, 0, st>>>(            \
+    k_density<D, T><<<grid_for(S.n, 256), 256, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
+                                                        S.list, S.lcount, F, P, rho, pc);
+#define SPH_PASS_A_NT(GEN, DBG, NT)                                                                             \
+  (f.surface ? k_pass_a<D, T, GEN, DBG, true, NT> : k_pass_a<D, T, GEN, DBG, false, NT>)<<<gb, tb, 0, st>>>(    \
                                               S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],           \
                                               S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount, F, P, \
                                               pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
                                               f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix,     \
                                               f.dt_rec, (const LL4*)S.X[0], (const LL4*)S.X[1], geo)
+#define SPH_PASS_A(GEN, DBG)           \
+  do {                                 \
+    if (tb == 128)                     \
+      SPH_PASS_A_NT(GEN, DBG, 128);    \
+    else                               \
+      SPH_PASS_A_NT(GEN, DBG, 256);    \
+  } while (0)
   if (f.general_eos) {
     if (f.nbr_debug) SPH_PASS_A(true, true);
     else SPH_PASS_A(true, false);
@@ -978,6 +1186,7 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
     else SPH_PASS_A(false, false);
   }
 #undef SPH_PASS_A
+#undef SPH_PASS_A_NT
   return cudaGetLastError();
 }
 
@@ -985,12 +1194,12 @@ template <int D, class T>
 cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& g, PassFlags f,
                           cudaStream_t st) {
   using VT = typename ViewOf<T>::type;
-  const int tb = SPH_PASS_THREADS, gb = grid_for(S.n, tb);
+  const int tb = S.pass_threads == 128 ? 128 : 256, gb = grid_for(S.n, tb);
   unsigned long long* wm = (unsigned long long*)&S.scal->wall_moved;
-  k_pass_b<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1], (VT*)S.view[0],
-                                    (VT*)S.view[1], (const VT*)S.vbuild, (LL4*)S.X[0], (LL4*)S.X[1], S.plist,
-                                    S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
-                                    f.record ? (V4<T>*)S.visc : nullptr, S.err, wm, f.move, S.meta[0], S.meta[1]);
+  (tb == 128 ? k_pass_b<D, T, 128> : k_pass_b<D, T, 256>)<<<gb, tb, 0, st>>>(
+      S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1], (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild,
+      (LL4*)S.X[0], (LL4*)S.X[1], S.plist, S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
+      f.record ? (V4<T>*)S.visc : nullptr, S.err, wm, f.move, S.meta[0], S.meta[1]);
   return cudaGetLastError();
 }
 

@@ -6,9 +6,10 @@ with recomputed sizes each side chooses its own (equal up to rounding).
 
 Tolerances (relative to the largest component of the compared gradient):
 FP64 1e-9 (the two sides differ only in summation order and the integer
-state's rounding, amplified over a few steps); FP32 2e-3 (per-step forward
-quantities carry ~1e-6 relative error, and the reverse pass multiplies by
-pair-sum Jacobians whose entries cancel to ~1e-3 of their magnitude).
+state's rounding, amplified over a few steps); FP32 1e-4, the bound the
+reverse pass is specified to (measured on GB300: at most 6e-7 for the
+parameters and 5e-7 for the positions, here and on the 262,144-particle,
+20-step workload).
 """
 import numpy as np
 import pytest
@@ -19,7 +20,7 @@ from parity_util import make_gpu
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp64": 1e-9, "fp32": 2e-3}
+TOL = {"fp64": 1e-9, "fp32": 1e-4}
 
 
 def poly2d(n=3000, seed=5):
@@ -133,35 +134,89 @@ def test_backward_P0_free_with_recomputed_steps(precision):
     assert abs(gf["grads"]["P0"]) > 1e-2 * scale
 
 
-def test_backward_full_size_adjoint_workload():
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_backward_full_size_adjoint_workload(precision):
     """The polynomial-field workload at its full size (262,144 particles, 32
-    colours, 20 FP32 steps, checkpoint every 5): finite result, the P0
-    component vanishes under recomputed step sizes, and the handle ends at
-    the state 20 plain steps reach."""
+    colours, 20 steps, checkpoint every 5, recomputed step sizes) against the
+    oracle's reverse pass from the same seeded state: every position and
+    parameter component, and the step sizes; the handle ends at the state 20
+    plain steps reach."""
     n = 1 << 18
     p = W.adjoint_poly_2d(n=n, n_colors=32, seed=3)
-    from paper_1906_07925_gb300 import Relaxation
-    r = Relaxation(p, n_particles=n, n_colors=32, precision="fp32", seed=3)
-    x0, c0 = r.positions(), r.colors()
+    pos, col, _ = W.sample_density(p, n, seed=3)
+    o = oracle.backward(p, pos, col, 20, 1.0)
+    r = make_gpu(p, pos, col, precision, use_graph=True)
     g = r.backward(20, lam=1.0, frozen_dt=False, ckpt_every=5)
-    assert np.isfinite(g["dpos0"]).all() and np.isfinite(g["L"])
-    scale = max(abs(v) for v in g["grads"].values())
-    assert scale > 0 and abs(g["grads"]["P0"]) <= 1e-3 * scale
-    r2 = Relaxation(p, n_particles=n, n_colors=32, precision="fp32", seed=3)
-    r2.set_state(x0, c0)
+    _compare(g, o, TOL[precision])
+    assert np.allclose(g["dt"], o["dt"], rtol=1e-5 if precision == "fp32" else 1e-11)
+    xk = r.positions()
+    r.close()
+    r2 = make_gpu(p, pos, col, precision, use_graph=True)
     r2.step(20)
-    assert np.abs(r.positions() - r2.positions()).max() <= 1e-6
+    assert np.abs(xk - r2.positions()).max() <= (1e-6 if precision == "fp32" else 1e-14)
+    r2.close()
 
 
-def test_autograd_function_matches_seed_alone():
+def test_autograd_function_gradients_match_differences():
+    """relax_fn as a torch.autograd.Function of (x0, sigma0, gamma, P0, poly):
+    the gradient of w . x_K + 0.5 L against central differences of the same
+    GPU forward run (FP64, recomputed step sizes), for every parameter and
+    sampled coordinates; and the position gradient of w . x_K alone equals the
+    oracle's seeded reverse pass."""
     import torch
     from paper_1906_07925_gb300 import relax_fn
     p, pos, col = poly2d(n=1500)
-    r = make_gpu(p, pos, col, "fp64")
-    f = relax_fn(r, 3, frozen_dt=False, ckpt_every=3)
-    x0 = torch.tensor(pos, dtype=torch.float64, device="cuda", requires_grad=True)
-    w = torch.tensor(np.random.default_rng(9).normal(size=pos.shape), dtype=torch.float64, device="cuda")
-    (f(x0) * w).sum().backward()
-    r2 = make_gpu(p, pos, col, "fp64")
-    ref = r2.backward(3, lam=0.0, density_weight=0.0, seed=w.cpu().numpy(), ckpt_every=3)["dpos0"]
-    assert np.allclose(x0.grad.cpu().numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+    K = 3
+    f = relax_fn(p, col, K, precision="fp64", lam=0.7, density_weight=1.0, frozen_dt=False, ckpt_every=2,
+                 use_graph=False)
+    rng = np.random.default_rng(9)
+    w = torch.tensor(rng.normal(size=pos.shape), dtype=torch.float64, device="cuda")
+    base = dict(sigma0=p.sigma0, gamma=p.gamma, P0=p.P0, poly=list(p.poly))
+
+    def args(v, grad=False):
+        x0 = torch.tensor(v["x0"], dtype=torch.float64, device="cuda", requires_grad=grad)
+        sc = [torch.tensor(v[k], dtype=torch.float64, requires_grad=grad) for k in ("sigma0", "gamma", "P0")]
+        poly = torch.tensor(v["poly"], dtype=torch.float64, requires_grad=grad)
+        return [x0] + sc + [poly]
+
+    def loss(v, grad=False):
+        a = args(v, grad)
+        xk, L = f(*a)
+        return (w * xk).sum() + 0.5 * L, a
+
+    v0 = dict(base, x0=pos)
+    l0, a = loss(v0, grad=True)
+    l0.backward()
+    g = {"sigma0": float(a[1].grad), "gamma": float(a[2].grad), "P0": float(a[3].grad)}
+    for m in range(8):
+        g[f"poly{m}"] = float(a[4].grad[m])
+    scale = max(abs(x) for x in g.values())
+    for name in g:
+        eps = 1e-4
+        vp, vm = dict(v0), dict(v0)
+        if name.startswith("poly"):
+            m = int(name[4:])
+            vp["poly"] = list(v0["poly"]); vp["poly"][m] += eps
+            vm["poly"] = list(v0["poly"]); vm["poly"][m] -= eps
+        else:
+            vp[name] = v0[name] + eps
+            vm[name] = v0[name] - eps
+        fd = (float(loss(vp)[0]) - float(loss(vm)[0])) / (2 * eps)
+        assert abs(g[name] - fd) <= 1e-4 * max(abs(fd), 1e-3 * scale), (name, g[name], fd)
+    gx = a[0].grad.cpu().numpy()
+    gs = np.abs(gx).max()
+    for t in range(6):
+        i, k = int(rng.integers(len(pos))), int(rng.integers(2))
+        h = 1e-7
+        xp, xm = pos.copy(), pos.copy()
+        xp[i, k] += h
+        xm[i, k] -= h
+        fd = (float(loss(dict(v0, x0=xp))[0]) - float(loss(dict(v0, x0=xm))[0])) / (2 * h)
+        assert abs(gx[i, k] - fd) <= 1e-4 * max(abs(fd), 1e-3 * gs), (i, k, gx[i, k], fd)
+    # the seed alone (w . x_K) against the oracle's reverse pass
+    a = args(v0, grad=True)
+    xk, _ = f(*a)
+    (w * xk).sum().backward()
+    wn = w.cpu().numpy()
+    ref = oracle.backward(p, pos, col, K, 1.0, seed=wn)["dpos0"] - oracle.backward(p, pos, col, K, 1.0)["dpos0"]
+    assert np.abs(a[0].grad.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()

@@ -518,3 +518,45 @@ def test_auto_ramp_fires_at_the_oracles_step():
     r.step(1)
     assert r.stats()["ramp_t0"] == 100
     r.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_color_volumes_match_oracle(precision):
+    """Per-colour volume sum m/rho and count (the sizes of the partition's
+    sub-domains) after one step from a seeded state, against the oracle's sums
+    over its own densities of the same step: FP64 to 1e-12, FP32 to the
+    density tolerance. Two calls give identical bits; before any step the call
+    is refused."""
+    from paper_1906_07925_gb300 import SphError
+    p, pos, col = graded2d_state(20000, ncol=16)
+    r = make_gpu(p, pos, col, precision)
+    with pytest.raises(SphError):
+        r.color_volumes()
+    r.step(1)
+    v, k = r.color_volumes()
+    v2, k2 = r.color_volumes()
+    assert np.array_equal(v, v2) and np.array_equal(k, k2)
+    _, _, f = oracle.step(p, pos, col, 0)
+    vo, ko = oracle.color_volumes(f["rho"], col, 16)
+    assert np.array_equal(k, ko)
+    tol = 1e-12 if precision == "fp64" else 2e-5
+    assert np.all(np.abs(v - vo) <= tol * vo), np.abs(v / vo - 1).max()
+    r.close()
+
+
+def test_color_volumes_at_benchmark_size():
+    """The 8,388,608-particle 3D workload's 256 colours (FP32): the device
+    reduction against the same sums taken on the host from the densities the
+    step recorded (FP64 sums), and the counts against the colours."""
+    from paper_1906_07925_gb300 import Relaxation
+    n = 1 << 23
+    p = W.graded_inclusion_3d(n, 256, rho_scale=0.0)
+    p = p.copy(rho_scale=oracle_rho_scale(p, n))
+    r = Relaxation(p, n, 256, precision="fp32", seed=2, use_graph=True, record_fields=True)
+    r.step(2)
+    v, k = r.color_volumes()
+    rho, col = r.field("rho"), r.colors()
+    vo, ko = oracle.color_volumes(rho, col, 256)
+    assert np.array_equal(k, ko) and k.sum() == n
+    assert np.all(np.abs(v - vo) <= 1e-12 * vo)
+    r.close()

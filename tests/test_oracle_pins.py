@@ -792,3 +792,23 @@ def test_cell_key_files_each_particle_at_its_level_and_cell(orc, dim):
     ks = keys[order].astype(np.int64)
     assert np.all(np.diff(ks) >= 0)
     assert np.all(np.diff(order.astype(np.int64))[np.diff(ks) == 0] > 0)
+
+
+# ------------------------------------------------------ partition sizes ----
+
+def test_color_volumes_of_a_symmetric_partition(orc):
+    """A perfect lattice at uniform target density cut into four quadrant
+    colours: by mirror symmetry the four sub-domains get equal volumes
+    V_c = sum m/rho (Sec. 2.1's equal-size partition), each within the
+    lattice-sum error of the quadrant's area 1/4, and the colour volumes add
+    up to the total sum over particles; counts are the quadrant sizes."""
+    nper = 32
+    p = W.Problem(dim=2, lo=[0, 0, 0], hi=[1, 1, 0], field_kind=W.FIELD_UNIFORM, s0=1.0 / nper, rho_scale=1.0)
+    x = W.lattice(p, nper)
+    col = ((x[:, 0] > 0.5).astype(np.uint8) + 2 * (x[:, 1] > 0.5)).astype(np.uint8)
+    _, _, f = orc.step(p, x, col, 0)
+    v, k = orc.color_volumes(f["rho"], col, 4)
+    assert np.all(k == len(x) // 4)
+    assert np.ptp(v) <= 1e-13 * v.max()
+    assert np.all(np.abs(v - 0.25) < 0.25 * 0.03)
+    assert v.sum() == pytest.approx(float(np.sum(1.0 / f["rho"])), rel=1e-14)
