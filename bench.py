@@ -586,7 +586,7 @@ def main():
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["precision"] == "fp32" else "f64",
            "data": "synthetic", "config": config, "clocks": res["clocks"], "e2e": res["e2e"],
            "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roof, "cpu_baseline": cpu,
-           "fp64": res.get("fp64"), "adjoint": res.get("adjoint"),
+           "fp64": res.get("fp64"), "adjoint": res.get("adjoint"), "batch": res.get("batch"),
            "step_stats": {"force_pairs_per_particle": 2 * st["force_pairs"] / n, "list_entries_per_particle": st["list_entries"] / n, "list_rebuilds": st["list_rebuilds"], "dt1": st["dt1"],
                           "err_l2_rms": math.sqrt(st["err_l2"] / n), "levels": res["info"]["grid"]["n_levels"],
                           "cells": cells}}

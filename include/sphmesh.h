@@ -220,17 +220,16 @@ sph_status sph_set_state(sph_handle* h, const double* xyz, const uint8_t* col, i
 
 /* Launch configuration (no counterpart in the paper: it changes how the work
  * is spread over the GPU, not what is computed). pass_threads: threads per
- * block of the two pair passes, 128 or 256 (0: keep); list_ppw: particles per
- * warp of the neighbour-list build, 1 (a warp walks one target's candidates)
- * or 32 (a thread per target) (0: keep); cell_factor: finest cell edge over
- * the smallest support, > 0 (0: keep), which rebuilds the multi-resolution
- * grid. The first two leave every result bit for bit unchanged; a new cell
- * factor changes the cell order and so the order of each particle's sums
- * (rounding only). The next step rebuilds the neighbour list; captured
- * graphs are re-captured. Synchronises. Errors: INVALID_ARG, OOM,
- * CELL_OVERFLOW. sph_get_tuning reads the configuration in use. */
-sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, int32_t list_ppw, double cell_factor);
-sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, int32_t* list_ppw, double* cell_factor);
+ * block of the two pair passes, 128 or 256 (0: keep; 256 at creation unless
+ * params.block_size says 128); cell_factor: finest cell edge over the
+ * smallest support, > 0 (0: keep), which rebuilds the multi-resolution grid.
+ * The block size leaves every result bit for bit unchanged; a new cell factor
+ * changes the cell order and so the order of each particle's sums (rounding
+ * only). The next step rebuilds the neighbour list; captured graphs are
+ * re-captured. Synchronises. Errors: INVALID_ARG, OOM, CELL_OVERFLOW.
+ * sph_get_tuning reads the configuration in use. */
+sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, double cell_factor);
+sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, double* cell_factor);
 
 /* Advance n_steps relaxation steps (Algorithm 1): cell list,
  * density + pressure + surface-tension forces, time step, viscous force,
@@ -396,19 +395,17 @@ sph_status sph_batch_create(const sph_instance_desc* descs, int32_t n_inst, cons
  * first, particles x dimension cost, to the least-loaded branch); then, one
  * knob at a time from the best so far, the launch configuration of every
  * instance (sph_set_tuning): 128 or 256 threads per block of the pair passes,
- * 1 or 32 particles per warp of the list build, cell factor 0.75, 1 or 1.5.
+ * then cell factor 0.75, 1 or 1.5.
  * Each trial starts from the same state; the trial steps are undone (the
  * state and step counters are restored). Synchronises. */
 sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_candidates, int32_t steps_each);
 
 /* One configuration the autotuner timed (or chose): graph branches, threads
- * per block of the pair passes, particles per warp of the list build, cell
- * factor, and its device time per batched step. */
+ * per block of the pair passes, cell factor, and its device time per batched
+ * step. */
 typedef struct {
   int32_t branches;
   int32_t pass_threads;
-  int32_t list_ppw;
-  int32_t reserved;
   double cell_factor;
   float ms_per_step;
   float reserved2;
@@ -432,7 +429,7 @@ sph_status sph_batch_get(sph_batch* b, int32_t k, sph_handle** h);
 
 /* Instance count, branch count in use, and the autotuner's trials (n_tuned
  * entries of branch count and ms per step; arrays may be NULL, else they hold
- * at least n_candidates + 4 entries after sph_batch_tune; sph_batch_tuning
+ * at least n_candidates + 3 entries after sph_batch_tune; sph_batch_tuning
  * gives the trials' full configurations). */
 sph_status sph_batch_info(const sph_batch* b, int32_t* n_inst, int32_t* n_branches, int32_t* n_tuned,
                           int32_t* tuned_branches, float* tuned_ms);

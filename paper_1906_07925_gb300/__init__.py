@@ -280,14 +280,14 @@ class Relaxation:
                                                fs.ctypes.data))
         return dict(dens_count=dc, force_count=fc, dens_idsum=ds, force_idsum=fs)
 
-    def set_tuning(self, pass_threads=0, list_ppw=0, cell_factor=0.0):
+    def set_tuning(self, pass_threads=0, cell_factor=0.0):
         """Launch configuration (sph_set_tuning); 0 keeps a value."""
-        self._check(self.lib.sph_set_tuning(self.h, int(pass_threads), int(list_ppw), float(cell_factor)))
+        self._check(self.lib.sph_set_tuning(self.h, int(pass_threads), float(cell_factor)))
 
     def tuning(self):
-        t, p, c = C.c_int32(), C.c_int32(), C.c_double()
-        self._check(self.lib.sph_get_tuning(self.h, C.byref(t), C.byref(p), C.byref(c)))
-        return dict(pass_threads=t.value, list_ppw=p.value, cell_factor=c.value)
+        t, c = C.c_int32(), C.c_double()
+        self._check(self.lib.sph_get_tuning(self.h, C.byref(t), C.byref(c)))
+        return dict(pass_threads=t.value, cell_factor=c.value)
 
     def color_volumes(self):
         """Per colour: sum of m/rho over its particles (the sub-domain's
@@ -460,8 +460,8 @@ class Batch:
 
     def tune(self, candidates=(1, 4, 8, 16, 32, 64, 128), steps_each=2):
         """Autotune the branch count, then the launch configuration (threads
-        per block of the pair passes, particles per warp of the list build,
-        cell factor); returns dict(chosen, trials, n_inst, n_branches)."""
+        per block of the pair passes, cell factor); returns dict(chosen,
+        trials, n_inst, n_branches)."""
         arr = (C.c_int32 * len(candidates))(*candidates)
         self._check(self.lib.sph_batch_tune(self.b, arr, len(candidates), int(steps_each)))
         return self.info()

@@ -612,8 +612,8 @@ __global__ void __launch_bounds__(256) k_bwd_local(int n, const StepCtl* __restr
                                                    const LL4* __restrict__ X0, const LL4* __restrict__ X1,
                                                    const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
                                                    const uint32_t* __restrict__ list,
-                                                   const uint32_t* __restrict__ lcount, Frame<T> F, Phys<T> P,
-                                                   Geom<T> geo, AdjBufs<T> B) {
+                                                   const uint32_t* __restrict__ lcount, int cap, Frame<T> F,
+                                                   Phys<T> P, Geom<T> geo, AdjBufs<T> B) {
   using VT = typename ViewOf<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   T v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -627,8 +627,7 @@ __global__ void __launch_bounds__(256) k_bwd_local(int n, const StepCtl* __restr
     if (DENS) {
       const T rbi = B.rhob[i];
       const T Hi = P.kappa * hi;
-      const int cnt = (int)(lcount[i] & ~kFastBit);
-      for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+      for_skin_list(list, view, n, i, lcount[i], cap, [&](uint32_t e, const VT& vj) {
         const int j = (int)(e >> 8);
         const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
         const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
@@ -672,7 +671,7 @@ __global__ void __launch_bounds__(256) k_obj(int n, const StepCtl* __restrict__ 
                                              const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
                                              const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
                                              const uint32_t* __restrict__ list, const uint32_t* __restrict__ lcount,
-                                             Frame<T> F, Phys<T> P, T wd, T lambda, AdjBufs<T> B) {
+                                             int cap, Frame<T> F, Phys<T> P, T wd, T lambda, AdjBufs<T> B) {
   using VT = typename ViewOf<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   T v[2] = {T(0), T(0)};
@@ -684,8 +683,7 @@ __global__ void __launch_bounds__(256) k_obj(int n, const StepCtl* __restrict__ 
     const T qv = F.qv, hv = view_h(vi), hi = hv * qv;
     const T Hi = P.kappa * hi, half_kappa = T(0.5) * P.kappa;
     T rho = 0, xx = 0, xy = 0, xz = 0, hbar = 0, wi = 0;
-    const int cnt = (int)(lcount[i] & ~kFastBit);
-    for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+    for_skin_list(list, view, n, i, lcount[i], cap, [&](uint32_t e, const VT& vj) {
       const int j = (int)(e >> 8);
       const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
       const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
@@ -775,7 +773,7 @@ cudaError_t launch_bwd_step(const DevState& S, const Frame<T>& F, const Phys<T>&
                                                 (const LL4*)S.X[1], S.pid[0], S.pid[1], geo, B);
   if (general_eos)
     k_bwd_local<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, (const LL4*)S.X[0], (const LL4*)S.X[1],
-                                               S.pid[0], S.pid[1], S.list, S.lcount, F, P, geo, B);
+                                               S.pid[0], S.pid[1], S.list, S.lcount, S.cap, F, P, geo, B);
   return cudaGetLastError();
 }
 
@@ -788,9 +786,9 @@ cudaError_t launch_objective(const DevState& S, const Frame<T>& F, const Phys<T>
   const VT* w0 = (const VT*)S.view[0];
   const VT* w1 = (const VT*)S.view[1];
   k_obj<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount,
-                                 F, P, (T)wd, (T)lambda, B);
+                                 S.cap, F, P, (T)wd, (T)lambda, B);
   k_bwd_local<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, (const LL4*)S.X[0], (const LL4*)S.X[1], S.pid[0],
-                                             S.pid[1], S.list, S.lcount, F, P, geo, B);
+                                             S.pid[1], S.list, S.lcount, S.cap, F, P, geo, B);
   return cudaGetLastError();
 }
 

@@ -739,7 +739,7 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   S.n = nn;
   S.dim = d;
   S.fp64 = h->prec == SPH_PREC_FP64;
-  S.cap = h->par.list_capacity > 0 ? h->par.list_capacity : auto_capacity(h);
+  S.cap = h->par.list_capacity > 0 ? h->par.list_capacity : std::min(auto_capacity(h), kMaxListCapacity);
   S.pass_threads = h->par.block_size == 128 ? 128 : 256;
   const size_t v4 = S.fp64 ? 32 : 16, t1 = S.fp64 ? 8 : 4;
   const size_t N = (size_t)std::max<int64_t>(n_particles, 1);
@@ -808,8 +808,8 @@ static sph_status create_common(const sph_domain* dom, const sph_field* field, c
     why = "at most 2^24 particles per instance";
     vs = SPH_ERR_INVALID_ARG;
   }
-  if (vs == SPH_OK && (params->skin < 0 || params->list_capacity < 0)) {
-    why = "skin and list_capacity must be >= 0";
+  if (vs == SPH_OK && (params->skin < 0 || params->list_capacity < 0 || params->list_capacity > kMaxListCapacity)) {
+    why = "skin must be >= 0 and list_capacity in 0..32767";
     vs = SPH_ERR_INVALID_ARG;
   }
   if (vs == SPH_OK && params->block_size != 0 && params->block_size != 128 && params->block_size != 256) {
@@ -879,15 +879,14 @@ sph_status sph_set_surface(sph_handle* h, const uint8_t* flags) {
   return SPH_OK;
 }
 
-sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, int32_t list_ppw, double cell_factor) {
+sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, double cell_factor) {
   if (!h) return SPH_ERR_INVALID_ARG;
-  if ((pass_threads != 0 && pass_threads != 128 && pass_threads != 256) ||
-      (list_ppw != 0 && list_ppw != 1 && list_ppw != 32) || !(cell_factor >= 0.0) || cell_factor > 16.0)
-    return fail(h, SPH_ERR_INVALID_ARG, "pass_threads in {0, 128, 256}, list_ppw in {0, 1, 32}, 0 <= cell_factor <= 16");
+  if ((pass_threads != 0 && pass_threads != 128 && pass_threads != 256) || !(cell_factor >= 0.0) ||
+      cell_factor > 16.0)
+    return fail(h, SPH_ERR_INVALID_ARG, "pass_threads in {0, 128, 256}, 0 <= cell_factor <= 16");
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graphs(h);
   if (pass_threads) h->S.pass_threads = pass_threads;
-  if (list_ppw) h->S.list_ppw = list_ppw;
   const double cf_now = h->par.cell_factor > 0 ? h->par.cell_factor : 1.0;
   if (cell_factor > 0 && cell_factor != cf_now) {
     HostGrid hg;
@@ -917,20 +916,16 @@ sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, int32_t list_ppw,
       T.total_cells = cells;
     }
   }
-  for (DevState& T : h->adj.tape) {
-    T.pass_threads = h->S.pass_threads;
-    T.list_ppw = h->S.list_ppw;
-  }
+  for (DevState& T : h->adj.tape) T.pass_threads = h->S.pass_threads;
   // the next step rebuilds the list (and, after a new grid, the views)
   SPH_CUDA(h, launch_request_rebuild(h->S, h->stream));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   return SPH_OK;
 }
 
-sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, int32_t* list_ppw, double* cell_factor) {
+sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, double* cell_factor) {
   if (!h) return SPH_ERR_INVALID_ARG;
   if (pass_threads) *pass_threads = h->S.pass_threads;
-  if (list_ppw) *list_ppw = h->S.list_ppw;
   if (cell_factor) *cell_factor = h->par.cell_factor > 0 ? h->par.cell_factor : 1.0;
   return SPH_OK;
 }
@@ -1564,7 +1559,7 @@ sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_can
   // the same launch configuration on every instance
   auto configure = [&](const sph_batch_trial& c) -> sph_status {
     for (sph_handle* h : b->inst) {
-      sph_status s = sph_set_tuning(h, c.pass_threads, c.list_ppw, c.cell_factor);
+      sph_status s = sph_set_tuning(h, c.pass_threads, c.cell_factor);
       if (s != SPH_OK) return s;
     }
     return SPH_OK;
@@ -1601,7 +1596,6 @@ sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_can
   sph_batch_trial best{};
   best.branches = 0;
   best.pass_threads = h0->S.pass_threads;
-  best.list_ppw = h0->S.list_ppw;
   best.cell_factor = h0->par.cell_factor > 0 ? h0->par.cell_factor : 1.0;
   float best_ms = 0.0f;
   sph_status st = SPH_OK;
@@ -1617,28 +1611,21 @@ sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_can
     }
   }
   // 2. then, one knob at a time from the best so far: threads per block of
-  // the pair passes, particles per warp of the list build, cell factor
+  // the pair passes, cell factor
   const int threads_alt[] = {128, 256};
-  const int ppw_alt[] = {1, 32};
   const double cf_alt[] = {0.75, 1.0, 1.5};
+  const int threads0 = best.pass_threads;
+  const double cf0 = best.cell_factor;
   for (int v : threads_alt) {
-    if (st != SPH_OK || v == best.pass_threads) continue;
+    if (st != SPH_OK || v == threads0) continue;
     sph_batch_trial t = best;
     t.pass_threads = v;
     float ms = 0.0f;
     st = trial(t, &ms);
     if (st == SPH_OK && ms < best_ms) { best = t; best_ms = ms; }
   }
-  for (int v : ppw_alt) {
-    if (st != SPH_OK || v == best.list_ppw) continue;
-    sph_batch_trial t = best;
-    t.list_ppw = v;
-    float ms = 0.0f;
-    st = trial(t, &ms);
-    if (st == SPH_OK && ms < best_ms) { best = t; best_ms = ms; }
-  }
   for (double v : cf_alt) {
-    if (st != SPH_OK || v == best.cell_factor) continue;
+    if (st != SPH_OK || v == cf0) continue;
     sph_batch_trial t = best;
     t.cell_factor = v;
     float ms = 0.0f;

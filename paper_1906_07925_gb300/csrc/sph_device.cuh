@@ -11,6 +11,7 @@ namespace sph {
 
 constexpr int kMaxLevels = 8;
 constexpr int kMaxShapes = 4;
+constexpr int kMaxListCapacity = 0x7FFF;  // neighbour-list entries per particle (15-bit counts)
 
 // error bits latched in the device error word (1 << sph_status value)
 constexpr int kErrNonfinite = 1 << 4;

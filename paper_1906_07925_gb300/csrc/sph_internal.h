@@ -17,7 +17,6 @@ namespace sph {
 struct DevState {
   int n = 0, dim = 2, fp64 = 0, cap = 0;
   int pass_threads = 256;  // threads per block of the pair passes (128 or 256)
-  int list_ppw = 1;        // neighbour-list build: 1 target per warp, or 32 (one per thread)
   void* X[2] = {nullptr, nullptr};       // int64 x, y, z (+ pad) per particle
   uint32_t* meta[2] = {nullptr, nullptr};  // colour
   uint32_t* pid[2] = {nullptr, nullptr};   // particle id

@@ -50,20 +50,6 @@
 
 namespace sph {
 
-// streaming multiprocessors of the current device (queried once per process)
-inline int sm_count() {
-  static int cached = 0;
-  if (!cached) {
-    int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
-      cached = nsm;
-    else
-      return 152;
-  }
-  return cached;
-}
-
 // ---------------------------------------------------------------- views ----
 template <class T> struct ViewOf;
 template <> struct ViewOf<float> { using type = int4; };
@@ -101,9 +87,22 @@ __device__ __forceinline__ T screen_radius(T H) {
 __device__ __forceinline__ float view_h(const int4& v) { return __int_as_float(v.w); }
 __device__ __forceinline__ double view_h(const V4<double>& v) { return v.w; }
 
-// the list count of particle i; bit 31 certifies that every listed pair stays
-// within the exact range of the FP32 fast conversion until the next rebuild
+// The neighbour list of particle i is column i of a cap x n array, split at
+// its build: the entries then inside their support (r < max(kappa h_i,
+// kappa h_ij)) fill rows 0, 1, ... in candidate order, the others rows cap-1,
+// cap-2, ... in candidate order. A pass walks the inside part first, so the
+// entries that pass its exact tests cluster at the start of every list and a
+// warp skips the pair body on the later rows, where no lane's entry passes.
+// lcount packs both counts (bits 0-14 and 15-29); bit 31 certifies that
+// every listed pair stays within the exact range of the FP32 fast conversion
+// until the next rebuild.
 constexpr uint32_t kFastBit = 0x80000000u;
+constexpr uint32_t kCountMask = 0x7FFFu;
+constexpr int kOutShift = 15;
+__device__ __forceinline__ int list_in(uint32_t lc) { return (int)(lc & kCountMask); }
+__device__ __forceinline__ int list_cnt(uint32_t lc) {
+  return (int)(lc & kCountMask) + (int)((lc >> kOutShift) & kCountMask);
+}
 
 struct alignas(32) LL4 {
   long long x, y, z, w;
@@ -138,25 +137,42 @@ __device__ __forceinline__ V4<double> with_w(V4<double> v, double w) { return V4
 #ifndef SPH_LIST_BATCH
 #define SPH_LIST_BATCH 4
 #endif
+// Entry k of a list whose first n_in entries sit in rows 0.. and the rest in
+// rows cap-1, cap-2, ... (a compact list: n_in = cnt).
+__device__ __forceinline__ size_t list_row(int k, int n_in, int cap) {
+  return (size_t)(k < n_in ? k : cap - 1 - (k - n_in));
+}
 template <class VT, class Fn>
 __device__ __forceinline__ void for_list(const uint32_t* __restrict__ list, const VT* __restrict__ view, int n, int i,
-                                         int cnt, Fn&& pair) {
+                                         int cnt, int n_in, int cap, Fn&& pair) {
   constexpr int B = SPH_LIST_BATCH;
   int k = 0;
   for (; k + B <= cnt; k += B) {
     uint32_t e[B];
     VT v[B];
 #pragma unroll
-    for (int q = 0; q < B; ++q) e[q] = __ldcs(list + (size_t)(k + q) * n + i);
+    for (int q = 0; q < B; ++q) e[q] = __ldcs(list + list_row(k + q, n_in, cap) * n + i);
 #pragma unroll
     for (int q = 0; q < B; ++q) v[q] = view[e[q] >> 8];
 #pragma unroll
     for (int q = 0; q < B; ++q) pair(e[q], v[q]);
   }
   for (; k < cnt; ++k) {
-    const uint32_t e = __ldcs(list + (size_t)k * n + i);
+    const uint32_t e = __ldcs(list + list_row(k, n_in, cap) * n + i);
     pair(e, view[e >> 8]);
   }
+}
+// a compact list (rows 0 .. cnt-1)
+template <class VT, class Fn>
+__device__ __forceinline__ void for_list(const uint32_t* __restrict__ list, const VT* __restrict__ view, int n, int i,
+                                         int cnt, Fn&& pair) {
+  for_list(list, view, n, i, cnt, cnt, 0, pair);
+}
+// the skin list of particle i (split at its build, see kFastBit)
+template <class VT, class Fn>
+__device__ __forceinline__ void for_skin_list(const uint32_t* __restrict__ list, const VT* __restrict__ view, int n,
+                                              int i, uint32_t lc, int cap, Fn&& pair) {
+  for_list(list, view, n, i, list_cnt(lc), list_in(lc), cap, pair);
 }
 
 template <class T> __device__ __forceinline__ T pair_r(T r2);
@@ -335,9 +351,10 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   const T qv = F.qv;
   const int l0 = level_of_h(G, hlo * qv), l1 = level_of_h(G, hhi * qv);
   const T R2 = Rs * Rs;
-  int cnt = 0;
+  int cnt = 0, n_in = 0, n_out = 0;  // accepted; written inside / outside entries
   bool over = false;
   T reach = 0;
+  const T Hd = kappa * hv;
   for (int l = l0; l <= l1; ++l) {
     const int sh = G.cshift + l;
     const long long cxl = min((long long)G.nx[l] - 1, X.x >> sh);
@@ -392,8 +409,16 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
           // h_j is known here: only rounding and the h change over the skin need a margin
           const T Rl = kappa * hm * T(1.00001) + smax * (T(1) + T(0.5) * kappa * lip);
           if (r2 < Rl * Rl) {
-            if (cnt < cap) list[(size_t)cnt * n + i] = ((uint32_t)j << 8) | (meta[j] & 0xFFu);
-            else over = true;
+            // inside its support now (density or force): the front of the list
+            const T Hf = T(0.5) * kappa * (hv + hj);
+            const T Hp = Hf > Hd ? Hf : Hd;
+            const bool inside = r2 < Hp * Hp;
+            if (cnt < cap) {
+              const int row = inside ? n_in++ : cap - 1 - n_out++;
+              list[(size_t)row * n + i] = ((uint32_t)j << 8) | (meta[j] & 0xFFu);
+            } else {
+              over = true;
+            }
             ++cnt;
             // largest axis separation this pair can reach before the next rebuild
             const T ax = fabs(dx) > fabs(dy2) ? fabs(dx) : fabs(dy2);
@@ -406,194 +431,12 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   }
   // the coarse FP32 conversion is exact below 2^22 coarse integers = 2^(22 - kCoarseBits) c0
   const bool fast = reach < T(0.999) * T(1 << (22 - kCoarseBits));
-  lcount[i] = (uint32_t)(cnt < cap ? cnt : cap) | (fast ? kFastBit : 0u);
+  lcount[i] = (uint32_t)n_in | ((uint32_t)n_out << kOutShift) | (fast ? kFastBit : 0u);
   if (over) atomicOr(err, kErrListOverflow);
   // longest list of this build (one atomic per warp)
   const unsigned mask = __activemask();
   const int wmax = __reduce_max_sync(mask, cnt);
   if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicMax(&ctl->lmax, wmax);
-}
-
-// The same lists built by one warp per target: the warp's lanes enumerate the
-// target's candidate rows 32 at a time (lane q decodes row q of the levels,
-// z and y offsets the search visits, in the order the per-thread build walks
-// them, and looks up its row's range of sorted particles), a warp prefix sum
-// of the row lengths flattens the rows into one candidate sequence, and the
-// candidates are tested 32 at a time, each lane finding its row by a binary
-// search over the prefix sums. Accepted candidates are written in candidate
-// order (ballot ranks), so every list holds exactly the entries, in exactly
-// the order, of the per-thread build; the lanes stay busy whatever the row
-// lengths.
-template <int D, class T>
-__global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build_warp(int n, StepCtl* __restrict__ ctl,
-                                                    const LL4* __restrict__ X0, const LL4* __restrict__ X1,
-                                                    const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
-                                                    const typename ViewOf<T>::type* __restrict__ v0,
-                                                    const typename ViewOf<T>::type* __restrict__ v1,
-                                                    const uint32_t* __restrict__ cstart, Frame<T> F, Grid<T> G,
-                                                    T kappa, int cap, uint32_t* __restrict__ list,
-                                                    uint32_t* __restrict__ lcount, int* __restrict__ err) {
-  using VT = typename ViewOf<T>::type;
-  if (!ctl->rebuild) return;
-  const int lane = threadIdx.x & 31;
-  const unsigned full = 0xffffffffu;
-  const int buf = ctl->buf;
-  const VT* __restrict__ view = ctl->vp ? v1 : v0;
-  const uint32_t* __restrict__ meta = buf ? m1 : m0;
-  const int nwarps = (int)((gridDim.x * (size_t)blockDim.x) >> 5);
-  int wmax = 0;
-  bool any_over = false;
-  // targets are dealt to warps round-robin: neighbouring warps take
-  // neighbouring targets (and so the same cells) at the same time
-  for (int i = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5); i < n; i += nwarps) {
-    const LL4 X = (buf ? X1 : X0)[i];
-    const VT vi = view[i];
-    const T hv = view_h(vi);
-    const T sk = F.skin * hv;
-    const T sk_hv = F.skin;
-    const T lip = G.lip_h;
-    T hhi = hv, Rs = kappa * hv * G.rfac + sk * (T(1) + T(0.5) * kappa * lip);
-    for (int it = 0; it < 2; ++it) {
-      hhi = hv * T(1.00001) + lip * Rs;
-      const T shi = sk * hhi / hv;
-      Rs = kappa * hhi * G.rfac + shi * (T(1) + T(0.5) * kappa * lip);
-      Rs = Rs > kappa * hv * G.rfac ? Rs : kappa * hv * G.rfac;
-    }
-    const T hlo = hv * T(0.99999) - lip * Rs;
-    const T qv = F.qv;
-    const int l0 = level_of_h(G, hlo * qv), l1 = level_of_h(G, hhi * qv);
-    const T R2 = Rs * Rs;
-    // rows of every searched level: (l, dz, dy) with dy fastest
-    int nrows = 0;
-    for (int l = l0; l <= l1; ++l) {
-      const int sh = G.cshift + l;
-      const T c = G.cellv[l], ic = T(1) / c;
-      const long long cyl = min((long long)G.ny[l] - 1, X.y >> sh);
-      const long long czl = D == 3 ? min((long long)G.nz[l] - 1, X.z >> sh) : 0;
-      const T fy = (T)((double)(X.y - (cyl << sh)) * F.s2v);
-      const T fz = D == 3 ? (T)((double)(X.z - (czl << sh)) * F.s2v) : T(0);
-      const int nyr = (int)dfloor((fy + Rs) * ic) - (int)dfloor((fy - Rs) * ic) + 1;
-      const int nzr = D == 3 ? (int)dfloor((fz + Rs) * ic) - (int)dfloor((fz - Rs) * ic) + 1 : 1;
-      nrows += nyr * nzr;
-    }
-    int cnt = 0;
-    bool over = false;
-    T reach = 0;
-    for (int r0 = 0; r0 < nrows; r0 += 32) {
-      // lane q: row r0 + q -> its range [jb, je) of candidates
-      int jb = 0, len = 0;
-      int q = r0 + lane;
-      if (q < nrows) {
-        for (int l = l0; l <= l1; ++l) {
-          const int sh = G.cshift + l;
-          const long long cxl = min((long long)G.nx[l] - 1, X.x >> sh);
-          const long long cyl = min((long long)G.ny[l] - 1, X.y >> sh);
-          const long long czl = D == 3 ? min((long long)G.nz[l] - 1, X.z >> sh) : 0;
-          const T c = G.cellv[l], ic = T(1) / c;
-          const T fx = (T)((double)(X.x - (cxl << sh)) * F.s2v);
-          const T fy = (T)((double)(X.y - (cyl << sh)) * F.s2v);
-          const T fz = D == 3 ? (T)((double)(X.z - (czl << sh)) * F.s2v) : T(0);
-          const int ylo = (int)dfloor((fy - Rs) * ic), nyr = (int)dfloor((fy + Rs) * ic) - ylo + 1;
-          const int zlo = D == 3 ? (int)dfloor((fz - Rs) * ic) : 0;
-          const int nzr = D == 3 ? (int)dfloor((fz + Rs) * ic) - zlo + 1 : 1;
-          if (q >= nyr * nzr) {
-            q -= nyr * nzr;
-            continue;
-          }
-          const int dz = zlo + q / nyr, dy = ylo + q % nyr;
-          const long long czz = czl + dz, cyy = cyl + dy;
-          if ((D == 3 && (czz < 0 || czz >= G.nz[l])) || cyy < 0 || cyy >= G.ny[l]) break;
-          T dzp = 0;
-          if (D == 3) {
-            const T zrel = fz - (T)dz * c;
-            dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
-          }
-          const T yrel = fy - (T)dy * c;
-          const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
-          const T dp2 = dyp * dyp + dzp * dzp;
-          if (dp2 >= R2) break;
-          const T half = dsqrt(R2 - dp2);
-          long long x0 = cxl + (long long)dfloor((fx - half) * ic);
-          long long x1 = cxl + (long long)dfloor((fx + half) * ic);
-          x0 = x0 < 0 ? 0 : x0;
-          x1 = x1 > G.nx[l] - 1 ? G.nx[l] - 1 : x1;
-          if (x0 > x1) break;
-          const uint32_t krow =
-              G.base[l] + (uint32_t)G.nx[l] * ((uint32_t)cyy + (uint32_t)G.ny[l] * (uint32_t)(D == 3 ? czz : 0));
-          jb = (int)cstart[krow + (uint32_t)x0];
-          len = (int)cstart[krow + (uint32_t)x1 + 1] - jb;
-          break;
-        }
-      }
-      // flatten the rows: inclusive prefix of the lengths
-      int incl = len;
-  #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(full, incl, o);
-        if (lane >= o) incl += y;
-      }
-      const int total = __shfl_sync(full, incl, 31);
-      const int first = incl - len;  // first flattened index of this lane's row
-      for (int b = 0; b < total; b += 32) {
-        const int cidx = b + lane;
-        // row holding cidx: the number of rows whose inclusive prefix is <= cidx
-        int r = 0;
-  #pragma unroll
-        for (int step = 16; step >= 1; step >>= 1) {
-          const int v = __shfl_sync(full, incl, r + step - 1);
-          if (v <= cidx) r += step;
-        }
-        const int rjb = __shfl_sync(full, jb, r);
-        const int rfirst = __shfl_sync(full, first, r);
-        bool acc = false;
-        int j = 0;
-        T dx = 0, dy2 = 0, dz2 = 0, smax = 0;
-        if (cidx < total) {
-          j = rjb + (cidx - rfirst);
-          const VT vj = view[j];
-          dx = vd<false>(F, vi.x, vj.x);
-          dy2 = vd<false>(F, vi.y, vj.y);
-          dz2 = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
-          const T r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-          if (r2 < R2) {
-            const T hj = view_h(vj);
-            const T skj = sk_hv * hj;
-            smax = sk > skj ? sk : skj;
-            const T hm = hv > hj ? hv : hj;  // symmetric: j lists i whenever i lists j
-            const T Rl = kappa * hm * T(1.00001) + smax * (T(1) + T(0.5) * kappa * lip);
-            acc = r2 < Rl * Rl;
-          }
-        }
-        const unsigned ball = __ballot_sync(full, acc);
-        if (acc) {
-          const int pos = cnt + __popc(ball & ((1u << lane) - 1u));
-          if (pos < cap) list[(size_t)pos * n + i] = ((uint32_t)j << 8) | (meta[j] & 0xFFu);
-          else over = true;
-          const T ax = fabs(dx) > fabs(dy2) ? fabs(dx) : fabs(dy2);
-          const T am = (ax > fabs(dz2) ? ax : fabs(dz2)) + smax;
-          reach = reach > am ? reach : am;
-        }
-        cnt += __popc(ball);
-      }
-    }
-    // the coarse FP32 conversion is exact below 2^22 coarse integers = 2^(22 - kCoarseBits) c0
-  #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T other = __shfl_xor_sync(full, reach, o);
-      reach = reach > other ? reach : other;
-    }
-    if (lane == 0) {
-      const bool fast = reach < T(0.999) * T(1 << (22 - kCoarseBits));
-      lcount[i] = (uint32_t)(cnt < cap ? cnt : cap) | (fast ? kFastBit : 0u);
-    }
-    any_over |= __any_sync(full, over);
-    wmax = wmax > cnt ? wmax : cnt;
-  }  // targets
-  // longest list and overflow: one atomic per warp
-  if (lane == 0) {
-    if (any_over) atomicOr(err, kErrListOverflow);
-    if (wmax > 0) atomicMax(&ctl->lmax, wmax);
-  }
 }
 
 // --------------------------------------------------------------------------
@@ -605,8 +448,8 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
                                                  const typename ViewOf<T>::type* __restrict__ v0,
                                                  const typename ViewOf<T>::type* __restrict__ v1,
                                                  const uint32_t* __restrict__ list,
-                                                 const uint32_t* __restrict__ lcount, Frame<T> F, Phys<T> P,
-                                                 T* __restrict__ rho_out, T* __restrict__ pc_out) {
+                                                 const uint32_t* __restrict__ lcount, int cap, Frame<T> F,
+                                                 Phys<T> P, T* __restrict__ rho_out, T* __restrict__ pc_out) {
   using VT = typename ViewOf<T>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -615,13 +458,13 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
   const T hv = view_h(vi);
   const T Hd = P.kappa * hv, Hd2 = Hd * Hd, invHd = T(1) / Hd;
   const uint32_t lc = lcount[i];
-  const int cnt = (int)(lc & ~kFastBit);
+  const int cnt = list_cnt(lc), n_in = list_in(lc);
   const T Hs = (lc & kFastBit) ? screen_radius<T>(Hd) : Hd, Hs2 = Hs * Hs;
   T acc = 0;
   auto loop = [&](auto fastc) {
     constexpr bool FAST = decltype(fastc)::value;
     for (int k = 0; k < cnt; ++k) {
-      const uint32_t e = list[(size_t)k * n + i];
+      const uint32_t e = list[list_row(k, n_in, cap) * n + i];
       const VT vj = view[e >> 8];
       T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
       T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
@@ -673,8 +516,8 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
                                                 const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
                                                 const uint32_t* __restrict__ p0, const uint32_t* __restrict__ p1,
                                                 const uint32_t* __restrict__ list,
-                                                const uint32_t* __restrict__ lcount, Frame<T> F, Phys<T> P,
-                                                const T* __restrict__ pc, V4<T>* __restrict__ acc_out,
+                                                const uint32_t* __restrict__ lcount, int cap, Frame<T> F,
+                                                Phys<T> P, const T* __restrict__ pc, V4<T>* __restrict__ acc_out,
                                                 T* __restrict__ rho_out, Partial* __restrict__ partials,
                                                 Scalars* __restrict__ scal, unsigned* __restrict__ ticket,
                                                 int* __restrict__ err, int advance, int* __restrict__ dbg_count,
@@ -713,13 +556,13 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
     int nf = 0, ni = 0, nd = 0;
     long long sd = 0, sf = 0;
     const uint32_t lc = lcount[i];
-    const int cnt = (int)(lc & ~kFastBit);
+    const int cnt = list_cnt(lc);
     // Every skin-list entry: a screening test on the coarse vectors (when the
     // list build certified them), then the exact vectors and criteria for the
     // pairs that pass. This step's force pairs go to column i of plist.
     auto loop = [&](auto fastc) {
       constexpr bool FAST = decltype(fastc)::value;
-      for_list(list, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+      for_skin_list(list, view, n, i, lc, cap, [&](uint32_t e, const VT& vj) {
         const int j = (int)(e >> 8);
         T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
         T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
@@ -1127,11 +970,7 @@ cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& 
   const LL4* X0 = (const LL4*)S.X[0];
   const LL4* X1 = (const LL4*)S.X[1];
   k_rekey<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, F, G, g, S.key);
-  // one warp per target (list_ppw = 1), round-robin over a grid of 16 blocks
-  // of 8 warps per SM, or one thread per target (list_ppw = 32)
-  const bool per_warp = S.list_ppw != 32;
-  const int gbw = per_warp ? (int)std::min<size_t>(((size_t)S.n * 32 + tb - 1) / tb, (size_t)sm_count() * 16) : gb;
-#define SPH_LIST_BUILD(TT) (per_warp ? k_list_build_warp<D, TT> : k_list_build<D, TT>)<<<gbw, tb, 0, st>>>
+#define SPH_LIST_BUILD(TT) k_list_build<D, TT><<<gb, tb, 0, st>>>
   cudaError_t e = build_cells(S, st);
   if (e != cudaSuccess) return e;
   k_make_view<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, 0, X0, X1, F, g, (VT*)S.view[0], (VT*)S.view[1],
@@ -1163,11 +1002,12 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
   T* pc = (T*)S.pc;
   if (f.general_eos)
     k_density<D, T><<<grid_for(S.n, 256), 256, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
-                                                        S.list, S.lcount, F, P, rho, pc);
+                                                        S.list, S.lcount, S.cap, F, P, rho, pc);
 #define SPH_PASS_A_NT(GEN, DBG, NT)                                                                             \
   (f.surface ? k_pass_a<D, T, GEN, DBG, true, NT> : k_pass_a<D, T, GEN, DBG, false, NT>)<<<gb, tb, 0, st>>>(    \
                                               S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],           \
-                                              S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount, F, P, \
+                                              S.meta[0], S.meta[1], S.pid[0], S.pid[1], S.list, S.lcount, S.cap, \
+                                              F, P,                                                             \
                                               pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
                                               f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix,     \
                                               f.dt_rec, (const LL4*)S.X[0], (const LL4*)S.X[1], geo)

@@ -71,11 +71,11 @@ def test_batch_tune_restores_state_and_picks_a_trial():
     trials = info["trials"]
     # the branch counts first, then one trial per other value of each knob
     assert [t["branches"] for t in trials[:4]] == [1, 2, 6, 12]
-    assert len(trials) == 4 + 1 + 1 + 2
+    assert len(trials) == 4 + 1 + 2  # the other of (128, 256), two of (0.75, 1, 1.5)
     ch = info["chosen"]
     assert info["n_branches"] == ch["branches"] in (1, 2, 6, 12)
     assert ch["ms_per_step"] == min(t["ms_per_step"] for t in trials)
-    assert any(all(t[k] == ch[k] for k in ("branches", "pass_threads", "list_ppw", "cell_factor")) for t in trials)
+    assert any(all(t[k] == ch[k] for k in ("branches", "pass_threads", "cell_factor")) for t in trials)
     for k in range(12):
         assert np.abs(b.positions(k) - before[k]).max() <= 1e-14
         assert b.stats(k)["step"] == 2
@@ -85,27 +85,25 @@ def test_batch_tune_restores_state_and_picks_a_trial():
 
 
 def test_launch_configuration_leaves_results_unchanged():
-    """Threads per block of the pair passes and particles per warp of the list
-    build change how the work is spread, not what is computed: positions after
-    a few steps are bit-identical across them (graph replay and direct
-    launches); a new cell factor only reorders sums, and the step still matches
-    the oracle."""
-    import oracle
+    """Threads per block of the pair passes change how the work is spread, not
+    what is computed: positions after a few steps are bit-identical (graph
+    replay and direct launches); a new cell factor only reorders sums, and the
+    step still matches the oracle."""
     from parity_util import compare_step, make_gpu
     p = W.graded_inclusion_3d(20000, 8)
     pos, col, _ = W.sample_density(p, 20000, 5)
     ref = None
-    for threads, ppw in ((256, 1), (128, 1), (256, 32), (128, 32)):
+    for threads in (256, 128):
         for graph in (True, False):
             r = make_gpu(p, pos, col, "fp32", use_graph=graph)
-            r.set_tuning(pass_threads=threads, list_ppw=ppw)
-            assert r.tuning()["pass_threads"] == threads and r.tuning()["list_ppw"] == ppw
+            r.set_tuning(pass_threads=threads)
+            assert r.tuning()["pass_threads"] == threads
             r.step(4)
             x = r.positions()
             r.close()
             if ref is None:
                 ref = x
-            assert np.array_equal(x, ref), (threads, ppw, graph)
+            assert np.array_equal(x, ref), (threads, graph)
     r = make_gpu(p, pos, col, "fp32")
     r.set_tuning(cell_factor=1.5)
     assert r.tuning()["cell_factor"] == 1.5
