@@ -78,7 +78,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # bytes per particle of one k_pass_a launch and the hash of the kernel sources
 # it was captured from; the figure is reported only while the sources still
 # have that hash (else the counters describe another kernel and traffic is null)
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_pass_a_traffic_c3_1m.md")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "k_pass_a_traffic_c3_1m.txt")
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_1906_07925_gb300", "csrc", f)
                   for f in ("sph_step_impl.cuh", "sph_device.cuh", "sph_internal.h")]
 

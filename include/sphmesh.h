@@ -312,7 +312,12 @@ sph_status sph_sync(sph_handle* h);
 
 /* Checkpoint: the full state is positions + colours + step counter + the
  * sigma schedule (velocity is not state). With buf == NULL, *nbytes receives
- * the size needed. Synchronises. */
+ * the size needed. Synchronises. Layout (host byte order): a header of 8
+ * int64 {magic 0x3148534D48505300, version 1, n, dim, step counter, 0, 0, 0},
+ * the ramp window {t0, t1} as 2 doubles (-1: none), n x dim doubles
+ * (positions, particle-id order), n bytes (colours). sph_load checks magic,
+ * version, n and dim and takes the state, the step counter and the ramp
+ * window from the blob. */
 sph_status sph_save(sph_handle* h, void* buf, size_t* nbytes);
 sph_status sph_load(sph_handle* h, const void* buf, size_t nbytes);
 

@@ -244,9 +244,11 @@ __global__ void __launch_bounds__(256) k_bwd_out(int n, const StepCtl* __restric
 
 // ------------------------------------------------------------------------
 // k_bwd_visc: viscous pairs (this step's force pairs) and the local eta map.
+// Three gathers per pair (view, a, adjoint of a~): FP32 builds are held to 64
+// registers so that four blocks per SM keep enough loads in flight.
 // ------------------------------------------------------------------------
 template <int D, class T>
-__global__ void __launch_bounds__(256) k_bwd_visc(int n, const StepCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_bwd_visc(int n, const StepCtl* __restrict__ ctl,
                                                   const typename ViewOf<T>::type* __restrict__ v0,
                                                   const typename ViewOf<T>::type* __restrict__ v1,
                                                   const uint32_t* __restrict__ plist,

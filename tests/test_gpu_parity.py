@@ -133,9 +133,16 @@ def test_ramped_step_parity():
     p, pos, col = graded2d_state(8000)
     q = p.copy(t0=0, t1=3)  # step 1 of this schedule uses sigma = 3 (1 - 1/3) = 2
     r = make_gpu(q, pos, col, "fp32")
+    # the checkpoint's documented header: 8 int64 then the ramp window
+    hdr_t = np.dtype([("magic", "<i8"), ("version", "<i8"), ("n", "<i8"), ("dim", "<i8"), ("step", "<i8"),
+                      ("zero", "<i8", 3), ("t0", "<f8"), ("t1", "<f8")])
     blob = bytearray(r.save())
-    blob[32:40] = np.int64(1).tobytes()  # checkpoint header: step counter = 1
+    hdr = np.frombuffer(bytes(blob[:hdr_t.itemsize]), dtype=hdr_t).copy()
+    assert hdr["n"][0] == len(pos) and hdr["dim"][0] == 2 and hdr["step"][0] == 0
+    hdr["step"] = 1
+    blob[:hdr_t.itemsize] = hdr.tobytes()
     r.load(bytes(blob))
+    assert r.stats()["step"] == 1
     assert oracle.sigma(q, 1) == pytest.approx(2.0)
     r2, out = compare_step(q, pos, col, "fp32", step_index=1, gpu=r)
     assert out["stats"]["sigma"] == pytest.approx(2.0)
