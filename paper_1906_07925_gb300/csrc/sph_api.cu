@@ -131,9 +131,10 @@ sph_status status_from_flags(sph_handle* h, int flags) {
 }
 
 // list skin (fraction of kappa h) when params.skin = 0: a longer list costs
-// every step, a shorter one more frequent rebuilds; 0.2 was the faster of
-// 0.12 / 0.2 / 0.3 on the 8M-particle graded 3D workload
-constexpr double kDefaultSkin = 0.2;
+// every step, a shorter one more frequent rebuilds; on the 8M-particle graded
+// 3D workload (20 graph-replayed steps after 5 warm-up steps) 0.15 took 5.94
+// ms per step against 6.6 / 6.33 / 6.16 ms for 0.12 / 0.2 / 0.25
+constexpr double kDefaultSkin = 0.15;
 
 // position frames and kernel grids (make_frames in sph_host.h)
 void setup_frames(sph_handle* h) {
