@@ -112,7 +112,7 @@ typedef struct {
   int32_t record_fields; /* 1: keep rho, a_n and a~ of the last step for sph_get_field */
   int32_t list_capacity; /* neighbour-list entries per particle; 0 -> auto */
   double skin;           /* neighbour-list skin as a fraction of the support kappa h;
-                            0 -> 0.15; the list is rebuilt when a particle has moved
+                            0 -> 0.15 in 3D, 0.2 in 2D; the list is rebuilt when a particle has moved
                             half its skin (results do not depend on it) */
 } sph_params;
 

@@ -131,15 +131,17 @@ sph_status status_from_flags(sph_handle* h, int flags) {
 }
 
 // list skin (fraction of kappa h) when params.skin = 0: a longer list costs
-// every step, a shorter one more frequent rebuilds; on the 8M-particle graded
-// 3D workload (20 graph-replayed steps after 5 warm-up steps) 0.15 took 5.94
-// ms per step against 6.6 / 6.33 / 6.16 ms for 0.12 / 0.2 / 0.25
-constexpr double kDefaultSkin = 0.15;
+// every step, a shorter one more frequent rebuilds. 3D: on the 8M-particle
+// graded workload (20 graph-replayed steps after 5 warm-up steps) 0.15 took
+// 5.94 ms per step against 6.6 / 6.33 / 6.16 ms for 0.12 / 0.2 / 0.25 (5.93
+// vs 6.16 ms for 0.15 / 0.2 over 50 steps). 2D: 0.2 (the 262,144-particle
+// polynomial-field workload: 20 steps in 2.77 ms against 2.82 at 0.15).
+inline double default_skin(int dim) { return dim == 3 ? 0.15 : 0.2; }
 
 // position frames and kernel grids (make_frames in sph_host.h)
 void setup_frames(sph_handle* h) {
   Frames fr;
-  make_frames(h->dom, h->par.kappa, h->par.skin > 0 ? h->par.skin : kDefaultSkin, h->hg, fr);
+  make_frames(h->dom, h->par.kappa, h->par.skin > 0 ? h->par.skin : default_skin(h->dim), h->hg, fr);
   h->Ff = fr.f;
   h->Fd = fr.d;
   h->Gf = fr.gf;
@@ -155,7 +157,7 @@ void setup_frames(sph_handle* h) {
 // twice that and that plus ten standard deviations of a Poisson count (random
 // initial states cluster), plus 16.
 int auto_capacity(const sph_handle* h) {
-  const double skin = h->par.skin > 0 ? h->par.skin : kDefaultSkin;
+  const double skin = h->par.skin > 0 ? h->par.skin : default_skin(h->dim);
   const double k1 = h->par.kappa * (1.0 + skin);
   const double L = std::min(h->lip_h, 0.5 / k1);
   const double g = k1 / (1.0 - L * k1);
