@@ -18,8 +18,9 @@
 // Kernels, in launch order per step (state, list and forward quantities of the
 // step already in place):
 //   k_bwd_out    projection and drift: adjoints of y, v~ (partly) and a~
-//   k_bwd_visc   viscous pairs and eta: adjoints of v~, a, h, T, rho_t
-//   k_bwd_dt     (recomputed step sizes) the argmin particle's share
+//   k_bwd_visc   viscous pairs and eta: adjoints of v~, a, h, T, rho_t; its
+//                last block adds the argmin particle's share of recomputed
+//                step sizes
 //   k_bwd_force  pressure / surface-tension pairs and the equation of state
 //                (gamma = 2 form: then also the target field, as below)
 //   k_bwd_local  density pairs (where rho has an adjoint), then the target
@@ -336,34 +337,25 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_bwd_visc(int n,
     B.acc[kAdjDt1b] = out[0];
     // recomputed sizes: dt1 = 0.25 sqrt(m), dt2 = 0.2 sqrt(m), m = r_c,k/|a_k|
     const double m = scal->min_rc_a;
-    B.acc[kAdjMbar] = (recomputed_dt && m > 0.0 && m < DBL_MAX)
-                          ? (0.125 * out[0] + 0.1 * B.acc[kAdjDt2b]) / sqrt(m)
-                          : 0.0;
+    const double mb = (recomputed_dt && m > 0.0 && m < DBL_MAX) ? (0.125 * out[0] + 0.1 * B.acc[kAdjDt2b]) / sqrt(m)
+                                                                : 0.0;
+    B.acc[kAdjMbar] = mb;
+    // the argmin particle k of m takes m's adjoint through a_k and h_k (every
+    // block has written its adjoints: this is the last block to finish)
+    const long long k = scal->argmin;
+    if (k >= 0 && mb != 0.0) {
+      const VT* __restrict__ view = ctl->vp ? v1 : v0;
+      const double h = (double)view_h(view[k]) * (double)F.qv;
+      const V4<T> a = acc[k];
+      const double ax = a.x, ay = a.y, az = a.z;
+      const double an = sqrt(ax * ax + ay * ay + az * az);
+      const double c = -mb * (double)P.kappa * h / (an * an * an);
+      const T* abp = (const T*)&B.ab[k];
+      B.ab[k] = V4<T>{(T)(__ldcg(abp + 0) + (T)(c * ax)), (T)(__ldcg(abp + 1) + (T)(c * ay)),
+                      (T)(__ldcg(abp + 2) + (T)(c * az)), __ldcg(abp + 3)};
+      B.hb[k] = __ldcg(&B.hb[k]) + (T)(mb * (double)P.kappa / an);
+    }
   }
-}
-
-// the argmin particle k of m = r_c,k/|a_k|: a_k and h_k get m's adjoint
-template <int D, class T>
-__global__ void k_bwd_dt(const StepCtl* __restrict__ ctl, const typename ViewOf<T>::type* __restrict__ v0,
-                         const typename ViewOf<T>::type* __restrict__ v1, const V4<T>* __restrict__ acc,
-                         const Scalars* __restrict__ scal, Frame<T> F, Phys<T> P, AdjBufs<T> B) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const long long k = scal->argmin;
-  const double mb = B.acc[kAdjMbar];
-  if (k < 0 || mb == 0.0) return;
-  const auto* view = ctl->vp ? v1 : v0;
-  const double h = (double)view_h(view[k]) * (double)F.qv;
-  const V4<T> a = acc[k];
-  const double ax = a.x, ay = a.y, az = a.z;
-  const double an = sqrt(ax * ax + ay * ay + az * az);
-  const double rc = (double)P.kappa * h;
-  const double c = -mb * rc / (an * an * an);
-  V4<T> ab = B.ab[k];
-  ab.x += (T)(c * ax);
-  ab.y += (T)(c * ay);
-  ab.z += (T)(c * az);
-  B.ab[k] = ab;
-  B.hb[k] += (T)(mb * (double)P.kappa / an);
 }
 
 // gradient of the signed inside distance of shape s (the branch its value takes)
@@ -764,7 +756,6 @@ cudaError_t launch_bwd_step(const DevState& S, const Frame<T>& F, const Phys<T>&
   k_bwd_out<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, (const LL4*)S.X[0], (const LL4*)S.X[1], S.pid[0], S.pid[1], acc,
                                      (const V4<T>*)S.visc, S.scal, F, geo, B);
   k_bwd_visc<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, S.plist, S.pcount, acc, S.scal, F, P, recomputed_dt, B);
-  if (recomputed_dt) k_bwd_dt<D, T><<<1, 32, 0, st>>>(S.ctl, w0, w1, acc, S.scal, F, P, B);
   if (general_eos)
     k_bwd_force<D, T, true><<<gb, tb, 0, st>>>(S.n, S.ctl, w0, w1, S.meta[0], S.meta[1], S.plist, S.pcount,
                                                (const T*)S.rho, (const T*)S.pc, S.scal, F, P, (const LL4*)S.X[0],

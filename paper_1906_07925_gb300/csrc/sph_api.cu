@@ -54,6 +54,10 @@ struct sph_handle {
   double auto_tol = 0.0, auto_theta = 0.0;
   bool recorded = false;
   bool rho_valid = false;
+  // step-size history of a running sph_backward (the control block's dt_*)
+  double* dt_hist = nullptr;
+  long long dt_base = 0;
+  int dt_len = 0, dt_mode = 0;
   uint32_t cells_cap = 0;  // cells the cell arrays hold  // S.rho holds the summation density of the current positions' last pass A
   // per-colour volume scratch (sph_get_color_volumes; allocated on first use)
   double* cv_part = nullptr;
@@ -70,7 +74,6 @@ struct sph_handle {
     unsigned* ticket = nullptr;
     uint8_t* col = nullptr;  // colours by particle id
     std::vector<DevState> tape;  // taped-step slots (grown on demand, freed with the handle)
-    std::vector<double*> tape_dt;  // per slot: {dt1, dt2} a re-run step reads
     std::vector<cudaGraphExec_t> g_rerun;     // per slot: re-run step
     std::vector<cudaGraphExec_t> g_rev[2][2];  // per step-size mode, direction (g0 -> g1, g1 -> g0) and slot
     double *ck = nullptr, *xk = nullptr, *dts = nullptr, *seed = nullptr;  // checkpoints, x_K, step sizes, seed
@@ -316,7 +319,25 @@ sph_status write_ctl_all(sph_handle* h) {
   c.auto_tol = h->auto_tol;
   c.auto_theta = h->auto_theta;
   c.auto_ref = -1;
+  c.dt_hist = h->dt_hist;
+  c.dt_base = h->dt_base;
+  c.dt_len = h->dt_len;
+  c.dt_mode = h->dt_mode;
   SPH_CUDA(h, launch_write_ctl(h->S, c, h->stream));
+  return SPH_OK;
+}
+
+// the step-size history fields of the control block only (the list
+// bookkeeping and the schedule stay on the device)
+sph_status write_ctl_hist(sph_handle* h) {
+  struct {
+    double* hist;
+    long long base;
+    int len, mode;
+  } v{h->dt_hist, h->dt_base, h->dt_len, h->dt_mode};
+  static_assert(sizeof v == offsetof(StepCtl, dt_mode) + sizeof(int) - offsetof(StepCtl, dt_hist), "layout");
+  SPH_CUDA(h, cudaMemcpyAsync((char*)h->S.ctl + offsetof(StepCtl, dt_hist), &v, sizeof v, cudaMemcpyHostToDevice,
+                              h->stream));
   return SPH_OK;
 }
 
@@ -553,10 +574,7 @@ sph_status ensure_tape(sph_handle* h, int slots) {
       SPH_TRY(grab(h, T.list, N * cap));
       SPH_TRY(grab(h, T.lcount, N));
     }
-    double* dt = nullptr;
-    SPH_TRY(grab(h, dt, 2));
     tape.push_back(T);
-    h->adj.tape_dt.push_back(dt);
     h->adj.g_rerun.push_back(nullptr);
     for (auto& m : h->adj.g_rev)
       for (auto& v : m) v.push_back(nullptr);
@@ -1309,29 +1327,44 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   SPH_CUDA(h, cudaMemsetAsync(h->S.err, 0, sizeof(int), h->stream));
   SPH_CUDA(h, cudaMemsetAsync(a.acc, 0, sizeof(double) * kAdjSlots, h->stream));
   if (launch_get_colors(h->S, a.col, h->stream) != cudaSuccess) return fail(h, SPH_ERR_CUDA, "colours");
-  // Forward run with a position checkpoint at the start of every segment; the
-  // step sizes are recorded (or prescribed). The last segment is taped on the
-  // way; every other segment is re-run from its checkpoint (with the recorded
-  // sizes) into the tape just before its reverse sweep.
+  // The step sizes of this run go through a history the control block names:
+  // every step of the forward run records the sizes it chose (or, with dt_in,
+  // replays the prescribed ones), and every re-run step replays them; no
+  // per-step copies. The history is switched off whichever way this returns.
+  struct HistOff {
+    sph_handle* h;
+    ~HistOff() {
+      if (h->dt_mode) {
+        h->dt_mode = 0;
+        h->dt_hist = nullptr;
+        h->dt_len = 0;
+        write_ctl_hist(h);
+      }
+    }
+  } hist_off{h};
+  h->dt_hist = dts;
+  h->dt_base = t0;
+  h->dt_len = K;
+  h->dt_mode = dt_in ? 2 : 1;
+  SPH_TRY(write_ctl_hist(h));
+  // Forward run with a position checkpoint at the start of every segment. The
+  // last segment is taped on the way; every other segment is re-run from its
+  // checkpoint (with the recorded sizes) into the tape just before its
+  // reverse sweep.
   SPH_TRY(ensure_tape(h, (int)nseg));
   const std::vector<DevState>& tape = h->adj.tape;
   const int last0 = nck > 0 ? (nck - 1) * c : 0;
   for (int s = 0; s < K; ++s) {
     if (s % c == 0) SPH_TRY(positions_to(h, ck + nd * (size_t)(s / c)));
-    const double* fix = dt_in ? dts + 2 * s : nullptr;
-    double* rec = dt_in ? nullptr : dts + 2 * s;
     if (s >= last0) {
-      SPH_TRY(taped_step(h, tape[s - last0], fix, rec));
-    } else if (!fix) {
-      // the handle's graph of one step, then its step sizes copied out
-      SPH_TRY(ensure_graph(h, 0));
-      SPH_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
-      SPH_CUDA(h, cudaMemcpyAsync(rec, &h->S.scal->dt1, 2 * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+      SPH_TRY(taped_step(h, tape[s - last0], nullptr, nullptr));
     } else {
-      SPH_TRY(launch_step(h, 0, 0, nullptr, fix, rec));
+      SPH_TRY(ensure_graph(h, 0));  // the handle's graph of one step
+      SPH_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
     }
     h->steps += 1;
   }
+  h->dt_mode = 2;  // from here on every step replays the recorded sizes
   SPH_TRY(positions_to(h, xk));
   // objective at x_K: the gradient seed (g[cur])
   int cur = 0;
@@ -1343,13 +1376,11 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   for (int seg = nck - 1; seg >= 0; --seg) {
     const int s0 = seg * c, s1 = std::min(K, s0 + c);
     if (seg != nck - 1) {
-      SPH_TRY(set_state_at(h, ck + nd * (size_t)seg, a.col, t0 + s0));
+      SPH_TRY(set_state_at(h, ck + nd * (size_t)seg, a.col, t0 + s0));  // control block: replay
       for (int s = s0; s < s1; ++s) {
         const int k = s - s0;
         if (!a.g_rerun[k])
-          SPH_TRY(capture(h, &a.g_rerun[k], [&] { return taped_step(h, tape[k], a.tape_dt[k], nullptr); }));
-        SPH_CUDA(h, cudaMemcpyAsync(a.tape_dt[k], dts + 2 * s, 2 * sizeof(double), cudaMemcpyDeviceToDevice,
-                                    h->stream));
+          SPH_TRY(capture(h, &a.g_rerun[k], [&] { return taped_step(h, tape[k], nullptr, nullptr); }));
         SPH_CUDA(h, cudaGraphLaunch(a.g_rerun[k], h->stream));
       }
     }
@@ -1373,7 +1404,10 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
     if (dt_out && K > 0)
       SPH_CUDA(h, cudaMemcpyAsync(dt_out, dts, sizeof(double) * 2 * (size_t)K, cudaMemcpyDeviceToHost, h->stream));
   }
-  // leave the handle at x_K
+  // leave the handle at x_K (history off)
+  h->dt_mode = 0;
+  h->dt_hist = nullptr;
+  h->dt_len = 0;
   SPH_TRY(set_state_at(h, xk, a.col, t0 + K));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   grad->L = acc[kAdjL];

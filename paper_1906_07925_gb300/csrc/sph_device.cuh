@@ -123,6 +123,12 @@ struct StepCtl {
   int auto_on, auto_window, auto_stable, auto_done;
   double auto_tol, auto_theta;
   long long auto_ref;
+  // step-size history of a reverse-pass run (device array of {dt1, dt2} per
+  // step, step counter dt_base at entry 0): mode 1 records the sizes each step
+  // chose, mode 2 makes each step use the recorded ones; 0: neither
+  double* dt_hist;
+  long long dt_base;
+  int dt_len, dt_mode;
 };
 
 __device__ __forceinline__ double sigma_of(const StepCtl& c, long long t) {

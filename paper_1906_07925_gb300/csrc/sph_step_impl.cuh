@@ -711,6 +711,17 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
       dt_rec[0] = dt1;
       dt_rec[1] = dt2;
     }
+    // the step-size history of a reverse-pass run: replay or record
+    const long long hk = step - cc.dt_base;
+    if (cc.dt_mode && cc.dt_hist && hk >= 0 && hk < cc.dt_len) {
+      if (cc.dt_mode == 2) {
+        dt1 = cc.dt_hist[2 * hk];
+        dt2 = cc.dt_hist[2 * hk + 1];
+      } else {
+        cc.dt_hist[2 * hk] = dt1;
+        cc.dt_hist[2 * hk + 1] = dt2;
+      }
+    }
     scal->dt1 = dt1;
     scal->dt2 = dt2;
     scal->min_rc_a = m;
