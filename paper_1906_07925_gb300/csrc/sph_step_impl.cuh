@@ -174,30 +174,6 @@ __device__ __forceinline__ void for_skin_list(const uint32_t* __restrict__ list,
                                               int i, uint32_t lc, int cap, Fn&& pair) {
   for_list(list, view, n, i, list_cnt(lc), list_in(lc), cap, pair);
 }
-// the skin list with a third argument to pair: whether the entry lies in the
-// inside part (inside its support at the build: it passes the exact tests in
-// nearly every step, so a screen in front of them would only cost)
-template <class VT, class Fn>
-__device__ __forceinline__ void for_skin_list_io(const uint32_t* __restrict__ list, const VT* __restrict__ view,
-                                                 int n, int i, uint32_t lc, int cap, Fn&& pair) {
-  constexpr int B = SPH_LIST_BATCH;
-  const int cnt = list_cnt(lc), n_in = list_in(lc);
-  int k = 0;
-  for (; k + B <= cnt; k += B) {
-    uint32_t e[B];
-    VT v[B];
-#pragma unroll
-    for (int q = 0; q < B; ++q) e[q] = __ldcs(list + list_row(k + q, n_in, cap) * n + i);
-#pragma unroll
-    for (int q = 0; q < B; ++q) v[q] = view[e[q] >> 8];
-#pragma unroll
-    for (int q = 0; q < B; ++q) pair(e[q], v[q], k + q < n_in);
-  }
-  for (; k < cnt; ++k) {
-    const uint32_t e = __ldcs(list + list_row(k, n_in, cap) * n + i);
-    pair(e, view[e >> 8], k < n_in);
-  }
-}
 
 template <class T> __device__ __forceinline__ T pair_r(T r2);
 template <> __device__ __forceinline__ float pair_r<float>(float r2) { return r2 * rsqrtf(r2); }
@@ -499,15 +475,17 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
     for (int k = 0; k < cnt; ++k) {
       const uint32_t e = list[list_row(k, n_in, cap) * n + i];
       const VT vj = view[e >> 8];
-      if (FAST && k >= n_in) {  // the outside part: coarse screen first
-        const T cx = vd<true>(F, vi.x, vj.x), cy = vd<true>(F, vi.y, vj.y);
-        const T cz = D == 3 ? vd<true>(F, vi.z, vj.z) : T(0);
-        if (!(cx * cx + cy * cy + cz * cz < Hs2)) continue;
-      }
-      const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
-      const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
-      const T r2 = dx * dx + dy * dy + dz * dz;
-      if (r2 < Hd2) {
+      T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
+      T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
+      T r2 = dx * dx + dy * dy + dz * dz;
+      if (r2 < Hs2) {
+        if (FAST) {
+          dx = vd<false>(F, vi.x, vj.x);
+          dy = vd<false>(F, vi.y, vj.y);
+          dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+          r2 = dx * dx + dy * dy + dz * dz;
+          if (!(r2 < Hd2)) continue;
+        }
         const T q = r2 > T(0) ? pair_r<T>(r2) * invHd : T(0);
         const T u = T(1) - q, u2 = u * u;
         acc += u2 * u2 * (T(1) + T(4) * q);
@@ -588,26 +566,26 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
     long long sd = 0, sf = 0;
     const uint32_t lc = lcount[i];
     const int cnt = list_cnt(lc);
-    // Every skin-list entry: the exact vectors and criteria; in front of them,
-    // for entries of the outside part, a screening test on the coarse vectors
-    // (when the list build certified them), so that the entries that were
-    // outside their support at the build and still are cost only the screen.
-    // This step's force pairs go to column i of plist.
+    // Every skin-list entry: a screening test on the coarse vectors (when the
+    // list build certified them), then the exact vectors and criteria for the
+    // pairs that pass. This step's force pairs go to column i of plist.
     auto loop = [&](auto fastc) {
       constexpr bool FAST = decltype(fastc)::value;
-      for_skin_list_io(list, view, n, i, lc, cap, [&](uint32_t e, const VT& vj, bool inside) {
+      for_skin_list(list, view, n, i, lc, cap, [&](uint32_t e, const VT& vj) {
         const int j = (int)(e >> 8);
+        T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
+        T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
+        T r2 = dx * dx + dy * dy + dz * dz;
         const T hj = view_h(vj);
         const T Hf = half_kappa * (hv + hj);
-        if (FAST && !inside) {
-          const T cx = vd<true>(F, vi.x, vj.x), cy = vd<true>(F, vi.y, vj.y);
-          const T cz = D == 3 ? vd<true>(F, vi.z, vj.z) : T(0);
+        if (FAST) {
           const T Hm = screen_radius<T>(GENERAL || Hf > Hd ? Hf : Hd);
-          if (!(cx * cx + cy * cy + cz * cz < Hm * Hm)) return;
+          if (!(r2 < Hm * Hm)) return;
+          dx = vd<false>(F, vi.x, vj.x);
+          dy = vd<false>(F, vi.y, vj.y);
+          dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+          r2 = dx * dx + dy * dy + dz * dz;
         }
-        const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
-        const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
-        const T r2 = dx * dx + dy * dy + dz * dz;
         const bool inD = !GENERAL && r2 < Hd2;
         const bool inF = r2 < Hf * Hf && j != i && (!surf || (meta[j] & kSurfaceBit));
         if (!(inD || inF)) return;
