@@ -316,7 +316,14 @@ __global__ void __launch_bounds__(256) k_view32(int n, const StepCtl* __restrict
 // s = skin (kappa folded) of i and j: after both moved at most half their skin
 // (and h changed by at most lip_h times that), any pair inside the exact
 // criteria is still listed. Candidates come from rows of cells of every level
-// that can hold such a j.
+// that can hold such a j, in the order (level, z row, y row, x).
+//
+// Each lane walks its own rows with a small state machine instead of nested
+// loops: with nested loops a lane waits at every row's end for the longest row
+// of the warp. Here the warp tests candidates while at least half of its live
+// lanes still have some in their current row, then every lane whose row ran
+// out moves to its next non-empty row at once. The candidate order of each
+// list is that of the nested loops, so the lists are the same.
 template <int D, class T>
 __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, StepCtl* __restrict__ ctl,
                                                     const LL4* __restrict__ X0, const LL4* __restrict__ X1,
@@ -329,13 +336,18 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   using VT = typename ViewOf<T>::type;
   if (!ctl->rebuild) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  // lanes past n stay in the warp (they take part in the votes) with no rows
+  const bool valid = i < n;
   const int buf = ctl->buf;
-  const LL4 X = (buf ? X1 : X0)[i];
   const VT* __restrict__ view = ctl->vp ? v1 : v0;
   const uint32_t* __restrict__ meta = buf ? m1 : m0;
-  const VT vi = view[i];
-  const T hv = view_h(vi);                 // view units
+  LL4 X{};
+  VT vi{};
+  if (valid) {
+    X = (buf ? X1 : X0)[i];
+    vi = view[i];
+  }
+  const T hv = valid ? view_h(vi) : T(1);  // view units
   const T sk = F.skin * hv;                // skin of i, view units (kappa folded in by the host)
   const T sk_hv = F.skin;                  // skin per unit h
   const T lip = G.lip_h;
@@ -349,95 +361,156 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   }
   const T hlo = hv * T(0.99999) - lip * Rs;
   const T qv = F.qv;
-  const int l0 = level_of_h(G, hlo * qv), l1 = level_of_h(G, hhi * qv);
+  const int l0 = level_of_h(G, hlo * qv), l1 = valid ? level_of_h(G, hhi * qv) : l0 - 1;
   const T R2 = Rs * Rs;
   int cnt = 0, n_in = 0, n_out = 0;  // accepted; written inside / outside entries
   bool over = false;
   T reach = 0;
   const T Hd = kappa * hv;
-  for (int l = l0; l <= l1; ++l) {
+
+  // row walker: level l (its cell of i, i's offset in it, the z and y row
+  // ranges the search ball reaches), row (dz, dy), candidates [j, je)
+  int l = l0 - 1, dz = 0, zlo = 0, zhi = 0, dy = 0, ylo = 0, yhi = 0;
+  int cxl = 0, cyl = 0, czl = 0, nx = 0, ny = 0, nz = 0;
+  uint32_t base = 0;
+  T fx = 0, fy = 0, fz = 0, c = 1, ic = 1;
+  int j = 0, je = 0;
+  auto enter_level = [&]() {
     const int sh = G.cshift + l;
-    const long long cxl = min((long long)G.nx[l] - 1, X.x >> sh);
-    const long long cyl = min((long long)G.ny[l] - 1, X.y >> sh);
-    const long long czl = D == 3 ? min((long long)G.nz[l] - 1, X.z >> sh) : 0;
-    const T c = G.cellv[l], ic = T(1) / c;
+    nx = G.nx[l];
+    ny = G.ny[l];
+    nz = G.nz[l];
+    cxl = (int)min((long long)nx - 1, X.x >> sh);
+    cyl = (int)min((long long)ny - 1, X.y >> sh);
+    czl = D == 3 ? (int)min((long long)nz - 1, X.z >> sh) : 0;
+    c = G.cellv[l];
+    ic = T(1) / c;
     // target position inside its level-l cell, view units
-    const T fx = (T)((double)(X.x - (cxl << sh)) * F.s2v);
-    const T fy = (T)((double)(X.y - (cyl << sh)) * F.s2v);
-    const T fz = D == 3 ? (T)((double)(X.z - (czl << sh)) * F.s2v) : T(0);
-    const int nx = G.nx[l], ny = G.ny[l], nz = G.nz[l];
-    const uint32_t base = G.base[l];
-    int zlo = 0, zhi = 0;
+    fx = (T)((double)(X.x - ((long long)cxl << sh)) * F.s2v);
+    fy = (T)((double)(X.y - ((long long)cyl << sh)) * F.s2v);
+    fz = D == 3 ? (T)((double)(X.z - ((long long)czl << sh)) * F.s2v) : T(0);
+    base = G.base[l];
+    zlo = zhi = 0;
     if (D == 3) {
       zlo = (int)dfloor((fz - Rs) * ic);
       zhi = (int)dfloor((fz + Rs) * ic);
     }
-    const int ylo = (int)dfloor((fy - Rs) * ic), yhi = (int)dfloor((fy + Rs) * ic);
-    for (int dz = zlo; dz <= zhi; ++dz) {
-      const long long czz = czl + dz;
+    ylo = (int)dfloor((fy - Rs) * ic);
+    yhi = (int)dfloor((fy + Rs) * ic);
+    dz = zlo - 1;  // the next step moves to the first row of zlo
+  };
+  // next (level, dz, dy) in loop order; false past the last level
+  auto step_row = [&]() -> bool {
+    if (++dy <= yhi) return true;
+    while (++dz > zhi) {
+      if (++l > l1) return false;
+      enter_level();
+    }
+    dy = ylo;
+    return true;
+  };
+  // next row holding candidates; false when i has none left
+  auto next_row = [&]() -> bool {
+    while (step_row()) {
+      const int czz = czl + dz;
       if (D == 3 && (czz < 0 || czz >= nz)) continue;
+      const int cyy = cyl + dy;
+      if (cyy < 0 || cyy >= ny) continue;
       T dzp = 0;
       if (D == 3) {
         const T zrel = fz - (T)dz * c;
         dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
       }
-      for (int dy = ylo; dy <= yhi; ++dy) {
-        const long long cyy = cyl + dy;
-        if (cyy < 0 || cyy >= ny) continue;
-        const T yrel = fy - (T)dy * c;
-        const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
-        const T dp2 = dyp * dyp + dzp * dzp;
-        if (dp2 >= R2) continue;
-        const T half = dsqrt(R2 - dp2);
-        long long x0 = cxl + (long long)dfloor((fx - half) * ic);
-        long long x1 = cxl + (long long)dfloor((fx + half) * ic);
-        x0 = x0 < 0 ? 0 : x0;
-        x1 = x1 > nx - 1 ? nx - 1 : x1;
-        if (x0 > x1) continue;
-        const uint32_t krow = base + (uint32_t)nx * ((uint32_t)cyy + (uint32_t)ny * (uint32_t)(D == 3 ? czz : 0));
-        const int jb = (int)cstart[krow + (uint32_t)x0], je = (int)cstart[krow + (uint32_t)x1 + 1];
-        auto cand = [&](int j, const VT& vj) {
-          const T dx = vd<false>(F, vi.x, vj.x), dy2 = vd<false>(F, vi.y, vj.y);
-          const T dz2 = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
-          const T r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
-          if (r2 >= R2) return;
-          const T hj = view_h(vj);
-          const T skj = sk_hv * hj;
-          const T smax = sk > skj ? sk : skj;
-          const T hm = hv > hj ? hv : hj;  // symmetric: j lists i whenever i lists j
-          // h_j is known here: only rounding and the h change over the skin need a margin
-          const T Rl = kappa * hm * T(1.00001) + smax * (T(1) + T(0.5) * kappa * lip);
-          if (r2 < Rl * Rl) {
-            // inside its support now (density or force): the front of the list
-            const T Hf = T(0.5) * kappa * (hv + hj);
-            const T Hp = Hf > Hd ? Hf : Hd;
-            const bool inside = r2 < Hp * Hp;
-            if (cnt < cap) {
-              const int row = inside ? n_in++ : cap - 1 - n_out++;
-              list[(size_t)row * n + i] = ((uint32_t)j << 8) | (meta[j] & 0xFFu);
-            } else {
-              over = true;
-            }
-            ++cnt;
-            // largest axis separation this pair can reach before the next rebuild
-            const T ax = fabs(dx) > fabs(dy2) ? fabs(dx) : fabs(dy2);
-            const T am = (ax > fabs(dz2) ? ax : fabs(dz2)) + smax;
-            reach = reach > am ? reach : am;
-          }
-        };
-        // candidates in ascending order, two views loaded before either is
-        // tested (two loads in flight per thread: a rebuild of the 8M 3D
-        // workload 3.5 % faster than one at a time)
-        int j = jb;
-        for (; j + 2 <= je; j += 2) {
-          const VT va = view[j], vb = view[j + 1];
-          cand(j, va);
-          cand(j + 1, vb);
+      const T yrel = fy - (T)dy * c;
+      const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
+      const T dp2 = dyp * dyp + dzp * dzp;
+      if (dp2 >= R2) continue;
+      const T half = dsqrt(R2 - dp2);
+      int x0 = cxl + (int)dfloor((fx - half) * ic);
+      int x1 = cxl + (int)dfloor((fx + half) * ic);
+      x0 = x0 < 0 ? 0 : x0;
+      x1 = x1 > nx - 1 ? nx - 1 : x1;
+      if (x0 > x1) continue;
+      const uint32_t krow = base + (uint32_t)nx * ((uint32_t)cyy + (uint32_t)ny * (uint32_t)(D == 3 ? czz : 0));
+      j = (int)cstart[krow + (uint32_t)x0];
+      je = (int)cstart[krow + (uint32_t)x1 + 1];
+      if (j < je) return true;
+    }
+    j = je = 0;
+    return false;
+  };
+  // one candidate: every test is evaluated without a branch (most candidates
+  // fail, and a branch over the acceptance tests ran for a few lanes of the
+  // warp in nearly every iteration); only the list store is conditional
+  const T cl = T(1) + T(0.5) * kappa * lip;
+  auto cand = [&](int jc, const VT& vj) {
+    const T dx = vd<false>(F, vi.x, vj.x), dy2 = vd<false>(F, vi.y, vj.y);
+    const T dz2 = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
+    const T r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+    const T hj = view_h(vj);
+    const T skj = sk_hv * hj;
+    const T smax = sk > skj ? sk : skj;
+    const T hm = hv > hj ? hv : hj;  // symmetric: j lists i whenever i lists j
+    // h_j is known here: only rounding and the h change over the skin need a margin
+    const T Rl = kappa * hm * T(1.00001) + smax * cl;
+    const bool acc = r2 < R2 && r2 < Rl * Rl;
+    // inside its support now (density or force): the front of the list
+    const T Hf = T(0.5) * kappa * (hv + hj);
+    const T Hp = Hf > Hd ? Hf : Hd;
+    const bool inside = r2 < Hp * Hp;
+    // largest axis separation this pair can reach before the next rebuild
+    const T ax = fabs(dx) > fabs(dy2) ? fabs(dx) : fabs(dy2);
+    const T am = (ax > fabs(dz2) ? ax : fabs(dz2)) + smax;
+    reach = acc && am > reach ? am : reach;
+    if (acc) {
+      if (cnt < cap) {
+        const int row = inside ? n_in++ : cap - 1 - n_out++;
+        list[(size_t)row * n + i] = ((uint32_t)jc << 8) | (meta[jc] & 0xFFu);
+      } else {
+        over = true;
+      }
+      ++cnt;
+    }
+  };
+
+  if (valid) {
+    for (l = l0; l <= l1; ++l) {
+      enter_level();
+      for (dz = zlo; dz <= zhi; ++dz) {
+        const int czz = czl + dz;
+        if (D == 3 && (czz < 0 || czz >= nz)) continue;
+        T dzp = 0;
+        if (D == 3) {
+          const T zrel = fz - (T)dz * c;
+          dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
         }
-        for (; j < je; ++j) cand(j, view[j]);
+        for (dy = ylo; dy <= yhi; ++dy) {
+          const int cyy = cyl + dy;
+          if (cyy < 0 || cyy >= ny) continue;
+          const T yrel = fy - (T)dy * c;
+          const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
+          const T dp2 = dyp * dyp + dzp * dzp;
+          if (dp2 >= R2) continue;
+          const T half = dsqrt(R2 - dp2);
+          int x0 = cxl + (int)dfloor((fx - half) * ic);
+          int x1 = cxl + (int)dfloor((fx + half) * ic);
+          x0 = x0 < 0 ? 0 : x0;
+          x1 = x1 > nx - 1 ? nx - 1 : x1;
+          if (x0 > x1) continue;
+          const uint32_t krow = base + (uint32_t)nx * ((uint32_t)cyy + (uint32_t)ny * (uint32_t)(D == 3 ? czz : 0));
+          const int jb = (int)cstart[krow + (uint32_t)x0], jend = (int)cstart[krow + (uint32_t)x1 + 1];
+          int jj = jb;
+          for (; jj + 2 <= jend; jj += 2) {
+            const VT va = view[jj], vb = view[jj + 1];
+            cand(jj, va);
+            cand(jj + 1, vb);
+          }
+          for (; jj < jend; ++jj) cand(jj, view[jj]);
+        }
       }
     }
   }
+  if (!valid) return;
   // the coarse FP32 conversion is exact below 2^22 coarse integers = 2^(22 - kCoarseBits) c0
   const bool fast = reach < T(0.999) * T(1 << (22 - kCoarseBits));
   lcount[i] = (uint32_t)n_in | ((uint32_t)n_out << kOutShift) | (fast ? kFastBit : 0u);
