@@ -65,7 +65,8 @@ ALG_BYTES = {"cells": 54, "pass_a": 33, "pass_b": 49}
 ALG_BYTES_FP64 = {"cells": 92, "pass_a": 56, "pass_b": 83}
 # launches per step (gamma = 2): gate; rekey, count, 3 scan, scatter, gather,
 # make_view, list_build (predicated: they exit at once unless the list is
-# rebuilt); pass A; pass B
+# rebuilt); pass A; pass B; with the staged pass A one more predicated
+# rebuild kernel (the blocks' neighbour sets)
 KERNELS_PER_STEP = 12
 # pair arithmetic (FP32 flop, counted from the equations as the kernels evaluate
 # them): distance of a pair 10 (differences, squared norm, root), density term 8
@@ -251,6 +252,9 @@ def run_gpu(args, wl, rank, world):
     t_setup = time.perf_counter()
     r = Relaxation(p, n, wl["ncol"], precision=wl["precision"], seed=wl["seed"] + 1000 * rank, use_graph=True,
                    skin=args.skin, cell_factor=args.cell_factor)
+    if args.stage >= 0 and wl["precision"] == "fp32":
+        r.set_tuning(stage_views=args.stage)
+    staged = r.tuning()["stage_views"]
     torch.cuda.synchronize()
     log(f"[rank {rank}] create {time.perf_counter() - t_setup:.2f}s, grid {r.grid()['n_levels']} levels")
     stream = r.stream
@@ -309,7 +313,8 @@ def run_gpu(args, wl, rank, world):
     e2e_s = max_over_ranks(e2e_s, world)
     e2e = {"value": job_rate(n, world, args.steps, e2e_s), "unit": METRIC,
            "h2d_bytes_per_step": (n * d * 8 + n) / args.steps, "d2h_bytes_per_step": (n * d * 8 + 128) / args.steps}
-    info = dict(grid=r.grid(), stats=st, stats_e2e=st2)
+    info = dict(grid=r.grid(), stats=st, stats_e2e=st2, stage=dict(r.stage_info(), enabled=staged),
+                kernels_per_step=KERNELS_PER_STEP + (1 if staged else 0))
     r.close()
     out = dict(ms=ms, ms_step=ms_step, value=value, clocks=ck, phase_ms=phase_ms, e2e=e2e, info=info)
     if not args.no_extras and wl["precision"] == "fp32":
@@ -484,6 +489,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skin", type=float, default=0.0, help="neighbour-list skin / (kappa h); 0: library default")
     ap.add_argument("--cell-factor", type=float, default=0.0, help="finest cell edge / smallest support; 0: default")
+    ap.add_argument("--precision", default=None, choices=["fp32", "fp64"],
+                    help="override the workload's precision (the FP64 path of the same workload)")
+    ap.add_argument("--stage", type=int, default=-1, choices=[-1, 0, 1],
+                    help="staged density/force pass: 1 on, 0 off, -1 library default")
     ap.add_argument("--particles", type=int, default=0,
                     help="override the particle count (small cases for profiler captures)")
     ap.add_argument("--cpu-budget", type=float, default=20.0)
@@ -497,6 +506,9 @@ def main():
     if args.particles > 0:
         wl["n"] = args.particles
         wl["desc"] = wl["desc"].split(",")[0] + f", {args.particles} particles (reduced)"
+    if args.precision and args.precision != wl["precision"]:
+        wl["precision"] = args.precision
+        wl["desc"] = wl["desc"].replace("FP32 split-precision", "FP64").replace(", FP64, ", ", FP64, ")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     config = {"workload": wl["desc"], "particles": wl["n"], "dim": wl["dim"], "colors": wl["ncol"],
@@ -585,11 +597,12 @@ def main():
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_step"], "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if wl["precision"] == "fp32" else "f64",
            "data": "synthetic", "config": config, "clocks": res["clocks"], "e2e": res["e2e"],
-           "gpu_launches": KERNELS_PER_STEP * args.steps, "roofline": roof, "cpu_baseline": cpu,
+           "gpu_launches": res["info"]["kernels_per_step"] * args.steps, "roofline": roof, "cpu_baseline": cpu,
            "fp64": res.get("fp64"), "adjoint": res.get("adjoint"), "batch": res.get("batch"),
            "step_stats": {"force_pairs_per_particle": 2 * st["force_pairs"] / n, "list_entries_per_particle": st["list_entries"] / n, "list_rebuilds": st["list_rebuilds"], "dt1": st["dt1"],
                           "err_l2_rms": math.sqrt(st["err_l2"] / n), "levels": res["info"]["grid"]["n_levels"],
-                          "cells": cells}}
+                          "cells": cells},
+           "staged_pass": res["info"]["stage"]}
     print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -653,7 +666,8 @@ def main_batch(args):
                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                "data": "synthetic", "config": config, "clocks": res["clocks"], "e2e": res["e2e"],
-               "gpu_launches": KERNELS_PER_STEP * 512 * args.steps,
+               "gpu_launches": (KERNELS_PER_STEP + (1 if res["tune"]["chosen"].get("stage_views") else 0))
+               * 512 * args.steps,
                "per_instance_graphs": {"value": job_rate(res["total"], world, args.steps, res["ms_each"] * 1e-3),
                                        "ms_per_step": res["ms_each"] / args.steps,
                                        "speedup_of_batched": res["ms_each"] / res["ms"]},

@@ -222,14 +222,30 @@ sph_status sph_set_state(sph_handle* h, const double* xyz, const uint8_t* col, i
  * is spread over the GPU, not what is computed). pass_threads: threads per
  * block of the two pair passes, 128 or 256 (0: keep; 256 at creation unless
  * params.block_size says 128); cell_factor: finest cell edge over the
- * smallest support, > 0 (0: keep), which rebuilds the multi-resolution grid.
- * The block size leaves every result bit for bit unchanged; a new cell factor
- * changes the cell order and so the order of each particle's sums (rounding
- * only). The next step rebuilds the neighbour list; captured graphs are
- * re-captured. Synchronises. Errors: INVALID_ARG, OOM, CELL_OVERFLOW.
- * sph_get_tuning reads the configuration in use. */
-sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, double cell_factor);
-sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, double* cell_factor);
+ * smallest support, > 0 (0: keep), which rebuilds the multi-resolution grid;
+ * stage_views: 1 runs the density/force pass (Algorithm 1's neighbour loop,
+ * Sec. 3.3) staged, 0 unstaged, -1 keeps the setting. Staged, each list
+ * rebuild also finds, per block of 256 particles (in cell order), the
+ * distinct neighbours of their lists (at most 2,560, else that block stays
+ * unstaged) and numbers every list entry by its rank in that set; every step
+ * the pass copies the block's neighbour views into shared memory once and
+ * reads them there instead of gathering each pair's view from global memory.
+ * It applies to FP32 handles with gamma = 2, 256 threads per block and no
+ * feature-surface particles (other configurations run unstaged) and costs a
+ * second list array (4 bytes x list capacity per particle) plus 40 bytes per
+ * particle of neighbour sets. The block size and staging leave every result
+ * bit for bit unchanged; a new cell factor changes the cell order and so the
+ * order of each particle's sums (rounding only). The next step rebuilds the
+ * neighbour list; captured graphs are re-captured. Synchronises. Errors:
+ * INVALID_ARG (stage_views = 1 on an FP64 handle), OOM, CELL_OVERFLOW.
+ * sph_get_tuning reads the configuration in use (any pointer may be NULL). */
+sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, double cell_factor, int32_t stage_views);
+sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, double* cell_factor, int32_t* stage_views);
+
+/* Coverage of the staged pass (sph_set_tuning): blocks of 256 particles,
+ * how many of them the last list rebuild staged, and the neighbour views
+ * they stage in all (0 and 0 while staging is off). Synchronises. */
+sph_status sph_get_stage_info(sph_handle* h, int64_t* blocks, int64_t* staged_blocks, int64_t* staged_views);
 
 /* Advance n_steps relaxation steps (Algorithm 1): cell list,
  * density + pressure + surface-tension forces, time step, viscous force,
@@ -400,20 +416,21 @@ sph_status sph_batch_create(const sph_instance_desc* descs, int32_t n_inst, cons
  * first, particles x dimension cost, to the least-loaded branch); then, one
  * knob at a time from the best so far, the launch configuration of every
  * instance (sph_set_tuning): 128 or 256 threads per block of the pair passes,
- * then cell factor 0.75, 1 or 1.5.
+ * then cell factor 0.75, 1 or 1.5, then the staged pass on or off (FP32
+ * instances).
  * Each trial starts from the same state; the trial steps are undone (the
  * state and step counters are restored). Synchronises. */
 sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_candidates, int32_t steps_each);
 
 /* One configuration the autotuner timed (or chose): graph branches, threads
- * per block of the pair passes, cell factor, and its device time per batched
- * step. */
+ * per block of the pair passes, cell factor, its device time per batched
+ * step, and whether the pass ran staged. */
 typedef struct {
   int32_t branches;
   int32_t pass_threads;
   double cell_factor;
   float ms_per_step;
-  float reserved2;
+  int32_t stage_views;
 } sph_batch_trial;
 
 /* The autotuner's choice and its trials in order (trials may be NULL; at most
@@ -434,7 +451,7 @@ sph_status sph_batch_get(sph_batch* b, int32_t k, sph_handle** h);
 
 /* Instance count, branch count in use, and the autotuner's trials (n_tuned
  * entries of branch count and ms per step; arrays may be NULL, else they hold
- * at least n_candidates + 3 entries after sph_batch_tune; sph_batch_tuning
+ * at least n_candidates + 4 entries after sph_batch_tune; sph_batch_tuning
  * gives the trials' full configurations). */
 sph_status sph_batch_info(const sph_batch* b, int32_t* n_inst, int32_t* n_branches, int32_t* n_tuned,
                           int32_t* tuned_branches, float* tuned_ms);

@@ -280,14 +280,21 @@ class Relaxation:
                                                fs.ctypes.data))
         return dict(dens_count=dc, force_count=fc, dens_idsum=ds, force_idsum=fs)
 
-    def set_tuning(self, pass_threads=0, cell_factor=0.0):
-        """Launch configuration (sph_set_tuning); 0 keeps a value."""
-        self._check(self.lib.sph_set_tuning(self.h, int(pass_threads), float(cell_factor)))
+    def set_tuning(self, pass_threads=0, cell_factor=0.0, stage_views=-1):
+        """Launch configuration (sph_set_tuning); 0 (stage_views: -1) keeps a value."""
+        self._check(self.lib.sph_set_tuning(self.h, int(pass_threads), float(cell_factor), int(stage_views)))
 
     def tuning(self):
-        t, c = C.c_int32(), C.c_double()
-        self._check(self.lib.sph_get_tuning(self.h, C.byref(t), C.byref(c)))
-        return dict(pass_threads=t.value, cell_factor=c.value)
+        t, c, s = C.c_int32(), C.c_double(), C.c_int32()
+        self._check(self.lib.sph_get_tuning(self.h, C.byref(t), C.byref(c), C.byref(s)))
+        return dict(pass_threads=t.value, cell_factor=c.value, stage_views=s.value)
+
+    def stage_info(self):
+        """Blocks of 256 particles, how many the last list rebuild staged, and
+        the neighbour views they stage (sph_get_stage_info)."""
+        b, sb, sv = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.lib.sph_get_stage_info(self.h, C.byref(b), C.byref(sb), C.byref(sv)))
+        return dict(blocks=b.value, staged_blocks=sb.value, staged_views=sv.value)
 
     def color_volumes(self):
         """Per colour: sum of m/rho over its particles (the sub-domain's

@@ -86,7 +86,7 @@ class sph_grad(C.Structure):
 
 class sph_batch_trial(C.Structure):
     _fields_ = [("branches", C.c_int32), ("pass_threads", C.c_int32), ("cell_factor", C.c_double),
-                ("ms_per_step", C.c_float), ("reserved2", C.c_float)]
+                ("ms_per_step", C.c_float), ("stage_views", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if not k.startswith("reserved")}
@@ -153,8 +153,9 @@ def load():
             "sph_batch_info": [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
             "sph_batch_sync": [H],
             "sph_batch_tuning": [H, P(sph_batch_trial), C.c_void_p, C.c_int32, P(C.c_int32)],
-            "sph_set_tuning": [H, C.c_int32, C.c_double],
-            "sph_get_tuning": [H, P(C.c_int32), P(C.c_double)],
+            "sph_set_tuning": [H, C.c_int32, C.c_double, C.c_int32],
+            "sph_get_tuning": [H, P(C.c_int32), P(C.c_double), P(C.c_int32)],
+            "sph_get_stage_info": [H, P(C.c_int64), P(C.c_int64), P(C.c_int64)],
             "sph_get_color_volumes": [H, C.c_void_p, C.c_void_p],
             "sph_eval_forces_noalloc": [P(sph_domain), P(sph_field), P(sph_params), C.c_int64, C.c_void_p,
                                         C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],

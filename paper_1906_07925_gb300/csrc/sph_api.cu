@@ -171,6 +171,24 @@ int auto_capacity(const sph_handle* h) {
   return (cap + 7) & ~7;
 }
 
+// FP32 handles start with the staged pass A on (sph_set_tuning switches it)
+constexpr bool kStageDefault = false;
+
+// buffers of the staged pass A (FP32 handles): the list again with ranks in
+// each block's neighbour set, the sets and their counts (-1: not staged until
+// the next list rebuild fills them)
+sph_status ensure_stage(sph_handle* h) {
+  DevState& S = h->S;
+  if (S.llist) return SPH_OK;
+  const size_t N = (size_t)std::max<int64_t>(h->n, 1), nb = (N + kStageBlock - 1) / kStageBlock;
+  SPH_TRY(grab(h, S.llist, N * (size_t)S.cap));
+  SPH_TRY(grab(h, S.scount, nb));
+  SPH_TRY(grab(h, S.sj, nb * (size_t)kStageCap));
+  SPH_CUDA(h, cudaMemsetAsync(S.scount, 0xFF, sizeof(int) * nb, h->stream));
+  SPH_CUDA(h, h->dim == 2 ? prepare_staged_pass<2>() : prepare_staged_pass<3>());
+  return SPH_OK;
+}
+
 // one relaxation step on the handle's stream; dt_fix (device, may be null)
 // prescribes {dt1, dt2}, dt_rec (device, may be null) receives them. Sx (may
 // be null: the handle's own) redirects buffers; with `tape`, the state pass A
@@ -799,6 +817,10 @@ static sph_status create_impl(sph_handle* h, const sph_domain* dom, const sph_fi
   SPH_CUDA(h, cudaMemsetAsync(S.err, 0, sizeof(int), h->stream));
   SPH_CUDA(h, cudaMemsetAsync(S.scal, 0, sizeof(Scalars) * 2, h->stream));
   SPH_CUDA(h, cudaMemsetAsync(S.lcount, 0, sizeof(uint32_t) * N, h->stream));
+  if (!S.fp64 && kStageDefault) {
+    SPH_TRY(ensure_stage(h));
+    S.stage = 1;
+  }
 
   // ---- initial state ----
   {
@@ -900,14 +922,19 @@ sph_status sph_set_surface(sph_handle* h, const uint8_t* flags) {
   return SPH_OK;
 }
 
-sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, double cell_factor) {
+sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, double cell_factor, int32_t stage_views) {
   if (!h) return SPH_ERR_INVALID_ARG;
   if ((pass_threads != 0 && pass_threads != 128 && pass_threads != 256) || !(cell_factor >= 0.0) ||
-      cell_factor > 16.0)
-    return fail(h, SPH_ERR_INVALID_ARG, "pass_threads in {0, 128, 256}, 0 <= cell_factor <= 16");
+      cell_factor > 16.0 || stage_views < -1 || stage_views > 1)
+    return fail(h, SPH_ERR_INVALID_ARG,
+                "pass_threads in {0, 128, 256}, 0 <= cell_factor <= 16, stage_views in {-1, 0, 1}");
+  if (stage_views == 1 && h->S.fp64)
+    return fail(h, SPH_ERR_INVALID_ARG, "the staged pass exists for the FP32 split precision only");
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   drop_graphs(h);
   if (pass_threads) h->S.pass_threads = pass_threads;
+  if (stage_views == 1) SPH_TRY(ensure_stage(h));
+  if (stage_views >= 0) h->S.stage = stage_views;
   const double cf_now = h->par.cell_factor > 0 ? h->par.cell_factor : 1.0;
   if (cell_factor > 0 && cell_factor != cf_now) {
     HostGrid hg;
@@ -937,17 +964,44 @@ sph_status sph_set_tuning(sph_handle* h, int32_t pass_threads, double cell_facto
       T.total_cells = cells;
     }
   }
-  for (DevState& T : h->adj.tape) T.pass_threads = h->S.pass_threads;
+  for (DevState& T : h->adj.tape) {
+    T.pass_threads = h->S.pass_threads;
+    T.stage = h->S.stage;
+    T.llist = h->S.llist;
+    T.scount = h->S.scount;
+    T.sj = h->S.sj;
+  }
   // the next step rebuilds the list (and, after a new grid, the views)
   SPH_CUDA(h, launch_request_rebuild(h->S, h->stream));
   SPH_CUDA(h, cudaStreamSynchronize(h->stream));
   return SPH_OK;
 }
 
-sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, double* cell_factor) {
+sph_status sph_get_tuning(const sph_handle* h, int32_t* pass_threads, double* cell_factor, int32_t* stage_views) {
   if (!h) return SPH_ERR_INVALID_ARG;
   if (pass_threads) *pass_threads = h->S.pass_threads;
   if (cell_factor) *cell_factor = h->par.cell_factor > 0 ? h->par.cell_factor : 1.0;
+  if (stage_views) *stage_views = h->S.stage;
+  return SPH_OK;
+}
+
+sph_status sph_get_stage_info(sph_handle* h, int64_t* blocks, int64_t* staged_blocks, int64_t* staged_views) {
+  if (!h) return SPH_ERR_INVALID_ARG;
+  const size_t nb = ((size_t)std::max<int64_t>(h->n, 1) + kStageBlock - 1) / kStageBlock;
+  int64_t sb = 0, sv = 0;
+  if (h->S.stage && h->S.scount) {
+    std::vector<int> c(nb);
+    SPH_CUDA(h, cudaMemcpyAsync(c.data(), h->S.scount, sizeof(int) * nb, cudaMemcpyDeviceToHost, h->stream));
+    SPH_CUDA(h, cudaStreamSynchronize(h->stream));
+    for (int v : c)
+      if (v >= 0) {
+        ++sb;
+        sv += v;
+      }
+  }
+  if (blocks) *blocks = (int64_t)nb;
+  if (staged_blocks) *staged_blocks = sb;
+  if (staged_views) *staged_views = sv;
   return SPH_OK;
 }
 
@@ -1596,7 +1650,7 @@ sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_can
   // the same launch configuration on every instance
   auto configure = [&](const sph_batch_trial& c) -> sph_status {
     for (sph_handle* h : b->inst) {
-      sph_status s = sph_set_tuning(h, c.pass_threads, c.cell_factor);
+      sph_status s = sph_set_tuning(h, c.pass_threads, c.cell_factor, h->S.fp64 ? -1 : c.stage_views);
       if (s != SPH_OK) return s;
     }
     return SPH_OK;
@@ -1634,6 +1688,7 @@ sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_can
   best.branches = 0;
   best.pass_threads = h0->S.pass_threads;
   best.cell_factor = h0->par.cell_factor > 0 ? h0->par.cell_factor : 1.0;
+  best.stage_views = h0->S.stage;
   float best_ms = 0.0f;
   sph_status st = SPH_OK;
   // 1. branch count
@@ -1665,6 +1720,15 @@ sph_status sph_batch_tune(sph_batch* b, const int32_t* candidates, int32_t n_can
     if (st != SPH_OK || v == cf0) continue;
     sph_batch_trial t = best;
     t.cell_factor = v;
+    float ms = 0.0f;
+    st = trial(t, &ms);
+    if (st == SPH_OK && ms < best_ms) { best = t; best_ms = ms; }
+  }
+  // 3. the staged pass A on or off (FP32 instances)
+  const int stage0 = best.stage_views;
+  if (st == SPH_OK) {
+    sph_batch_trial t = best;
+    t.stage_views = stage0 ? 0 : 1;
     float ms = 0.0f;
     st = trial(t, &ms);
     if (st == SPH_OK && ms < best_ms) { best = t; best_ms = ms; }

@@ -12,6 +12,12 @@ namespace sph {
 constexpr int kMaxLevels = 8;
 constexpr int kMaxShapes = 4;
 constexpr int kMaxListCapacity = 0x7FFF;  // neighbour-list entries per particle (15-bit counts)
+// Staged pass A (FP32, 256-target blocks): the distinct neighbours of a block's
+// lists are gathered into shared memory once per step, at most kStageCap of
+// them (40 KB of views); kStageHash slots of the hash set that finds them
+constexpr int kStageBlock = 256;
+constexpr int kStageCap = 2560;
+constexpr int kStageHash = 4096;
 
 // error bits latched in the device error word (1 << sph_status value)
 constexpr int kErrNonfinite = 1 << 4;
@@ -81,9 +87,12 @@ struct Frame {
 
 // The view unit is the level-0 cell edge c0. FP32 view integers are 2^-24 c0;
 // the coarse inside/outside test of a listed pair uses them shifted down to
-// 2^-20 c0, whose differences convert exactly without the conversion unit.
+// 2^-16 c0, whose differences convert exactly without the conversion unit
+// while they stay below 2^22 coarse integers = 64 c0 per axis: every list of
+// the coarser levels qualifies (a list whose pairs reach beyond that range
+// takes the exact test alone).
 constexpr int kViewBits = 24;
-constexpr int kCoarseBits = 20;
+constexpr int kCoarseBits = 16;
 
 template <class T>
 struct Phys {

@@ -32,6 +32,13 @@ struct DevState {
   uint32_t* list = nullptr;              // cap x n entries (j << 8 | colour_j), column per particle
   uint32_t* lcount = nullptr;            // entries per particle; bit 31: FP32 coarse test exact
   uint32_t* plist = nullptr;             // cap x n: the force pairs of the current step (pass A -> B)
+  // staged pass A (FP32, 256-thread pair passes): per 256-target block its
+  // distinct neighbours sj (kStageCap per block), their count scount (-1: not
+  // staged) and the list again with ranks in that set (llist, cap x n)
+  int stage = 0;
+  uint32_t* llist = nullptr;
+  int* scount = nullptr;
+  int* sj = nullptr;
   uint32_t* pcount = nullptr;
   void* acc4 = nullptr;   // V4<T>: a_n and g = 0.05 rho_t r_c |a|
   void* rho = nullptr;    // T
@@ -76,6 +83,15 @@ cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& 
                            cudaStream_t st, const Grid<float>* G32 = nullptr, const Frame<float>* F32 = nullptr);
 template <int D, class T>
 cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P, PassFlags f, cudaStream_t st);
+// the staged pass A wants the largest shared-memory carveout (5 blocks of
+// 256 threads with 40 KB of staged views each); once per process
+template <int D>
+cudaError_t prepare_staged_pass();
+// whether pass A runs staged for these flags (the variant exists for FP32,
+// gamma = 2, no feature-surface particles, no neighbour diagnostics, 256 threads)
+inline bool staged_pass(const DevState& S, const PassFlags& f) {
+  return S.stage && !S.fp64 && S.pass_threads == 256 && !f.general_eos && !f.nbr_debug && !f.surface;
+}
 template <int D, class T>
 cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P, const Geom<T>& g, PassFlags f,
                           cudaStream_t st);

@@ -4,4 +4,5 @@
 namespace sph {
 SPH_INSTANTIATE_STEP(2, float)
 SPH_INSTANTIATE_STEP(2, double)
+template cudaError_t prepare_staged_pass<2>();
 }  // namespace sph

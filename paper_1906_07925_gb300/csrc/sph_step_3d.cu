@@ -4,4 +4,5 @@
 namespace sph {
 SPH_INSTANTIATE_STEP(3, float)
 SPH_INSTANTIATE_STEP(3, double)
+template cudaError_t prepare_staged_pass<3>();
 }  // namespace sph

@@ -47,6 +47,13 @@
 #ifndef SPH_LIST_MIN_BLOCKS
 #define SPH_LIST_MIN_BLOCKS 4
 #endif
+// the FP64 variants (FP64 pair arithmetic keeps more values live)
+#ifndef SPH_PASS_MIN_BLOCKS_FP64
+#define SPH_PASS_MIN_BLOCKS_FP64 SPH_PASS_MIN_BLOCKS
+#endif
+#ifndef SPH_PASSB_MIN_BLOCKS_FP64
+#define SPH_PASSB_MIN_BLOCKS_FP64 SPH_PASSB_MIN_BLOCKS
+#endif
 
 namespace sph {
 
@@ -173,6 +180,48 @@ template <class VT, class Fn>
 __device__ __forceinline__ void for_skin_list(const uint32_t* __restrict__ list, const VT* __restrict__ view, int n,
                                               int i, uint32_t lc, int cap, Fn&& pair) {
   for_list(list, view, n, i, list_cnt(lc), list_in(lc), cap, pair);
+}
+
+// Staged lists (pass A, FP32): in a block whose distinct neighbours fit in
+// shared memory, entry k of particle i's list is also stored, at the same
+// position of llist, as (rank << 8 | colour_j) with bit kStageSelf set for
+// j = i; rank numbers j within the block's staged set (sj). The views of the
+// set are gathered into shared memory once per step, so the list walk reads
+// them there instead of gathering each from global memory.
+constexpr uint32_t kStageSelf = 1u << 20;
+__device__ __forceinline__ int stage_rank(uint32_t e) {
+  const int r = (int)((e >> 8) & 0xFFFu);
+  return r < kStageCap ? r : kStageCap - 1;  // in range by construction; the clamp keeps any stale word in bounds
+}
+template <class VT, class Fn>
+__device__ __forceinline__ void for_staged_list(const uint32_t* __restrict__ llist, const VT* sview, int n, int i,
+                                                uint32_t lc, int cap, Fn&& pair) {
+  constexpr int B = SPH_LIST_BATCH;
+  const int cnt = list_cnt(lc), n_in = list_in(lc);
+  int k = 0;
+  for (; k + B <= cnt; k += B) {
+    uint32_t e[B];
+    VT v[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) e[q] = __ldcs(llist + list_row(k + q, n_in, cap) * n + i);
+#pragma unroll
+    for (int q = 0; q < B; ++q) v[q] = sview[stage_rank(e[q])];
+#pragma unroll
+    for (int q = 0; q < B; ++q) pair(e[q], v[q]);
+  }
+  for (; k < cnt; ++k) {
+    const uint32_t e = __ldcs(llist + list_row(k, n_in, cap) * n + i);
+    pair(e, sview[stage_rank(e)]);
+  }
+}
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only), and the wait
+// for every copy this thread issued
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(a), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
 template <class T> __device__ __forceinline__ T pair_r(T r2);
@@ -317,13 +366,6 @@ __global__ void __launch_bounds__(256) k_view32(int n, const StepCtl* __restrict
 // (and h changed by at most lip_h times that), any pair inside the exact
 // criteria is still listed. Candidates come from rows of cells of every level
 // that can hold such a j, in the order (level, z row, y row, x).
-//
-// Each lane walks its own rows with a small state machine instead of nested
-// loops: with nested loops a lane waits at every row's end for the longest row
-// of the warp. Here the warp tests candidates while at least half of its live
-// lanes still have some in their current row, then every lane whose row ran
-// out moves to its next non-empty row at once. The candidate order of each
-// list is that of the nested loops, so the lists are the same.
 template <int D, class T>
 __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, StepCtl* __restrict__ ctl,
                                                     const LL4* __restrict__ X0, const LL4* __restrict__ X1,
@@ -336,18 +378,13 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   using VT = typename ViewOf<T>::type;
   if (!ctl->rebuild) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  // lanes past n stay in the warp (they take part in the votes) with no rows
-  const bool valid = i < n;
+  if (i >= n) return;
   const int buf = ctl->buf;
   const VT* __restrict__ view = ctl->vp ? v1 : v0;
   const uint32_t* __restrict__ meta = buf ? m1 : m0;
-  LL4 X{};
-  VT vi{};
-  if (valid) {
-    X = (buf ? X1 : X0)[i];
-    vi = view[i];
-  }
-  const T hv = valid ? view_h(vi) : T(1);  // view units
+  const LL4 X = (buf ? X1 : X0)[i];
+  const VT vi = view[i];
+  const T hv = view_h(vi);                 // view units
   const T sk = F.skin * hv;                // skin of i, view units (kappa folded in by the host)
   const T sk_hv = F.skin;                  // skin per unit h
   const T lip = G.lip_h;
@@ -361,84 +398,13 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   }
   const T hlo = hv * T(0.99999) - lip * Rs;
   const T qv = F.qv;
-  const int l0 = level_of_h(G, hlo * qv), l1 = valid ? level_of_h(G, hhi * qv) : l0 - 1;
+  const int l0 = level_of_h(G, hlo * qv), l1 = level_of_h(G, hhi * qv);
   const T R2 = Rs * Rs;
   int cnt = 0, n_in = 0, n_out = 0;  // accepted; written inside / outside entries
   bool over = false;
   T reach = 0;
   const T Hd = kappa * hv;
 
-  // row walker: level l (its cell of i, i's offset in it, the z and y row
-  // ranges the search ball reaches), row (dz, dy), candidates [j, je)
-  int l = l0 - 1, dz = 0, zlo = 0, zhi = 0, dy = 0, ylo = 0, yhi = 0;
-  int cxl = 0, cyl = 0, czl = 0, nx = 0, ny = 0, nz = 0;
-  uint32_t base = 0;
-  T fx = 0, fy = 0, fz = 0, c = 1, ic = 1;
-  int j = 0, je = 0;
-  auto enter_level = [&]() {
-    const int sh = G.cshift + l;
-    nx = G.nx[l];
-    ny = G.ny[l];
-    nz = G.nz[l];
-    cxl = (int)min((long long)nx - 1, X.x >> sh);
-    cyl = (int)min((long long)ny - 1, X.y >> sh);
-    czl = D == 3 ? (int)min((long long)nz - 1, X.z >> sh) : 0;
-    c = G.cellv[l];
-    ic = T(1) / c;
-    // target position inside its level-l cell, view units
-    fx = (T)((double)(X.x - ((long long)cxl << sh)) * F.s2v);
-    fy = (T)((double)(X.y - ((long long)cyl << sh)) * F.s2v);
-    fz = D == 3 ? (T)((double)(X.z - ((long long)czl << sh)) * F.s2v) : T(0);
-    base = G.base[l];
-    zlo = zhi = 0;
-    if (D == 3) {
-      zlo = (int)dfloor((fz - Rs) * ic);
-      zhi = (int)dfloor((fz + Rs) * ic);
-    }
-    ylo = (int)dfloor((fy - Rs) * ic);
-    yhi = (int)dfloor((fy + Rs) * ic);
-    dz = zlo - 1;  // the next step moves to the first row of zlo
-  };
-  // next (level, dz, dy) in loop order; false past the last level
-  auto step_row = [&]() -> bool {
-    if (++dy <= yhi) return true;
-    while (++dz > zhi) {
-      if (++l > l1) return false;
-      enter_level();
-    }
-    dy = ylo;
-    return true;
-  };
-  // next row holding candidates; false when i has none left
-  auto next_row = [&]() -> bool {
-    while (step_row()) {
-      const int czz = czl + dz;
-      if (D == 3 && (czz < 0 || czz >= nz)) continue;
-      const int cyy = cyl + dy;
-      if (cyy < 0 || cyy >= ny) continue;
-      T dzp = 0;
-      if (D == 3) {
-        const T zrel = fz - (T)dz * c;
-        dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
-      }
-      const T yrel = fy - (T)dy * c;
-      const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
-      const T dp2 = dyp * dyp + dzp * dzp;
-      if (dp2 >= R2) continue;
-      const T half = dsqrt(R2 - dp2);
-      int x0 = cxl + (int)dfloor((fx - half) * ic);
-      int x1 = cxl + (int)dfloor((fx + half) * ic);
-      x0 = x0 < 0 ? 0 : x0;
-      x1 = x1 > nx - 1 ? nx - 1 : x1;
-      if (x0 > x1) continue;
-      const uint32_t krow = base + (uint32_t)nx * ((uint32_t)cyy + (uint32_t)ny * (uint32_t)(D == 3 ? czz : 0));
-      j = (int)cstart[krow + (uint32_t)x0];
-      je = (int)cstart[krow + (uint32_t)x1 + 1];
-      if (j < je) return true;
-    }
-    j = je = 0;
-    return false;
-  };
   // one candidate: every test is evaluated without a branch (most candidates
   // fail, and a branch over the acceptance tests ran for a few lanes of the
   // warp in nearly every iteration); only the list store is conditional
@@ -473,44 +439,60 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
     }
   };
 
-  if (valid) {
-    for (l = l0; l <= l1; ++l) {
-      enter_level();
-      for (dz = zlo; dz <= zhi; ++dz) {
-        const int czz = czl + dz;
-        if (D == 3 && (czz < 0 || czz >= nz)) continue;
-        T dzp = 0;
-        if (D == 3) {
-          const T zrel = fz - (T)dz * c;
-          dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
+  for (int l = l0; l <= l1; ++l) {
+    const int sh = G.cshift + l;
+    const int nx = G.nx[l], ny = G.ny[l], nz = G.nz[l];
+    const int cxl = (int)min((long long)nx - 1, X.x >> sh);
+    const int cyl = (int)min((long long)ny - 1, X.y >> sh);
+    const int czl = D == 3 ? (int)min((long long)nz - 1, X.z >> sh) : 0;
+    const T c = G.cellv[l], ic = T(1) / c;
+    // target position inside its level-l cell, view units
+    const T fx = (T)((double)(X.x - ((long long)cxl << sh)) * F.s2v);
+    const T fy = (T)((double)(X.y - ((long long)cyl << sh)) * F.s2v);
+    const T fz = D == 3 ? (T)((double)(X.z - ((long long)czl << sh)) * F.s2v) : T(0);
+    const uint32_t base = G.base[l];
+    int zlo = 0, zhi = 0;
+    if (D == 3) {
+      zlo = (int)dfloor((fz - Rs) * ic);
+      zhi = (int)dfloor((fz + Rs) * ic);
+    }
+    const int ylo = (int)dfloor((fy - Rs) * ic), yhi = (int)dfloor((fy + Rs) * ic);
+    for (int dz = zlo; dz <= zhi; ++dz) {
+      const int czz = czl + dz;
+      if (D == 3 && (czz < 0 || czz >= nz)) continue;
+      T dzp = 0;
+      if (D == 3) {
+        const T zrel = fz - (T)dz * c;
+        dzp = zrel < T(0) ? -zrel : (zrel > c ? zrel - c : T(0));
+      }
+      for (int dy = ylo; dy <= yhi; ++dy) {
+        const int cyy = cyl + dy;
+        if (cyy < 0 || cyy >= ny) continue;
+        const T yrel = fy - (T)dy * c;
+        const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
+        const T dp2 = dyp * dyp + dzp * dzp;
+        if (dp2 >= R2) continue;
+        const T half = dsqrt(R2 - dp2);
+        int x0 = cxl + (int)dfloor((fx - half) * ic);
+        int x1 = cxl + (int)dfloor((fx + half) * ic);
+        x0 = x0 < 0 ? 0 : x0;
+        x1 = x1 > nx - 1 ? nx - 1 : x1;
+        if (x0 > x1) continue;
+        const uint32_t krow = base + (uint32_t)nx * ((uint32_t)cyy + (uint32_t)ny * (uint32_t)(D == 3 ? czz : 0));
+        const int jb = (int)cstart[krow + (uint32_t)x0], je = (int)cstart[krow + (uint32_t)x1 + 1];
+        // candidates in ascending order, two views loaded before either is
+        // tested (two loads in flight per thread: a rebuild of the 8M 3D
+        // workload 3.5 % faster than one at a time)
+        int j = jb;
+        for (; j + 2 <= je; j += 2) {
+          const VT va = view[j], vb = view[j + 1];
+          cand(j, va);
+          cand(j + 1, vb);
         }
-        for (dy = ylo; dy <= yhi; ++dy) {
-          const int cyy = cyl + dy;
-          if (cyy < 0 || cyy >= ny) continue;
-          const T yrel = fy - (T)dy * c;
-          const T dyp = yrel < T(0) ? -yrel : (yrel > c ? yrel - c : T(0));
-          const T dp2 = dyp * dyp + dzp * dzp;
-          if (dp2 >= R2) continue;
-          const T half = dsqrt(R2 - dp2);
-          int x0 = cxl + (int)dfloor((fx - half) * ic);
-          int x1 = cxl + (int)dfloor((fx + half) * ic);
-          x0 = x0 < 0 ? 0 : x0;
-          x1 = x1 > nx - 1 ? nx - 1 : x1;
-          if (x0 > x1) continue;
-          const uint32_t krow = base + (uint32_t)nx * ((uint32_t)cyy + (uint32_t)ny * (uint32_t)(D == 3 ? czz : 0));
-          const int jb = (int)cstart[krow + (uint32_t)x0], jend = (int)cstart[krow + (uint32_t)x1 + 1];
-          int jj = jb;
-          for (; jj + 2 <= jend; jj += 2) {
-            const VT va = view[jj], vb = view[jj + 1];
-            cand(jj, va);
-            cand(jj + 1, vb);
-          }
-          for (; jj < jend; ++jj) cand(jj, view[jj]);
-        }
+        for (; j < je; ++j) cand(j, view[j]);
       }
     }
   }
-  if (!valid) return;
   // the coarse FP32 conversion is exact below 2^22 coarse integers = 2^(22 - kCoarseBits) c0
   const bool fast = reach < T(0.999) * T(1 << (22 - kCoarseBits));
   lcount[i] = (uint32_t)n_in | ((uint32_t)n_out << kOutShift) | (fast ? kFastBit : 0u);
@@ -519,6 +501,93 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   const unsigned mask = __activemask();
   const int wmax = __reduce_max_sync(mask, cnt);
   if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicMax(&ctl->lmax, wmax);
+}
+
+// Staged pass A, set up at a list rebuild: one block per kStageBlock targets
+// (the blocks of pass A). The distinct neighbours j of the block's lists go
+// into a hash set in shared memory (linear probing); the occupied slots in slot
+// order number them (rank), sj[block][rank] = j and scount[block] = their
+// count; every list entry is written again into llist as (rank << 8 | colour),
+// with kStageSelf for j = i. A block with more than kStageCap neighbours, or a
+// set too crowded to probe, gets scount = -1: pass A gathers its views from
+// global memory. The ranks depend on the order of the hash inserts, but pass
+// A's sums follow the list order, so its results do not.
+constexpr int kStageHashBits = 12;
+static_assert((1 << kStageHashBits) == kStageHash, "hash set size");
+constexpr int kStageProbe = 64;
+__device__ __forceinline__ uint32_t stage_hash(int j) { return ((uint32_t)j * 2654435761u) >> (32 - kStageHashBits); }
+
+template <int D>
+__global__ void __launch_bounds__(kStageBlock) k_stage(int n, const StepCtl* __restrict__ ctl,
+                                                      const uint32_t* __restrict__ list,
+                                                      const uint32_t* __restrict__ lcount, int cap,
+                                                      uint32_t* __restrict__ llist, int* __restrict__ scount,
+                                                      int* __restrict__ sj) {
+  if (!ctl->rebuild) return;
+  __shared__ int tab[kStageHash];
+  __shared__ int rnk[kStageHash];
+  __shared__ int wsum[kStageBlock / 32];
+  __shared__ int bad;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int q = t; q < kStageHash; q += kStageBlock) tab[q] = -1;
+  if (t == 0) bad = 0;
+  __syncthreads();
+  const int i = blockIdx.x * kStageBlock + t;
+  const uint32_t lc = i < n ? lcount[i] : 0u;
+  const int cnt = list_cnt(lc), n_in = list_in(lc);
+  for (int k = 0; k < cnt; ++k) {
+    const int j = (int)(list[list_row(k, n_in, cap) * n + i] >> 8);
+    uint32_t q = stage_hash(j);
+    int p = 0;
+    for (; p < kStageProbe; ++p) {
+      const int old = atomicCAS(&tab[q], -1, j);
+      if (old == -1 || old == j) break;
+      q = (q + 1) & (kStageHash - 1);
+    }
+    if (p == kStageProbe) bad = 1;
+  }
+  __syncthreads();
+  const bool crowded = bad != 0;
+  // ranks: thread t owns slots [per t, per (t + 1)); exclusive scan of the counts
+  constexpr int per = kStageHash / kStageBlock;
+  int c = 0;
+  for (int q = 0; q < per; ++q) c += tab[t * per + q] >= 0;
+  int x = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  int r = x - c, m = 0;
+  for (int q = 0; q < kStageBlock / 32; ++q) {
+    r += q < w ? wsum[q] : 0;
+    m += wsum[q];
+  }
+  if (crowded || m > kStageCap) {
+    if (t == 0) scount[blockIdx.x] = -1;
+    return;
+  }
+  int* __restrict__ sjb = sj + (size_t)blockIdx.x * kStageCap;
+  for (int q = 0; q < per; ++q) {
+    const int slot = t * per + q;
+    const int j = tab[slot];
+    if (j >= 0) {
+      rnk[slot] = r;
+      sjb[r] = j;
+      ++r;
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < cnt; ++k) {
+    const size_t pos = list_row(k, n_in, cap) * n + i;
+    const uint32_t e = list[pos];
+    const int j = (int)(e >> 8);
+    uint32_t q = stage_hash(j);
+    for (int p = 0; p < kStageProbe && tab[q] != j; ++p) q = (q + 1) & (kStageHash - 1);
+    llist[pos] = ((uint32_t)rnk[q] << 8) | (e & 0xFFu) | (j == i ? kStageSelf : 0u);
+  }
+  if (t == 0) scount[blockIdx.x] = m;
 }
 
 // --------------------------------------------------------------------------
@@ -591,8 +660,8 @@ __global__ void __launch_bounds__(256) k_density(int n, const StepCtl* __restric
 // pair counts; the last block reduces them in fixed order and sets dt1, dt2
 // (Eq. time_step_size, see below).
 // --------------------------------------------------------------------------
-template <int D, class T, bool GENERAL, bool DBG, bool SURF, int NT>
-__global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(int n, StepCtl* ctl,
+template <int D, class T, bool GENERAL, bool DBG, bool SURF, int NT, bool STG = false>
+__global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASS_MIN_BLOCKS_FP64 : SPH_PASS_MIN_BLOCKS) * 256 / NT) k_pass_a(int n, StepCtl* ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
@@ -606,10 +675,15 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
                                                 long long* __restrict__ dbg_sum, uint32_t* __restrict__ plist,
                                                 uint32_t* __restrict__ pcount, const double* __restrict__ dt_fix,
                                                 double* __restrict__ dt_rec, const LL4* __restrict__ X0,
-                                                const LL4* __restrict__ X1, Geom<T> geo) {
+                                                const LL4* __restrict__ X1, Geom<T> geo,
+                                                const uint32_t* __restrict__ llist, const int* __restrict__ scount,
+                                                const int* __restrict__ sj) {
   using VT = typename ViewOf<T>::type;
+  static_assert(!STG || (std::is_same<T, float>::value && !GENERAL && !DBG && !SURF && NT == kStageBlock),
+                "staged pass A: FP32, gamma = 2, 256-target blocks");
   __shared__ Partial sm[8];
   __shared__ bool last;
+  extern __shared__ __align__(16) unsigned char stage_smem[];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const StepCtl cc = *ctl;
   const long long step = cc.step;
@@ -617,6 +691,20 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
   const VT* __restrict__ view = cc.vp ? v1 : v0;
   const T sigma = (T)sigma_of(cc, step);
   Partial part{DBL_MAX, 0.0, 0.0, 0.0, 0.0, 0, 0, 0, -1};
+  // staged block: this step's views of its neighbour set into shared memory
+  bool staged = false;
+  const int* __restrict__ sjb = nullptr;
+  VT* sview = reinterpret_cast<VT*>(stage_smem);
+  if constexpr (STG) {
+    const int m = min(scount[blockIdx.x], kStageCap);
+    staged = m >= 0;
+    if (staged) {
+      sjb = sj + (size_t)blockIdx.x * kStageCap;
+      for (int k = threadIdx.x; k < m; k += NT) cp_async16(sview + k, view + min(__ldg(sjb + k), n - 1));
+      cp_async_wait_all();
+    }
+    __syncthreads();
+  }
   if (i < n) {
     const uint32_t* __restrict__ pid = buf ? p1 : p0;
     const VT vi = view[i];
@@ -642,10 +730,12 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
     // Every skin-list entry: a screening test on the coarse vectors (when the
     // list build certified them), then the exact vectors and criteria for the
     // pairs that pass. This step's force pairs go to column i of plist.
-    auto loop = [&](auto fastc) {
+    auto loop = [&](auto fastc, auto stagedc) {
       constexpr bool FAST = decltype(fastc)::value;
-      for_skin_list(list, view, n, i, lc, cap, [&](uint32_t e, const VT& vj) {
-        const int j = (int)(e >> 8);
+      constexpr bool ST = decltype(stagedc)::value;  // e = (rank << 8 | colour), view from shared memory
+      auto pair = [&](uint32_t e, const VT& vj) {
+        const int j = ST ? -1 : (int)(e >> 8);  // global index (unstaged entries)
+        const bool self = ST ? (e & kStageSelf) != 0 : j == i;
         T dx = vd<FAST>(F, vi.x, vj.x), dy = vd<FAST>(F, vi.y, vj.y);
         T dz = D == 3 ? vd<FAST>(F, vi.z, vj.z) : T(0);
         T r2 = dx * dx + dy * dy + dz * dz;
@@ -660,7 +750,7 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
           r2 = dx * dx + dy * dy + dz * dz;
         }
         const bool inD = !GENERAL && r2 < Hd2;
-        const bool inF = r2 < Hf * Hf && j != i && (!surf || (meta[j] & kSurfaceBit));
+        const bool inF = r2 < Hf * Hf && !self && (!surf || (meta[j] & kSurfaceBit));
         if (!(inD || inF)) return;
         const T r = r2 > T(0) ? pair_r<T>(r2) : T(0);
         if (inD) {
@@ -686,15 +776,24 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
           ax += s * dx;
           ay += s * dy;
           az += s * dz;
-          SPH_PLIST_STORE(plist + (size_t)nf * n + i, e);  // this step's force pairs, for pass B
+          // this step's force pairs (global index | colour), for pass B
+          const uint32_t eg = ST ? ((uint32_t)__ldg(sjb + stage_rank(e)) << 8) | (e & 0xFFu) : e;
+          SPH_PLIST_STORE(plist + (size_t)nf * n + i, eg);
           ++nf;
           ni += other;
           if (DBG) sf += pid[j];
         }
-      });
+      };
+      if constexpr (ST) for_staged_list(llist, (const VT*)sview, n, i, lc, cap, pair);
+      else for_skin_list(list, view, n, i, lc, cap, pair);
     };
-    if (lc & kFastBit) loop(std::true_type{});
-    else loop(std::false_type{});
+    if (STG && staged) {
+      if (lc & kFastBit) loop(std::true_type{}, std::integral_constant<bool, STG>{});
+      else loop(std::false_type{}, std::integral_constant<bool, STG>{});
+    } else {
+      if (lc & kFastBit) loop(std::true_type{}, std::false_type{});
+      else loop(std::false_type{}, std::false_type{});
+    }
     pcount[i] = (uint32_t)nf;
     // back to physical units: rho ~ 1/H^D, a ~ (view length)^-(D+1)
     const T Hphys = Hd * qv;
@@ -847,7 +946,7 @@ __global__ void __launch_bounds__(NT, SPH_PASS_MIN_BLOCKS * 256 / NT) k_pass_a(i
 // skin since the list was built raises need_rebuild.
 // --------------------------------------------------------------------------
 template <int D, class T, int NT>
-__global__ void __launch_bounds__(NT, SPH_PASSB_MIN_BLOCKS * 256 / NT) k_pass_b(int n, StepCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASSB_MIN_BLOCKS_FP64 : SPH_PASSB_MIN_BLOCKS) * 256 / NT) k_pass_b(int n, StepCtl* __restrict__ ctl,
                                                 const typename ViewOf<T>::type* __restrict__ v0,
                                                 const typename ViewOf<T>::type* __restrict__ v1,
                                                 typename ViewOf<T>::type* __restrict__ w0,
@@ -1080,6 +1179,9 @@ cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& 
   } else {
     SPH_LIST_BUILD(T)(S.n, S.ctl, X0, X1, S.meta[0], S.meta[1], (const VT*)S.view[0], (const VT*)S.view[1],
                       S.cstart, F, G, kappa, S.cap, S.list, S.lcount, S.err);
+    if (S.stage && S.llist)
+      k_stage<D><<<grid_for(S.n, kStageBlock), kStageBlock, 0, st>>>(S.n, S.ctl, S.list, S.lcount, S.cap, S.llist,
+                                                                  S.scount, S.sj);
   }
 #undef SPH_LIST_BUILD
   return cudaGetLastError();
@@ -1103,7 +1205,8 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
                                               F, P,                                                             \
                                               pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
                                               f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix,     \
-                                              f.dt_rec, (const LL4*)S.X[0], (const LL4*)S.X[1], geo)
+                                              f.dt_rec, (const LL4*)S.X[0], (const LL4*)S.X[1], geo, S.llist,     \
+                                              S.scount, S.sj)
 #define SPH_PASS_A(GEN, DBG)           \
   do {                                 \
     if (tb == 128)                     \
@@ -1111,6 +1214,17 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
     else                               \
       SPH_PASS_A_NT(GEN, DBG, 256);    \
   } while (0)
+  if constexpr (std::is_same<T, float>::value) {
+    if (staged_pass(S, f)) {
+      k_pass_a<D, float, false, false, false, kStageBlock, true>
+          <<<grid_for(S.n, kStageBlock), kStageBlock, kStageCap * sizeof(int4), st>>>(
+              S.n, S.ctl, (const int4*)S.view[0], (const int4*)S.view[1], S.meta[0], S.meta[1], S.pid[0], S.pid[1],
+              S.list, S.lcount, S.cap, F, P, pc, (V4<float>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,
+              f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix, f.dt_rec, (const LL4*)S.X[0],
+              (const LL4*)S.X[1], geo, S.llist, S.scount, S.sj);
+      return cudaGetLastError();
+    }
+  }
   if (f.general_eos) {
     if (f.nbr_debug) SPH_PASS_A(true, true);
     else SPH_PASS_A(true, false);
@@ -1121,6 +1235,14 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
 #undef SPH_PASS_A
 #undef SPH_PASS_A_NT
   return cudaGetLastError();
+}
+
+template <int D>
+cudaError_t prepare_staged_pass() {
+  static cudaError_t e = cudaFuncSetAttribute(k_pass_a<D, float, false, false, false, kStageBlock, true>,
+                                              cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              (int)cudaSharedmemCarveoutMaxShared);
+  return e;
 }
 
 template <int D, class T>

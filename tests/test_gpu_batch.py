@@ -71,11 +71,12 @@ def test_batch_tune_restores_state_and_picks_a_trial():
     trials = info["trials"]
     # the branch counts first, then one trial per other value of each knob
     assert [t["branches"] for t in trials[:4]] == [1, 2, 6, 12]
-    assert len(trials) == 4 + 1 + 2  # the other of (128, 256), two of (0.75, 1, 1.5)
+    assert len(trials) == 4 + 1 + 2 + 1  # the other of (128, 256), two of (0.75, 1, 1.5), staging flipped
     ch = info["chosen"]
     assert info["n_branches"] == ch["branches"] in (1, 2, 6, 12)
     assert ch["ms_per_step"] == min(t["ms_per_step"] for t in trials)
-    assert any(all(t[k] == ch[k] for k in ("branches", "pass_threads", "cell_factor")) for t in trials)
+    assert any(all(t[k] == ch[k] for k in ("branches", "pass_threads", "cell_factor", "stage_views")) for t in trials)
+    assert trials[-1]["stage_views"] != trials[-2]["stage_views"]
     for k in range(12):
         assert np.abs(b.positions(k) - before[k]).max() <= 1e-14
         assert b.stats(k)["step"] == 2
@@ -93,17 +94,21 @@ def test_launch_configuration_leaves_results_unchanged():
     p = W.graded_inclusion_3d(20000, 8)
     pos, col, _ = W.sample_density(p, 20000, 5)
     ref = None
-    for threads in (256, 128):
+    for threads, stage in ((256, 0), (128, 0), (256, 1)):
         for graph in (True, False):
             r = make_gpu(p, pos, col, "fp32", use_graph=graph)
-            r.set_tuning(pass_threads=threads)
+            r.set_tuning(pass_threads=threads, stage_views=stage)
             assert r.tuning()["pass_threads"] == threads
+            assert r.tuning()["stage_views"] == stage
             r.step(4)
             x = r.positions()
+            if stage:
+                info = r.stage_info()
+                assert info["staged_blocks"] == info["blocks"] > 0, info
             r.close()
             if ref is None:
                 ref = x
-            assert np.array_equal(x, ref), (threads, graph)
+            assert np.array_equal(x, ref), (threads, stage, graph)
     r = make_gpu(p, pos, col, "fp32")
     r.set_tuning(cell_factor=1.5)
     assert r.tuning()["cell_factor"] == 1.5
