@@ -47,12 +47,14 @@
 #ifndef SPH_LIST_MIN_BLOCKS
 #define SPH_LIST_MIN_BLOCKS 4
 #endif
-// the FP64 variants (FP64 pair arithmetic keeps more values live)
+// the FP64 variants keep twice the registers live: at 5 blocks (48 registers)
+// they spilled 600-1,000 bytes per thread; at 2 blocks (128 registers) none,
+// and the 8M 3D FP64 step took 86 ms instead of 99.5 (3 blocks: 99.1)
 #ifndef SPH_PASS_MIN_BLOCKS_FP64
-#define SPH_PASS_MIN_BLOCKS_FP64 SPH_PASS_MIN_BLOCKS
+#define SPH_PASS_MIN_BLOCKS_FP64 2
 #endif
 #ifndef SPH_PASSB_MIN_BLOCKS_FP64
-#define SPH_PASSB_MIN_BLOCKS_FP64 SPH_PASSB_MIN_BLOCKS
+#define SPH_PASSB_MIN_BLOCKS_FP64 2
 #endif
 
 namespace sph {
