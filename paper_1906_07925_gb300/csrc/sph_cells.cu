@@ -40,14 +40,16 @@ __global__ void k_write_ctl(StepCtl* __restrict__ ctl, StepCtl v) { *ctl = v; }
 __global__ void __launch_bounds__(256) k_count(int n, const StepCtl* __restrict__ ctl, const uint32_t* __restrict__ key,
                                                uint32_t* __restrict__ cnt) {
   if (!ctl->rebuild) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  bool active = i < n;
-  unsigned mask = __ballot_sync(0xffffffffu, active);
-  if (!active) return;
-  uint32_t k = key[i];
-  unsigned peers = __match_any_sync(mask, k);
-  int leader = __ffs(peers) - 1;
-  if ((int)(threadIdx.x & 31) == leader) atomicAdd(&cnt[k], (uint32_t)__popc(peers));
+  for (int b0 = blockIdx.x * blockDim.x; b0 < n; b0 += gridDim.x * blockDim.x) {
+    const int i = b0 + threadIdx.x;
+    const bool active = i < n;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) continue;
+    const uint32_t k = key[i];
+    const unsigned peers = __match_any_sync(mask, k);
+    const int leader = __ffs(peers) - 1;
+    if ((int)(threadIdx.x & 31) == leader) atomicAdd(&cnt[k], (uint32_t)__popc(peers));
+  }
 }
 
 __global__ void __launch_bounds__(256) k_scatter(int n, const StepCtl* __restrict__ ctl,
@@ -56,19 +58,21 @@ __global__ void __launch_bounds__(256) k_scatter(int n, const StepCtl* __restric
                                                  uint32_t* __restrict__ cnt,
                                                  uint32_t* __restrict__ slots) {
   if (!ctl->rebuild) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  bool active = i < n;
-  unsigned mask = __ballot_sync(0xffffffffu, active);
-  if (!active) return;
-  uint32_t k = key[i];
-  unsigned peers = __match_any_sync(mask, k);
-  int lane = threadIdx.x & 31;
-  int leader = __ffs(peers) - 1;
-  uint32_t top = 0;
-  if (lane == leader) top = atomicSub(&cnt[k], (uint32_t)__popc(peers));
-  top = __shfl_sync(peers, top, leader);
-  int rank = __popc(peers & ((1u << lane) - 1u));
-  slots[cstart[k] + top - 1 - rank] = (uint32_t)i;
+  for (int b0 = blockIdx.x * blockDim.x; b0 < n; b0 += gridDim.x * blockDim.x) {
+    const int i = b0 + threadIdx.x;
+    const bool active = i < n;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) continue;
+    const uint32_t k = key[i];
+    const unsigned peers = __match_any_sync(mask, k);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t top = 0;
+    if (lane == leader) top = atomicSub(&cnt[k], (uint32_t)__popc(peers));
+    top = __shfl_sync(peers, top, leader);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    slots[cstart[k] + top - 1 - rank] = (uint32_t)i;
+  }
 }
 
 // per block: sum of a tile of kScanTile counts
@@ -183,20 +187,20 @@ __global__ void __launch_bounds__(256) k_stable_gather(
     const uint32_t* __restrict__ cstart, State64* __restrict__ X0, State64* __restrict__ X1,
     uint32_t* __restrict__ m0, uint32_t* __restrict__ m1, uint32_t* __restrict__ p0, uint32_t* __restrict__ p1) {
   if (!ctl->rebuild) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= n) return;
   const int nb = ctl->buf;  // new buffer; the old order lives in the other one
   const uint32_t* __restrict__ pold = nb ? p0 : p1;
-  uint32_t i = slots[s];
-  uint32_t k = key[i];
-  const uint32_t id = pold[i];
-  uint32_t b = cstart[k], e = cstart[k + 1];
-  uint32_t rank = 0;
-  for (uint32_t t = b; t < e; ++t) rank += pold[slots[t]] < id;
-  uint32_t d = b + rank;
-  (nb ? X1 : X0)[d] = (nb ? X0 : X1)[i];
-  (nb ? m1 : m0)[d] = (nb ? m0 : m1)[i];
-  (nb ? p1 : p0)[d] = (nb ? p0 : p1)[i];
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    const uint32_t i = slots[s];
+    const uint32_t k = key[i];
+    const uint32_t id = pold[i];
+    const uint32_t b = cstart[k], e = cstart[k + 1];
+    uint32_t rank = 0;
+    for (uint32_t t = b; t < e; ++t) rank += pold[slots[t]] < id;
+    const uint32_t d = b + rank;
+    (nb ? X1 : X0)[d] = (nb ? X0 : X1)[i];
+    (nb ? m1 : m0)[d] = (nb ? m0 : m1)[i];
+    (nb ? p1 : p0)[d] = (nb ? p0 : p1)[i];
+  }
 }
 
 // feature-surface flags by particle id into the current meta words (colours kept)
@@ -255,7 +259,7 @@ cudaError_t build_cells(const DevState& S, cudaStream_t st) {
   const int n = S.n;
   if (n <= 0) return cudaSuccess;
   const int tb = 256;
-  const int gb = (n + tb - 1) / tb;
+  const int gb = rebuild_grid(n, tb, 8);
   k_count<<<gb, tb, 0, st>>>(n, S.ctl, S.key, S.cnt);
   const uint32_t m = S.total_cells;
   const int nb = (int)((m + kScanTile - 1) / kScanTile);

@@ -66,6 +66,25 @@ cudaError_t build_cells(const DevState& S, cudaStream_t st);
 cudaError_t launch_set_surface(const DevState& S, const uint8_t* flags, cudaStream_t st);
 cudaError_t launch_get_colors(const DevState& S, uint8_t* out, cudaStream_t st);
 
+// streaming multiprocessors of the current device (cached once per process)
+inline int device_sms() {
+  static const int sms = [] {
+    int d = 0, v = 0;
+    if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
+      return 152;
+    return v > 0 ? v : 152;
+  }();
+  return sms;
+}
+// Grid of a predicated list-rebuild kernel: grid-stride over n with at most
+// per_sm blocks per SM. Most steps do not rebuild, and such a kernel then
+// exits at once: with one block per 256 particles an 8M-particle grid took
+// about 19 us to launch and retire its 32,768 blocks, a capped grid a few.
+inline int rebuild_grid(int n, int tb, int per_sm) {
+  const int g = (n + tb - 1) / tb, cap = device_sms() * per_sm;
+  return g < 1 ? 1 : (g < cap ? g : cap);
+}
+
 struct PassFlags {
   int general_eos = 0;  // gamma != 2: density pass first, pressure p/rho^2
   int record = 0;       // keep rho and a~ for output

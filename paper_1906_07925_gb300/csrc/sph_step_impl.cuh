@@ -311,16 +311,16 @@ __global__ void __launch_bounds__(256) k_rekey(int n, const StepCtl* __restrict_
                                                const LL4* __restrict__ X1, Frame<T> F, Grid<T> G, Geom<T> geo,
                                                uint32_t* __restrict__ key) {
   if (!ctl->rebuild) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const LL4 X = (ctl->buf ? X0 : X1)[i];
-  T x[3];
-  abs_pos<D, T>(F, X, x);
-  const int l = level_of_h(G, h_of<D, T>(geo, x));
-  const int sh = G.cshift + l;
-  const int c[3] = {(int)min((long long)G.nx[l] - 1, X.x >> sh), (int)min((long long)G.ny[l] - 1, X.y >> sh),
-                    D == 3 ? (int)min((long long)G.nz[l] - 1, X.z >> sh) : 0};
-  key[i] = G.base[l] + (uint32_t)c[0] + (uint32_t)G.nx[l] * ((uint32_t)c[1] + (uint32_t)G.ny[l] * (uint32_t)c[2]);
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const LL4 X = (ctl->buf ? X0 : X1)[i];
+    T x[3];
+    abs_pos<D, T>(F, X, x);
+    const int l = level_of_h(G, h_of<D, T>(geo, x));
+    const int sh = G.cshift + l;
+    const int c[3] = {(int)min((long long)G.nx[l] - 1, X.x >> sh), (int)min((long long)G.ny[l] - 1, X.y >> sh),
+                      D == 3 ? (int)min((long long)G.nz[l] - 1, X.z >> sh) : 0};
+    key[i] = G.base[l] + (uint32_t)c[0] + (uint32_t)G.nx[l] * ((uint32_t)c[1] + (uint32_t)G.ny[l] * (uint32_t)c[2]);
+  }
 }
 
 // views of the (new) current order and the reference view for the skin test
@@ -331,15 +331,15 @@ __global__ void __launch_bounds__(256) k_make_view(int n, const StepCtl* __restr
                                                    typename ViewOf<T>::type* __restrict__ v1,
                                                    typename ViewOf<T>::type* __restrict__ vbuild) {
   if (!force && !ctl->rebuild) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const LL4 X = (ctl->buf ? X1 : X0)[i];
-  T x[3];
-  abs_pos<D, T>(F, X, x);
-  const T h = h_of<D, T>(geo, x);
-  const auto v = make_view<D>(F, X, h);
-  (ctl->vp ? v1 : v0)[i] = v;
-  vbuild[i] = with_w(v, T(0.5) * F.skin * view_h(v));  // half the skin, view units (kappa folded in by the host)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const LL4 X = (ctl->buf ? X1 : X0)[i];
+    T x[3];
+    abs_pos<D, T>(F, X, x);
+    const T h = h_of<D, T>(geo, x);
+    const auto v = make_view<D>(F, X, h);
+    (ctl->vp ? v1 : v0)[i] = v;
+    vbuild[i] = with_w(v, T(0.5) * F.skin * view_h(v));  // half the skin, view units (kappa folded in by the host)
+  }
 }
 
 // FP32 view of the FP64 path's particles, made at a list rebuild for its list
@@ -353,13 +353,13 @@ __global__ void __launch_bounds__(256) k_view32(int n, const StepCtl* __restrict
                                                 Frame<float> F, const V4<double>* __restrict__ vd0,
                                                 const V4<double>* __restrict__ vd1, int4* __restrict__ out) {
   if (!ctl->rebuild) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const LL4 X = (ctl->buf ? X1 : X0)[i];
-  const double hv = (ctl->vp ? vd1 : vd0)[i].w;  // h in view units (c0, both precisions)
   const long long half = 1LL << (F.sv - 1);
-  out[i] = make_int4((int)((X.x + half) >> F.sv), (int)((X.y + half) >> F.sv),
-                     D == 3 ? (int)((X.z + half) >> F.sv) : 0, __float_as_int((float)hv));
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const LL4 X = (ctl->buf ? X1 : X0)[i];
+    const double hv = (ctl->vp ? vd1 : vd0)[i].w;  // h in view units (c0, both precisions)
+    out[i] = make_int4((int)((X.x + half) >> F.sv), (int)((X.y + half) >> F.sv),
+                       D == 3 ? (int)((X.z + half) >> F.sv) : 0, __float_as_int((float)hv));
+  }
 }
 
 // Neighbour list of each particle: every j (itself included) with
@@ -379,11 +379,13 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
                                                     uint32_t* __restrict__ lcount, int* __restrict__ err) {
   using VT = typename ViewOf<T>::type;
   if (!ctl->rebuild) return;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
   const int buf = ctl->buf;
   const VT* __restrict__ view = ctl->vp ? v1 : v0;
   const uint32_t* __restrict__ meta = buf ? m1 : m0;
+  int cmax = 0;  // longest list of this thread's targets
+  bool over_any = false;
+  // grid-stride over the targets (one per thread at the grid it is launched with)
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
   const LL4 X = (buf ? X1 : X0)[i];
   const VT vi = view[i];
   const T hv = view_h(vi);                 // view units
@@ -498,11 +500,13 @@ __global__ void __launch_bounds__(256, SPH_LIST_MIN_BLOCKS) k_list_build(int n, 
   // the coarse FP32 conversion is exact below 2^22 coarse integers = 2^(22 - kCoarseBits) c0
   const bool fast = reach < T(0.999) * T(1 << (22 - kCoarseBits));
   lcount[i] = (uint32_t)n_in | ((uint32_t)n_out << kOutShift) | (fast ? kFastBit : 0u);
-  if (over) atomicOr(err, kErrListOverflow);
-  // longest list of this build (one atomic per warp)
-  const unsigned mask = __activemask();
-  const int wmax = __reduce_max_sync(mask, cnt);
-  if ((threadIdx.x & 31) == __ffs(mask) - 1) atomicMax(&ctl->lmax, wmax);
+  over_any |= over;
+  cmax = cnt > cmax ? cnt : cmax;
+  }  // targets
+  if (over_any) atomicOr(err, kErrListOverflow);
+  // longest list of this build (one atomic per warp; every lane gets here)
+  const int wmax = __reduce_max_sync(0xffffffffu, cmax);
+  if ((threadIdx.x & 31) == 0 && wmax > 0) atomicMax(&ctl->lmax, wmax);
 }
 
 // Staged pass A, set up at a list rebuild: one block per kStageBlock targets
@@ -1160,11 +1164,16 @@ template <int D, class T>
 cudaError_t launch_rebuild(const DevState& S, const Grid<T>& G, const Frame<T>& F, const Geom<T>& g, T kappa,
                            cudaStream_t st, const Grid<float>* G32, const Frame<float>* F32) {
   using VT = typename ViewOf<T>::type;
-  const int tb = 256, gb = grid_for(S.n, tb);
+  // the cheap per-particle kernels on a capped grid (an idle launch costs a
+  // few us); the list build on one block per 256 targets: a grid capped at
+  // 16 or 32 blocks per SM made its rebuilds of the 8M 3D workload slower
+  // (cells 2.01 / 1.93 vs 1.86 ms per step), its blocks no longer finishing
+  // and refilling the SMs independently
+  const int tb = 256, gb = rebuild_grid(S.n, tb, 8), gl = grid_for(S.n, tb);
   const LL4* X0 = (const LL4*)S.X[0];
   const LL4* X1 = (const LL4*)S.X[1];
   k_rekey<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, X0, X1, F, G, g, S.key);
-#define SPH_LIST_BUILD(TT) k_list_build<D, TT><<<gb, tb, 0, st>>>
+#define SPH_LIST_BUILD(TT) k_list_build<D, TT><<<gl, tb, 0, st>>>
   cudaError_t e = build_cells(S, st);
   if (e != cudaSuccess) return e;
   k_make_view<D, T><<<gb, tb, 0, st>>>(S.n, S.ctl, 0, X0, X1, F, g, (VT*)S.view[0], (VT*)S.view[1],
