@@ -31,6 +31,12 @@
 
 #include "sph_step_impl.cuh"
 
+// resident 256-thread blocks per SM asked of the FP32 k_bwd_force (caps its
+// registers: 4 -> 64)
+#ifndef SPH_BWD_FORCE_MIN_BLOCKS
+#define SPH_BWD_FORCE_MIN_BLOCKS 4
+#endif
+
 namespace sph {
 
 // Wendland C2 pieces in physical units, c = alpha_d (7/pi, 21/(2 pi)):
@@ -476,7 +482,7 @@ __device__ __forceinline__ void field_adjoint(const Frame<T>& F, const Geom<T>& 
 // Q = p/rho^2 = P0 (rho/rho_t)^gamma / rho^2 (P0 T in the gamma = 2 form).
 // ------------------------------------------------------------------------
 template <int D, class T, bool GENERAL>
-__global__ void __launch_bounds__(256) k_bwd_force(int n, const StepCtl* __restrict__ ctl,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? SPH_BWD_FORCE_MIN_BLOCKS : 2) k_bwd_force(int n, const StepCtl* __restrict__ ctl,
                                                    const typename ViewOf<T>::type* __restrict__ v0,
                                                    const typename ViewOf<T>::type* __restrict__ v1,
                                                    const uint32_t* __restrict__ m0, const uint32_t* __restrict__ m1,
