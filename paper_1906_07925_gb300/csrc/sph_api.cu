@@ -1411,7 +1411,12 @@ sph_status sph_backward(sph_handle* h, int32_t K, const sph_objective* obj, cons
   for (int s = 0; s < K; ++s) {
     if (s % c == 0) SPH_TRY(positions_to(h, ck + nd * (size_t)(s / c)));
     if (s >= last0) {
-      SPH_TRY(taped_step(h, tape[s - last0], nullptr, nullptr));
+      // the graph of a taped step into slot k, shared with the re-runs (the
+      // step-size history mode is read from the control block at run time)
+      const int k = s - last0;
+      if (!a.g_rerun[k])
+        SPH_TRY(capture(h, &a.g_rerun[k], [&] { return taped_step(h, tape[k], nullptr, nullptr); }));
+      SPH_CUDA(h, cudaGraphLaunch(a.g_rerun[k], h->stream));
     } else {
       SPH_TRY(ensure_graph(h, 0));  // the handle's graph of one step
       SPH_CUDA(h, cudaGraphLaunch(h->gexec, h->stream));
