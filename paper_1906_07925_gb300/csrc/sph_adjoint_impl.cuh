@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(256) k_bwd_out(int n, const StepCtl* __restric
     for (int k = 0; k < 3; ++k) z[0][k] = T(0);
     for (int k = 0; k < D; ++k) {
       const T dk = (vt[k] + T(0.5) * dt2 * att[k]) * dt2;
-      long long u = Xc[k] + (long long)llrint((double)(dk * F.inv_q64t));
+      long long u = Xc[k] + state_units(dk * F.inv_q64t);
       if (u < 0) {
         u = 0;
         clamped[k] = true;
@@ -280,7 +280,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_bwd_visc(int n,
     T xx = 0, xy = 0, xz = 0;        // adjoint of x_i from the pairs
     T hbar = 0, Tbar = 0, etab = 0;
     const int cnt = (int)pcount[i];
-    for_list(plist, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+    struct Rec {
+      V4<T> a, atb;
+    };
+    for_list_x(plist, view, n, i, cnt, [&](int j) { return Rec{acc[j], B.atb[j]}; },
+               [&](uint32_t e, const VT& vj, const Rec& rj) {
       const int j = (int)(e >> 8);
       const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
       const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
@@ -291,8 +295,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_bwd_visc(int n,
       const T irv = drsqrt<T>(r2);  // 1/r, view units
       const T r = r2 * irv * qv, ir = irv * F.inv_qv, ex = dx * qv, ey = dy * qv, ez = dz * qv;
       const ForceD<D, T> f = force_fn<D, T>(r, Hv * qv, P.alpha);
-      const V4<T> aj = acc[j];
-      const V4<T> atbj = B.atb[j];
+      const V4<T>& aj = rj.a;
+      const V4<T>& atbj = rj.atb;
       const T Tj = inv_rho_t2<D, T>(hvj * qv, P.inv_tau);
       const T etaj = dt1 * aj.w;
       const T es = etai + etaj;
@@ -511,7 +515,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SPH_BWD_FORCE_MIN_BLOCKS
     T xx = 0, xy = 0, xz = 0, hbar = 0, Tbar = 0, Qbar = 0;
     T sb = 0, pb = 0;
     const int cnt = (int)pcount[i];
-    for_list(plist, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+    for_list_x(plist, view, n, i, cnt, [&](int j) { return B.ab[j]; }, [&](uint32_t e, const VT& vj, const V4<T>& abj) {
       const int j = (int)(e >> 8);
       const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
       const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
@@ -529,7 +533,6 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? SPH_BWD_FORCE_MIN_BLOCKS
       const T Ts = Ti + Tj;
       const T coef = Qi + Qj + beta * P0 * Ts;
       const T S = -coef * f.F;
-      const V4<T> abj = B.ab[j];
       const T gx = abi.x - abj.x, gy = abi.y - abj.y, gz = abi.z - abj.z;
       xx += S * gx;
       xy += S * gy;

@@ -177,6 +177,39 @@ __device__ __forceinline__ void for_list(const uint32_t* __restrict__ list, cons
                                          int cnt, Fn&& pair) {
   for_list(list, view, n, i, cnt, cnt, 0, pair);
 }
+// A compact list (rows 0 .. cnt-1) whose pair body also needs a record of
+// the neighbour (its acceleration, an adjoint): that record, fetch(j), is
+// loaded for the whole batch together with the views, so each thread keeps
+// 2 x SPH_LIST_BATCH_X independent gathers in flight instead of meeting the
+// record's latency inside every pair body.
+#ifndef SPH_LIST_BATCH_X
+#define SPH_LIST_BATCH_X 2  // 4 spilled at the 48 / 64-register budgets of the passes using it
+#endif
+template <class VT, class Fetch, class Fn>
+__device__ __forceinline__ void for_list_x(const uint32_t* __restrict__ list, const VT* __restrict__ view, int n,
+                                           int i, int cnt, Fetch&& fetch, Fn&& pair) {
+  using XT = decltype(fetch(0));
+  constexpr int B = SPH_LIST_BATCH_X;
+  int k = 0;
+  for (; k + B <= cnt; k += B) {
+    uint32_t e[B];
+    VT v[B];
+    XT x[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) e[q] = __ldcs(list + (size_t)(k + q) * n + i);
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      v[q] = view[e[q] >> 8];
+      x[q] = fetch((int)(e[q] >> 8));
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) pair(e[q], v[q], x[q]);
+  }
+  for (; k < cnt; ++k) {
+    const uint32_t e = __ldcs(list + (size_t)k * n + i);
+    pair(e, view[e >> 8], fetch((int)(e >> 8)));
+  }
+}
 // the skin list of particle i (split at its build, see kFastBit)
 template <class VT, class Fn>
 __device__ __forceinline__ void for_skin_list(const uint32_t* __restrict__ list, const VT* __restrict__ view, int n,
@@ -225,6 +258,12 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
+
+// a length in state units rounded to the nearest integer (ties to even): the
+// FP32 value converts directly (the same integer as rounding its exact FP64
+// widening, without the FP64 conversion)
+__device__ __forceinline__ long long state_units(float x) { return __float2ll_rn(x); }
+__device__ __forceinline__ long long state_units(double x) { return llrint(x); }
 
 template <class T> __device__ __forceinline__ T pair_r(T r2);
 template <> __device__ __forceinline__ float pair_r<float>(float r2) { return r2 * rsqrtf(r2); }
@@ -984,7 +1023,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASSB_MIN_BLOCKS_FP6
     // this step's pairs as pass A compacted them (same positions); the force
     // support is tested again on the exact vectors
     const int cnt = (int)pcount[i];
-    for_list(plist, view, n, i, cnt, [&](uint32_t e, const VT& vj) {
+    for_list_x(plist, view, n, i, cnt, [&](int j) { return acc[j]; }, [&](uint32_t e, const VT& vj, const V4<T>& aj) {
       const int j = (int)(e >> 8);
       const T dx = vd<false>(F, vi.x, vj.x), dy = vd<false>(F, vi.y, vj.y);
       const T dz = D == 3 ? vd<false>(F, vi.z, vj.z) : T(0);
@@ -992,7 +1031,6 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASSB_MIN_BLOCKS_FP6
       const T hj = view_h(vj);
       const T Hf = half_kappa * (hv + hj);
       if (!(r2 < Hf * Hf) || j == i) return;
-      const V4<T> aj = acc[j];
       const T gs = ai.w + aj.w;
       const T hm = gs > T(0) ? T(2) * ai.w * aj.w * drcp<T>(gs) : T(0);
       const T invH = drcp<T>(Hf);
@@ -1038,7 +1076,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASSB_MIN_BLOCKS_FP6
     if (finite) {
       long long* Xc[3] = {&X.x, &X.y, &X.z};
       for (int k = 0; k < D; ++k) {
-        long long v = *Xc[k] + (long long)llrint((double)(d[k] * F.inv_q64t));
+        long long v = *Xc[k] + state_units(d[k] * F.inv_q64t);
         // bounding box (first constraint): clamp, the closest point
         if (v < 0) { v = 0; moved |= !surf; }
         if (v > F.xmax[k]) { v = F.xmax[k]; moved |= !surf; }
@@ -1058,7 +1096,7 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASSB_MIN_BLOCKS_FP6
       }
       if (mv) {
         for (int k = 0; k < D; ++k) {
-          long long v = (long long)llrint((double)((xa[k] - F.lo[k]) * F.inv_q64t));
+          long long v = state_units((xa[k] - F.lo[k]) * F.inv_q64t);
           v = v < 0 ? 0 : (v > F.xmax[k] ? F.xmax[k] : v);
           *Xc[k] = v;
         }
