@@ -198,6 +198,7 @@ sph_status launch_step(sph_handle* h, int record, int force_rebuild = 0, cudaEve
                        const DevState* tape = nullptr) {
   const DevState& S = Sx ? *Sx : h->S;
   PassFlags f;
+  f.f32 = &h->Ff;
   f.general_eos = h->par.gamma != 2.0;
   f.record = record;
   f.dt_fix = dt_fix;
@@ -251,6 +252,7 @@ sph_status launch_evaluate(sph_handle* h, int nbr_debug) {
   DevState S = h->S;
   S.scal = h->S.scal + 1;  // keep the last step's statistics
   PassFlags f;
+  f.f32 = &h->Ff;
   f.general_eos = h->par.gamma != 2.0;
   f.nbr_debug = nbr_debug;
   f.advance = 0;
@@ -448,6 +450,7 @@ sph_status positions_to(sph_handle* h, double* dst_dev) {
 sph_status reverse_setup(sph_handle* h, bool forward, const double* dt_fix) {
   DevState& S = h->S;
   PassFlags f;
+  f.f32 = &h->Ff;
   f.general_eos = h->par.gamma != 2.0;
   f.record = 1;
   f.advance = 0;

@@ -22,7 +22,7 @@ struct DevState {
   uint32_t* pid[2] = {nullptr, nullptr};   // particle id
   void* view[2] = {nullptr, nullptr};    // int4 (FP32) or double4 (FP64)
   void* vbuild = nullptr;                // view at the list build, w = half skin
-  void* view32 = nullptr;                // FP64 path: FP32 view for the list build (rebuild only)
+  void* view32 = nullptr;                // FP64 path: FP32 view (list build; pass A's screen)
   uint32_t* key = nullptr;               // cell key (old order, rebuild only)
   uint32_t* tmp = nullptr;               // scatter slots
   uint32_t* cnt = nullptr;               // per-cell counters (all zero between rebuilds)
@@ -95,6 +95,8 @@ struct PassFlags {
   double* dt_rec = nullptr;        // pass A: record {dt1, dt2} (device)
   const void* geo = nullptr;       // pass A: the Geom<T> of the handle (feature-surface normals)
   int surface = 0;                 // pass A: feature-surface particles may be flagged
+  const Frame<float>* f32 = nullptr;  // FP64 path: frame of its FP32 views (view32), kept current
+                                      // by pass B and screened on by pass A
 };
 
 template <int D, class T>

@@ -217,6 +217,43 @@ __device__ __forceinline__ void for_skin_list(const uint32_t* __restrict__ list,
   for_list(list, view, n, i, list_cnt(lc), list_in(lc), cap, pair);
 }
 
+// The FP64 path's skin list screened on its FP32 views (v32, kept current
+// every step): each entry is first tested on coarse FP32 differences
+// (screen), and only the entries that pass gather their FP64 view for the
+// exact FP64 tests (pair). The screen is conservative, so the pairs the
+// exact tests accept are the same as with an FP64 screen; the entries it
+// rejects cost no FP64 arithmetic (the FP64 pipe bounds that pass).
+template <class VT, class Screen, class Fn>
+__device__ __forceinline__ void for_skin_list_s32(const uint32_t* __restrict__ list, const int4* __restrict__ v32,
+                                                  const VT* __restrict__ view, int n, int i, uint32_t lc, int cap,
+                                                  Screen&& screen, Fn&& pair) {
+  constexpr int B = SPH_LIST_BATCH;
+  const int cnt = list_cnt(lc), n_in = list_in(lc);
+  int k = 0;
+  for (; k + B <= cnt; k += B) {
+    uint32_t e[B];
+    int4 w[B];
+    bool ok[B];
+    VT v[B];
+#pragma unroll
+    for (int q = 0; q < B; ++q) e[q] = __ldcs(list + list_row(k + q, n_in, cap) * n + i);
+#pragma unroll
+    for (int q = 0; q < B; ++q) w[q] = v32[e[q] >> 8];
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+      ok[q] = screen(w[q]);
+      if (ok[q]) v[q] = view[e[q] >> 8];
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q)
+      if (ok[q]) pair(e[q], v[q]);
+  }
+  for (; k < cnt; ++k) {
+    const uint32_t e = __ldcs(list + list_row(k, n_in, cap) * n + i);
+    if (screen(v32[e >> 8])) pair(e, view[e >> 8]);
+  }
+}
+
 // Staged lists (pass A, FP32): in a block whose distinct neighbours fit in
 // shared memory, entry k of particle i's list is also stored, at the same
 // position of llist, as (rank << 8 | colour_j) with bit kStageSelf set for
@@ -382,10 +419,11 @@ __global__ void __launch_bounds__(256) k_make_view(int n, const StepCtl* __restr
 }
 
 // FP32 view of the FP64 path's particles, made at a list rebuild for its list
-// build: the list only has to hold every pair the exact FP64 tests can accept
-// before the next rebuild, and an FP32 candidate test errs by ~1e-7 of the
-// distance, far inside the list's margins (the skin and the 1e-5 factor),
-// while FP64 arithmetic runs at a small fraction of the FP32 rate on this GPU.
+// build (and kept current every step by pass B for pass A's FP32 screen): the
+// list only has to hold every pair the exact FP64 tests can accept before the
+// next rebuild, and an FP32 candidate test errs by ~1e-7 of the distance, far
+// inside the list's margins (the skin and the 1e-5 factor), while FP64
+// arithmetic runs at a small fraction of the FP32 rate on this GPU.
 template <int D>
 __global__ void __launch_bounds__(256) k_view32(int n, const StepCtl* __restrict__ ctl,
                                                 const LL4* __restrict__ X0, const LL4* __restrict__ X1,
@@ -722,7 +760,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASS_MIN_BLOCKS_FP64
                                                 double* __restrict__ dt_rec, const LL4* __restrict__ X0,
                                                 const LL4* __restrict__ X1, Geom<T> geo,
                                                 const uint32_t* __restrict__ llist, const int* __restrict__ scount,
-                                                const int* __restrict__ sj) {
+                                                const int* __restrict__ sj, const int4* __restrict__ v32,
+                                                Frame<float> F32) {
   using VT = typename ViewOf<T>::type;
   static_assert(!STG || (std::is_same<T, float>::value && !GENERAL && !DBG && !SURF && NT == kStageBlock),
                 "staged pass A: FP32, gamma = 2, 256-target blocks");
@@ -775,9 +814,12 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASS_MIN_BLOCKS_FP64
     // Every skin-list entry: a screening test on the coarse vectors (when the
     // list build certified them), then the exact vectors and criteria for the
     // pairs that pass. This step's force pairs go to column i of plist.
-    auto loop = [&](auto fastc, auto stagedc) {
+    // FP64 path with current FP32 views: the screen in FP32 (for_skin_list_s32)
+    constexpr bool S32_OK = std::is_same<T, double>::value && !GENERAL && !DBG && !SURF;
+    auto loop = [&](auto fastc, auto stagedc, auto s32c) {
       constexpr bool FAST = decltype(fastc)::value;
       constexpr bool ST = decltype(stagedc)::value;  // e = (rank << 8 | colour), view from shared memory
+      constexpr bool S32 = decltype(s32c)::value;    // entries arrive screened on the FP32 views
       auto pair = [&](uint32_t e, const VT& vj) {
         const int j = ST ? -1 : (int)(e >> 8);  // global index (unstaged entries)
         const bool self = ST ? (e & kStageSelf) != 0 : j == i;
@@ -829,15 +871,31 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASS_MIN_BLOCKS_FP64
           if (DBG) sf += pid[j];
         }
       };
-      if constexpr (ST) for_staged_list(llist, (const VT*)sview, n, i, lc, cap, pair);
-      else for_skin_list(list, view, n, i, lc, cap, pair);
+      if constexpr (ST) {
+        for_staged_list(llist, (const VT*)sview, n, i, lc, cap, pair);
+      } else if constexpr (S32) {
+        const int4 wi = v32[i];
+        const float hv32 = __int_as_float(wi.w), hk32 = 0.5f * (float)P.kappa, Hd32 = (float)P.kappa * hv32;
+        auto screen = [&](const int4& w) {
+          const float cx = vd<true>(F32, wi.x, w.x), cy = vd<true>(F32, wi.y, w.y);
+          const float cz = D == 3 ? vd<true>(F32, wi.z, w.z) : 0.0f;
+          const float Hf32 = hk32 * (hv32 + __int_as_float(w.w));
+          const float Hm = screen_radius<float>(Hf32 > Hd32 ? Hf32 : Hd32);
+          return cx * cx + cy * cy + cz * cz < Hm * Hm;
+        };
+        for_skin_list_s32(list, v32, view, n, i, lc, cap, screen, pair);
+      } else {
+        for_skin_list(list, view, n, i, lc, cap, pair);
+      }
     };
     if (STG && staged) {
-      if (lc & kFastBit) loop(std::true_type{}, std::integral_constant<bool, STG>{});
-      else loop(std::false_type{}, std::integral_constant<bool, STG>{});
+      if (lc & kFastBit) loop(std::true_type{}, std::integral_constant<bool, STG>{}, std::false_type{});
+      else loop(std::false_type{}, std::integral_constant<bool, STG>{}, std::false_type{});
+    } else if (S32_OK && v32 && (lc & kFastBit)) {
+      loop(std::false_type{}, std::false_type{}, std::integral_constant<bool, S32_OK>{});
     } else {
-      if (lc & kFastBit) loop(std::true_type{}, std::false_type{});
-      else loop(std::false_type{}, std::false_type{});
+      if (lc & kFastBit) loop(std::true_type{}, std::false_type{}, std::false_type{});
+      else loop(std::false_type{}, std::false_type{}, std::false_type{});
     }
     pcount[i] = (uint32_t)nf;
     // back to physical units: rho ~ 1/H^D, a ~ (view length)^-(D+1)
@@ -1004,7 +1062,8 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASSB_MIN_BLOCKS_FP6
                                                 const Scalars* __restrict__ scal, V4<T>* __restrict__ visc_out,
                                                 int* __restrict__ err, unsigned long long* __restrict__ wall_moved,
                                                 int move, const uint32_t* __restrict__ m0,
-                                                const uint32_t* __restrict__ m1) {
+                                                const uint32_t* __restrict__ m1, int4* __restrict__ v32out,
+                                                int sv32) {
   using VT = typename ViewOf<T>::type;
   __shared__ int moved_sm[8];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1107,6 +1166,11 @@ __global__ void __launch_bounds__(NT, (sizeof(T) == 8 ? SPH_PASSB_MIN_BLOCKS_FP6
       const T hn = h_of<D, T>(geo, xa);
       const VT vn = make_view<D>(F, X, hn);
       (vp ? w0 : w1)[i] = vn;
+      if (v32out) {  // FP64 path: its FP32 view of the next step (as k_view32 makes it)
+        const long long half = 1LL << (sv32 - 1);
+        v32out[i] = make_int4((int)((X.x + half) >> sv32), (int)((X.y + half) >> sv32),
+                              D == 3 ? (int)((X.z + half) >> sv32) : 0, __float_as_int((float)view_h(vn)));
+      }
       // skin test against the view at list build
       const VT vb = vbuild[i];
       const T ex = vd<false>(F, vn.x, vb.x), ey = vd<false>(F, vn.y, vb.y);
@@ -1244,6 +1308,10 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
   const int tb = S.pass_threads == 128 ? 128 : 256, gb = grid_for(S.n, tb);
   T* rho = (T*)S.rho;
   T* pc = (T*)S.pc;
+  // the FP64 path screens on its FP32 views when the caller passes their frame
+  const bool s32 = std::is_same<T, double>::value && S.view32 && f.f32;
+  const int4* v32 = s32 ? (const int4*)S.view32 : nullptr;
+  const Frame<float> f32 = s32 ? *f.f32 : Frame<float>{};
   if (f.general_eos)
     k_density<D, T><<<grid_for(S.n, 256), 256, 0, st>>>(S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1],
                                                         S.list, S.lcount, S.cap, F, P, rho, pc);
@@ -1255,7 +1323,7 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
                                               pc, (V4<T>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,   \
                                               f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix,     \
                                               f.dt_rec, (const LL4*)S.X[0], (const LL4*)S.X[1], geo, S.llist,     \
-                                              S.scount, S.sj)
+                                              S.scount, S.sj, v32, f32)
 #define SPH_PASS_A(GEN, DBG)           \
   do {                                 \
     if (tb == 128)                     \
@@ -1270,7 +1338,7 @@ cudaError_t launch_pass_a(const DevState& S, const Frame<T>& F, const Phys<T>& P
               S.n, S.ctl, (const int4*)S.view[0], (const int4*)S.view[1], S.meta[0], S.meta[1], S.pid[0], S.pid[1],
               S.list, S.lcount, S.cap, F, P, pc, (V4<float>*)S.acc4, rho, S.partials, S.scal, S.tickets, S.err,
               f.advance, S.dbg_count, S.dbg_sum, S.plist, S.pcount, f.dt_fix, f.dt_rec, (const LL4*)S.X[0],
-              (const LL4*)S.X[1], geo, S.llist, S.scount, S.sj);
+              (const LL4*)S.X[1], geo, S.llist, S.scount, S.sj, nullptr, Frame<float>{});
       return cudaGetLastError();
     }
   }
@@ -1303,7 +1371,8 @@ cudaError_t launch_pass_b(const DevState& S, const Frame<T>& F, const Phys<T>& P
   (tb == 128 ? k_pass_b<D, T, 128> : k_pass_b<D, T, 256>)<<<gb, tb, 0, st>>>(
       S.n, S.ctl, (const VT*)S.view[0], (const VT*)S.view[1], (VT*)S.view[0], (VT*)S.view[1], (const VT*)S.vbuild,
       (LL4*)S.X[0], (LL4*)S.X[1], S.plist, S.pcount, (const V4<T>*)S.acc4, F, P, g, S.scal,
-      f.record ? (V4<T>*)S.visc : nullptr, S.err, wm, f.move, S.meta[0], S.meta[1]);
+      f.record ? (V4<T>*)S.visc : nullptr, S.err, wm, f.move, S.meta[0], S.meta[1],
+      (std::is_same<T, double>::value && S.view32 && f.f32) ? (int4*)S.view32 : nullptr, f.f32 ? f.f32->sv : 0);
   return cudaGetLastError();
 }
 
