@@ -32,18 +32,20 @@ def test_struct_layouts_match_header(tmp_path):
     src = tmp_path / "sizes.c"
     src.write_text(
         '#include <stdio.h>\n#include <stddef.h>\n#include "sphmesh.h"\n'
-        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+        "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
         "sizeof(sph_shape),sizeof(sph_domain),sizeof(sph_field),sizeof(sph_params),"
         "sizeof(sph_alloc),sizeof(sph_stats),sizeof(sph_grid_info),"
         "offsetof(sph_params,seed),offsetof(sph_stats,rho_scale),"
-        "sizeof(sph_background),offsetof(sph_background,spacing));return 0;}\n")
+        "sizeof(sph_background),offsetof(sph_background,spacing),"
+        "sizeof(sph_batch_trial),offsetof(sph_batch_trial,stage_views));return 0;}\n")
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = list(map(int, subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()))
     want = [C.sizeof(B.sph_shape), C.sizeof(B.sph_domain), C.sizeof(B.sph_field), C.sizeof(B.sph_params),
             C.sizeof(B.sph_alloc), C.sizeof(B.sph_stats), C.sizeof(B.sph_grid_info),
             B.sph_params.seed.offset, B.sph_stats.rho_scale.offset,
-            C.sizeof(B.sph_background), B.sph_background.spacing.offset]
+            C.sizeof(B.sph_background), B.sph_background.spacing.offset,
+            C.sizeof(B.sph_batch_trial), B.sph_batch_trial.stage_views.offset]
     assert got == want
 
 
@@ -80,6 +82,9 @@ def test_null_handle_calls(lib):
     assert lib.sph_sync(None) == 1
     assert lib.sph_last_error(None) == b"null handle"
     assert lib.sph_set_surface(None, None) == 1
+    assert lib.sph_set_tuning(None, 256, 1.0, 1) == 1
+    assert lib.sph_get_tuning(None, None, None, None) == 1
+    assert lib.sph_get_stage_info(None, None, None, None) == 1
     d, f, q = problem_structs(W.uniform_square_2d(16))
     h = B.H()
     assert lib.sph_create_background(C.byref(d), C.byref(f), None, 10, 1, C.byref(q), None, None, C.byref(h)) == 1
